@@ -1,0 +1,350 @@
+"""Pins for the FP64 oracle: checks against things other than itself.
+
+* brute-force state vectors (the PEPS definition, Section 2) on 4x4 and 4x5;
+* exactness: chi >= (D^2)^(Lx/2) reproduces the exact contraction;
+* closed forms for D=1 product states;
+* a cluster covering the lattice is the full method (Section 4: CU_{L-1});
+* cluster windows with CU_0 closures vs brute force of the closed window;
+* CU_0 positivity (Section 4.1) and its fixed point checked as a stationary
+  point of the overlap, computed with dense vectors;
+* the var local update vs a dense least-squares solve (Section 2, N A = b);
+* gauge invariance, and top-down vs bottom-up norms;
+* the paper's exact 4x4 Heisenberg energy (Appendix A) pins the S.S
+  operator and the brute-force bond observables.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import bruteforce as BF
+from oracle import peps_oracle as O
+from paper_1311_6696_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _bf_all(A):
+    Ly, Lx = A.shape[:2]
+    psi = BF.state_vector(BF.dense_lattice(A))
+    dims = [A.shape[2]] * (Ly * Lx)
+    site = lambda op: [BF.expect_site(psi, dims, i, op) for i in range(Ly * Lx)]
+    hb = [BF.expect_bond(psi, dims, y * Lx + x, y * Lx + x + 1, O.SDOTS)
+          for y in range(Ly) for x in range(Lx - 1)]
+    vb = [BF.expect_bond(psi, dims, y * Lx + x, (y + 1) * Lx + x, O.SDOTS)
+          for y in range(Ly - 1) for x in range(Lx)]
+    return dict(lnN=math.log(BF.norm(psi)), sz=site(O.SZ), sx=site(O.SX), hb=hb, vb=vb)
+
+
+def _maxdiff(a, b):
+    return max(abs(x - y) for x, y in zip(a, b))
+
+
+def _check_env_vs_bf(env, bf, tol):
+    assert abs(env["ln_norm"] - bf["lnN"]) < tol
+    assert env["sign"] == 1
+    assert _maxdiff(O.expect_all(env, "site", O.SZ), bf["sz"]) < tol
+    assert _maxdiff(O.expect_all(env, "site", O.SX), bf["sx"]) < tol
+    assert _maxdiff(O.expect_all(env, "hbond", O.SDOTS), bf["hb"]) < tol
+    assert _maxdiff(O.expect_all(env, "vbond", O.SDOTS), bf["vb"]) < tol
+
+
+# ---------------------------------------------------------------- golden
+def test_golden_heisenberg_4x4_energy_pins_sdots_and_bonds():
+    sp = pytest.importorskip("scipy.sparse")
+    sla = pytest.importorskip("scipy.sparse.linalg")
+    vals = {}
+    for line in open(os.path.join(GOLDEN, "heisenberg_4x4_ed.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            vals[k] = float(v)
+    L = int(vals["L"])
+    N = L * L
+    # Hamiltonian from Pauli matrices directly (independent of O.SDOTS).
+    sx = sp.csr_matrix([[0.0, 1.0], [1.0, 0.0]])
+    sy_im = sp.csr_matrix([[0.0, -1.0], [1.0, 0.0]])      # sigma_y = i * sy_im
+    sz = sp.csr_matrix([[1.0, 0.0], [0.0, -1.0]])
+
+    def op(o, i):
+        return sp.kron(sp.kron(sp.identity(2 ** i), o), sp.identity(2 ** (N - i - 1)), format="csr")
+
+    bonds = [(y * L + x, y * L + x + 1) for y in range(L) for x in range(L - 1)] + \
+            [(y * L + x, (y + 1) * L + x) for y in range(L - 1) for x in range(L)]
+    H = sp.csr_matrix((2 ** N, 2 ** N))
+    for i, j in bonds:
+        # sigma_y x sigma_y = (i*sy_im) x (i*sy_im) = - sy_im x sy_im
+        H = H + 0.25 * (op(sx, i) @ op(sx, j) - op(sy_im, i) @ op(sy_im, j) + op(sz, i) @ op(sz, j))
+    w, v = sla.eigsh(H, k=1, which="SA")
+    e0 = w[0] / N
+    assert abs(e0 - vals["e0_per_site"]) < 0.6 * 10 ** (-vals["digits"])
+    psi = v[:, 0]
+    e_bf = sum(BF.expect_bond(psi, [2] * N, i, j, O.SDOTS) for i, j in bonds) / N
+    assert abs(e_bf - e0) < 1e-10
+
+
+# ---------------------------------------------------------------- brute force / exactness
+@pytest.mark.parametrize("mode", ["svd", "var"])
+def test_4x4_D2_exact_chi_matches_bruteforce(mode):
+    A = synth.workload("4x4_D2")            # uniform[0,1) from seed 1, unit-norm tensors
+    env = O.env_full(A, chi=16, mode=mode)  # (D^2)^(Lx/2) = 16: exact
+    _check_env_vs_bf(env, _bf_all(A), 1e-12)
+
+
+@pytest.mark.parametrize("mode", ["svd", "var"])
+def test_4x5_D2_exact_chi_matches_bruteforce(mode):
+    A = synth.peps_gauss(4, 5, 2, 2, seed=11)
+    env = O.env_full(A, chi=16, mode=mode)  # (D^2)^floor(5/2) = 16
+    _check_env_vs_bf(env, _bf_all(A), 1e-12)
+
+
+def test_3x3_D3_exact_chi_matches_bruteforce():
+    A = synth.peps_gauss(3, 3, 2, 3, seed=12)
+    env = O.env_full(A, chi=9, mode="svd")  # (D^2)^1 = 9
+    _check_env_vs_bf(env, _bf_all(A), 1e-12)
+
+
+def test_truncation_error_decreases_with_chi():
+    A = synth.peps_uniform(4, 5, 2, 2, seed=13)
+    bf = _bf_all(A)
+    errs = [_maxdiff(O.expect_all(O.env_full(A, chi=c, mode="svd"), "site", O.SZ), bf["sz"])
+            for c in (2, 4, 8)]
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-5
+
+
+# ---------------------------------------------------------------- D = 1 closed forms
+@pytest.mark.parametrize("mode", ["svd", "var"])
+def test_product_state_closed_forms(mode):
+    A = synth.peps_product(3, 4, 2, seed=5)
+    a = A[:, :, :, 0, 0, 0, 0]
+    env = O.env_full(A, chi=4, mode=mode)
+    lnN = float(np.sum(np.log(np.sum(a * a, axis=2))))
+    assert abs(env["ln_norm"] - lnN) < 1e-12
+    n2 = np.sum(a * a, axis=2)
+    z = (a[..., 0] ** 2 - a[..., 1] ** 2) / n2
+    x = 2 * a[..., 0] * a[..., 1] / n2
+    assert _maxdiff(O.expect_all(env, "site", O.SZ), z.ravel()) < 1e-13
+    assert _maxdiff(O.expect_all(env, "site", O.SX), x.ravel()) < 1e-13
+    hb = [(x[i, j] * x[i, j + 1] + z[i, j] * z[i, j + 1]) / 4 for i in range(3) for j in range(3)]
+    vb = [(x[i, j] * x[i + 1, j] + z[i, j] * z[i + 1, j]) / 4 for i in range(2) for j in range(4)]
+    assert _maxdiff(O.expect_all(env, "hbond", O.SDOTS), hb) < 1e-13
+    assert _maxdiff(O.expect_all(env, "vbond", O.SDOTS), vb) < 1e-13
+    # CU_0 is exact for product states: every cluster size gives the same values.
+    for n in (1, 2):
+        ec = O.env_cluster(A, n=n, chi=4, mode=mode)
+        assert _maxdiff(O.expect_all(ec, "site", O.SZ), z.ravel()) < 1e-13
+    assert _maxdiff(O.expect_all(ec, "hbond", O.SDOTS), hb) < 1e-13
+    assert _maxdiff(O.expect_all(ec, "vbond", O.SDOTS), vb) < 1e-13
+
+
+# ---------------------------------------------------------------- clusters
+@pytest.mark.parametrize("mode", ["svd", "var"])
+def test_cluster_covering_lattice_is_full(mode):
+    A = synth.peps_gauss(4, 4, 2, 2, seed=7)
+    ef = O.env_full(A, chi=6, mode=mode)     # truncated on purpose
+    ec = O.env_cluster(A, n=8, chi=6, mode=mode)
+    for k in ("rho_site", "rho_h", "rho_v"):
+        for ra, rb in zip(ef[k], ec[k]):
+            for a, b in zip(ra, rb):
+                assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_cluster_window_matches_bruteforce_of_closed_window(n):
+    A = synth.peps_gauss(4, 5, 2, 2, seed=8)
+    lat = O.lattice_from_dense(A)
+    cu0 = O.cu0_all(lat)
+    for (y, x) in [(0, 0), (1, 1), (2, 3), (3, 4), (1, 4), (3, 0)]:
+        W, (r0, r1, c0, c1) = O.window_lattice(lat, cu0, y, x, n)
+        s, h, v = O.cluster_anchor(W, y - r0, x - c0, 64, "svd", 2, 0)
+        rows, extra = BF.absorb_closures(W.A, W.top, W.bottom, W.left, W.right)
+        psi = BF.state_vector(rows)
+        dims = [2 * extra[i][j] for i in range(W.Ly) for j in range(W.Lx)]
+        i = (y - r0) * W.Lx + (x - c0)
+        assert abs(O.expect(s, O.SZ) - BF.expect_site(psi, dims, i, O.SZ)) < 1e-12
+        assert abs(O.expect(s, O.SX) - BF.expect_site(psi, dims, i, O.SX)) < 1e-12
+        if h is not None:
+            assert abs(O.expect(h, O.SDOTS) - BF.expect_bond(psi, dims, i, i + 1, O.SDOTS)) < 1e-12
+        if v is not None:
+            assert abs(O.expect(v, O.SDOTS) - BF.expect_bond(psi, dims, i, i + W.Lx, O.SDOTS)) < 1e-12
+
+
+def test_window_shape_clipped_not_shifted():
+    assert O.window_bounds(14, 0, 6) == (0, 3)
+    assert O.window_bounds(14, 7, 6) == (5, 10)
+    assert O.window_bounds(14, 13, 6) == (11, 13)
+    assert O.window_bounds(14, 5, 2) == (5, 6)
+    assert O.window_bounds(14, 13, 2) == (13, 13)
+    assert O.window_bounds(14, 3, 28) == (0, 13)
+
+
+# ---------------------------------------------------------------- CU_0
+def test_cu0_positive_symmetric_and_init_independent():
+    A = synth.peps_gauss(5, 4, 2, 3, seed=9)
+    lat = O.lattice_from_dense(A)
+    s1 = O.cu0_sweep(lat)
+    s2 = O.cu0_sweep(lat, init="random", init_seed=4)
+    for r1, r2 in zip(s1[1:], s2[1:]):
+        for a, b in zip(r1, r2):
+            assert np.max(np.abs(a - b)) < 1e-10
+            assert np.max(np.abs(a - a.T)) < 1e-14
+            assert np.linalg.eigvalsh(a).min() > -1e-14
+
+
+def test_cu0_fixed_point_is_stationary_overlap():
+    """The D'=1 fixed point maximises the overlap locally: each sigma_x is
+    parallel to the derivative of <Sigma|T> w.r.t. sigma_x, where T is the
+    row applied to the previous separable boundary, built as a dense vector."""
+    A = synth.peps_gauss(3, 3, 2, 2, seed=10)
+    lat = O.lattice_from_dense(A)
+    sig = O.cu0_sweep(lat)
+    for r in range(2):
+        prev, new = sig[r], sig[r + 1]
+        # dense target T over (n_0, o_0, n_1, o_1, n_2, o_2)
+        t = None
+        for x in range(3):
+            a = lat.A[r][x]
+            site = np.einsum("uv,sulnr,svmoq->lmnorq", prev[x], a, a)
+            if t is None:
+                t = site[0, 0]                          # left legs of dim 1
+            else:
+                t = np.einsum("...rq,rqnoRQ->...noRQ", t, site)
+        t = t[..., 0, 0]
+        for x in range(3):
+            # contract every other site's sigma into the dense target
+            idx = "abcdef"
+            specs, ops = [], []
+            for k in range(3):
+                if k != x:
+                    specs.append(idx[2 * k] + idx[2 * k + 1])
+                    ops.append(new[k])
+            out = idx[2 * x] + idx[2 * x + 1]
+            g = np.einsum(idx + "," + ",".join(specs) + "->" + out, t, *ops)
+            g = g / np.linalg.norm(g)
+            assert np.max(np.abs(g - new[x])) < 1e-9
+
+
+def test_cu0_exact_for_product_state():
+    A = synth.peps_product(3, 3, 2, seed=2)
+    lat = O.lattice_from_dense(A)
+    sig = O.cu0_sweep(lat)
+    for r in range(1, 3):
+        for m in sig[r]:
+            assert m.shape == (1, 1) and abs(m[0, 0] - 1.0) < 1e-15
+
+
+# ---------------------------------------------------------------- var local update
+def test_var_local_update_is_dense_least_squares():
+    """b_0 from the chain equals the least-squares optimum of ||T' - O T||^2
+    over the first tensor of T' with the others right-orthonormal (Section 2)."""
+    A = synth.peps_gauss(3, 3, 2, 2, seed=14)
+    lat = O.lattice_from_dense(A)
+    T, _ = O.boundary_sweep(lat, chi=4, mode="svd", upto=1)
+    T1 = T[1]
+    y = 1
+    Lx = 3
+    A1 = lat.A[y]
+    phys = [A1[x].shape[3] ** 2 for x in range(Lx)]
+    prod = [T1[k].shape[3] * A1[k].shape[4] ** 2 for k in range(Lx - 1)]
+    caps = O.bond_caps(phys, prod, 3)
+    N = O.right_canonicalize(O.var_init(T1, caps, [A1[x].shape[3] for x in range(Lx)], 0, 0, y))
+    R = [None] * Lx
+    R[Lx - 1] = O.closure_right(lat.right[y])
+    for x in range(Lx - 1, 0, -1):
+        R[x - 1] = O.renv_prev(O.chain_right(R[x], T1[x], A1[x]), N[x])
+    b0 = O.close_left(O.chain_left(O.closure_left(lat.left[y]), T1[0], A1[0]), R[0])
+    # dense target O T
+    P = O.product_mps(T1, lat, y)
+    target = P[0]
+    for k in range(1, Lx):
+        target = np.tensordot(target, P[k], axes=([target.ndim - 1], [0]))
+    target = target.reshape(-1)
+    # dense T' as a linear map of N[0]
+    rest = N[1]
+    for k in range(2, Lx):
+        rest = np.tensordot(rest, N[k], axes=([rest.ndim - 1], [0]))
+    rest = rest.reshape(rest.shape[0], -1)                  # [e, rest]
+    c, n, o, e = N[0].shape
+    cols = []
+    for idx in range(c * n * o * e):
+        unit = np.zeros(c * n * o * e)
+        unit[idx] = 1.0
+        U = unit.reshape(c, n, o, e)
+        v = np.tensordot(U, rest, axes=([3], [0])).reshape(-1)
+        cols.append(v)
+    Jd = np.stack(cols, axis=1)
+    sol, *_ = np.linalg.lstsq(Jd, target, rcond=None)
+    assert np.max(np.abs(sol.reshape(b0.shape) - b0)) < 1e-12 * max(1.0, np.max(np.abs(b0)))
+
+
+# ---------------------------------------------------------------- consistency
+def test_top_down_and_bottom_up_norms_agree_at_exact_chi():
+    A = synth.peps_gauss(4, 4, 2, 2, seed=15)
+    lat = O.lattice_from_dense(A)
+    l1, s1 = O.norm(lat, chi=16)
+    l2, s2 = O.norm(O.flip_ud(lat), chi=16)
+    l3, s3 = O.norm(O.transpose(lat), chi=16)
+    assert abs(l1 - l2) < 1e-12 and abs(l1 - l3) < 1e-12 and s1 == s2 == s3 == 1
+
+
+def _gauged(A, G, horizontal=True, vertical=True):
+    Gi = np.linalg.inv(G)
+    B = A.copy()
+    if horizontal:   # bond (1,1)-(1,2): G on the right leg, G^-1 on the left leg
+        B[1, 1] = np.einsum("sulnr,rk->sulnk", B[1, 1], G)
+        B[1, 2] = np.einsum("kl,sulnr->suknr", Gi, B[1, 2])
+    if vertical:     # bond (0,2)-(1,2): G on the down leg, G^-1 on the up leg
+        B[0, 2] = np.einsum("sulnr,nk->sulkr", B[0, 2], G)
+        B[1, 2] = np.einsum("ku,sulnr->sklnr", Gi, B[1, 2])
+    return B
+
+
+def test_gauge_invariance_exact_chi():
+    A = synth.peps_gauss(4, 4, 2, 2, seed=16)
+    B = _gauged(A, synth.random_gauge(2, seed=17))
+    e1 = O.env_full(A, chi=16, mode="svd")
+    e2 = O.env_full(B, chi=16, mode="svd")
+    assert abs(e1["ln_norm"] - e2["ln_norm"]) < 1e-12
+    for kind, op in (("site", O.SZ), ("hbond", O.SDOTS), ("vbond", O.SDOTS)):
+        assert _maxdiff(O.expect_all(e1, kind, op), O.expect_all(e2, kind, op)) < 1e-12
+
+
+def test_horizontal_gauge_leaves_truncated_top_down_norm_unchanged():
+    """A gauge on a bond inside a row only changes the gauge of the product
+    MPS bond, which the canonical form removes before truncation."""
+    A = synth.peps_gauss(4, 4, 2, 3, seed=16)
+    B = _gauged(A, synth.random_gauge(3, seed=17), vertical=False)
+    l1, _ = O.norm(A, chi=6, mode="svd")
+    l2, _ = O.norm(B, chi=6, mode="svd")
+    assert abs(l1 - l2) < 1e-12
+
+
+# ---------------------------------------------------------------- planted mistakes
+def test_planted_mistake_in_chain_is_caught(monkeypatch):
+    """A transposed operand in the ket stage must fail the brute-force pin."""
+    A = synth.peps_gauss(3, 3, 2, 2, seed=18)
+    bf = _bf_all(A)
+    good = O.chain_left
+
+    def bad(L, M, Aa):
+        X1 = O._ein("clma,auvb->clmuvb", L, M)
+        X2 = O._ein("clmuvb,slunr->cmvbsnr", X1, Aa)    # u and l swapped
+        return O._ein("cmvbsnr,svmoq->cbnroq", X2, Aa)
+
+    monkeypatch.setattr(O, "chain_left", bad)
+    env = O.env_full(A, chi=9, mode="svd")
+    monkeypatch.setattr(O, "chain_left", good)
+    assert _maxdiff(O.expect_all(env, "site", O.SZ), bf["sz"]) > 1e-6
+
+
+def test_planted_mistake_in_noise_free_cu0_is_caught(monkeypatch):
+    """A dropped right environment in the CU_0 update breaks stationarity."""
+    A = synth.peps_gauss(3, 3, 2, 2, seed=10)
+    lat = O.lattice_from_dense(A)
+    good = O.cu0_local
+    monkeypatch.setattr(O, "cu0_local", lambda Lm, S, Aa, Rm: good(Lm, S, Aa, np.eye(Rm.shape[0])))
+    bad = O.cu0_sweep(lat)
+    monkeypatch.setattr(O, "cu0_local", good)
+    ok = O.cu0_sweep(lat)
+    assert max(np.max(np.abs(a - b)) for ra, rb in zip(ok[1:], bad[1:]) for a, b in zip(ra, rb)) > 1e-6
