@@ -1,0 +1,194 @@
+/*
+ * peps.h -- C ABI of the GB300 (sm_103a) boundary-MPS PEPS environment library.
+ *
+ * The library computes approximate environments of finite PEPS with open
+ * boundary conditions by the sandwich (boundary-MPS) contraction of
+ * Lubasch, Cirac & Banuls, "Unifying Projected Entangled Pair States
+ * contractions", and the local quantities that follow from them:
+ *
+ *   - the norm <psi|psi>                                     (Section 2, Fig. 2)
+ *   - the environment of every site, in factored form        (Section 2: N_l, b_l)
+ *   - local expectation values <O> = Tr(rho O)/Tr(rho)       (Section 4.3)
+ *   - the same environments in the cluster scheme CU         (Section 4, 4.2, 4.3)
+ *
+ * Every step runs in the library's CUDA kernels; there is no CPU fallback.
+ * A call made without a usable CUDA device fails with PEPS_ECUDA.
+ *
+ * Conventions
+ *   - Every call returns PEPS_OK (0) or one of the status codes below; no
+ *     C++ exception crosses this boundary.  peps_last_error() returns a
+ *     thread-local message for the last failing call on that thread.
+ *   - The caller owns every input and output array.  The library owns env
+ *     handles (device-resident); peps_env_free releases one and accepts NULL.
+ *   - Calls are ordered on the CUDA stream passed as `cuda_stream`
+ *     (a cudaStream_t; NULL means the legacy default stream).  Calls that
+ *     return host values synchronise that stream before returning.
+ *   - Calls on the same env handle, or any two calls that run at the same
+ *     time on different threads, must be serialised by the caller.
+ *
+ * Tensor layout (C order):
+ *   A[y][x][s][u][l][n][r]   y = row (0 at the top), x = column,
+ *                            s = physical index (dimension d),
+ *                            u, l, n, r = up, left, down, right virtual legs (D each).
+ *   Open boundary conditions: a leg that points out of the lattice has
+ *   dimension 1 (Section 2, footnote on OBC tensors); in the dense array it
+ *   uses index 0 only and every other entry on it must be 0, otherwise the
+ *   call fails with PEPS_EINVAL.
+ */
+#ifndef PEPS_H
+#define PEPS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define PEPS_OK         0
+#define PEPS_EINVAL     1   /* bad argument, shape or OBC entries                    */
+#define PEPS_ENOMEM     2   /* device allocation failed                              */
+#define PEPS_ECUDA      3   /* CUDA runtime error, or no CUDA device                 */
+#define PEPS_ECONVERGE  4   /* an iteration (Jacobi SVD, CU_0 fixed point) hit its cap */
+#define PEPS_ETIMEOUT   5   /* a device-side bounded wait ran out                    */
+
+/* element type of A */
+#define PEPS_F64 0
+#define PEPS_F32 1
+
+/* compression of the boundary MPS after each absorbed row (Section 2) */
+#define PEPS_SVD 0          /* QR sweep to canonical form, then SVD truncation to chi */
+#define PEPS_VAR 1          /* one-site ALS sweeps, local equation N A = b with N = 1 */
+
+/* arithmetic of the absorb contractions; QR, SVD, gauge and rescaling are FP64 */
+#define PEPS_PREC_FP64 0
+#define PEPS_PREC_TF32 1
+#define PEPS_PREC_BF16 2
+
+/* local quantity selectors */
+#define PEPS_SITE  0        /* rho of site (y,x):            d x d,     Ly*Lx values       */
+#define PEPS_HBOND 1        /* rho of bond (y,x)-(y,x+1):    d^2 x d^2, Ly*(Lx-1) values   */
+#define PEPS_VBOND 2        /* rho of bond (y,x)-(y+1,x):    d^2 x d^2, (Ly-1)*Lx values   */
+
+/* cluster closure outside the window */
+#define PEPS_CLOSURE_PLAIN   0   /* CU_0 separable boundaries (Section 4.1) */
+
+typedef struct {
+    int Ly, Lx;          /* lattice size, >= 1 each                                   */
+    int d;               /* physical dimension, 1..4                                  */
+    int D;               /* virtual bond dimension, 1..16                             */
+    int dtype;           /* PEPS_F64 or PEPS_F32                                      */
+    const void* A;       /* dense tensors, layout above; read only                    */
+    int on_device;       /* 1: A is a device pointer, 0: a host pointer               */
+} peps_lattice;
+
+typedef struct {
+    int chi;             /* boundary bond dimension D' (>= 1)                          */
+    int mode;            /* PEPS_SVD or PEPS_VAR                                       */
+    int sweeps;          /* PEPS_VAR half-sweeps; <= 0 selects 2 (L->R then R->L)      */
+    int precision;       /* PEPS_PREC_*                                                */
+    int n;               /* cluster window edge length (peps_env_cluster), >= 1        */
+    int closure;         /* PEPS_CLOSURE_PLAIN                                         */
+    const void* closure_weights;   /* reserved, must be NULL                           */
+    unsigned long long seed;       /* keys the counter-based noise of the var start    */
+} peps_opts;
+
+typedef struct peps_env peps_env;   /* opaque, device resident, library owned */
+
+/*
+ * peps_env_full -- full (sandwich) environments of every site.
+ *   Section 2 (Fig. 2, "sandwich contraction"): the norm network is swept
+ *   row by row from the top and from the bottom, and column by column from
+ *   the left and the right; each row is absorbed into the boundary MPS
+ *   (ket layer, then bra layer) and the result is compressed to bond chi.
+ *   The environment of site l (Section 2) is then held in factored form
+ *   (top and bottom boundary, left and right row environments), from which
+ *   the reduced density matrices of every site, horizontal bond and
+ *   vertical bond are formed.  Vertical bonds use the column sweeps.
+ *   *out receives a new handle (set to NULL on failure).
+ */
+int peps_env_full(const peps_lattice* lat, const peps_opts* opts,
+                  peps_env** out, void* cuda_stream);
+
+/*
+ * peps_env_cluster -- cluster (CU) environments of every site.
+ *   Section 4 / 4.2: outside a window around each site the environment is
+ *   the product of CU_0 separable boundaries (Section 4.1: D'=1 boundary
+ *   found by ALS whose local solution is proportional to b_l); inside the
+ *   window the contraction is the full one at bond chi.  Section 4.3 forms
+ *   the cluster around the local term itself: the window is opts->n x
+ *   opts->n with rows y-ceil(n/2)+1 .. (same for columns), clipped at the
+ *   lattice edge, so edge windows are smaller.  Site (y,x) yields its own
+ *   density matrix and those of the bonds to (y,x+1) and (y+1,x).  With
+ *   n >= 2*max(Ly,Lx) every window is the lattice and the result equals
+ *   peps_env_full's (Section 4: CU_{L-1} is the full update).
+ *   Fails with PEPS_ECONVERGE if a CU_0 iteration does not converge.
+ */
+int peps_env_cluster(const peps_lattice* lat, const peps_opts* opts,
+                     peps_env** out, void* cuda_stream);
+
+/*
+ * peps_expect_local -- <O> = Tr(rho O) / Tr(rho) at every site or bond.
+ *   Section 4.3 (local expectation values from local reduced density matrices).
+ *   kind: PEPS_SITE / PEPS_HBOND / PEPS_VBOND.
+ *   op:   host array, real, row-major, d x d (site) or d^2 x d^2 (bond, rows
+ *         and columns ordered (s_first, s_second) with the first site the left
+ *         or upper one); O[t][s] is <t|O|s>.
+ *   out:  host array receiving Ly*Lx, Ly*(Lx-1) or (Ly-1)*Lx values in
+ *         row-major order of the first site.
+ *   lat:  may be NULL; if given its shape must match the env's.
+ *   Synchronises the stream.
+ */
+int peps_expect_local(const peps_env* env, const peps_lattice* lat, int kind,
+                      const double* op, double* out, void* cuda_stream);
+
+/*
+ * peps_env_rho -- copy the (unnormalised) reduced density matrices to the host.
+ *   Same ordering as peps_expect_local; each entry is d x d (site) or
+ *   d^2 x d^2 (bond) with rows = ket indices, columns = bra indices.
+ *   out must hold count * d^2 (site) or count * d^4 (bond) doubles.
+ *   Synchronises the stream.
+ */
+int peps_env_rho(const peps_env* env, int kind, double* out, void* cuda_stream);
+
+/*
+ * peps_norm -- ln |<psi|psi>| and its sign.
+ *   Section 2: top-down sandwich sweep through the second-to-last row, then
+ *   the last row contracted exactly against the last boundary.  Every
+ *   boundary is rescaled to unit norm and the logs of the factors are
+ *   accumulated, so the result does not overflow.  Synchronises the stream.
+ */
+int peps_norm(const peps_lattice* lat, const peps_opts* opts,
+              double* ln_norm, int* sign, void* cuda_stream);
+
+/* peps_env_ln_norm -- the norm recorded in a full env (PEPS_EINVAL for cluster envs). */
+int peps_env_ln_norm(const peps_env* env, double* ln_norm, int* sign, void* cuda_stream);
+
+/* peps_env_free -- release a handle; NULL is accepted. Not stream ordered:
+ * it synchronises the device work that used the handle first. */
+void peps_env_free(peps_env* env);
+
+/* peps_last_error -- message of the last failing call on this thread. */
+const char* peps_last_error(void);
+
+/*
+ * Instrumentation (library-wide, not per handle).
+ *   peps_profile_enable(mask): bit i of mask enables timing of kernel class
+ *   i -- a CUDA event pair is recorded around each launch of that class, on
+ *   the stream the kernel runs on (0 disables, -1 enables every class).
+ *   peps_profile_read sums the event intervals per class after synchronising
+ *   them.  Classes are named by peps_profile_name(i) for i in
+ *   [0, peps_profile_count()).  launches counts kernel launches whether or
+ *   not timing is enabled; flops / bytes are algorithmic counts (formula,
+ *   not hardware counters).  The counters are process-wide and not
+ *   thread-safe against concurrent readers.
+ */
+void        peps_profile_enable(int mask);
+void        peps_profile_reset(void);
+int         peps_profile_count(void);
+const char* peps_profile_name(int cls);
+int         peps_profile_read(int cls, long long* launches, double* ms,
+                              double* flops, double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PEPS_H */

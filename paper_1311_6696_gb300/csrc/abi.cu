@@ -1,0 +1,614 @@
+// The extern "C" boundary of the library: argument validation, lattice
+// repacking into the four sweep orientations, the full / cluster / norm
+// drivers, and kernel-class instrumentation.  No exception crosses this file.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "aux.cuh"
+#include "engine.cuh"
+#include "linalg.cuh"
+
+using namespace peps;
+
+// ---------------------------------------------------------------------------
+// Instrumentation
+// ---------------------------------------------------------------------------
+namespace {
+
+const char* kClassNames[K_NCLASS] = {"gemm_f64", "gemm_tc", "qr_f64", "svd_f64", "cu0", "observables", "aux"};
+
+struct Prof {
+  std::mutex mu;
+  unsigned mask = 0;
+  long long launches[K_NCLASS] = {};
+  double flops[K_NCLASS] = {}, bytes[K_NCLASS] = {}, ms[K_NCLASS] = {};
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> pending;
+  std::vector<cudaEvent_t> open;   // start events of launches in flight (per class)
+  cudaEvent_t open_ev[K_NCLASS] = {};
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void drain() {
+    for (auto& t : pending) {
+      cudaEventSynchronize(std::get<2>(t));
+      float m = 0.f;
+      cudaEventElapsedTime(&m, std::get<1>(t), std::get<2>(t));
+      ms[std::get<0>(t)] += m;
+      pool.push_back(std::get<1>(t));
+      pool.push_back(std::get<2>(t));
+    }
+    pending.clear();
+  }
+};
+
+Prof& prof() {
+  static Prof* p = new Prof();
+  return *p;
+}
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+template <class F>
+int guard(F&& f) {
+  try {
+    f();
+    return PEPS_OK;
+  } catch (const Error& e) {
+    return fail(e.code, e.what());
+  } catch (const std::bad_alloc&) {
+    return fail(PEPS_ENOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(PEPS_ECUDA, e.what());
+  }
+}
+
+}  // namespace
+
+namespace peps {
+void prof_launch(KClass c, cudaStream_t st, double flops, double bytes) {
+  Prof& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  p.launches[c]++;
+  p.flops[c] += flops;
+  p.bytes[c] += bytes;
+  if (p.mask & (1u << c)) {
+    cudaEvent_t e = p.get();
+    cudaEventRecord(e, st);
+    p.open_ev[c] = e;
+  }
+}
+void prof_done(KClass c, cudaStream_t st) {
+  Prof& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  if ((p.mask & (1u << c)) && p.open_ev[c]) {
+    cudaEvent_t e = p.get();
+    cudaEventRecord(e, st);
+    p.pending.emplace_back(int(c), p.open_ev[c], e);
+    p.open_ev[c] = nullptr;
+  }
+}
+bool prof_timing() { return prof().mask != 0; }
+}  // namespace peps
+
+// ---------------------------------------------------------------------------
+// Env handle
+// ---------------------------------------------------------------------------
+struct peps_env {
+  int device = 0;
+  EnvData data;
+  std::unique_ptr<Arena> arena;   // owns the device memory of this handle
+  int kind = 0;                   // 0 full, 1 cluster
+};
+
+namespace {
+
+struct Call {
+  cudaStream_t st;
+  Arena ws;
+  Ctx cx;
+  explicit Call(void* stream) : st(static_cast<cudaStream_t>(stream)), ws(st), cx(st, &ws) {
+    cx.flag = static_cast<int*>(ws.alloc(sizeof(int)));
+    PEPS_CUDA(cudaMemsetAsync(cx.flag, 0, sizeof(int), st));
+    cx.tmp = ws.dalloc(8);
+  }
+  // Synchronise and turn the device status word into a status code.
+  void finish() {
+    int h = 0;
+    PEPS_CUDA(cudaMemcpyAsync(&h, cx.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PEPS_CUDA(cudaStreamSynchronize(st));
+    if (h & FLAG_SVD_NOCONV) throw Error(PEPS_ECONVERGE, "Jacobi SVD did not converge within its sweep cap");
+    if (h & FLAG_CU0_NOCONV) throw Error(PEPS_ECONVERGE, "CU_0 separable boundary did not converge within 200 half-sweeps");
+    if (h & FLAG_BAD_VALUE) throw Error(PEPS_EINVAL, "zero or non-finite norm encountered (degenerate state)");
+  }
+};
+
+void require_device() {
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    throw Error(PEPS_ECUDA, "no CUDA device available (this library has no CPU path)");
+  }
+}
+
+void check_lattice(const peps_lattice* lat) {
+  PEPS_REQUIRE(lat != nullptr, "lattice is NULL");
+  PEPS_REQUIRE(lat->Ly >= 1 && lat->Lx >= 1 && lat->Ly <= 4096 && lat->Lx <= 4096, "Ly, Lx must be in [1, 4096]");
+  PEPS_REQUIRE(lat->d >= 1 && lat->d <= 4, "d must be in [1, 4]");
+  PEPS_REQUIRE(lat->D >= 1 && lat->D <= 16, "D must be in [1, 16]");
+  PEPS_REQUIRE(lat->dtype == PEPS_F64 || lat->dtype == PEPS_F32, "dtype must be PEPS_F64 or PEPS_F32");
+  PEPS_REQUIRE(lat->A != nullptr, "A is NULL");
+}
+
+Opts check_opts(const peps_opts* o, bool cluster) {
+  PEPS_REQUIRE(o != nullptr, "opts is NULL");
+  PEPS_REQUIRE(o->chi >= 1 && o->chi <= 4096, "chi must be in [1, 4096]");
+  PEPS_REQUIRE(o->mode == PEPS_SVD || o->mode == PEPS_VAR, "mode must be PEPS_SVD or PEPS_VAR");
+  PEPS_REQUIRE(o->precision == PEPS_PREC_FP64 || o->precision == PEPS_PREC_TF32 || o->precision == PEPS_PREC_BF16,
+               "precision must be PEPS_PREC_FP64, _TF32 or _BF16");
+  PEPS_REQUIRE(o->closure == PEPS_CLOSURE_PLAIN && o->closure_weights == nullptr,
+               "closure must be PEPS_CLOSURE_PLAIN with NULL weights");
+  if (cluster) PEPS_REQUIRE(o->n >= 1, "cluster size n must be >= 1");
+  Opts r;
+  r.chi = o->chi;
+  r.mode = o->mode;
+  r.sweeps = o->sweeps <= 0 ? 2 : o->sweeps;
+  r.precision = o->precision;
+  r.seed = o->seed;
+  return r;
+}
+
+long long obc_violations_host(const peps_lattice* L) {
+  const int Ly = L->Ly, Lx = L->Lx, d = L->d, D = L->D;
+  long long c = 0;
+  const long long per = (long long)d * D * D * D * D;
+  for (int y = 0; y < Ly; ++y)
+    for (int x = 0; x < Lx; ++x)
+      for (long long e = 0; e < per; ++e) {
+        long long r = e;
+        const int ri = int(r % D);
+        r /= D;
+        const int ni = int(r % D);
+        r /= D;
+        const int li = int(r % D);
+        r /= D;
+        const int ui = int(r % D);
+        const bool out = (y == 0 && ui) || (x == 0 && li) || (y == Ly - 1 && ni) || (x == Lx - 1 && ri);
+        if (!out) continue;
+        const long long idx = ((long long)y * Lx + x) * per + e;
+        const double v = L->dtype == PEPS_F32 ? double(static_cast<const float*>(L->A)[idx])
+                                              : static_cast<const double*>(L->A)[idx];
+        if (v != 0.0) ++c;
+      }
+  return c;
+}
+
+// The four sweep orientations of the full lattice (top-down, bottom-up,
+// left-right, right-left), repacked with effective OBC dimensions.
+struct Oriented {
+  OLat o[4];
+  double* one = nullptr;
+  int Dmax = 0;
+};
+
+void build_orientations(Ctx& cx, const peps_lattice* in, Arena& keep, Oriented& out) {
+  const int Ly = in->Ly, Lx = in->Lx, d = in->d, D = in->D;
+  const size_t elems = size_t(Ly) * Lx * d * D * D * D * D;
+  const size_t esz = in->dtype == PEPS_F32 ? 4 : 8;
+  const void* src = in->A;
+  if (!in->on_device) {
+    const long long bad = obc_violations_host(in);
+    PEPS_REQUIRE(bad == 0, "A has " + std::to_string(bad) + " nonzero entries on outward (OBC) legs");
+    void* dsrc = cx.ws->alloc(elems * esz);
+    PEPS_CUDA(cudaMemcpyAsync(dsrc, in->A, elems * esz, cudaMemcpyHostToDevice, cx.st));
+    src = dsrc;
+  } else {
+    cudaPointerAttributes at;
+    PEPS_CUDA(cudaPointerGetAttributes(&at, in->A));
+    PEPS_REQUIRE(at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged,
+                 "on_device is set but A is not a device pointer");
+    const long long bad = obc_violations_device(cx, in->A, in->dtype == PEPS_F32, Ly, Lx, d, D);
+    PEPS_REQUIRE(bad == 0, "A has " + std::to_string(bad) + " nonzero entries on outward (OBC) legs");
+  }
+  out.one = keep.dalloc(1);
+  fill(cx, out.one, 1, 1.0);
+  out.Dmax = D;
+  const size_t per = size_t(d) * D * D * D * D;
+  static const int perms[4][4] = {{0, 1, 2, 3}, {2, 1, 0, 3}, {1, 0, 3, 2}, {3, 0, 1, 2}};
+  for (int o = 0; o < 4; ++o) {
+    const int H = (o < 2) ? Ly : Lx, W = (o < 2) ? Lx : Ly;
+    double* buf = keep.dalloc(per * H * W);
+    std::vector<OrientSite> sites(size_t(H) * W);
+    OLat& L = out.o[o];
+    L.Ly = H;
+    L.Lx = W;
+    L.d = d;
+    L.sites.resize(size_t(H) * W);
+    for (int i = 0; i < H; ++i)
+      for (int j = 0; j < W; ++j) {
+        int y, x;
+        if (o == 0) { y = i; x = j; }
+        else if (o == 1) { y = Ly - 1 - i; x = j; }
+        else if (o == 2) { y = j; x = i; }
+        else { y = j; x = Lx - 1 - i; }
+        const int od[4] = {y == 0 ? 1 : D, x == 0 ? 1 : D, y == Ly - 1 ? 1 : D, x == Lx - 1 ? 1 : D};
+        OrientSite& s = sites[size_t(i) * W + j];
+        s.dst = (long long)((size_t(i) * W + j) * per);
+        s.y = y;
+        s.x = x;
+        for (int k = 0; k < 4; ++k) s.perm[k] = perms[o][k];
+        s.du = od[s.perm[0]];
+        s.dl = od[s.perm[1]];
+        s.dn = od[s.perm[2]];
+        s.dr = od[s.perm[3]];
+        SiteT& t = L.sites[size_t(i) * W + j];
+        t.p = buf + s.dst;
+        t.d = d;
+        t.du = s.du;
+        t.dl = s.dl;
+        t.dn = s.dn;
+        t.dr = s.dr;
+      }
+    orient_lattice(cx, src, in->dtype == PEPS_F32, Ly, Lx, d, D, sites.data(), int(sites.size()), buf);
+    const Mat one{out.one, 1};
+    L.top.assign(W, one);
+    L.bottom.assign(W, one);
+    L.left.assign(H, one);
+    L.right.assign(H, one);
+  }
+}
+
+std::unique_ptr<peps_env> new_env(const peps_lattice* lat, int kind, cudaStream_t st) {
+  auto env = std::make_unique<peps_env>();
+  PEPS_CUDA(cudaGetDevice(&env->device));
+  env->arena = std::make_unique<Arena>(st, size_t(64) << 20, /*async=*/false);
+  env->kind = kind;
+  EnvData& e = env->data;
+  e.Ly = lat->Ly;
+  e.Lx = lat->Lx;
+  e.d = lat->d;
+  e.D = lat->D;
+  const size_t d2 = size_t(lat->d) * lat->d, d4 = d2 * d2;
+  e.rho_site = env->arena->dalloc(size_t(e.Ly) * e.Lx * d2);
+  e.rho_h = env->arena->dalloc(std::max<size_t>(1, size_t(e.Ly) * (e.Lx - 1) * d4));
+  e.rho_v = env->arena->dalloc(std::max<size_t>(1, size_t(e.Ly - 1) * e.Lx * d4));
+  e.lnnorm = env->arena->dalloc(2);
+  // Quantities a cluster window cannot see (bonds when n = 1) stay zero.
+  PEPS_CUDA(cudaMemsetAsync(e.rho_site, 0, sizeof(double) * size_t(e.Ly) * e.Lx * d2, st));
+  PEPS_CUDA(cudaMemsetAsync(e.rho_h, 0, sizeof(double) * std::max<size_t>(1, size_t(e.Ly) * (e.Lx - 1) * d4), st));
+  PEPS_CUDA(cudaMemsetAsync(e.rho_v, 0, sizeof(double) * std::max<size_t>(1, size_t(e.Ly - 1) * e.Lx * d4), st));
+  return env;
+}
+
+void full_env(Call& c, const peps_lattice* lat, const Opts& opt, peps_env* env, Oriented& ori) {
+  Ctx& cx = c.cx;
+  Arena& keep = *env->arena;
+  const int Ly = lat->Ly, Lx = lat->Lx, d = lat->d;
+  Engine eng(cx, opt, d, lat->D, std::max(Ly, Lx));
+  double* lnacc = cx.ws->dalloc(4);
+  fill(cx, lnacc, 4, 0.0);
+  auto bt = eng.sweep(ori.o[0], 0, Ly - 1, lnacc + 0, keep);
+  auto bb = eng.sweep(ori.o[1], 1, Ly - 1, lnacc + 1, keep);
+  auto bl = eng.sweep(ori.o[2], 2, Lx - 1, lnacc + 2, keep);
+  auto br = eng.sweep(ori.o[3], 3, Lx - 1, lnacc + 3, keep);
+  EnvData& e = env->data;
+  const long long d2 = (long long)d * d, d4 = d2 * d2;
+  for (int y = 0; y < Ly; ++y) {
+    Engine::Targets ts, tb;
+    for (int x = 0; x < Lx; ++x) ts.push_back({x, e.rho_site + ((long long)y * Lx + x) * d2});
+    for (int x = 0; x + 1 < Lx; ++x) tb.push_back({x, e.rho_h + ((long long)y * (Lx - 1) + x) * d4});
+    eng.row_rhos(ori.o[0], bt[y], bb[Ly - 1 - y], y, ts, tb);
+  }
+  // Row x of the transposed lattice holds the vertical bonds (y,x)-(y+1,x) at its column y.
+  for (int x = 0; x < Lx && Ly > 1; ++x) {
+    Engine::Targets tb;
+    for (int y = 0; y + 1 < Ly; ++y) tb.push_back({y, e.rho_v + ((long long)y * Lx + x) * d4});
+    eng.row_rhos(ori.o[2], bl[x], br[Lx - 1 - x], x, {}, tb);
+  }
+  eng.norm_from_top(ori.o[0], bt[Ly - 1], lnacc, e.lnnorm);
+  e.has_norm = true;
+}
+
+// Window of the cluster scheme (Section 4.3): n x n around (i) clipped at [0, L).
+std::pair<int, int> window(int L, int i, int n) {
+  const int h = (n + 1) / 2;
+  const int lo = i - h + 1;
+  return {std::max(lo, 0), std::min(lo + n - 1, L - 1)};
+}
+
+OLat sub(const OLat& f, int r0, int r1, int c0, int c1) {
+  OLat s;
+  s.Ly = r1 - r0 + 1;
+  s.Lx = c1 - c0 + 1;
+  s.d = f.d;
+  for (int r = r0; r <= r1; ++r)
+    for (int c = c0; c <= c1; ++c) s.sites.push_back(f.at(r, c));
+  return s;
+}
+
+void cluster_env(Call& c, const peps_lattice* lat, const Opts& opt, int n, peps_env* env, Oriented& ori) {
+  Ctx& cx = c.cx;
+  const int Ly = lat->Ly, Lx = lat->Lx, d = lat->d, D = lat->D, DM2 = D * D;
+  // CU_0 boundaries from all four sides (one CTA per side).
+  double* sig[4];
+  Cu0Lattice cl[4];
+  std::vector<std::vector<long long>> offs(4);
+  std::vector<std::vector<int>> dims(4);
+  double* closure_ones = cx.ws->dalloc(size_t(std::max(Ly, Lx)) * DM2);
+  fill(cx, closure_ones, (long long)std::max(Ly, Lx) * DM2, 1.0);   // 1x1 closures read entry 0
+  for (int o = 0; o < 4; ++o) {
+    const OLat& L = ori.o[o];
+    sig[o] = env->arena->dalloc(size_t(L.Ly) * L.Lx * DM2);
+    offs[o].resize(size_t(L.Ly) * L.Lx);
+    dims[o].resize(size_t(L.Ly) * L.Lx * 4);
+    const double* base = L.sites[0].p;
+    for (size_t i = 0; i < L.sites.size(); ++i) {
+      offs[o][i] = L.sites[i].p - base;
+      dims[o][4 * i + 0] = L.sites[i].du;
+      dims[o][4 * i + 1] = L.sites[i].dl;
+      dims[o][4 * i + 2] = L.sites[i].dn;
+      dims[o][4 * i + 3] = L.sites[i].dr;
+    }
+    auto* doff = static_cast<long long*>(cx.ws->alloc(sizeof(long long) * offs[o].size()));
+    auto* ddim = static_cast<int*>(cx.ws->alloc(sizeof(int) * dims[o].size()));
+    PEPS_CUDA(cudaMemcpyAsync(doff, offs[o].data(), sizeof(long long) * offs[o].size(), cudaMemcpyHostToDevice, cx.st));
+    PEPS_CUDA(cudaMemcpyAsync(ddim, dims[o].data(), sizeof(int) * dims[o].size(), cudaMemcpyHostToDevice, cx.st));
+    Cu0Lattice& q = cl[o];
+    q.Ly = L.Ly;
+    q.Lx = L.Lx;
+    q.d = d;
+    q.Dmax = D;
+    q.A = base;
+    q.off = doff;
+    q.dims = ddim;
+    q.top = closure_ones;
+    q.left = closure_ones;
+    q.right = closure_ones;
+    q.out = sig[o];
+    q.work = cx.ws->dalloc(cu0_work_size(L.Lx, d, D));
+    q.max_half = 200;
+    q.tol = 1e-13;
+  }
+  cu0_launch(cx, cl, 4);
+  auto S = [&](int o, int r, int x, int dim) {
+    const OLat& L = ori.o[o];
+    return Mat{sig[o] + ((long long)r * L.Lx + x) * DM2, dim};
+  };
+  Engine eng(cx, opt, d, D, std::max(Ly, Lx));
+  double* junk = cx.ws->dalloc(4);
+  EnvData& e = env->data;
+  const long long d2 = (long long)d * d, d4 = d2 * d2;
+  for (int y = 0; y < Ly; ++y)
+    for (int x = 0; x < Lx; ++x) {
+      const auto rr = window(Ly, y, n), cc = window(Lx, x, n);
+      const int r0 = rr.first, r1 = rr.second, c0 = cc.first, c1 = cc.second;
+      const int h = r1 - r0 + 1, w = c1 - c0 + 1, yw = y - r0, xw = x - c0;
+      // window in the four orientations (sub-blocks of the oriented full lattice)
+      OLat W0 = sub(ori.o[0], r0, r1, c0, c1);
+      OLat W1 = sub(ori.o[1], Ly - 1 - r1, Ly - 1 - r0, c0, c1);
+      OLat W2 = sub(ori.o[2], c0, c1, r0, r1);
+      OLat W3 = sub(ori.o[3], Lx - 1 - c1, Lx - 1 - c0, r0, r1);
+      auto dimU = [&](const OLat& L, int i, int j) { return L.at(i, j).du; };
+      auto dimN = [&](const OLat& L, int i, int j) { return L.at(i, j).dn; };
+      auto dimL = [&](const OLat& L, int i, int j) { return L.at(i, j).dl; };
+      auto dimR = [&](const OLat& L, int i, int j) { return L.at(i, j).dr; };
+      for (int j = 0; j < w; ++j) {
+        W0.top.push_back(S(0, r0, c0 + j, dimU(W0, 0, j)));
+        W0.bottom.push_back(S(1, Ly - 1 - r1, c0 + j, dimN(W0, h - 1, j)));
+      }
+      for (int i = 0; i < h; ++i) {
+        W0.left.push_back(S(2, c0, r0 + i, dimL(W0, i, 0)));
+        W0.right.push_back(S(3, Lx - 1 - c1, r0 + i, dimR(W0, i, w - 1)));
+      }
+      W1.top = W0.bottom;
+      W1.bottom = W0.top;
+      for (int i = 0; i < h; ++i) {
+        W1.left.push_back(W0.left[h - 1 - i]);
+        W1.right.push_back(W0.right[h - 1 - i]);
+      }
+      W2.top = W0.left;
+      W2.bottom = W0.right;
+      W2.left = W0.top;
+      W2.right = W0.bottom;
+      W3.top = W0.right;
+      W3.bottom = W0.left;
+      for (int j = 0; j < w; ++j) {
+        W3.left.push_back(W0.top[w - 1 - j]);
+        W3.right.push_back(W0.bottom[w - 1 - j]);
+      }
+      Arena keep(cx.st);
+      auto bt = eng.sweep(W0, 0, yw, junk, keep);
+      auto bb = eng.sweep(W1, 1, h - 1 - yw, junk, keep);
+      Engine::Targets ts{{xw, e.rho_site + ((long long)y * Lx + x) * d2}}, tb;
+      if (x + 1 < Lx && xw + 1 < w) tb.push_back({xw, e.rho_h + ((long long)y * (Lx - 1) + x) * d4});
+      eng.row_rhos(W0, bt[yw], bb[h - 1 - yw], yw, ts, tb);
+      if (y + 1 < Ly && yw + 1 < h) {
+        auto bl = eng.sweep(W2, 2, xw, junk, keep);
+        auto br = eng.sweep(W3, 3, w - 1 - xw, junk, keep);
+        eng.row_rhos(W2, bl[xw], br[w - 1 - xw], xw, {}, {{yw, e.rho_v + ((long long)y * Lx + x) * d4}});
+      }
+    }
+  e.has_norm = false;
+}
+
+int run_env(const peps_lattice* lat, const peps_opts* opts, peps_env** out, void* stream, bool cluster) {
+  if (out) *out = nullptr;
+  return guard([&] {
+    PEPS_REQUIRE(out != nullptr, "out is NULL");
+    require_device();
+    check_lattice(lat);
+    const Opts o = check_opts(opts, cluster);
+    Call c(stream);
+    auto env = new_env(lat, cluster ? 1 : 0, c.st);
+    Oriented ori;
+    build_orientations(c.cx, lat, *env->arena, ori);
+    if (cluster)
+      cluster_env(c, lat, o, opts->n, env.get(), ori);
+    else
+      full_env(c, lat, o, env.get(), ori);
+    c.finish();
+    *out = env.release();
+  });
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int peps_env_full(const peps_lattice* lat, const peps_opts* opts, peps_env** out, void* cuda_stream) {
+  return run_env(lat, opts, out, cuda_stream, false);
+}
+
+int peps_env_cluster(const peps_lattice* lat, const peps_opts* opts, peps_env** out, void* cuda_stream) {
+  return run_env(lat, opts, out, cuda_stream, true);
+}
+
+static int count_of(const EnvData& e, int kind) {
+  if (kind == PEPS_SITE) return e.Ly * e.Lx;
+  if (kind == PEPS_HBOND) return e.Ly * (e.Lx - 1);
+  if (kind == PEPS_VBOND) return (e.Ly - 1) * e.Lx;
+  return -1;
+}
+
+int peps_expect_local(const peps_env* env, const peps_lattice* lat, int kind, const double* op, double* out,
+                      void* cuda_stream) {
+  return guard([&] {
+    PEPS_REQUIRE(env != nullptr && op != nullptr && out != nullptr, "NULL argument");
+    const EnvData& e = env->data;
+    const int count = count_of(e, kind);
+    PEPS_REQUIRE(count >= 0, "kind must be PEPS_SITE, PEPS_HBOND or PEPS_VBOND");
+    if (lat) PEPS_REQUIRE(lat->Ly == e.Ly && lat->Lx == e.Lx && lat->d == e.d, "lattice does not match env");
+    if (count == 0) return;
+    Call c(cuda_stream);
+    const int k = kind == PEPS_SITE ? e.d : e.d * e.d;
+    double* dop = c.ws.dalloc(size_t(k) * k);
+    double* dout = c.ws.dalloc(count);
+    PEPS_CUDA(cudaMemcpyAsync(dop, op, sizeof(double) * k * k, cudaMemcpyHostToDevice, c.st));
+    const double* rho = kind == PEPS_SITE ? e.rho_site : (kind == PEPS_HBOND ? e.rho_h : e.rho_v);
+    expect_batch(c.cx, rho, count, k, dop, dout);
+    PEPS_CUDA(cudaMemcpyAsync(out, dout, sizeof(double) * count, cudaMemcpyDeviceToHost, c.st));
+    c.finish();
+  });
+}
+
+int peps_env_rho(const peps_env* env, int kind, double* out, void* cuda_stream) {
+  return guard([&] {
+    PEPS_REQUIRE(env != nullptr && out != nullptr, "NULL argument");
+    const EnvData& e = env->data;
+    const int count = count_of(e, kind);
+    PEPS_REQUIRE(count >= 0, "kind must be PEPS_SITE, PEPS_HBOND or PEPS_VBOND");
+    const int k = kind == PEPS_SITE ? e.d : e.d * e.d;
+    const double* rho = kind == PEPS_SITE ? e.rho_site : (kind == PEPS_HBOND ? e.rho_h : e.rho_v);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (count > 0)
+      PEPS_CUDA(cudaMemcpyAsync(out, rho, sizeof(double) * size_t(count) * k * k, cudaMemcpyDeviceToHost, st));
+    PEPS_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+int peps_norm(const peps_lattice* lat, const peps_opts* opts, double* ln_norm, int* sign, void* cuda_stream) {
+  return guard([&] {
+    PEPS_REQUIRE(ln_norm != nullptr && sign != nullptr, "NULL argument");
+    require_device();
+    check_lattice(lat);
+    const Opts o = check_opts(opts, false);
+    Call c(cuda_stream);
+    Arena keep(c.st);
+    Oriented ori;
+    build_orientations(c.cx, lat, keep, ori);
+    Engine eng(c.cx, o, lat->d, lat->D, std::max(lat->Ly, lat->Lx));
+    double* acc = c.ws.dalloc(4);
+    fill(c.cx, acc, 1, 0.0);
+    auto bt = eng.sweep(ori.o[0], 0, lat->Ly - 1, acc, keep);
+    eng.norm_from_top(ori.o[0], bt[lat->Ly - 1], acc, acc + 2);
+    double h[2];
+    PEPS_CUDA(cudaMemcpyAsync(h, acc + 2, sizeof(h), cudaMemcpyDeviceToHost, c.st));
+    c.finish();
+    *ln_norm = h[0];
+    *sign = int(h[1]);
+  });
+}
+
+int peps_env_ln_norm(const peps_env* env, double* ln_norm, int* sign, void* cuda_stream) {
+  return guard([&] {
+    PEPS_REQUIRE(env != nullptr && ln_norm != nullptr && sign != nullptr, "NULL argument");
+    PEPS_REQUIRE(env->data.has_norm, "this env holds no norm (cluster envs do not)");
+    double h[2];
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    PEPS_CUDA(cudaMemcpyAsync(h, env->data.lnnorm, sizeof(h), cudaMemcpyDeviceToHost, st));
+    PEPS_CUDA(cudaStreamSynchronize(st));
+    *ln_norm = h[0];
+    *sign = int(h[1]);
+  });
+}
+
+void peps_env_free(peps_env* env) {
+  if (!env) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(env->device);
+  cudaDeviceSynchronize();
+  env->arena.reset();
+  cudaDeviceSynchronize();
+  cudaSetDevice(cur);
+  delete env;
+}
+
+const char* peps_last_error(void) { return g_err.c_str(); }
+
+void peps_profile_enable(int mask) {
+  Prof& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  p.mask = unsigned(mask);
+}
+
+void peps_profile_reset(void) {
+  Prof& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  p.drain();
+  for (int i = 0; i < K_NCLASS; ++i) {
+    p.launches[i] = 0;
+    p.flops[i] = p.bytes[i] = p.ms[i] = 0.0;
+  }
+}
+
+int peps_profile_count(void) { return K_NCLASS; }
+
+const char* peps_profile_name(int cls) { return (cls >= 0 && cls < K_NCLASS) ? kClassNames[cls] : ""; }
+
+int peps_profile_read(int cls, long long* launches, double* ms, double* flops, double* bytes) {
+  if (cls < 0 || cls >= K_NCLASS) return fail(PEPS_EINVAL, "bad kernel class");
+  Prof& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  p.drain();
+  if (launches) *launches = p.launches[cls];
+  if (ms) *ms = p.ms[cls];
+  if (flops) *flops = p.flops[cls];
+  if (bytes) *bytes = p.bytes[cls];
+  return PEPS_OK;
+}
+
+}  // extern "C"

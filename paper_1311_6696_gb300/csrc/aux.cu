@@ -1,0 +1,569 @@
+// Auxiliary kernels: lattice repacking, OBC validation, norms and rescaling,
+// counter-based var initialisation, local observables and CU_0.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "aux.cuh"
+#include "linalg.cuh"
+
+namespace peps {
+namespace {
+
+constexpr int RED_BLOCKS = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+    if (threadIdx.x == 0) red[0] = s;
+  }
+  __syncthreads();
+  s = red[0];
+  __syncthreads();
+  return s;
+}
+
+__global__ void k_orient(const void* src, int f32, int Lx, int d, int D, const OrientSite* sites,
+                         double* dst) {
+  const OrientSite s = sites[blockIdx.x];
+  const int dims[4] = {s.du, s.dl, s.dn, s.dr};
+  const int n = d * s.du * s.dl * s.dn * s.dr;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    int t = e;
+    int idx[4];
+    for (int k = 3; k >= 0; --k) {
+      idx[k] = t % dims[k];
+      t /= dims[k];
+    }
+    const int ph = t;
+    int o[4] = {0, 0, 0, 0};
+    for (int k = 0; k < 4; ++k) o[s.perm[k]] = idx[k];
+    const long long so = (((((long long)s.y * Lx + s.x) * d + ph) * D + o[0]) * D + o[1]) * D * D +
+                         (long long)o[2] * D + o[3];
+    dst[s.dst + e] = f32 ? double(static_cast<const float*>(src)[so])
+                         : static_cast<const double*>(src)[so];
+  }
+}
+
+__global__ void k_obc_count(const void* src, int f32, int Ly, int Lx, int d, int D,
+                            unsigned long long* count) {
+  const long long per = (long long)d * D * D * D * D;
+  const long long total = (long long)Ly * Lx * per;
+  unsigned long long c = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long site = e / per;
+    const int y = int(site / Lx), x = int(site % Lx);
+    long long r = e % per;
+    const int ri = int(r % D);
+    r /= D;
+    const int ni = int(r % D);
+    r /= D;
+    const int li = int(r % D);
+    r /= D;
+    const int ui = int(r % D);
+    const bool out = (y == 0 && ui) || (x == 0 && li) || (y == Ly - 1 && ni) || (x == Lx - 1 && ri);
+    if (out) {
+      const double v = f32 ? double(static_cast<const float*>(src)[e]) : static_cast<const double*>(src)[e];
+      if (v != 0.0) ++c;
+    }
+  }
+  if (c) atomicAdd(count, c);
+}
+
+__global__ void k_sumsq_partial(const double* x, long long n, double* part) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    s += v * v;
+  }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_sumsq_finish(const double* part, int np, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) out[0] = sqrt(s);
+}
+
+__global__ void k_rescale(double* x, long long n, const double* nrm, double* lnacc, int* flag) {
+  const double v = nrm[0];
+  const bool ok = v > 0.0 && isfinite(v);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (!ok && flag) atomicOr(flag, FLAG_BAD_VALUE);
+    if (lnacc && ok) lnacc[0] += log(v);
+  }
+  if (!ok) return;
+  const double inv = 1.0 / v;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] *= inv;
+}
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+struct VarInitArgs {
+  const double* src;
+  int s0, s1, s2, s3;
+  double* dst;
+  int d0, d1, d2, d3;
+  unsigned long long key;
+  const double* srcnorm;
+};
+
+__global__ void k_var_init(const VarInitArgs a) {
+  const long long n = (long long)a.d0 * a.d1 * a.d2 * a.d3;
+  const double scale = 1e-3 * a.srcnorm[0] / sqrt(double(n));
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long t = e;
+    const int i3 = int(t % a.d3);
+    t /= a.d3;
+    const int i2 = int(t % a.d2);
+    t /= a.d2;
+    const int i1 = int(t % a.d1);
+    const int i0 = int(t / a.d1);
+    const bool inside = i0 < a.s0 && i1 < a.s1 && i2 < a.s1 && i2 < a.s2 && i3 < a.s3;
+    if (inside) {
+      a.dst[e] = a.src[(((long long)i0 * a.s1 + i1) * a.s2 + i2) * a.s3 + i3];
+    } else {
+      const unsigned long long z = mix64(a.key + (unsigned long long)e + 0x9E3779B97F4A7C15ULL);
+      const double u = double(z >> 11) * (1.0 / 4503599627370496.0) - 1.0;   // 2^-52
+      a.dst[e] = scale * u;
+    }
+  }
+}
+
+__global__ void k_expect(const double* rho, int count, int k, const double* op, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const double* r = rho + (long long)i * k * k;
+  double num = 0.0, tr = 0.0;
+  for (int a = 0; a < k; ++a) {
+    tr += r[a * k + a];
+    for (int b = 0; b < k; ++b) num += r[a * k + b] * op[b * k + a];
+  }
+  out[i] = num / tr;
+}
+
+__global__ void k_finish_norm(const double* lns, int nl, const double* extra, const double* s,
+                              double* out_ln, double* out_sign) {
+  if (threadIdx.x || blockIdx.x) return;
+  double acc = extra ? extra[0] : 0.0;
+  for (int i = 0; i < nl; ++i) acc += lns[i];
+  const double v = s[0];
+  out_ln[0] = acc + log(fabs(v));
+  out_sign[0] = v > 0 ? 1.0 : (v < 0 ? -1.0 : 0.0);
+}
+
+__global__ void k_fill(double* x, long long n, double v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+
+__global__ void k_copy(double* dst, const double* src, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+unsigned grid_for(long long n) {
+  return unsigned(std::max<long long>(1, std::min<long long>((n + 255) / 256, 2048)));
+}
+
+// ----------------------------------------------------------------------------
+// CU_0 (Section 4.1): one CTA per oriented lattice.
+// ----------------------------------------------------------------------------
+struct SiteDims {
+  int du, dl, dn, dr;
+};
+
+__device__ __forceinline__ long long aidx(const SiteDims& s, int ph, int u, int l, int n, int r) {
+  return ((((long long)ph * s.du + u) * s.dl + l) * s.dn + n) * s.dr + r;
+}
+
+// b[n,o] = sum Lm[l,m] S[u,v] A[s,u,l,n,r] A[s,v,m,o,q] Rm[r,q]   (O(d D^5))
+__device__ void cu0_local(const double* Lm, const double* S, const double* A, const SiteDims& sd,
+                          int d, const double* Rm, double* Y, double* Z, double* b) {
+  const int du = sd.du, dl = sd.dl, dn = sd.dn, dr = sd.dr;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // Y[s,m,u,n,r] = sum_l Lm[l,m] A[s,u,l,n,r]
+  const int nY = d * dl * du * dn * dr;
+  for (int e = tid; e < nY; e += nt) {
+    int t = e;
+    const int r = t % dr; t /= dr;
+    const int n = t % dn; t /= dn;
+    const int u = t % du; t /= du;
+    const int m = t % dl; t /= dl;
+    const int s = t;
+    double acc = 0.0;
+    for (int l = 0; l < dl; ++l) acc += Lm[l * dl + m] * A[aidx(sd, s, u, l, n, r)];
+    Y[e] = acc;
+  }
+  __syncthreads();
+  // Z[s,m,v,n,r] = sum_u Y[s,m,u,n,r] S[u,v]
+  for (int e = tid; e < nY; e += nt) {
+    int t = e;
+    const int r = t % dr; t /= dr;
+    const int n = t % dn; t /= dn;
+    const int v = t % du; t /= du;
+    const int sm = t;   // s*dl + m
+    double acc = 0.0;
+    for (int u = 0; u < du; ++u) acc += Y[(((long long)sm * du + u) * dn + n) * dr + r] * S[u * du + v];
+    Z[e] = acc;
+  }
+  __syncthreads();
+  // Y[s,m,v,n,q] = sum_r Z[s,m,v,n,r] Rm[r,q]
+  for (int e = tid; e < nY; e += nt) {
+    const int q = e % dr;
+    const long long base = (long long)(e / dr) * dr;
+    double acc = 0.0;
+    for (int r = 0; r < dr; ++r) acc += Z[base + r] * Rm[r * dr + q];
+    Y[e] = acc;
+  }
+  __syncthreads();
+  // b[n,o] = sum_{s,m,v,q} Y[s,m,v,n,q] A[s,v,m,o,q]
+  for (int e = tid; e < dn * dn; e += nt) {
+    const int n = e / dn, o = e % dn;
+    double acc = 0.0;
+    for (int s = 0; s < d; ++s)
+      for (int m = 0; m < dl; ++m)
+        for (int v = 0; v < du; ++v)
+          for (int q = 0; q < dr; ++q)
+            acc += Y[((((long long)s * dl + m) * du + v) * dn + n) * dr + q] * A[aidx(sd, s, v, m, o, q)];
+    b[e] = acc;
+  }
+  __syncthreads();
+}
+
+// L'[r,q] = sum Lm[l,m] S[u,v] A[s,u,l,n,r] A[s,v,m,o,q] N[n,o]
+__device__ void cu0_lenv(const double* Lm, const double* S, const double* A, const SiteDims& sd,
+                         int d, const double* N, double* Y, double* Z, double* out) {
+  const int du = sd.du, dl = sd.dl, dn = sd.dn, dr = sd.dr;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nY = d * dl * du * dn * dr;
+  for (int e = tid; e < nY; e += nt) {
+    int t = e;
+    const int r = t % dr; t /= dr;
+    const int n = t % dn; t /= dn;
+    const int u = t % du; t /= du;
+    const int m = t % dl; t /= dl;
+    const int s = t;
+    double acc = 0.0;
+    for (int l = 0; l < dl; ++l) acc += Lm[l * dl + m] * A[aidx(sd, s, u, l, n, r)];
+    Y[e] = acc;
+  }
+  __syncthreads();
+  for (int e = tid; e < nY; e += nt) {
+    int t = e;
+    const int r = t % dr; t /= dr;
+    const int n = t % dn; t /= dn;
+    const int v = t % du; t /= du;
+    const int sm = t;
+    double acc = 0.0;
+    for (int u = 0; u < du; ++u) acc += Y[(((long long)sm * du + u) * dn + n) * dr + r] * S[u * du + v];
+    Z[e] = acc;
+  }
+  __syncthreads();
+  // Y[s,m,v,o,r] = sum_n Z[s,m,v,n,r] N[n,o]
+  for (int e = tid; e < nY; e += nt) {
+    int t = e;
+    const int r = t % dr; t /= dr;
+    const int o = t % dn; t /= dn;
+    const int smv = t;
+    double acc = 0.0;
+    for (int n = 0; n < dn; ++n) acc += Z[((long long)smv * dn + n) * dr + r] * N[n * dn + o];
+    Y[e] = acc;
+  }
+  __syncthreads();
+  // out[r,q] = sum_{s,m,v,o} Y[s,m,v,o,r] A[s,v,m,o,q]
+  for (int e = tid; e < dr * dr; e += nt) {
+    const int r = e / dr, q = e % dr;
+    double acc = 0.0;
+    for (int s = 0; s < d; ++s)
+      for (int m = 0; m < dl; ++m)
+        for (int v = 0; v < du; ++v)
+          for (int o = 0; o < dn; ++o)
+            acc += Y[((((long long)s * dl + m) * du + v) * dn + o) * dr + r] * A[aidx(sd, s, v, m, o, q)];
+    out[e] = acc;
+  }
+  __syncthreads();
+}
+
+// R'[l,m] = sum Rm[r,q] S[u,v] A[s,u,l,n,r] A[s,v,m,o,q] N[n,o]
+__device__ void cu0_renv(const double* Rm, const double* S, const double* A, const SiteDims& sd,
+                         int d, const double* N, double* Y, double* Z, double* out) {
+  const int du = sd.du, dl = sd.dl, dn = sd.dn, dr = sd.dr;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nY = d * du * dl * dn * dr;
+  // Y[s,u,l,n,q] = sum_r Rm[r,q] A[s,u,l,n,r]
+  for (int e = tid; e < nY; e += nt) {
+    const int q = e % dr;
+    const long long base = (long long)(e / dr) * dr;
+    double acc = 0.0;
+    for (int r = 0; r < dr; ++r) acc += A[base + r] * Rm[r * dr + q];
+    Y[e] = acc;
+  }
+  __syncthreads();
+  // Z[s,v,l,n,q] = sum_u Y[s,u,l,n,q] S[u,v]
+  for (int e = tid; e < nY; e += nt) {
+    int t = e;
+    const int q = t % dr; t /= dr;
+    const int n = t % dn; t /= dn;
+    const int l = t % dl; t /= dl;
+    const int v = t % du; t /= du;
+    const int s = t;
+    double acc = 0.0;
+    for (int u = 0; u < du; ++u) acc += Y[aidx(sd, s, u, l, n, q)] * S[u * du + v];
+    Z[e] = acc;
+  }
+  __syncthreads();
+  // Y[s,v,l,o,q] = sum_n Z[s,v,l,n,q] N[n,o]
+  for (int e = tid; e < nY; e += nt) {
+    int t = e;
+    const int q = t % dr; t /= dr;
+    const int o = t % dn; t /= dn;
+    const int svl = t;
+    double acc = 0.0;
+    for (int n = 0; n < dn; ++n) acc += Z[((long long)svl * dn + n) * dr + q] * N[n * dn + o];
+    Y[e] = acc;
+  }
+  __syncthreads();
+  // out[l,m] = sum_{s,v,o,q} Y[s,v,l,o,q] A[s,v,m,o,q]
+  for (int e = tid; e < dl * dl; e += nt) {
+    const int l = e / dl, m = e % dl;
+    double acc = 0.0;
+    for (int s = 0; s < d; ++s)
+      for (int v = 0; v < du; ++v)
+        for (int o = 0; o < dn; ++o)
+          for (int q = 0; q < dr; ++q)
+            acc += Y[aidx(sd, s, v, l, o, q)] * A[aidx(sd, s, v, m, o, q)];
+    out[e] = acc;
+  }
+  __syncthreads();
+}
+
+__device__ double cta_fro_normalize(double* x, int n, double* red) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[i] * x[i];
+  s = sqrt(block_sum(s, red));
+  const double inv = s > 0.0 ? 1.0 / s : 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] *= inv;
+  __syncthreads();
+  return s;
+}
+
+__global__ void __launch_bounds__(256) k_cu0(const Cu0Lattice* lats, int* flag) {
+  __shared__ double red[32];
+  const Cu0Lattice L = lats[blockIdx.x];
+  const int Ly = L.Ly, Lx = L.Lx, d = L.d, DM2 = L.Dmax * L.Dmax;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long big = (long long)d * L.Dmax * L.Dmax * L.Dmax * L.Dmax;
+  double* Y = L.work;
+  double* Z = Y + big;
+  double* Lm = Z + big;
+  double* Rm = Lm + (long long)Lx * DM2;
+  double* b = Rm + (long long)Lx * DM2;
+  auto dims = [&](int y, int x) {
+    const int* p = L.dims + 4 * (y * Lx + x);
+    return SiteDims{p[0], p[1], p[2], p[3]};
+  };
+  auto site = [&](int y, int x) { return L.A + L.off[y * Lx + x]; };
+  auto outm = [&](int r, int x) { return L.out + ((long long)r * Lx + x) * DM2; };
+  // row 0: top closures
+  for (int x = 0; x < Lx; ++x) {
+    const int du = dims(0, x).du;
+    for (int e = tid; e < du * du; e += nt) outm(0, x)[e] = L.top[(long long)x * DM2 + e];
+  }
+  __syncthreads();
+  for (int r = 0; r + 1 < Ly; ++r) {
+    // identity start, unit Frobenius norm
+    for (int x = 0; x < Lx; ++x) {
+      const int dn = dims(r, x).dn;
+      const double v = 1.0 / sqrt(double(dn));
+      for (int e = tid; e < dn * dn; e += nt) outm(r + 1, x)[e] = (e / dn == e % dn) ? v : 0.0;
+    }
+    __syncthreads();
+    {
+      const int dr = dims(r, Lx - 1).dr;
+      for (int e = tid; e < dr * dr; e += nt) Rm[(long long)(Lx - 1) * DM2 + e] = L.right[(long long)r * DM2 + e];
+      const int dl = dims(r, 0).dl;
+      for (int e = tid; e < dl * dl; e += nt) Lm[e] = L.left[(long long)r * DM2 + e];
+    }
+    __syncthreads();
+    for (int x = Lx - 1; x >= 1; --x) {
+      const SiteDims sd = dims(r, x);
+      cu0_renv(Rm + (long long)x * DM2, outm(r, x), site(r, x), sd, d, outm(r + 1, x), Y, Z,
+               Rm + (long long)(x - 1) * DM2);
+      cta_fro_normalize(Rm + (long long)(x - 1) * DM2, sd.dl * sd.dl, red);
+    }
+    bool conv = false;
+    for (int h = 0; h < L.max_half && !conv; ++h) {
+      double change = 0.0;
+      for (int step = 0; step < Lx; ++step) {
+        const int x = (h % 2 == 0) ? step : Lx - 1 - step;
+        const SiteDims sd = dims(r, x);
+        cu0_local(Lm + (long long)x * DM2, outm(r, x), site(r, x), sd, d, Rm + (long long)x * DM2, Y, Z, b);
+        cta_fro_normalize(b, sd.dn * sd.dn, red);
+        double* cur = outm(r + 1, x);
+        double part = 0.0;
+        for (int e = tid; e < sd.dn * sd.dn; e += nt) {
+          const double df = b[e] - cur[e];
+          part += df * df;
+        }
+        change = fmax(change, sqrt(block_sum(part, red)));
+        for (int e = tid; e < sd.dn * sd.dn; e += nt) cur[e] = b[e];
+        __syncthreads();
+        if (h % 2 == 0 && x < Lx - 1) {
+          cu0_lenv(Lm + (long long)x * DM2, outm(r, x), site(r, x), sd, d, cur, Y, Z,
+                   Lm + (long long)(x + 1) * DM2);
+          cta_fro_normalize(Lm + (long long)(x + 1) * DM2, sd.dr * sd.dr, red);
+        } else if (h % 2 == 1 && x > 0) {
+          cu0_renv(Rm + (long long)x * DM2, outm(r, x), site(r, x), sd, d, cur, Y, Z,
+                   Rm + (long long)(x - 1) * DM2);
+          cta_fro_normalize(Rm + (long long)(x - 1) * DM2, sd.dl * sd.dl, red);
+        }
+      }
+      conv = change < L.tol;
+    }
+    if (!conv && tid == 0) atomicOr(flag, FLAG_CU0_NOCONV);
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+void orient_lattice(Ctx& cx, const void* src, int src_f32, int Ly, int Lx, int d, int D,
+                    const OrientSite* host_sites, int nsites, double* dst) {
+  auto* dev = static_cast<OrientSite*>(cx.ws->alloc(sizeof(OrientSite) * nsites));
+  PEPS_CUDA(cudaMemcpyAsync(dev, host_sites, sizeof(OrientSite) * nsites, cudaMemcpyHostToDevice, cx.st));
+  Launch L(K_AUX, cx.st);
+  k_orient<<<nsites, 256, 0, cx.st>>>(src, src_f32, Lx, d, D, dev, dst);
+  PEPS_CHECK_LAUNCH();
+  // host_sites must stay alive until the copy is done
+  PEPS_CUDA(cudaStreamSynchronize(cx.st));
+}
+
+long long obc_violations_device(Ctx& cx, const void* src, int src_f32, int Ly, int Lx, int d, int D) {
+  auto* cnt = static_cast<unsigned long long*>(cx.ws->alloc(sizeof(unsigned long long)));
+  PEPS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), cx.st));
+  {
+    Launch L(K_AUX, cx.st);
+    k_obc_count<<<1024, 256, 0, cx.st>>>(src, src_f32, Ly, Lx, d, D, cnt);
+    PEPS_CHECK_LAUNCH();
+  }
+  unsigned long long h = 0;
+  PEPS_CUDA(cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, cx.st));
+  PEPS_CUDA(cudaStreamSynchronize(cx.st));
+  return (long long)h;
+}
+
+void fro_norm(Ctx& cx, const double* x, long long n, double* out) {
+  double* part = cx.scratch(RED_BLOCKS);
+  const unsigned nb = unsigned(std::max<long long>(1, std::min<long long>(RED_BLOCKS, (n + 255) / 256)));
+  Launch L(K_AUX, cx.st);
+  k_sumsq_partial<<<nb, 256, 0, cx.st>>>(x, n, part);
+  k_sumsq_finish<<<1, 256, 0, cx.st>>>(part, int(nb), out);
+  PEPS_CHECK_LAUNCH();
+}
+
+void rescale(Ctx& cx, double* x, long long n, const double* nrm, double* lnacc) {
+  Launch L(K_AUX, cx.st);
+  k_rescale<<<grid_for(n), 256, 0, cx.st>>>(x, n, nrm, lnacc, cx.flag);
+  PEPS_CHECK_LAUNCH();
+}
+
+void normalize(Ctx& cx, double* x, long long n, double* lnacc) {
+  double* t = cx.tmp;
+  fro_norm(cx, x, n, t);
+  rescale(cx, x, n, t, lnacc);
+}
+
+void var_init(Ctx& cx, const double* src, const int sdims[4], double* dst, const int ddims[4],
+              unsigned long long seed, int tag, int y, int x) {
+  const long long ns = (long long)sdims[0] * sdims[1] * sdims[2] * sdims[3];
+  double* sn = cx.tmp + 1;
+  fro_norm(cx, src, ns, sn);
+  VarInitArgs a;
+  a.src = src;
+  a.s0 = sdims[0];
+  a.s1 = sdims[1];
+  a.s2 = sdims[2];
+  a.s3 = sdims[3];
+  a.dst = dst;
+  a.d0 = ddims[0];
+  a.d1 = ddims[1];
+  a.d2 = ddims[2];
+  a.d3 = ddims[3];
+  a.key = seed * 0x9E3779B97F4A7C15ULL + ((unsigned long long)tag << 56) +
+          ((unsigned long long)y << 44) + ((unsigned long long)x << 32);
+  a.srcnorm = sn;
+  const long long n = (long long)ddims[0] * ddims[1] * ddims[2] * ddims[3];
+  Launch L(K_AUX, cx.st);
+  k_var_init<<<grid_for(n), 256, 0, cx.st>>>(a);
+  PEPS_CHECK_LAUNCH();
+}
+
+void expect_batch(Ctx& cx, const double* rho, int count, int k, const double* op, double* out) {
+  Launch L(K_OBS, cx.st, 2.0 * count * k * k, 8.0 * count * k * k);
+  k_expect<<<(count + 127) / 128, 128, 0, cx.st>>>(rho, count, k, op, out);
+  PEPS_CHECK_LAUNCH();
+}
+
+void finish_norm(Ctx& cx, const double* lns, int nl, const double* extra, const double* s,
+                 double* out_ln, double* out_sign) {
+  Launch L(K_AUX, cx.st);
+  k_finish_norm<<<1, 32, 0, cx.st>>>(lns, nl, extra, s, out_ln, out_sign);
+  PEPS_CHECK_LAUNCH();
+}
+
+void fill(Ctx& cx, double* x, long long n, double v) {
+  Launch L(K_AUX, cx.st);
+  k_fill<<<grid_for(n), 256, 0, cx.st>>>(x, n, v);
+  PEPS_CHECK_LAUNCH();
+}
+
+void copy(Ctx& cx, double* dst, const double* src, long long n) {
+  Launch L(K_AUX, cx.st);
+  k_copy<<<grid_for(n), 256, 0, cx.st>>>(dst, src, n);
+  PEPS_CHECK_LAUNCH();
+}
+
+size_t cu0_work_size(int Lx, int d, int Dmax) {
+  const size_t D2 = size_t(Dmax) * Dmax;
+  return 2 * size_t(d) * D2 * D2 + 2 * size_t(Lx) * D2 + D2;
+}
+
+void cu0_launch(Ctx& cx, const Cu0Lattice* lats, int nlat) {
+  auto* dev = static_cast<Cu0Lattice*>(cx.ws->alloc(sizeof(Cu0Lattice) * nlat));
+  PEPS_CUDA(cudaMemcpyAsync(dev, lats, sizeof(Cu0Lattice) * nlat, cudaMemcpyHostToDevice, cx.st));
+  Launch L(K_CU0, cx.st);
+  k_cu0<<<nlat, 256, 0, cx.st>>>(dev, cx.flag);
+  PEPS_CHECK_LAUNCH();
+  PEPS_CUDA(cudaStreamSynchronize(cx.st));
+}
+
+}  // namespace peps

@@ -1,0 +1,64 @@
+// Auxiliary kernels: lattice repacking, norms, var initialisation, observables, CU_0.
+#pragma once
+#include "ein.cuh"
+
+namespace peps {
+
+// Per-site gather descriptor for building an oriented lattice from the dense input.
+struct OrientSite {
+  long long dst;        // element offset of the site tensor in the destination
+  int y, x;             // source site
+  int du, dl, dn, dr;   // effective dims of the destination legs
+  int perm[4];          // destination leg k reads source leg perm[k] (0 u, 1 l, 2 n, 3 r)
+};
+
+void orient_lattice(Ctx& cx, const void* src, int src_f32, int Ly, int Lx, int d, int D,
+                    const OrientSite* host_sites, int nsites, double* dst);
+
+// Number of nonzero entries on outward (OBC) legs of the dense device array.
+long long obc_violations_device(Ctx& cx, const void* src, int src_f32, int Ly, int Lx, int d, int D);
+
+// out[0] = ||x||_F (device scalar).
+void fro_norm(Ctx& cx, const double* x, long long n, double* out);
+// x /= *nrm; if lnacc: *lnacc += log(*nrm).  Sets FLAG_BAD_VALUE on 0 / inf / nan.
+void rescale(Ctx& cx, double* x, long long n, const double* nrm, double* lnacc);
+// Both in sequence, using a small device temporary.
+void normalize(Ctx& cx, double* x, long long n, double* lnacc);
+
+// var start: dst[c,n,o,e] = src[c,n,o,e] where inside src's extent, else
+// noise * 1e-3 * ||src|| / sqrt(numel(dst)); noise from SplitMix64 keyed by
+// (seed, tag, y, x, flat index of dst).
+void var_init(Ctx& cx, const double* src, const int sdims[4], double* dst, const int ddims[4],
+              unsigned long long seed, int tag, int y, int x);
+
+// out[i] = sum_ab rho_i[a][b] op[b][a] / sum_a rho_i[a][a] for count matrices k x k.
+void expect_batch(Ctx& cx, const double* rho, int count, int k, const double* op, double* out);
+
+// ln_norm = sum(lns[0..nl)) + extra + log|s|, sign = sign(s) (device scalars).
+void finish_norm(Ctx& cx, const double* lns, int nl, const double* extra, const double* s,
+                 double* out_ln, double* out_sign);
+
+void fill(Ctx& cx, double* x, long long n, double v);
+void copy(Ctx& cx, double* dst, const double* src, long long n);
+
+// CU_0 separable boundaries of one oriented lattice (Section 4.1), computed
+// by one CTA.  Site tensors at `sites` (per-site offsets/dims in `meta`),
+// closures as device matrices.  Output: out[r][x] = D x D matrix (stride
+// out_stride per row, mat_stride per site) on the up legs of row r, r = 1..Ly-1.
+struct Cu0Lattice {
+  int Ly, Lx, d, Dmax;
+  const double* A;              // site tensors base
+  const long long* off;         // [Ly*Lx] element offsets of site tensors
+  const int* dims;              // [Ly*Lx*4] du, dl, dn, dr
+  const double* top;            // [Lx] closures on row 0 up legs, stride Dmax^2
+  const double* left;           // [Ly] closures, stride Dmax^2
+  const double* right;          // [Ly]
+  double* out;                  // [Ly][Lx][Dmax^2]
+  double* work;                 // scratch, see cu0_work_size
+  int max_half;
+  double tol;
+};
+size_t cu0_work_size(int Lx, int d, int Dmax);
+void cu0_launch(Ctx& cx, const Cu0Lattice* lats, int nlat);
+
+}  // namespace peps

@@ -1,0 +1,376 @@
+// Boundary-MPS sweeps, one-site ALS compression, row environments and local
+// density matrices (Sections 2, 4.1-4.3), orchestrated on the host, executed
+// on the device.  No host synchronisation happens inside a sweep: bond
+// dimensions depend on shapes only, and every data-dependent quantity (norms,
+// log-scales, convergence) stays on the device.
+#include <algorithm>
+#include <cmath>
+
+#include "aux.cuh"
+#include "engine.cuh"
+#include "linalg.cuh"
+
+namespace peps {
+
+std::vector<int> bond_caps(const std::vector<int>& phys, const std::vector<long long>& prod, int chi) {
+  const int Lx = int(phys.size());
+  std::vector<int> caps(std::max(0, Lx - 1));
+  const long long big = 1LL << 40;
+  for (int k = 0; k + 1 < Lx; ++k) {
+    long long lp = 1, rp = 1;
+    for (int x = 0; x <= k; ++x) lp = std::min(lp * phys[x], big);
+    for (int x = k + 1; x < Lx; ++x) rp = std::min(rp * phys[x], big);
+    caps[k] = int(std::min<long long>({(long long)chi, lp, rp, prod[k]}));
+  }
+  for (int k = 1; k + 1 < Lx; ++k) caps[k] = std::min<long long>(caps[k], (long long)caps[k - 1] * phys[k]);
+  for (int k = Lx - 3; k >= 0; --k) caps[k] = std::min<long long>(caps[k], (long long)caps[k + 1] * phys[k + 1]);
+  return caps;
+}
+
+Engine::Engine(Ctx& c, const Opts& o, int d, int Dmax, int Lmax)
+    : cx(c), opt(o), d_(d), Dmax_(Dmax), Lmax_(Lmax) {
+  const size_t chi = size_t(o.chi), D2 = size_t(Dmax) * Dmax, dd = size_t(d) * d;
+  bigN_ = chi * chi * D2 * D2;
+  // X1: chain stage 1 (chi^2 D^4), or bond stage 1 (d^2 chi^2 D^4) / bond stage 4 (d^4 chi^2 D^2)
+  X1_ = cx.ws->dalloc(std::max(bigN_ * dd, chi * chi * D2 * dd * dd));
+  X2_ = cx.ws->dalloc(bigN_ * dd * d);   // ket stage with up to one open pair
+  X3_ = cx.ws->dalloc(bigN_ * dd * dd);  // bra stage with up to two open pairs
+  envN_ = chi * D2 * chi * dd;
+  bb_ = cx.ws->dalloc(envN_);
+  Lmax = std::max(Lmax, 2);
+  Lenv_.resize(Lmax);
+  Renv_.resize(Lmax);
+  for (int i = 0; i < Lmax; ++i) {
+    Lenv_[i] = cx.ws->dalloc(envN_);
+    Renv_[i] = cx.ws->dalloc(envN_);
+  }
+  one_ = cx.ws->dalloc(1);
+  fill(cx, one_, 1, 1.0);
+}
+
+Mps Engine::closure_mps(const std::vector<Mat>& mats, Arena&) {
+  Mps T;
+  for (const Mat& m : mats) {
+    T.p.push_back(const_cast<double*>(m.p));
+    T.dims.push_back({1, m.n, m.n, 1});
+  }
+  return T;
+}
+
+Dims Engine::chain_left(const double* L, const Dims& ld, const double* M, const Dims& md,
+                        const SiteT& A, double* X3) {
+  const Dims ad = A.dims();
+  const Dims x1 = ein_dims("clma,auvb->clmuvb", ld, md);
+  ein(cx, "clma,auvb->clmuvb", L, ld, M, md, X1_);
+  const Dims x2 = ein_dims("clmuvb,sulnr->cmvbsnr", x1, ad);
+  ein(cx, "clmuvb,sulnr->cmvbsnr", X1_, x1, A.p, ad, X2_);
+  const Dims x3 = ein_dims("cmvbsnr,svmoq->cbnroq", x2, ad);
+  ein(cx, "cmvbsnr,svmoq->cbnroq", X2_, x2, A.p, ad, X3);
+  return x3;
+}
+
+Dims Engine::chain_right(const double* R, const Dims& rd, const double* M, const Dims& md,
+                         const SiteT& A, double* Y3) {
+  const Dims ad = A.dims();
+  const Dims y1 = ein_dims("auvb,brqc->auvrqc", md, rd);
+  ein(cx, "auvb,brqc->auvrqc", M, md, R, rd, X1_);
+  const Dims y2 = ein_dims("auvrqc,sulnr->avqcsln", y1, ad);
+  ein(cx, "auvrqc,sulnr->avqcsln", X1_, y1, A.p, ad, X2_);
+  const Dims y3 = ein_dims("avqcsln,svmoq->aclnmo", y2, ad);
+  ein(cx, "avqcsln,svmoq->aclnmo", X2_, y2, A.p, ad, Y3);
+  return y3;
+}
+
+Mps Engine::product_mps(const Mps& T, const OLat& lat, int y, Arena& step) {
+  const int Lx = lat.Lx;
+  Mps P;
+  for (int x = 0; x < Lx; ++x) {
+    const SiteT& A = lat.at(y, x);
+    const Dims ad = A.dims();
+    const Dims t1 = ein_dims("auvb,sulnr->avbslnr", T.dims[x], ad);
+    ein(cx, "auvb,sulnr->avbslnr", T.p[x], T.dims[x], A.p, ad, X2_);
+    const Dims t2 = ein_dims("avbslnr,svmoq->almnobrq", t1, ad);
+    double* cur = step.dalloc(numel(t2));
+    ein(cx, "avbslnr,svmoq->almnobrq", X2_, t1, A.p, ad, cur);
+    Dims cd = t2;
+    if (x == 0) {
+      const Mat& c = lat.left[y];
+      const Dims nd = ein_dims("lm,almnobrq->anobrq", {c.n, c.n}, cd);
+      double* nx = step.dalloc(numel(nd));
+      ein(cx, "lm,almnobrq->anobrq", c.p, {c.n, c.n}, cur, cd, nx);
+      cur = nx;
+      cd = nd;
+    }
+    if (x == Lx - 1) {
+      const Mat& c = lat.right[y];
+      const char* spec = (x == 0) ? "anobrq,rq->anob" : "almnobrq,rq->almnob";
+      const Dims nd = ein_dims(spec, cd, {c.n, c.n});
+      double* nx = step.dalloc(numel(nd));
+      ein(cx, spec, cur, cd, c.p, {c.n, c.n}, nx);
+      cur = nx;
+      cd = nd;
+    }
+    Dims pd;
+    if (x == 0) {
+      pd = {cd[0], cd[1], cd[2], 1};
+      for (size_t i = 3; i < cd.size(); ++i) pd[3] *= cd[i];
+    } else {
+      pd = {cd[0] * cd[1] * cd[2], cd[3], cd[4], 1};
+      for (size_t i = 5; i < cd.size(); ++i) pd[3] *= cd[i];
+    }
+    P.p.push_back(cur);
+    P.dims.push_back(pd);
+  }
+  return P;
+}
+
+void Engine::left_canonicalize(Mps& P, Arena& step) {
+  const int Lx = int(P.p.size());
+  for (int x = 0; x + 1 < Lx; ++x) {
+    const Dims pd = P.dims[x];
+    const int m = pd[0] * pd[1] * pd[2], n = pd[3], k = std::min(m, n);
+    double* Q = step.dalloc(size_t(m) * k);
+    double* R = step.dalloc(size_t(k) * n);
+    qr_thin(cx, m, n, P.p[x], n, 1, Q, k, 1, R);
+    P.p[x] = Q;
+    P.dims[x] = {pd[0], pd[1], pd[2], k};
+    const Dims nd = ein_dims("kb,bnoc->knoc", {k, n}, P.dims[x + 1]);
+    double* nx = step.dalloc(numel(nd));
+    ein(cx, "kb,bnoc->knoc", R, {k, n}, P.p[x + 1], P.dims[x + 1], nx);
+    P.p[x + 1] = nx;
+    P.dims[x + 1] = nd;
+  }
+}
+
+void Engine::svd_truncate(Mps& P, const std::vector<int>& caps, Arena& step) {
+  const int Lx = int(P.p.size());
+  for (int x = Lx - 1; x >= 1; --x) {
+    const Dims pd = P.dims[x];
+    const int m = pd[0], n = pd[1] * pd[2] * pd[3];
+    const int kk = std::min(caps[x - 1], std::min(m, n));
+    double* US = step.dalloc(size_t(m) * kk);
+    double* Vt = step.dalloc(size_t(kk) * n);
+    svd_trunc(cx, m, n, P.p[x], kk, US, Vt);
+    P.p[x] = Vt;
+    P.dims[x] = {kk, pd[1], pd[2], pd[3]};
+    const Dims nd = ein_dims("anob,bk->anok", P.dims[x - 1], {m, kk});
+    double* nx = step.dalloc(numel(nd));
+    ein(cx, "anob,bk->anok", P.p[x - 1], P.dims[x - 1], US, {m, kk}, nx);
+    P.p[x - 1] = nx;
+    P.dims[x - 1] = nd;
+  }
+}
+
+Mps Engine::var_compress(const Mps& T, const OLat& lat, int y, const std::vector<int>& caps,
+                         int tag, int& centre, Arena& step) {
+  const int Lx = lat.Lx;
+  Mps N;
+  N.p.resize(Lx);
+  N.dims.resize(Lx);
+  for (int x = 0; x < Lx; ++x) {
+    const int c = x == 0 ? 1 : caps[x - 1];
+    const int e = x == Lx - 1 ? 1 : caps[x];
+    const int D = lat.at(y, x).dn;
+    N.dims[x] = {c, D, D, e};
+    N.p[x] = step.dalloc(numel(N.dims[x]));
+    var_init(cx, T.p[x], T.dims[x].data(), N.p[x], N.dims[x].data(), opt.seed, tag, y, x);
+  }
+  // right-canonicalise the start: N[x] = R^T Q^T (QR of N[x]^T), R^T moves left
+  for (int x = Lx - 1; x >= 1; --x) {
+    const Dims nd = N.dims[x];
+    const int c = nd[0], noe = nd[1] * nd[2] * nd[3];
+    PEPS_REQUIRE(c <= noe, "internal: inconsistent bond caps");
+    double* Rt = step.dalloc(size_t(c) * c);
+    qr_thin(cx, noe, c, N.p[x], 1, noe, N.p[x], 1, noe, Rt);
+    const Dims pd = N.dims[x - 1];
+    ein(cx, "anob,kb->anok", N.p[x - 1], pd, Rt, {c, c}, bb_);
+    copy(cx, N.p[x - 1], bb_, (long long)numel(pd));
+  }
+  std::vector<Dims> ld(Lx), rd(Lx);
+  {
+    const Mat& r = lat.right[y];
+    rd[Lx - 1] = {1, r.n, r.n, 1};
+    copy(cx, Renv_[Lx - 1], r.p, (long long)r.n * r.n);
+    const Mat& l = lat.left[y];
+    ld[0] = {1, l.n, l.n, 1};
+    copy(cx, Lenv_[0], l.p, (long long)l.n * l.n);
+  }
+  for (int x = Lx - 1; x >= 1; --x) {
+    const Dims y3 = chain_right(Renv_[x], rd[x], T.p[x], T.dims[x], lat.at(y, x), X3_);
+    rd[x - 1] = ein_dims("aelnmo,cnoe->almc", y3, N.dims[x]);
+    ein(cx, "aelnmo,cnoe->almc", X3_, y3, N.p[x], N.dims[x], Renv_[x - 1]);
+  }
+  for (int h = 0; h < opt.sweeps; ++h) {
+    if (h % 2 == 0) {
+      for (int x = 0; x < Lx; ++x) {
+        const Dims x3 = chain_left(Lenv_[x], ld[x], T.p[x], T.dims[x], lat.at(y, x), X3_);
+        const Dims bd = ein_dims("cbnroq,brqe->cnoe", x3, rd[x]);
+        ein(cx, "cbnroq,brqe->cnoe", X3_, x3, Renv_[x], rd[x], bb_);
+        PEPS_REQUIRE(bd == N.dims[x], "internal: local tensor shape");
+        if (x < Lx - 1) {
+          const int m = bd[0] * bd[1] * bd[2], n = bd[3];
+          PEPS_REQUIRE(n <= m, "internal: inconsistent bond caps");
+          qr_thin(cx, m, n, bb_, n, 1, N.p[x], n, 1, nullptr);
+          ld[x + 1] = ein_dims("cbnroq,cnoe->erqb", x3, N.dims[x]);
+          ein(cx, "cbnroq,cnoe->erqb", X3_, x3, N.p[x], N.dims[x], Lenv_[x + 1]);
+        } else {
+          copy(cx, N.p[x], bb_, (long long)numel(bd));
+        }
+      }
+      centre = Lx - 1;
+    } else {
+      for (int x = Lx - 1; x >= 0; --x) {
+        const Dims y3 = chain_right(Renv_[x], rd[x], T.p[x], T.dims[x], lat.at(y, x), X3_);
+        const Dims bd = ein_dims("clma,aelnmo->cnoe", ld[x], y3);
+        ein(cx, "clma,aelnmo->cnoe", Lenv_[x], ld[x], X3_, y3, bb_);
+        PEPS_REQUIRE(bd == N.dims[x], "internal: local tensor shape");
+        if (x > 0) {
+          const int c = bd[0], noe = bd[1] * bd[2] * bd[3];
+          qr_thin(cx, noe, c, bb_, 1, noe, N.p[x], 1, noe, nullptr);
+          rd[x - 1] = ein_dims("aelnmo,cnoe->almc", y3, N.dims[x]);
+          ein(cx, "aelnmo,cnoe->almc", X3_, y3, N.p[x], N.dims[x], Renv_[x - 1]);
+        } else {
+          copy(cx, N.p[x], bb_, (long long)numel(bd));
+        }
+      }
+      centre = 0;
+    }
+  }
+  return N;
+}
+
+Mps Engine::absorb_compress(const Mps& T, const OLat& lat, int y, int tag, double* lnacc, Arena& keep) {
+  const int Lx = lat.Lx;
+  std::vector<int> phys(Lx);
+  std::vector<long long> prod(std::max(0, Lx - 1));
+  for (int x = 0; x < Lx; ++x) phys[x] = lat.at(y, x).dn * lat.at(y, x).dn;
+  for (int k = 0; k + 1 < Lx; ++k) prod[k] = (long long)T.dims[k][3] * lat.at(y, k).dr * lat.at(y, k).dr;
+  const std::vector<int> caps = bond_caps(phys, prod, opt.chi);
+  Arena step(cx.st);
+  Mps P;
+  int centre = 0;
+  bool exact = true;
+  for (int k = 0; k + 1 < Lx; ++k) exact = exact && prod[k] <= caps[k];
+  if (opt.mode == PEPS_SVD) {
+    P = product_mps(T, lat, y, step);
+    left_canonicalize(P, step);
+    svd_truncate(P, caps, step);
+    centre = 0;
+  } else if (exact) {
+    P = product_mps(T, lat, y, step);
+    left_canonicalize(P, step);
+    centre = Lx - 1;
+  } else {
+    P = var_compress(T, lat, y, caps, tag, centre, step);
+  }
+  normalize(cx, P.p[centre], (long long)numel(P.dims[centre]), lnacc);
+  Mps out;
+  for (int x = 0; x < Lx; ++x) {
+    const size_t n = numel(P.dims[x]);
+    double* q = keep.dalloc(n);
+    copy(cx, q, P.p[x], (long long)n);
+    out.p.push_back(q);
+    out.dims.push_back(P.dims[x]);
+  }
+  return out;
+}
+
+std::vector<Mps> Engine::sweep(const OLat& lat, int tag, int upto, double* lnacc, Arena& keep) {
+  std::vector<Mps> out;
+  out.push_back(closure_mps(lat.top, keep));
+  for (int y = 0; y < upto; ++y) out.push_back(absorb_compress(out.back(), lat, y, tag, lnacc, keep));
+  return out;
+}
+
+void Engine::row_rhos(const OLat& lat, const Mps& T, const Mps& B, int y, const Targets& sites,
+                      const Targets& bonds) {
+  const int Lx = lat.Lx;
+  std::vector<Dims> ld(Lx), rd(Lx);
+  const Mat& lc = lat.left[y];
+  const Mat& rc = lat.right[y];
+  ld[0] = {1, lc.n, lc.n, 1};
+  copy(cx, Lenv_[0], lc.p, (long long)lc.n * lc.n);
+  rd[Lx - 1] = {1, rc.n, rc.n, 1};
+  copy(cx, Renv_[Lx - 1], rc.p, (long long)rc.n * rc.n);
+  int xmax = 0, xmin = lat.Lx;
+  for (const auto& t : sites) {
+    xmax = std::max(xmax, t.first + 1);
+    xmin = std::min(xmin, t.first);
+  }
+  for (const auto& t : bonds) {
+    xmax = std::max(xmax, t.first + 2);
+    xmin = std::min(xmin, t.first);
+  }
+  for (int x = 0; x + 1 < Lx && x + 1 < xmax; ++x) {
+    const Dims x3 = chain_left(Lenv_[x], ld[x], T.p[x], T.dims[x], lat.at(y, x), X3_);
+    ld[x + 1] = ein_dims("cbnroq,cnoe->erqb", x3, B.dims[x]);
+    ein(cx, "cbnroq,cnoe->erqb", X3_, x3, B.p[x], B.dims[x], Lenv_[x + 1]);
+    normalize(cx, Lenv_[x + 1], (long long)numel(ld[x + 1]), nullptr);
+  }
+  for (int x = Lx - 1; x >= 1 && x - 1 >= xmin; --x) {
+    const Dims y3 = chain_right(Renv_[x], rd[x], T.p[x], T.dims[x], lat.at(y, x), X3_);
+    rd[x - 1] = ein_dims("aelnmo,cnoe->almc", y3, B.dims[x]);
+    ein(cx, "aelnmo,cnoe->almc", X3_, y3, B.p[x], B.dims[x], Renv_[x - 1]);
+    normalize(cx, Renv_[x - 1], (long long)numel(rd[x - 1]), nullptr);
+  }
+  auto open_site = [&](int x) -> Dims {
+    const SiteT& A = lat.at(y, x);
+    const Dims ad = A.dims();
+    const Dims x1 = ein_dims("clma,auvb->clmuvb", ld[x], T.dims[x]);
+    ein(cx, "clma,auvb->clmuvb", Lenv_[x], ld[x], T.p[x], T.dims[x], X1_);
+    const Dims x2 = ein_dims("clmuvb,sulnr->cmvbsnr", x1, ad);
+    ein(cx, "clmuvb,sulnr->cmvbsnr", X1_, x1, A.p, ad, X2_);
+    const Dims x3 = ein_dims("cmvbsnr,tvmoq->cbsnrtoq", x2, ad);
+    ein(cx, "cmvbsnr,tvmoq->cbsnrtoq", X2_, x2, A.p, ad, X3_);
+    const Dims w = ein_dims("cbsnrtoq,cnoe->erqbst", x3, B.dims[x]);
+    ein(cx, "cbsnrtoq,cnoe->erqbst", X3_, x3, B.p[x], B.dims[x], bb_);
+    return w;
+  };
+  for (const auto& t : sites) {
+    const int x = t.first;
+    const Dims w = open_site(x);
+    ein(cx, "erqbst,brqe->st", bb_, w, Renv_[x], rd[x], t.second);
+  }
+  for (const auto& t : bonds) {
+    const int x = t.first;
+    PEPS_REQUIRE(x + 1 < Lx, "internal: bond outside the row");
+    const Dims w = open_site(x);
+    const SiteT& A2 = lat.at(y, x + 1);
+    const Dims ad = A2.dims();
+    const Dims x1 = ein_dims("clmaij,auvb->clmuvbij", w, T.dims[x + 1]);
+    ein(cx, "clmaij,auvb->clmuvbij", bb_, w, T.p[x + 1], T.dims[x + 1], X1_);
+    const Dims x2 = ein_dims("clmuvbij,sulnr->cmvbsnrij", x1, ad);
+    ein(cx, "clmuvbij,sulnr->cmvbsnrij", X1_, x1, A2.p, ad, X2_);
+    const Dims x3 = ein_dims("cmvbsnrij,tvmoq->cbsnrtoqij", x2, ad);
+    ein(cx, "cmvbsnrij,tvmoq->cbsnrtoqij", X2_, x2, A2.p, ad, X3_);
+    const Dims x4 = ein_dims("cbsnrtoqij,cnoe->erqbstij", x3, B.dims[x + 1]);
+    ein(cx, "cbsnrtoqij,cnoe->erqbstij", X3_, x3, B.p[x + 1], B.dims[x + 1], X1_);
+    ein(cx, "erqbstij,brqe->isjt", X1_, x4, Renv_[x + 1], rd[x + 1], t.second);
+  }
+}
+
+void Engine::norm_from_top(const OLat& lat, const Mps& T, const double* lns_acc, double* out) {
+  const int Lx = lat.Lx, y = lat.Ly - 1;
+  double* extra = cx.ws->dalloc(1);
+  double* s = cx.ws->dalloc(1);
+  fill(cx, extra, 1, 0.0);
+  const Mat& lc = lat.left[y];
+  Dims ld = {1, lc.n, lc.n, 1};
+  copy(cx, Lenv_[0], lc.p, (long long)lc.n * lc.n);
+  int cur = 0;
+  for (int x = 0; x < Lx; ++x) {
+    const Dims x3 = chain_left(Lenv_[cur], ld, T.p[x], T.dims[x], lat.at(y, x), X3_);
+    const Mat& bc = lat.bottom[x];
+    const Dims bd = {1, bc.n, bc.n, 1};
+    const Dims nd = ein_dims("cbnroq,cnoe->erqb", x3, bd);
+    ein(cx, "cbnroq,cnoe->erqb", X3_, x3, bc.p, bd, Lenv_[1 - cur]);
+    cur = 1 - cur;
+    ld = nd;
+    if (x + 1 < Lx) normalize(cx, Lenv_[cur], (long long)numel(ld), extra);
+  }
+  const Mat& rc = lat.right[y];
+  ein(cx, "erqb,rq->", Lenv_[cur], ld, rc.p, {rc.n, rc.n}, s);
+  finish_norm(cx, lns_acc, 1, extra, s, out, out + 1);
+}
+
+}  // namespace peps

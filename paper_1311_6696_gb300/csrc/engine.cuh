@@ -1,0 +1,100 @@
+// Host-side orchestration of the boundary-MPS contraction (device resident).
+#pragma once
+#include <memory>
+#include <vector>
+
+#include "ein.cuh"
+
+namespace peps {
+
+struct SiteT {
+  const double* p = nullptr;
+  int d = 0, du = 0, dl = 0, dn = 0, dr = 0;
+  Dims dims() const { return {d, du, dl, dn, dr}; }
+};
+
+struct Mat {
+  const double* p = nullptr;   // n x n, row-major (ket leg, bra leg)
+  int n = 0;
+};
+
+// A (sub-)lattice in one orientation, with a closure matrix on every outward leg.
+struct OLat {
+  int Ly = 0, Lx = 0, d = 0;
+  std::vector<SiteT> sites;    // row-major
+  std::vector<Mat> top, bottom, left, right;
+  const SiteT& at(int y, int x) const { return sites[size_t(y) * Lx + x]; }
+};
+
+struct Mps {
+  std::vector<double*> p;
+  std::vector<Dims> dims;      // [a, u, v, b]
+};
+
+struct Opts {
+  int chi = 16;
+  int mode = PEPS_SVD;
+  int sweeps = 2;
+  int precision = PEPS_PREC_FP64;
+  unsigned long long seed = 0;
+};
+
+// Everything a full or cluster environment keeps on the device.
+struct EnvData {
+  int Ly = 0, Lx = 0, d = 0, D = 0;
+  bool has_norm = false;
+  double* rho_site = nullptr;   // [Ly*Lx][d*d]
+  double* rho_h = nullptr;      // [Ly*(Lx-1)][d^4]
+  double* rho_v = nullptr;      // [(Ly-1)*Lx][d^4]
+  double* lnnorm = nullptr;     // [2]: ln|N|, sign
+};
+
+// Contraction engine bound to one stream/workspace.
+class Engine {
+ public:
+  Engine(Ctx& cx, const Opts& o, int d, int Dmax, int Lmax);
+
+  // Top-down boundaries of `lat`: out[y] = boundary above row y, y = 0..upto.
+  // lnacc (device scalar) accumulates the log of every rescaling factor.
+  std::vector<Mps> sweep(const OLat& lat, int tag, int upto, double* lnacc, Arena& keep);
+
+  // Density matrices of row y between top boundary T and bottom boundary B:
+  // rho_site of column x into dst for every (x, dst) in `sites`, rho of the
+  // bond (x, x+1) into dst for every (x, dst) in `bonds`.
+  using Targets = std::vector<std::pair<int, double*>>;
+  void row_rhos(const OLat& lat, const Mps& T, const Mps& B, int y, const Targets& sites,
+                const Targets& bonds);
+
+  // ln|<psi|psi>| from the top boundary above the last row (writes out[0], out[1] = sign).
+  void norm_from_top(const OLat& lat, const Mps& T, const double* lns_acc, double* out);
+
+  Ctx& cx;
+  Opts opt;
+
+ private:
+  Mps closure_mps(const std::vector<Mat>& mats, Arena& keep);
+  Mps absorb_compress(const Mps& T, const OLat& lat, int y, int tag, double* lnacc, Arena& keep);
+  Mps product_mps(const Mps& T, const OLat& lat, int y, Arena& keep);
+  void left_canonicalize(Mps& P, Arena& keep);
+  void svd_truncate(Mps& P, const std::vector<int>& caps, Arena& keep);
+  Mps var_compress(const Mps& T, const OLat& lat, int y, const std::vector<int>& caps, int tag,
+                   int& centre, Arena& keep);
+
+  // absorb chain pieces (all FP64 einsum at present)
+  Dims chain_left(const double* L, const Dims& ld, const double* M, const Dims& md, const SiteT& A,
+                  double* X3);
+  Dims chain_right(const double* R, const Dims& rd, const double* M, const Dims& md,
+                   const SiteT& A, double* Y3);
+
+  int d_, Dmax_, Lmax_;
+  size_t bigN_;                 // chi^2 * Dmax^4 (elements of the largest chain intermediate / d)
+  double *X1_, *X2_, *X3_, *bb_;
+  std::vector<double*> Lenv_, Renv_;
+  size_t envN_;
+  double* one_;                 // device scalar 1.0
+};
+
+// Caps of the new boundary (same rule as the documented reading).
+std::vector<int> bond_caps(const std::vector<int>& phys, const std::vector<long long>& prod, int chi);
+
+}  // namespace peps

@@ -1,0 +1,230 @@
+"""ctypes binding of the C ABI declared in include/peps.h (argument marshalling only).
+
+Every computation runs in ``libpeps.so``; this module converts arguments,
+checks status codes and raises :class:`PepsError` with the library's message.
+If the library is missing, importing this module raises -- there is no
+Python fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpeps.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ECONVERGE, ETIMEOUT = range(6)
+F64, F32 = 0, 1
+SVD, VAR = 0, 1
+PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
+KIND = {"site": 0, "hbond": 1, "vbond": 2}
+MODE = {"svd": SVD, "var": VAR}
+
+EXPORTS = [
+    "peps_env_full", "peps_env_cluster", "peps_expect_local", "peps_env_rho", "peps_norm",
+    "peps_env_ln_norm", "peps_env_free", "peps_last_error", "peps_profile_enable",
+    "peps_profile_reset", "peps_profile_count", "peps_profile_name", "peps_profile_read",
+]
+
+
+class PepsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"peps error {code}: {msg}")
+        self.code = code
+
+
+class Lattice(C.Structure):
+    _fields_ = [("Ly", C.c_int), ("Lx", C.c_int), ("d", C.c_int), ("D", C.c_int),
+                ("dtype", C.c_int), ("A", C.c_void_p), ("on_device", C.c_int)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("chi", C.c_int), ("mode", C.c_int), ("sweeps", C.c_int), ("precision", C.c_int),
+                ("n", C.c_int), ("closure", C.c_int), ("closure_weights", C.c_void_p),
+                ("seed", C.c_ulonglong)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    lib.peps_env_full.argtypes = [C.POINTER(Lattice), C.POINTER(Opts), C.POINTER(P), P]
+    lib.peps_env_cluster.argtypes = [C.POINTER(Lattice), C.POINTER(Opts), C.POINTER(P), P]
+    lib.peps_expect_local.argtypes = [P, C.POINTER(Lattice), C.c_int, P, P, P]
+    lib.peps_env_rho.argtypes = [P, C.c_int, P, P]
+    lib.peps_norm.argtypes = [C.POINTER(Lattice), C.POINTER(Opts), C.POINTER(C.c_double),
+                              C.POINTER(C.c_int), P]
+    lib.peps_env_ln_norm.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_int), P]
+    lib.peps_env_free.argtypes = [P]
+    lib.peps_env_free.restype = None
+    lib.peps_last_error.restype = C.c_char_p
+    lib.peps_profile_enable.argtypes = [C.c_int]
+    lib.peps_profile_enable.restype = None
+    lib.peps_profile_reset.restype = None
+    lib.peps_profile_name.restype = C.c_char_p
+    lib.peps_profile_read.argtypes = [C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    return lib
+
+
+lib = _load()
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise PepsError(rc, lib.peps_last_error().decode(errors="replace"))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)     # torch.cuda.Stream
+
+
+class _Input:
+    """Keeps the array alive and describes it as a peps_lattice."""
+
+    def __init__(self, A):
+        try:
+            import torch
+        except ImportError:          # numpy-only use
+            torch = None
+        if torch is not None and isinstance(A, torch.Tensor):
+            assert A.dim() == 7 and A.is_contiguous(), "A must be contiguous (Ly,Lx,d,D,D,D,D)"
+            assert A.dtype in (torch.float64, torch.float32)
+            self.keep = A
+            ptr, dev = A.data_ptr(), int(A.is_cuda)
+            dt = F64 if A.dtype == torch.float64 else F32
+        else:
+            A = np.ascontiguousarray(A)
+            if A.dtype not in (np.float64, np.float32):
+                A = A.astype(np.float64)
+            assert A.ndim == 7, "A must have shape (Ly,Lx,d,D,D,D,D)"
+            self.keep = A
+            ptr, dev = A.ctypes.data, 0
+            dt = F64 if A.dtype == np.float64 else F32
+        Ly, Lx, d, D = (int(v) for v in A.shape[:4])
+        self.lat = Lattice(Ly, Lx, d, D, dt, ptr, dev)
+
+
+def _opts(chi, mode, sweeps, precision, n, seed):
+    return Opts(int(chi), MODE[mode] if isinstance(mode, str) else int(mode), int(sweeps),
+                PREC[precision] if isinstance(precision, str) else int(precision), int(n), 0, None,
+                int(seed))
+
+
+class Env:
+    """A device-resident environment handle (freed with the object)."""
+
+    def __init__(self, handle, shape, stream):
+        self._h = handle
+        self.Ly, self.Lx, self.d = shape
+        self._stream = stream
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib.peps_env_free(h)
+            self._h = None
+
+    def free(self):
+        self.__del__()
+
+    def _count(self, kind):
+        return {"site": self.Ly * self.Lx, "hbond": self.Ly * (self.Lx - 1),
+                "vbond": (self.Ly - 1) * self.Lx}[kind]
+
+    def expect(self, kind: str, op) -> np.ndarray:
+        """<O> = Tr(rho O) / Tr(rho) at every site / bond (row-major)."""
+        op = np.ascontiguousarray(op, dtype=np.float64)
+        out = np.zeros(self._count(kind))
+        _check(lib.peps_expect_local(self._h, None, KIND[kind], op.ctypes.data, out.ctypes.data,
+                                     _stream_ptr(self._stream)))
+        return out
+
+    def rho(self, kind: str) -> np.ndarray:
+        k = self.d if kind == "site" else self.d * self.d
+        out = np.zeros((self._count(kind), k, k))
+        _check(lib.peps_env_rho(self._h, KIND[kind], out.ctypes.data, _stream_ptr(self._stream)))
+        return out
+
+    def ln_norm(self):
+        ln = C.c_double()
+        sg = C.c_int()
+        _check(lib.peps_env_ln_norm(self._h, C.byref(ln), C.byref(sg), _stream_ptr(self._stream)))
+        return ln.value, sg.value
+
+
+def _set_device(device):
+    if device is None:
+        return
+    import torch
+    torch.cuda.set_device(device)
+
+
+def env_full(A, chi: int, mode="svd", sweeps: int = 2, precision="fp64", seed: int = 0,
+             stream=None, device=None) -> Env:
+    """Full (sandwich) environments of every site; see peps_env_full."""
+    _set_device(device)
+    inp = _Input(A)
+    o = _opts(chi, mode, sweeps, precision, 1, seed)
+    h = C.c_void_p()
+    _check(lib.peps_env_full(C.byref(inp.lat), C.byref(o), C.byref(h), _stream_ptr(stream)))
+    return Env(h.value, (inp.lat.Ly, inp.lat.Lx, inp.lat.d), stream)
+
+
+def env_cluster(A, n: int, chi: int, mode="svd", sweeps: int = 2, precision="fp64", seed: int = 0,
+                stream=None, device=None) -> Env:
+    """Cluster environments (window n x n around every site); see peps_env_cluster."""
+    _set_device(device)
+    inp = _Input(A)
+    o = _opts(chi, mode, sweeps, precision, n, seed)
+    h = C.c_void_p()
+    _check(lib.peps_env_cluster(C.byref(inp.lat), C.byref(o), C.byref(h), _stream_ptr(stream)))
+    return Env(h.value, (inp.lat.Ly, inp.lat.Lx, inp.lat.d), stream)
+
+
+def norm(A, chi: int, mode="svd", sweeps: int = 2, precision="fp64", seed: int = 0,
+         stream=None, device=None):
+    """(ln|<psi|psi>|, sign) by the top-down sweep; see peps_norm."""
+    _set_device(device)
+    inp = _Input(A)
+    o = _opts(chi, mode, sweeps, precision, 1, seed)
+    ln = C.c_double()
+    sg = C.c_int()
+    _check(lib.peps_norm(C.byref(inp.lat), C.byref(o), C.byref(ln), C.byref(sg), _stream_ptr(stream)))
+    return ln.value, sg.value
+
+
+# ---------------------------------------------------------------- instrumentation
+def profile_enable(mask: int = -1):
+    lib.peps_profile_enable(int(mask))
+
+
+def profile_reset():
+    lib.peps_profile_reset()
+
+
+def profile_read() -> dict:
+    out = {}
+    for i in range(lib.peps_profile_count()):
+        n = C.c_longlong()
+        ms = C.c_double()
+        fl = C.c_double()
+        by = C.c_double()
+        _check(lib.peps_profile_read(i, C.byref(n), C.byref(ms), C.byref(fl), C.byref(by)))
+        out[lib.peps_profile_name(i).decode()] = dict(launches=n.value, ms=ms.value,
+                                                       flops=fl.value, bytes=by.value)
+    return out
+
+
+def class_index(name: str) -> int:
+    for i in range(lib.peps_profile_count()):
+        if lib.peps_profile_name(i).decode() == name:
+            return i
+    raise KeyError(name)

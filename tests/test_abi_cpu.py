@@ -1,0 +1,48 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every symbol that
+include/peps.h declares, and fails loudly (no CPU fallback) without a GPU."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "peps.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(peps_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary_calls():
+    names = _declared()
+    for n in ("peps_env_full", "peps_env_cluster", "peps_expect_local", "peps_norm",
+              "peps_env_free", "peps_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1311_6696_gb300 import peps
+    for n in _declared():
+        assert hasattr(peps.lib, n), n
+    assert set(_declared()) <= set(peps.EXPORTS) | {n for n in _declared() if hasattr(peps.lib, n)}
+
+
+def test_no_gpu_means_a_loud_error():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1311_6696_gb300 import peps, synth
+    with pytest.raises(peps.PepsError) as e:
+        peps.env_full(synth.workload("4x4_D2"), chi=4)
+    assert e.value.code == peps.ECUDA
+
+
+def test_bond_caps_rule_matches_oracle():
+    """The host-side cap rule is reimplemented in C++; check the Python oracle's
+    rule on hand-worked cases (so a change to either shows up)."""
+    from oracle import peps_oracle as O
+    assert O.bond_caps([4, 4, 4, 4], [4, 16, 4], 16) == [4, 16, 4]
+    assert O.bond_caps([16] * 10, [256] * 9, 64) == [16, 64, 64, 64, 64, 64, 64, 64, 16]
+    assert O.bond_caps([1, 1], [1], 8) == [1]
+    assert O.bond_caps([4, 4, 4], [16, 16], 2) == [2, 2]
