@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark: full boundary-MPS environments of a 10x10 OBC PEPS (d=2, D=4).
+
+Workload (one step): every site environment of a 10x10 PEPS with d=2, D=4,
+entries 0.5 + 0.1*N(0,1) (unit-norm tensors, seeded), boundary bond chi=64,
+variational (2 half-sweep) compression -- four directional sweeps, the row
+and column environments, every site / bond density matrix -- followed by
+<S.S> on every one of the 180 nearest-neighbour bonds.  One step yields
+Ly*Lx = 100 site environments; the metric is environments per second.
+
+Launch: ``python bench.py [--gpus N --steps K --warmup W]``; for N > 1 run
+under ``torch.distributed.run`` with one process per GPU.  The full
+environment does not shard, so every rank computes its own replica (seed 2 +
+rank): weak scaling, no collective on the data path.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead
+(a bounded sample of the same workload, extrapolated by operation count).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="10x10_D4", Ly=10, Lx=10, d=2, D=4, seed=2)
+L2_BYTES = 129 * 2 ** 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# FP64 ALU peak of GB300 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def _clock_sampler():
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        return subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"],
+                                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except OSError:
+        return None
+
+
+def _clock_summary(proc, gpu_index):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        out, _ = proc.communicate(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+        out, _ = proc.communicate()
+    sms, mx, reasons = [], 0.0, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in out.splitlines():
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9 or f[0] != str(gpu_index):
+            continue
+        try:
+            sms.append(float(f[1]))
+            mx = max(mx, float(f[2]))
+        except ValueError:
+            continue
+        for n, v in zip(names, f[5:9]):
+            if v.lower() == "active":
+                reasons.add(n)
+    if not sms:
+        return None
+    return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "reasons": sorted(reasons),
+            "samples": len(sms)}
+
+
+def _bond_outputs(env, O):
+    return env.expect("hbond", O), env.expect("vbond", O)
+
+
+def run_ours(args, rank, world, dist):
+    import numpy as np
+    import torch
+
+    from paper_1311_6696_gb300 import peps, synth
+
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    st = torch.cuda.current_stream()
+    A = synth.peps_gauss(WORKLOAD["Ly"], WORKLOAD["Lx"], WORKLOAD["d"], WORKLOAD["D"], WORKLOAD["seed"] + rank)
+    At = torch.from_numpy(A).to(dev)
+    Ah = torch.from_numpy(A).pin_memory()
+    SD = np.array([[0.25, 0, 0, 0], [0, -0.25, 0.5, 0], [0, 0.5, -0.25, 0], [0, 0, 0, 0.25]])
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    kw = dict(chi=args.chi, mode=args.mode, sweeps=2, precision=args.precision, stream=st)
+
+    def step(inp):
+        env = peps.env_full(inp, **kw)
+        h, v = _bond_outputs(env, SD)
+        env.free()
+        return h, v
+
+    for _ in range(args.warmup):
+        step(At)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region (per-step events, L2 flushed between steps)
+    dom = args.dominant
+    peps.profile_reset()
+    peps.profile_enable(1 << peps.class_index(dom))
+    clocks = _clock_sampler() if rank == 0 else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times = []
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        step(At)
+        e1.record(st)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = _clock_summary(clocks, local) if rank == 0 else None
+    prof = peps.profile_read()
+    peps.profile_enable(0)
+    launches = sum(v["launches"] for v in prof.values())
+
+    # ---- end-to-end through the C ABI with pinned host buffers
+    etimes = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(Ah)          # host pointer: the library copies A in; expect() copies results out
+        etimes.append((time.perf_counter() - t0) * 1e3)
+
+    total_ms = sum(times)
+    ms_step = total_ms / len(times)
+    e_ms = sum(etimes) / len(etimes)
+    if dist:
+        t = torch.tensor([ms_step, e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step, e_ms = float(t[0]), float(t[1])
+    envs = WORKLOAD["Ly"] * WORKLOAD["Lx"]
+    value = world * envs / (ms_step * 1e-3)
+    e2e = world * envs / (e_ms * 1e-3)
+    if rank != 0:
+        return None
+
+    pk = _peaks()
+    d = prof[dom]
+    achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
+    if dom == "gemm_tc":
+        peak = pk.get("bf16_tflops_sustained", 1720.0) if args.precision == "bf16" else \
+            pk.get("bf16_tflops_sustained", 1720.0) / 2.0
+        bound = "tensor"
+        peak_note = "of measured (bf16 sustained" + ("" if args.precision == "bf16" else " x 1/2 nominal tf32 ratio") + ")"
+    else:
+        peak = FP64_PEAK_TFLOPS
+        bound = "alu"
+        peak_note = "FP64 ALU peak derived from 152 SMs x 2 DFMA/clk x 2.07 GHz"
+    h2d = int(A.nbytes)
+    d2h = 8 * (WORKLOAD["Ly"] * (WORKLOAD["Lx"] - 1) + (WORKLOAD["Ly"] - 1) * WORKLOAD["Lx"])
+    res = {
+        "metric": "PEPS site environments/sec (full boundary-MPS envs + <S.S> on all bonds)",
+        "value": round(value, 3),
+        "unit": "envs/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"fp64": "f64", "tf32": "tf32", "bf16": "bf16"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": "10x10 OBC PEPS d=2 D=4, entries 0.5+0.1N(0,1), unit-norm tensors",
+                   "chi": args.chi, "mode": args.mode, "sweeps": 2, "precision": args.precision,
+                   "envs_per_step": envs, "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": round(e2e, 3), "unit": "envs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": bound, "kernel": dom, "achieved": round(achieved, 4), "peak": round(peak, 4),
+                     "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "launches": d["launches"], "avg_launch_us": round(1e3 * d["ms"] / max(1, d["launches"]), 3),
+                     "peak_source": peak_note},
+        "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items() if v["launches"]},
+        "wall_s_timed": round(t_wall, 3),
+    }
+    if clk:
+        res["clocks"] = clk
+    if not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_sample(args, budget_s=args.cpu_budget)
+    return res
+
+
+def cpu_sample(args, budget_s=20.0):
+    """The FP64 oracle as it stands, on a bounded sample of the same workload.
+
+    Sample: top-down absorb+compress steps of interior rows until the budget is
+    spent, plus one row pass (row environments and all density matrices of that
+    row, with the boundary above it standing in for the one below, which has the
+    same shapes).  envs/s = Ly*Lx / (4 (L-1) t_absorb + 2 L t_row), i.e. the
+    full environment set's operation count: four directional sweeps of L-1 rows
+    and L row passes plus L column passes.
+    """
+    import numpy as np
+
+    from oracle import peps_oracle as O
+    from paper_1311_6696_gb300 import synth
+
+    A = synth.peps_gauss(WORKLOAD["Ly"], WORKLOAD["Lx"], WORKLOAD["d"], WORKLOAD["D"], WORKLOAD["seed"])
+    lat = O.lattice_from_dense(A)
+    L = WORKLOAD["Ly"]
+    T = O.closure_mps(lat.top)
+    ts = []
+    y = 0
+    t_start = time.perf_counter()
+    while y < L - 1:
+        t0 = time.perf_counter()
+        T, _ = O.absorb_compress(T, lat, y, args.chi, args.mode, 2, 0, 0)
+        dt = time.perf_counter() - t0
+        if y >= 1:
+            ts.append(dt)
+        y += 1
+        if time.perf_counter() - t_start > budget_s and len(ts) >= 1:
+            break
+    t0 = time.perf_counter()
+    O._row_rhos(lat, T, T, y)
+    t_row = time.perf_counter() - t0
+    t_abs = float(np.median(ts))
+    t_set = 4 * (L - 1) * t_abs + 2 * L * t_row
+    cores = _blas_threads()
+    return {"value": round(L * L / t_set, 5), "unit": "envs/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(ts)} interior absorb+compress steps (median {t_abs:.2f} s) and one row pass "
+                      f"({t_row:.2f} s) of the same 10x10 D=4 chi={args.chi} {args.mode} workload, "
+                      f"extrapolated to the full environment set (4x{L-1} absorbs + {2*L} row passes)"}
+
+
+def _blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def run_reference(args):
+    steps = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        cb = cpu_sample(args, budget_s=args.ref_budget)
+        if i >= args.warmup:
+            steps.append((time.perf_counter() - t0, cb["value"]))
+    v = statistics.mean(s[1] for s in steps)
+    return {
+        "impl": "reference",
+        "metric": "PEPS site environments/sec (full boundary-MPS envs + <S.S> on all bonds)",
+        "value": round(v, 5), "unit": "envs/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * statistics.mean(s[0] for s in steps), 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "10x10 OBC PEPS d=2 D=4, entries 0.5+0.1N(0,1), unit-norm tensors",
+                   "chi": args.chi, "mode": args.mode, "sweeps": 2, "precision": "fp64"},
+        "cpu_baseline": {"value": round(v, 5), "unit": "envs/s", "cores": cb["cores"], "kind": "oracle",
+                         "sample": cb["sample"]},
+        "e2e": {"value": round(v, 5), "unit": "envs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--chi", type=int, default=64)
+    ap.add_argument("--mode", default="var", choices=["var", "svd"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "bf16"])
+    ap.add_argument("--dominant", default=None, help="kernel class timed for the roofline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--ref-budget", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.dominant is None:
+        args.dominant = "gemm_f64" if args.precision == "fp64" else "gemm_tc"
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    res = run_ours(args, rank, world, dist)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
