@@ -159,6 +159,35 @@ int peps_env_rho(const peps_env* env, int kind, double* out, void* cuda_stream);
 int peps_norm(const peps_lattice* lat, const peps_opts* opts,
               double* ln_norm, int* sign, void* cuda_stream);
 
+/*
+ * peps_cu0_noalloc -- CU_0 separable boundaries without any device allocation.
+ *   The paper has no counterpart: this is a service of the library.  It
+ *   computes the same top-down separable (D'=1) boundaries that
+ *   peps_env_cluster uses outside its windows, for callers that cannot call
+ *   cudaMalloc -- e.g. a serving process whose own allocator already holds
+ *   the device memory it may use, code in a latency-critical loop where
+ *   cudaMalloc / cudaFree would synchronise the device, or a host framework
+ *   that forbids device allocation after start-up.
+ *   A:      device pointer, dense double [Ly][Lx][d][D][D][D][D] (layout and
+ *           OBC rule as above; not validated here).
+ *   sigma:  device pointer receiving double [Ly][Lx][D][D]: sigma[r][x] is
+ *           the positive matrix on the (ket, bra) up legs of site (r, x), in
+ *           the top-left du x du block (du = 1 on row 0, else D), zeros elsewhere;
+ *           row 0 holds the trivial 1 x 1 closure.  Other directions: pass the
+ *           lattice flipped or transposed.
+ *   Limits: Ly <= 4096, Lx <= 64, d <= 4, D <= 8; larger sizes fail with
+ *   PEPS_EINVAL.  Scratch is a file-scope device array of 65,608 doubles
+ *   (about 513 KiB) that every GPU loading the library holds until exit.
+ *   The first call on a device looks up that array's device address
+ *   (cudaGetSymbolAddress); make the first call before any stream capture.
+ *   Every call shares the array: two calls whose work overlaps on the GPU
+ *   (different streams, or different host threads) race.  The call clears
+ *   its status words itself.  Allocates nothing; synchronises the stream.
+ *   Fails with PEPS_ECONVERGE if a cut needs more than 200 half-sweeps.
+ */
+int peps_cu0_noalloc(const double* A, int Ly, int Lx, int d, int D, double* sigma,
+                     void* cuda_stream);
+
 /* peps_env_ln_norm -- the norm recorded in a full env (PEPS_EINVAL for cluster envs). */
 int peps_env_ln_norm(const peps_env* env, double* ln_norm, int* sign, void* cuda_stream);
 

@@ -85,6 +85,8 @@ int guard(F&& f) {
 }  // namespace
 
 namespace peps {
+int peps_set_error(int code, const std::string& msg) { return fail(code, msg); }
+
 void prof_launch(KClass c, cudaStream_t st, double flops, double bytes) {
   Prof& p = prof();
   std::lock_guard<std::mutex> g(p.mu);

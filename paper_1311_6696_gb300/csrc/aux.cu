@@ -2,6 +2,7 @@
 // counter-based var initialisation, local observables and CU_0.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "aux.cuh"
@@ -567,3 +568,190 @@ void cu0_launch(Ctx& cx, const Cu0Lattice* lats, int nlat) {
 }
 
 }  // namespace peps
+
+// ============================================================================
+// Allocation-free entry point: CU_0 boundaries with file-scope scratch.
+//
+// Some callers cannot call cudaMalloc: a serving process whose allocator has
+// already reserved the device memory it may use, code in a latency-critical
+// loop where cudaMalloc / cudaFree would synchronise the device, or a host
+// framework that forbids device allocation after start-up.  peps_cu0_noalloc
+// serves them: it reads the caller's dense lattice, writes the caller's
+// output buffer, and keeps its scratch in the static array below.
+// ============================================================================
+namespace peps {
+namespace {
+
+// Scratch: 8 words of status, then the repacked site tensor, two
+// intermediates (3 d D^4), the previous / current separable row and the left /
+// right environments (4 Lx D^2) and the local vector (D^2).
+constexpr int NOALLOC_MAX_D = 8;
+constexpr int NOALLOC_MAX_d = 4;
+constexpr int NOALLOC_MAX_LX = 64;
+constexpr int NOALLOC_MAX_LY = 4096;
+constexpr size_t NOALLOC_WORDS =
+    8 + 3 * size_t(NOALLOC_MAX_d) * NOALLOC_MAX_D * NOALLOC_MAX_D * NOALLOC_MAX_D * NOALLOC_MAX_D +
+    4 * size_t(NOALLOC_MAX_LX) * NOALLOC_MAX_D * NOALLOC_MAX_D + size_t(NOALLOC_MAX_D) * NOALLOC_MAX_D;
+
+static __device__ __align__(256) double g_cu0_scratch[NOALLOC_WORDS];
+
+struct DenseCu0 {
+  const double* A;   // dense [Ly][Lx][d][D][D][D][D]
+  double* out;       // [Ly][Lx][D][D], zero-padded
+  double* scr;       // device address of g_cu0_scratch
+  int Ly, Lx, d, D, max_half;
+  double tol;
+};
+
+__device__ SiteDims dense_dims(const DenseCu0& a, int y, int x) {
+  return SiteDims{y == 0 ? 1 : a.D, x == 0 ? 1 : a.D, y == a.Ly - 1 ? 1 : a.D, x == a.Lx - 1 ? 1 : a.D};
+}
+
+// Copy site (y,x) from the dense layout into `dst` with its effective dims.
+__device__ SiteDims load_dense_site(const DenseCu0& a, int y, int x, double* dst) {
+  const SiteDims sd = dense_dims(a, y, x);
+  const int D = a.D, n = a.d * sd.du * sd.dl * sd.dn * sd.dr;
+  const long long base = ((long long)y * a.Lx + x) * a.d * D * D * D * D;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    int t = e;
+    const int r = t % sd.dr; t /= sd.dr;
+    const int nn = t % sd.dn; t /= sd.dn;
+    const int l = t % sd.dl; t /= sd.dl;
+    const int u = t % sd.du;
+    const int s = t / sd.du;
+    dst[e] = a.A[base + ((((long long)s * D + u) * D + l) * D + nn) * D + r];
+  }
+  __syncthreads();
+  return sd;
+}
+
+__global__ void __launch_bounds__(256) k_cu0_dense(const DenseCu0 a) {
+  __shared__ double red[32];
+  const int Ly = a.Ly, Lx = a.Lx, d = a.d, D = a.D, DM2 = D * D;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long big = (long long)d * DM2 * DM2;
+  int* flag = reinterpret_cast<int*>(a.scr);
+  double* As = a.scr + 8;
+  double* Y = As + big;
+  double* Z = Y + big;
+  double* sigP = Z + big;
+  double* sigN = sigP + (long long)Lx * DM2;
+  double* Lm = sigN + (long long)Lx * DM2;
+  double* Rm = Lm + (long long)Lx * DM2;
+  double* b = Rm + (long long)Lx * DM2;
+  auto P = [&](int x) { return sigP + (long long)x * DM2; };
+  auto N = [&](int x) { return sigN + (long long)x * DM2; };
+  auto emit = [&](int r, const double* src, int x, int n) {   // padded D x D output
+    double* o = a.out + ((long long)r * Lx + x) * DM2;
+    for (int e = tid; e < DM2; e += nt) {
+      const int i = e / D, j = e % D;
+      o[e] = (i < n && j < n) ? src[i * n + j] : 0.0;
+    }
+  };
+  for (int x = 0; x < Lx; ++x) {
+    if (tid == 0) P(x)[0] = 1.0;   // top closure of the OBC lattice: 1 x 1 identity
+    __syncthreads();
+    emit(0, P(x), x, 1);
+  }
+  __syncthreads();
+  for (int r = 0; r + 1 < Ly; ++r) {
+    for (int x = 0; x < Lx; ++x) {
+      const int dn = dense_dims(a, r, x).dn;
+      const double v = 1.0 / sqrt(double(dn));
+      for (int e = tid; e < dn * dn; e += nt) N(x)[e] = (e / dn == e % dn) ? v : 0.0;
+    }
+    if (tid == 0) {
+      Rm[(long long)(Lx - 1) * DM2] = 1.0;
+      Lm[0] = 1.0;
+    }
+    __syncthreads();
+    for (int x = Lx - 1; x >= 1; --x) {
+      const SiteDims sd = load_dense_site(a, r, x, As);
+      cu0_renv(Rm + (long long)x * DM2, P(x), As, sd, d, N(x), Y, Z, Rm + (long long)(x - 1) * DM2);
+      cta_fro_normalize(Rm + (long long)(x - 1) * DM2, sd.dl * sd.dl, red);
+    }
+    bool conv = false;
+    for (int h = 0; h < a.max_half && !conv; ++h) {
+      double change = 0.0;
+      for (int step = 0; step < Lx; ++step) {
+        const int x = (h % 2 == 0) ? step : Lx - 1 - step;
+        const SiteDims sd = load_dense_site(a, r, x, As);
+        cu0_local(Lm + (long long)x * DM2, P(x), As, sd, d, Rm + (long long)x * DM2, Y, Z, b);
+        cta_fro_normalize(b, sd.dn * sd.dn, red);
+        double part = 0.0;
+        for (int e = tid; e < sd.dn * sd.dn; e += nt) {
+          const double df = b[e] - N(x)[e];
+          part += df * df;
+        }
+        change = fmax(change, sqrt(block_sum(part, red)));
+        for (int e = tid; e < sd.dn * sd.dn; e += nt) N(x)[e] = b[e];
+        __syncthreads();
+        if (h % 2 == 0 && x < Lx - 1) {
+          cu0_lenv(Lm + (long long)x * DM2, P(x), As, sd, d, N(x), Y, Z, Lm + (long long)(x + 1) * DM2);
+          cta_fro_normalize(Lm + (long long)(x + 1) * DM2, sd.dr * sd.dr, red);
+        } else if (h % 2 == 1 && x > 0) {
+          cu0_renv(Rm + (long long)x * DM2, P(x), As, sd, d, N(x), Y, Z, Rm + (long long)(x - 1) * DM2);
+          cta_fro_normalize(Rm + (long long)(x - 1) * DM2, sd.dl * sd.dl, red);
+        }
+      }
+      conv = change < a.tol;
+    }
+    if (!conv && tid == 0) atomicOr(flag, FLAG_CU0_NOCONV);
+    for (int x = 0; x < Lx; ++x) {
+      const int dn = dense_dims(a, r, x).dn;
+      emit(r + 1, N(x), x, dn);
+      for (int e = tid; e < dn * dn; e += nt) P(x)[e] = N(x)[e];
+    }
+    __syncthreads();
+  }
+}
+
+// Device address of the scratch array, looked up once per device.
+double* noalloc_scratch(int dev) {
+  static std::mutex mu;
+  static std::vector<double*> addr;
+  std::lock_guard<std::mutex> g(mu);
+  if (int(addr.size()) <= dev) addr.resize(dev + 1, nullptr);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    PEPS_CUDA(cudaGetSymbolAddress(&p, g_cu0_scratch));
+    addr[dev] = static_cast<double*>(p);
+  }
+  return addr[dev];
+}
+
+}  // namespace
+}  // namespace peps
+
+extern "C" int peps_cu0_noalloc(const double* A, int Ly, int Lx, int d, int D, double* sigma,
+                                void* cuda_stream) {
+  using namespace peps;
+  try {
+    PEPS_REQUIRE(A != nullptr && sigma != nullptr, "NULL argument");
+    PEPS_REQUIRE(Ly >= 1 && Lx >= 1 && d >= 1 && D >= 1, "sizes must be >= 1");
+    PEPS_REQUIRE(Ly <= NOALLOC_MAX_LY && Lx <= NOALLOC_MAX_LX && d <= NOALLOC_MAX_d && D <= NOALLOC_MAX_D,
+                 "peps_cu0_noalloc: sizes beyond the static scratch (Ly <= 4096, Lx <= 64, d <= 4, D <= 8)");
+    const size_t need = 8 + 3 * size_t(d) * D * D * D * D + 4 * size_t(Lx) * D * D + size_t(D) * D;
+    PEPS_REQUIRE(need <= NOALLOC_WORDS, "peps_cu0_noalloc: scratch too small for these sizes");
+    int dev = 0;
+    PEPS_CUDA(cudaGetDevice(&dev));
+    double* scr = noalloc_scratch(dev);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    PEPS_CUDA(cudaMemsetAsync(scr, 0, 8 * sizeof(double), st));   // status words start at zero
+    DenseCu0 a{A, sigma, scr, Ly, Lx, d, D, 200, 1e-13};
+    {
+      Launch L(K_CU0, st);
+      k_cu0_dense<<<1, 256, 0, st>>>(a);
+      PEPS_CHECK_LAUNCH();
+    }
+    int flag = 0;
+    PEPS_CUDA(cudaMemcpyAsync(&flag, scr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PEPS_CUDA(cudaStreamSynchronize(st));
+    if (flag & FLAG_CU0_NOCONV) throw Error(PEPS_ECONVERGE, "CU_0 separable boundary did not converge within 200 half-sweeps");
+    return PEPS_OK;
+  } catch (const Error& e) {
+    return peps_set_error(e.code, e.what());
+  } catch (const std::exception& e) {
+    return peps_set_error(PEPS_ECUDA, e.what());
+  }
+}

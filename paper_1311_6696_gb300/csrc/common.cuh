@@ -122,6 +122,9 @@ class Arena {
   size_t total_ = 0;
 };
 
+// Records `msg` as this thread's last error (peps_last_error) and returns `code`.
+int peps_set_error(int code, const std::string& msg);
+
 inline unsigned cdiv(long long a, long long b) { return unsigned((a + b - 1) / b); }
 
 }  // namespace peps

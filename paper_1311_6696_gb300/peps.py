@@ -26,6 +26,7 @@ EXPORTS = [
     "peps_env_full", "peps_env_cluster", "peps_expect_local", "peps_env_rho", "peps_norm",
     "peps_env_ln_norm", "peps_env_free", "peps_last_error", "peps_profile_enable",
     "peps_profile_reset", "peps_profile_count", "peps_profile_name", "peps_profile_read",
+    "peps_cu0_noalloc",
 ]
 
 
@@ -67,6 +68,7 @@ def _load():
     lib.peps_profile_name.restype = C.c_char_p
     lib.peps_profile_read.argtypes = [C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.peps_cu0_noalloc.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P]
     return lib
 
 
@@ -199,6 +201,16 @@ def norm(A, chi: int, mode="svd", sweeps: int = 2, precision="fp64", seed: int =
     sg = C.c_int()
     _check(lib.peps_norm(C.byref(inp.lat), C.byref(o), C.byref(ln), C.byref(sg), _stream_ptr(stream)))
     return ln.value, sg.value
+
+
+def cu0_noalloc(A_dev, sigma_dev, stream=None):
+    """Top-down CU_0 boundaries into a caller-owned device tensor, with no
+    device allocation (see peps_cu0_noalloc).  A_dev: contiguous float64 CUDA
+    tensor (Ly,Lx,d,D,D,D,D); sigma_dev: float64 CUDA tensor (Ly,Lx,D,D)."""
+    Ly, Lx, d, D = (int(v) for v in A_dev.shape[:4])
+    assert A_dev.is_contiguous() and sigma_dev.is_contiguous()
+    assert tuple(sigma_dev.shape) == (Ly, Lx, D, D)
+    _check(lib.peps_cu0_noalloc(A_dev.data_ptr(), Ly, Lx, d, D, sigma_dev.data_ptr(), _stream_ptr(stream)))
 
 
 # ---------------------------------------------------------------- instrumentation
