@@ -58,10 +58,15 @@ extern "C" {
 #define PEPS_SVD 0          /* QR sweep to canonical form, then SVD truncation to chi */
 #define PEPS_VAR 1          /* one-site ALS sweeps, local equation N A = b with N = 1 */
 
-/* arithmetic of the absorb contractions; QR, SVD, gauge and rescaling are FP64 */
-#define PEPS_PREC_FP64 0
-#define PEPS_PREC_TF32 1
-#define PEPS_PREC_BF16 2
+/* arithmetic of the absorb contractions (tensor cores, FP32 accumulation);
+ * QR, SVD, gauge fixing and rescaling are FP64 in every mode.  The X3 modes
+ * split each operand into a rounded high part and a rounded residual and sum
+ * the three leading products (hi*hi + hi*lo + lo*hi). */
+#define PEPS_PREC_FP64   0
+#define PEPS_PREC_TF32   1
+#define PEPS_PREC_BF16   2
+#define PEPS_PREC_TF32X3 3
+#define PEPS_PREC_BF16X3 4
 
 /* local quantity selectors */
 #define PEPS_SITE  0        /* rho of site (y,x):            d x d,     Ly*Lx values       */

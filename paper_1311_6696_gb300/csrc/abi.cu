@@ -2,13 +2,18 @@
 // repacking into the four sweep orientations, the full / cluster / norm
 // drivers, and kernel-class instrumentation.  No exception crosses this file.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <memory>
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <exception>
+#include <thread>
 #include <vector>
 
 #include "aux.cuh"
@@ -31,8 +36,7 @@ struct Prof {
   double flops[K_NCLASS] = {}, bytes[K_NCLASS] = {}, ms[K_NCLASS] = {};
   std::vector<cudaEvent_t> pool;
   std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> pending;
-  std::vector<cudaEvent_t> open;   // start events of launches in flight (per class)
-  cudaEvent_t open_ev[K_NCLASS] = {};
+
   cudaEvent_t get() {
     if (!pool.empty()) {
       cudaEvent_t e = pool.back();
@@ -60,6 +64,9 @@ Prof& prof() {
   static Prof* p = new Prof();
   return *p;
 }
+
+// Start event of the launch in flight, per class and per host thread.
+thread_local cudaEvent_t t_open_ev[K_NCLASS] = {};
 
 thread_local std::string g_err;
 
@@ -96,17 +103,17 @@ void prof_launch(KClass c, cudaStream_t st, double flops, double bytes) {
   if (p.mask & (1u << c)) {
     cudaEvent_t e = p.get();
     cudaEventRecord(e, st);
-    p.open_ev[c] = e;
+    t_open_ev[c] = e;
   }
 }
 void prof_done(KClass c, cudaStream_t st) {
   Prof& p = prof();
   std::lock_guard<std::mutex> g(p.mu);
-  if ((p.mask & (1u << c)) && p.open_ev[c]) {
+  if ((p.mask & (1u << c)) && t_open_ev[c]) {
     cudaEvent_t e = p.get();
     cudaEventRecord(e, st);
-    p.pending.emplace_back(int(c), p.open_ev[c], e);
-    p.open_ev[c] = nullptr;
+    p.pending.emplace_back(int(c), t_open_ev[c], e);
+    t_open_ev[c] = nullptr;
   }
 }
 bool prof_timing() { return prof().mask != 0; }
@@ -141,6 +148,7 @@ struct Call {
     if (h & FLAG_SVD_NOCONV) throw Error(PEPS_ECONVERGE, "Jacobi SVD did not converge within its sweep cap");
     if (h & FLAG_CU0_NOCONV) throw Error(PEPS_ECONVERGE, "CU_0 separable boundary did not converge within 200 half-sweeps");
     if (h & FLAG_BAD_VALUE) throw Error(PEPS_EINVAL, "zero or non-finite norm encountered (degenerate state)");
+    if (h & FLAG_TIMEOUT) throw Error(PEPS_ETIMEOUT, "a device-side bounded wait ran out");
   }
 };
 
@@ -166,8 +174,10 @@ Opts check_opts(const peps_opts* o, bool cluster) {
   PEPS_REQUIRE(o != nullptr, "opts is NULL");
   PEPS_REQUIRE(o->chi >= 1 && o->chi <= 4096, "chi must be in [1, 4096]");
   PEPS_REQUIRE(o->mode == PEPS_SVD || o->mode == PEPS_VAR, "mode must be PEPS_SVD or PEPS_VAR");
-  PEPS_REQUIRE(o->precision == PEPS_PREC_FP64 || o->precision == PEPS_PREC_TF32 || o->precision == PEPS_PREC_BF16,
-               "precision must be PEPS_PREC_FP64, _TF32 or _BF16");
+  PEPS_REQUIRE(o->precision >= PEPS_PREC_FP64 && o->precision <= PEPS_PREC_BF16X3,
+               "precision must be one of PEPS_PREC_FP64, _TF32, _BF16, _TF32X3, _BF16X3");
+  if (o->precision != PEPS_PREC_FP64)
+    PEPS_REQUIRE(tc_available(), "tensor-core precisions need an sm_103 (GB300) device");
   PEPS_REQUIRE(o->closure == PEPS_CLOSURE_PLAIN && o->closure_weights == nullptr,
                "closure must be PEPS_CLOSURE_PLAIN with NULL weights");
   if (cluster) PEPS_REQUIRE(o->n >= 1, "cluster size n must be >= 1");
@@ -302,32 +312,153 @@ std::unique_ptr<peps_env> new_env(const peps_lattice* lat, int kind, cudaStream_
   return env;
 }
 
+// ---------------------------------------------------------------------------
+// Lanes: independent work (the four sweeps, row passes, cluster windows) runs
+// on a small pool of non-blocking streams, each with its own workspace and
+// engine, forked from and joined back to the caller's stream with events.
+// ---------------------------------------------------------------------------
+// Number of lanes: PEPS_LANES (1..8) if set, else 4.
+int lane_count() {
+  static int n = [] {
+    const char* e = std::getenv("PEPS_LANES");
+    const int v = e ? std::atoi(e) : 4;
+    return v < 1 ? 1 : (v > 8 ? 8 : v);
+  }();
+  return n;
+}
+
+std::vector<cudaStream_t>& lane_streams() {
+  static std::mutex mu;
+  static std::vector<std::vector<cudaStream_t>> pool;
+  std::lock_guard<std::mutex> g(mu);
+  int dev = 0;
+  PEPS_CUDA(cudaGetDevice(&dev));
+  if (int(pool.size()) <= dev) pool.resize(dev + 1);
+  auto& v = pool[dev];
+  while (int(v.size()) < lane_count()) {
+    cudaStream_t s;
+    PEPS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    v.push_back(s);
+  }
+  return v;
+}
+
+void stream_after(cudaStream_t waiter, cudaStream_t producer) {
+  cudaEvent_t e;
+  PEPS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  PEPS_CUDA(cudaEventRecord(e, producer));
+  PEPS_CUDA(cudaStreamWaitEvent(waiter, e, 0));
+  PEPS_CUDA(cudaEventDestroy(e));
+}
+
+struct Lane {
+  cudaStream_t st;
+  std::unique_ptr<Arena> ws;
+  std::unique_ptr<Ctx> cx;
+  std::unique_ptr<Engine> eng;
+};
+
+struct Lanes {
+  cudaStream_t main;
+  std::vector<Lane> l;
+  Lanes(Call& c, const Opts& opt, int d, int D, int Lmax) : main(c.st) {
+    auto& pool = lane_streams();
+    l.resize(lane_count());
+    for (int i = 0; i < int(l.size()); ++i) {
+      Lane& a = l[i];
+      a.st = pool[i];
+      stream_after(a.st, main);
+      a.ws = std::make_unique<Arena>(a.st);
+      a.cx = std::make_unique<Ctx>(a.st, a.ws.get());
+      a.cx->flag = c.cx.flag;
+      a.cx->tmp = a.ws->dalloc(8);
+      a.eng = std::make_unique<Engine>(*a.cx, opt, d, D, Lmax);
+    }
+  }
+  // Fork: every lane waits for the caller's stream.
+  void fork() {
+    for (auto& a : l) stream_after(a.st, main);
+  }
+  // Join: the caller's stream waits for every lane.
+  void join() {
+    for (auto& a : l) stream_after(main, a.st);
+  }
+  ~Lanes() {
+    // Lane workspaces are freed on their own streams after their work; the
+    // caller's stream already waits for them (join), and the memory returns
+    // to the stream-ordered pool.
+    for (auto& a : l) {
+      a.eng.reset();
+      a.cx.reset();
+      a.ws.reset();
+    }
+  }
+};
+
+// Runs fn(lane, job) for job = 0..njobs-1, lane i taking jobs i, i+n, ...; one
+// host thread per lane, so every lane's stream is fed while the others block
+// on a full launch queue.  The first exception of any lane is rethrown.
+template <class F>
+void run_lanes(Lanes& lanes, int njobs, F fn) {
+  const int nl = int(lanes.l.size());
+  if (nl == 1) {
+    for (int j = 0; j < njobs; ++j) fn(lanes.l[0], j);
+    return;
+  }
+  int dev = 0;
+  PEPS_CUDA(cudaGetDevice(&dev));
+  std::vector<std::exception_ptr> errs(nl);
+  std::vector<std::thread> th;
+  for (int i = 0; i < nl; ++i)
+    th.emplace_back([&, i] {
+      try {
+        PEPS_CUDA(cudaSetDevice(dev));
+        for (int j = i; j < njobs; j += nl) fn(lanes.l[i], j);
+      } catch (...) {
+        errs[i] = std::current_exception();
+      }
+    });
+  for (auto& t : th) t.join();
+  for (auto& e : errs)
+    if (e) std::rethrow_exception(e);
+}
+
 void full_env(Call& c, const peps_lattice* lat, const Opts& opt, peps_env* env, Oriented& ori) {
   Ctx& cx = c.cx;
   Arena& keep = *env->arena;
   const int Ly = lat->Ly, Lx = lat->Lx, d = lat->d;
-  Engine eng(cx, opt, d, lat->D, std::max(Ly, Lx));
   double* lnacc = cx.ws->dalloc(4);
   fill(cx, lnacc, 4, 0.0);
-  auto bt = eng.sweep(ori.o[0], 0, Ly - 1, lnacc + 0, keep);
-  auto bb = eng.sweep(ori.o[1], 1, Ly - 1, lnacc + 1, keep);
-  auto bl = eng.sweep(ori.o[2], 2, Lx - 1, lnacc + 2, keep);
-  auto br = eng.sweep(ori.o[3], 3, Lx - 1, lnacc + 3, keep);
+  Lanes lanes(c, opt, d, lat->D, std::max(Ly, Lx));
+  // Four independent directional sweeps, one per lane.
+  std::vector<Mps> b[4];
+  run_lanes(lanes, 4, [&](Lane& L, int o) {
+    b[o] = L.eng->sweep(ori.o[o], o, (o < 2 ? Ly : Lx) - 1, lnacc + o, keep);
+  });
+  lanes.join();
+  lanes.fork();
   EnvData& e = env->data;
   const long long d2 = (long long)d * d, d4 = d2 * d2;
-  for (int y = 0; y < Ly; ++y) {
-    Engine::Targets ts, tb;
-    for (int x = 0; x < Lx; ++x) ts.push_back({x, e.rho_site + ((long long)y * Lx + x) * d2});
-    for (int x = 0; x + 1 < Lx; ++x) tb.push_back({x, e.rho_h + ((long long)y * (Lx - 1) + x) * d4});
-    eng.row_rhos(ori.o[0], bt[y], bb[Ly - 1 - y], y, ts, tb);
-  }
-  // Row x of the transposed lattice holds the vertical bonds (y,x)-(y+1,x) at its column y.
-  for (int x = 0; x < Lx && Ly > 1; ++x) {
-    Engine::Targets tb;
-    for (int y = 0; y + 1 < Ly; ++y) tb.push_back({y, e.rho_v + ((long long)y * Lx + x) * d4});
-    eng.row_rhos(ori.o[2], bl[x], br[Lx - 1 - x], x, {}, tb);
-  }
-  eng.norm_from_top(ori.o[0], bt[Ly - 1], lnacc, e.lnnorm);
+  const int ncol = Ly > 1 ? Lx : 0;
+  // Row passes, then column passes (vertical bonds), then the norm.
+  run_lanes(lanes, Ly + ncol + 1, [&](Lane& L, int job) {
+    if (job < Ly) {
+      const int y = job;
+      Engine::Targets ts, tb;
+      for (int x = 0; x < Lx; ++x) ts.push_back({x, e.rho_site + ((long long)y * Lx + x) * d2});
+      for (int x = 0; x + 1 < Lx; ++x) tb.push_back({x, e.rho_h + ((long long)y * (Lx - 1) + x) * d4});
+      L.eng->row_rhos(ori.o[0], b[0][y], b[1][Ly - 1 - y], y, ts, tb);
+    } else if (job < Ly + ncol) {
+      // row x of the transposed lattice holds the vertical bonds (y,x)-(y+1,x) at its column y
+      const int x = job - Ly;
+      Engine::Targets tb;
+      for (int y = 0; y + 1 < Ly; ++y) tb.push_back({y, e.rho_v + ((long long)y * Lx + x) * d4});
+      L.eng->row_rhos(ori.o[2], b[2][x], b[3][Lx - 1 - x], x, {}, tb);
+    } else {
+      L.eng->norm_from_top(ori.o[0], b[0][Ly - 1], lnacc, e.lnnorm);
+    }
+  });
+  lanes.join();
   e.has_norm = true;
 }
 
@@ -396,12 +527,17 @@ void cluster_env(Call& c, const peps_lattice* lat, const Opts& opt, int n, peps_
     const OLat& L = ori.o[o];
     return Mat{sig[o] + ((long long)r * L.Lx + x) * DM2, dim};
   };
-  Engine eng(cx, opt, d, D, std::max(Ly, Lx));
-  double* junk = cx.ws->dalloc(4);
+  Lanes lanes(c, opt, d, D, std::max(Ly, Lx));
+  const int nl = int(lanes.l.size());
+  double* junk = cx.ws->dalloc(4 * nl);
   EnvData& e = env->data;
   const long long d2 = (long long)d * d, d4 = d2 * d2;
-  for (int y = 0; y < Ly; ++y)
-    for (int x = 0; x < Lx; ++x) {
+  std::vector<std::vector<std::unique_ptr<Arena>>> keeps(nl);
+  run_lanes(lanes, Ly * Lx, [&](Lane& lane, int job) {
+      const int y = job / Lx, x = job % Lx;
+      const int li = int(&lane - lanes.l.data());
+      Engine& eng = *lane.eng;
+      double* lj = junk + 4 * li;
       const auto rr = window(Ly, y, n), cc = window(Lx, x, n);
       const int r0 = rr.first, r1 = rr.second, c0 = cc.first, c1 = cc.second;
       const int h = r1 - r0 + 1, w = c1 - c0 + 1, yw = y - r0, xw = x - c0;
@@ -438,18 +574,22 @@ void cluster_env(Call& c, const peps_lattice* lat, const Opts& opt, int n, peps_
         W3.left.push_back(W0.top[w - 1 - j]);
         W3.right.push_back(W0.bottom[w - 1 - j]);
       }
-      Arena keep(cx.st);
-      auto bt = eng.sweep(W0, 0, yw, junk, keep);
-      auto bb = eng.sweep(W1, 1, h - 1 - yw, junk, keep);
+      keeps[li].push_back(std::make_unique<Arena>(lane.st));
+      Arena& keep = *keeps[li].back();
+      auto bt = eng.sweep(W0, 0, yw, lj, keep);
+      auto bb = eng.sweep(W1, 1, h - 1 - yw, lj, keep);
       Engine::Targets ts{{xw, e.rho_site + ((long long)y * Lx + x) * d2}}, tb;
       if (x + 1 < Lx && xw + 1 < w) tb.push_back({xw, e.rho_h + ((long long)y * (Lx - 1) + x) * d4});
       eng.row_rhos(W0, bt[yw], bb[h - 1 - yw], yw, ts, tb);
       if (y + 1 < Ly && yw + 1 < h) {
-        auto bl = eng.sweep(W2, 2, xw, junk, keep);
-        auto br = eng.sweep(W3, 3, w - 1 - xw, junk, keep);
+        auto bl = eng.sweep(W2, 2, xw, lj, keep);
+        auto br = eng.sweep(W3, 3, w - 1 - xw, lj, keep);
         eng.row_rhos(W2, bl[xw], br[w - 1 - xw], xw, {}, {{yw, e.rho_v + ((long long)y * Lx + x) * d4}});
       }
-    }
+      if (keeps[li].size() > 2) keeps[li].erase(keeps[li].begin());   // stream-ordered free
+  });
+  keeps.clear();
+  lanes.join();
   e.has_norm = false;
 }
 
@@ -464,11 +604,19 @@ int run_env(const peps_lattice* lat, const peps_opts* opts, peps_env** out, void
     auto env = new_env(lat, cluster ? 1 : 0, c.st);
     Oriented ori;
     build_orientations(c.cx, lat, *env->arena, ori);
+    const auto t0 = std::chrono::steady_clock::now();
     if (cluster)
       cluster_env(c, lat, o, opts->n, env.get(), ori);
     else
       full_env(c, lat, o, env.get(), ori);
+    const auto t1 = std::chrono::steady_clock::now();
     c.finish();
+    if (std::getenv("PEPS_VERBOSE")) {
+      const auto t2 = std::chrono::steady_clock::now();
+      std::fprintf(stderr, "[peps] env: host enqueue %.1f ms, then device drain %.1f ms\n",
+                   std::chrono::duration<double, std::milli>(t1 - t0).count(),
+                   std::chrono::duration<double, std::milli>(t2 - t1).count());
+    }
     *out = env.release();
   });
 }

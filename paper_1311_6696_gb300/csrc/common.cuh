@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -75,6 +76,7 @@ class Arena {
   Arena& operator=(const Arena&) = delete;
 
   void* alloc(size_t bytes) {
+    std::lock_guard<std::mutex> g(mu_);   // shared by lane threads when it owns an env
     bytes = (bytes + 255) & ~size_t(255);
     if (bytes == 0) bytes = 256;
     if (bytes > left_) {
@@ -99,6 +101,7 @@ class Arena {
   double* dalloc(size_t n) { return static_cast<double*>(alloc(n * sizeof(double))); }
   float* falloc(size_t n) { return static_cast<float*>(alloc(n * sizeof(float))); }
   void release() {
+    std::lock_guard<std::mutex> g(mu_);
     for (void* p : chunks_) {
       if (async_)
         cudaFreeAsync(p, st_);
@@ -120,6 +123,7 @@ class Arena {
   char* cur_ = nullptr;
   size_t left_ = 0;
   size_t total_ = 0;
+  std::mutex mu_;
 };
 
 // Records `msg` as this thread's last error (peps_last_error) and returns `code`.

@@ -57,4 +57,12 @@ Dims ein_dims(const char* spec, const Dims& ad, const Dims& bd);
 void ein(Ctx& cx, const char* spec, const double* A, const Dims& ad, const double* B,
          const Dims& bd, double* C, double alpha = 1.0, double beta = 0.0);
 
+// C = alpha * contract(A, B) on the tensor cores (tcgen05): operands are
+// FP64 (x_f64 = 1) or FP32 tensors, repacked to TF32 / BF16; C is written as
+// FP64 or FP32 in any index order; with Clo (FP32 output only) C receives the
+// TF32-rounded value and Clo the rounded residual.  prec is PEPS_PREC_*.
+void ein_tc(Ctx& cx, const char* spec, const void* A, int a_f64, const Dims& ad, const void* B, int b_f64,
+            const Dims& bd, void* C, int c_f64, int prec, double alpha = 1.0, void* Clo = nullptr);
+int tc_available();
+
 }  // namespace peps

@@ -46,6 +46,17 @@ Engine::Engine(Ctx& c, const Opts& o, int d, int Dmax, int Lmax)
   }
   one_ = cx.ws->dalloc(1);
   fill(cx, one_, 1, 1.0);
+  tc_ = o.precision != PEPS_PREC_FP64;
+  x64_ = !tc_;
+}
+
+void Engine::con(const char* spec, const void* A, bool a64, const Dims& ad, const void* B, bool b64,
+                 const Dims& bd, void* C, bool c64) {
+  if (!tc_) {
+    ein(cx, spec, static_cast<const double*>(A), ad, static_cast<const double*>(B), bd, static_cast<double*>(C));
+    return;
+  }
+  ein_tc(cx, spec, A, a64 ? 1 : 0, ad, B, b64 ? 1 : 0, bd, C, c64 ? 1 : 0, opt.precision);
 }
 
 Mps Engine::closure_mps(const std::vector<Mat>& mats, Arena&) {
@@ -61,11 +72,11 @@ Dims Engine::chain_left(const double* L, const Dims& ld, const double* M, const 
                         const SiteT& A, double* X3) {
   const Dims ad = A.dims();
   const Dims x1 = ein_dims("clma,auvb->clmuvb", ld, md);
-  ein(cx, "clma,auvb->clmuvb", L, ld, M, md, X1_);
+  con("clma,auvb->clmuvb", L, true, ld, M, true, md, X1_, x64_);
   const Dims x2 = ein_dims("clmuvb,sulnr->cmvbsnr", x1, ad);
-  ein(cx, "clmuvb,sulnr->cmvbsnr", X1_, x1, A.p, ad, X2_);
+  con("clmuvb,sulnr->cmvbsnr", X1_, x64_, x1, A.p, true, ad, X2_, x64_);
   const Dims x3 = ein_dims("cmvbsnr,svmoq->cbnroq", x2, ad);
-  ein(cx, "cmvbsnr,svmoq->cbnroq", X2_, x2, A.p, ad, X3);
+  con("cmvbsnr,svmoq->cbnroq", X2_, x64_, x2, A.p, true, ad, X3, x64_);
   return x3;
 }
 
@@ -73,11 +84,11 @@ Dims Engine::chain_right(const double* R, const Dims& rd, const double* M, const
                          const SiteT& A, double* Y3) {
   const Dims ad = A.dims();
   const Dims y1 = ein_dims("auvb,brqc->auvrqc", md, rd);
-  ein(cx, "auvb,brqc->auvrqc", M, md, R, rd, X1_);
+  con("auvb,brqc->auvrqc", M, true, md, R, true, rd, X1_, x64_);
   const Dims y2 = ein_dims("auvrqc,sulnr->avqcsln", y1, ad);
-  ein(cx, "auvrqc,sulnr->avqcsln", X1_, y1, A.p, ad, X2_);
+  con("auvrqc,sulnr->avqcsln", X1_, x64_, y1, A.p, true, ad, X2_, x64_);
   const Dims y3 = ein_dims("avqcsln,svmoq->aclnmo", y2, ad);
-  ein(cx, "avqcsln,svmoq->aclnmo", X2_, y2, A.p, ad, Y3);
+  con("avqcsln,svmoq->aclnmo", X2_, x64_, y2, A.p, true, ad, Y3, x64_);
   return y3;
 }
 
@@ -88,10 +99,10 @@ Mps Engine::product_mps(const Mps& T, const OLat& lat, int y, Arena& step) {
     const SiteT& A = lat.at(y, x);
     const Dims ad = A.dims();
     const Dims t1 = ein_dims("auvb,sulnr->avbslnr", T.dims[x], ad);
-    ein(cx, "auvb,sulnr->avbslnr", T.p[x], T.dims[x], A.p, ad, X2_);
+    con("auvb,sulnr->avbslnr", T.p[x], true, T.dims[x], A.p, true, ad, X2_, x64_);
     const Dims t2 = ein_dims("avbslnr,svmoq->almnobrq", t1, ad);
     double* cur = step.dalloc(numel(t2));
-    ein(cx, "avbslnr,svmoq->almnobrq", X2_, t1, A.p, ad, cur);
+    con("avbslnr,svmoq->almnobrq", X2_, x64_, t1, A.p, true, ad, cur, true);
     Dims cd = t2;
     if (x == 0) {
       const Mat& c = lat.left[y];
@@ -198,21 +209,21 @@ Mps Engine::var_compress(const Mps& T, const OLat& lat, int y, const std::vector
   for (int x = Lx - 1; x >= 1; --x) {
     const Dims y3 = chain_right(Renv_[x], rd[x], T.p[x], T.dims[x], lat.at(y, x), X3_);
     rd[x - 1] = ein_dims("aelnmo,cnoe->almc", y3, N.dims[x]);
-    ein(cx, "aelnmo,cnoe->almc", X3_, y3, N.p[x], N.dims[x], Renv_[x - 1]);
+    con("aelnmo,cnoe->almc", X3_, x64_, y3, N.p[x], true, N.dims[x], Renv_[x - 1], true);
   }
   for (int h = 0; h < opt.sweeps; ++h) {
     if (h % 2 == 0) {
       for (int x = 0; x < Lx; ++x) {
         const Dims x3 = chain_left(Lenv_[x], ld[x], T.p[x], T.dims[x], lat.at(y, x), X3_);
         const Dims bd = ein_dims("cbnroq,brqe->cnoe", x3, rd[x]);
-        ein(cx, "cbnroq,brqe->cnoe", X3_, x3, Renv_[x], rd[x], bb_);
+        con("cbnroq,brqe->cnoe", X3_, x64_, x3, Renv_[x], true, rd[x], bb_, true);
         PEPS_REQUIRE(bd == N.dims[x], "internal: local tensor shape");
         if (x < Lx - 1) {
           const int m = bd[0] * bd[1] * bd[2], n = bd[3];
           PEPS_REQUIRE(n <= m, "internal: inconsistent bond caps");
           qr_thin(cx, m, n, bb_, n, 1, N.p[x], n, 1, nullptr);
           ld[x + 1] = ein_dims("cbnroq,cnoe->erqb", x3, N.dims[x]);
-          ein(cx, "cbnroq,cnoe->erqb", X3_, x3, N.p[x], N.dims[x], Lenv_[x + 1]);
+          con("cbnroq,cnoe->erqb", X3_, x64_, x3, N.p[x], true, N.dims[x], Lenv_[x + 1], true);
         } else {
           copy(cx, N.p[x], bb_, (long long)numel(bd));
         }
@@ -222,13 +233,13 @@ Mps Engine::var_compress(const Mps& T, const OLat& lat, int y, const std::vector
       for (int x = Lx - 1; x >= 0; --x) {
         const Dims y3 = chain_right(Renv_[x], rd[x], T.p[x], T.dims[x], lat.at(y, x), X3_);
         const Dims bd = ein_dims("clma,aelnmo->cnoe", ld[x], y3);
-        ein(cx, "clma,aelnmo->cnoe", Lenv_[x], ld[x], X3_, y3, bb_);
+        con("clma,aelnmo->cnoe", Lenv_[x], true, ld[x], X3_, x64_, y3, bb_, true);
         PEPS_REQUIRE(bd == N.dims[x], "internal: local tensor shape");
         if (x > 0) {
           const int c = bd[0], noe = bd[1] * bd[2] * bd[3];
           qr_thin(cx, noe, c, bb_, 1, noe, N.p[x], 1, noe, nullptr);
           rd[x - 1] = ein_dims("aelnmo,cnoe->almc", y3, N.dims[x]);
-          ein(cx, "aelnmo,cnoe->almc", X3_, y3, N.p[x], N.dims[x], Renv_[x - 1]);
+          con("aelnmo,cnoe->almc", X3_, x64_, y3, N.p[x], true, N.dims[x], Renv_[x - 1], true);
         } else {
           copy(cx, N.p[x], bb_, (long long)numel(bd));
         }
@@ -304,26 +315,26 @@ void Engine::row_rhos(const OLat& lat, const Mps& T, const Mps& B, int y, const 
   for (int x = 0; x + 1 < Lx && x + 1 < xmax; ++x) {
     const Dims x3 = chain_left(Lenv_[x], ld[x], T.p[x], T.dims[x], lat.at(y, x), X3_);
     ld[x + 1] = ein_dims("cbnroq,cnoe->erqb", x3, B.dims[x]);
-    ein(cx, "cbnroq,cnoe->erqb", X3_, x3, B.p[x], B.dims[x], Lenv_[x + 1]);
+    con("cbnroq,cnoe->erqb", X3_, x64_, x3, B.p[x], true, B.dims[x], Lenv_[x + 1], true);
     normalize(cx, Lenv_[x + 1], (long long)numel(ld[x + 1]), nullptr);
   }
   for (int x = Lx - 1; x >= 1 && x - 1 >= xmin; --x) {
     const Dims y3 = chain_right(Renv_[x], rd[x], T.p[x], T.dims[x], lat.at(y, x), X3_);
     rd[x - 1] = ein_dims("aelnmo,cnoe->almc", y3, B.dims[x]);
-    ein(cx, "aelnmo,cnoe->almc", X3_, y3, B.p[x], B.dims[x], Renv_[x - 1]);
+    con("aelnmo,cnoe->almc", X3_, x64_, y3, B.p[x], true, B.dims[x], Renv_[x - 1], true);
     normalize(cx, Renv_[x - 1], (long long)numel(rd[x - 1]), nullptr);
   }
   auto open_site = [&](int x) -> Dims {
     const SiteT& A = lat.at(y, x);
     const Dims ad = A.dims();
     const Dims x1 = ein_dims("clma,auvb->clmuvb", ld[x], T.dims[x]);
-    ein(cx, "clma,auvb->clmuvb", Lenv_[x], ld[x], T.p[x], T.dims[x], X1_);
+    con("clma,auvb->clmuvb", Lenv_[x], true, ld[x], T.p[x], true, T.dims[x], X1_, x64_);
     const Dims x2 = ein_dims("clmuvb,sulnr->cmvbsnr", x1, ad);
-    ein(cx, "clmuvb,sulnr->cmvbsnr", X1_, x1, A.p, ad, X2_);
+    con("clmuvb,sulnr->cmvbsnr", X1_, x64_, x1, A.p, true, ad, X2_, x64_);
     const Dims x3 = ein_dims("cmvbsnr,tvmoq->cbsnrtoq", x2, ad);
-    ein(cx, "cmvbsnr,tvmoq->cbsnrtoq", X2_, x2, A.p, ad, X3_);
+    con("cmvbsnr,tvmoq->cbsnrtoq", X2_, x64_, x2, A.p, true, ad, X3_, x64_);
     const Dims w = ein_dims("cbsnrtoq,cnoe->erqbst", x3, B.dims[x]);
-    ein(cx, "cbsnrtoq,cnoe->erqbst", X3_, x3, B.p[x], B.dims[x], bb_);
+    con("cbsnrtoq,cnoe->erqbst", X3_, x64_, x3, B.p[x], true, B.dims[x], bb_, true);
     return w;
   };
   for (const auto& t : sites) {
@@ -338,13 +349,13 @@ void Engine::row_rhos(const OLat& lat, const Mps& T, const Mps& B, int y, const 
     const SiteT& A2 = lat.at(y, x + 1);
     const Dims ad = A2.dims();
     const Dims x1 = ein_dims("clmaij,auvb->clmuvbij", w, T.dims[x + 1]);
-    ein(cx, "clmaij,auvb->clmuvbij", bb_, w, T.p[x + 1], T.dims[x + 1], X1_);
+    con("clmaij,auvb->clmuvbij", bb_, true, w, T.p[x + 1], true, T.dims[x + 1], X1_, x64_);
     const Dims x2 = ein_dims("clmuvbij,sulnr->cmvbsnrij", x1, ad);
-    ein(cx, "clmuvbij,sulnr->cmvbsnrij", X1_, x1, A2.p, ad, X2_);
+    con("clmuvbij,sulnr->cmvbsnrij", X1_, x64_, x1, A2.p, true, ad, X2_, x64_);
     const Dims x3 = ein_dims("cmvbsnrij,tvmoq->cbsnrtoqij", x2, ad);
-    ein(cx, "cmvbsnrij,tvmoq->cbsnrtoqij", X2_, x2, A2.p, ad, X3_);
+    con("cmvbsnrij,tvmoq->cbsnrtoqij", X2_, x64_, x2, A2.p, true, ad, X3_, x64_);
     const Dims x4 = ein_dims("cbsnrtoqij,cnoe->erqbstij", x3, B.dims[x + 1]);
-    ein(cx, "cbsnrtoqij,cnoe->erqbstij", X3_, x3, B.p[x + 1], B.dims[x + 1], X1_);
+    con("cbsnrtoqij,cnoe->erqbstij", X3_, x64_, x3, B.p[x + 1], true, B.dims[x + 1], X1_, true);
     ein(cx, "erqbstij,brqe->isjt", X1_, x4, Renv_[x + 1], rd[x + 1], t.second);
   }
 }
@@ -363,7 +374,7 @@ void Engine::norm_from_top(const OLat& lat, const Mps& T, const double* lns_acc,
     const Mat& bc = lat.bottom[x];
     const Dims bd = {1, bc.n, bc.n, 1};
     const Dims nd = ein_dims("cbnroq,cnoe->erqb", x3, bd);
-    ein(cx, "cbnroq,cnoe->erqb", X3_, x3, bc.p, bd, Lenv_[1 - cur]);
+    con("cbnroq,cnoe->erqb", X3_, x64_, x3, bc.p, true, bd, Lenv_[1 - cur], true);
     cur = 1 - cur;
     ld = nd;
     if (x + 1 < Lx) normalize(cx, Lenv_[cur], (long long)numel(ld), extra);

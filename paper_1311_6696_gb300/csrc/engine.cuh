@@ -80,7 +80,14 @@ class Engine {
   Mps var_compress(const Mps& T, const OLat& lat, int y, const std::vector<int>& caps, int tag,
                    int& centre, Arena& keep);
 
-  // absorb chain pieces (all FP64 einsum at present)
+  // One pairwise contraction.  FP64 mode: FP64 gather-GEMM, every operand FP64.
+  // Tensor-core modes: tcgen05 GEMM; a64/b64/c64 tag each tensor FP64 (else FP32).
+  void con(const char* spec, const void* A, bool a64, const Dims& ad, const void* B, bool b64, const Dims& bd,
+           void* C, bool c64);
+  bool tc_ = false;   // tensor-core contractions (chain intermediates stored FP32)
+  bool x64_ = true;   // dtype of the chain intermediates X1, X2, X3
+
+  // absorb chain pieces
   Dims chain_left(const double* L, const Dims& ld, const double* M, const Dims& md, const SiteT& A,
                   double* X3);
   Dims chain_right(const double* R, const Dims& rd, const double* M, const Dims& md,

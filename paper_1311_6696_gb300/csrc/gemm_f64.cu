@@ -173,6 +173,69 @@ __global__ void k_splitk_reduce(const GemmArgs g) {
   }
 }
 
+// Few outputs, long K (density matrices, scalars): each block reduces one K
+// chunk for every output at once; partials are summed in a fixed order.
+constexpr int DOT_MAXP = 16;
+
+__global__ void __launch_bounds__(256) k_dot_partial(const GemmArgs g, long long kchunk, double* part) {
+  __shared__ long long oa[DOT_MAXP], ob[DOT_MAXP];
+  __shared__ double red[8][DOT_MAXP];
+  const int P = int(g.M * g.N * g.NB);
+  const int tid = threadIdx.x;
+  if (tid < P) {
+    const long long bi = tid / (g.M * g.N), mn = tid % (g.M * g.N), m = mn / g.N, n = mn % g.N;
+    long long a0, b0, c0, a1, b1, c1, a2, b2, c2;
+    decomp(g.gb, bi, a0, b0, c0);
+    decomp(g.gm, m, a1, b1, c1);
+    decomp(g.gn, n, a2, b2, c2);
+    oa[tid] = a0 + a1;
+    ob[tid] = b0 + b2;
+  }
+  __syncthreads();
+  double acc[DOT_MAXP];
+#pragma unroll
+  for (int p = 0; p < DOT_MAXP; ++p) acc[p] = 0.0;
+  const long long k0 = blockIdx.x * kchunk, k1 = min(g.K, k0 + kchunk);
+  for (long long k = k0 + tid; k < k1; k += blockDim.x) {
+    long long ka, kb, kc;
+    decomp(g.gk, k, ka, kb, kc);
+#pragma unroll
+    for (int p = 0; p < DOT_MAXP; ++p)
+      if (p < P) acc[p] = fma(g.A[oa[p] + ka], g.B[ob[p] + kb], acc[p]);
+  }
+  const int lane = tid & 31, w = tid >> 5;
+#pragma unroll
+  for (int p = 0; p < DOT_MAXP; ++p) {
+    if (p >= P) break;
+    double v = acc[p];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[w][p] = v;
+  }
+  __syncthreads();
+  if (tid < P) {
+    double v = 0.0;
+    for (int i = 0; i < int(blockDim.x >> 5); ++i) v += red[i][tid];
+    part[(long long)blockIdx.x * DOT_MAXP + tid] = v;
+  }
+}
+
+__global__ void k_dot_finish(const GemmArgs g, int nblk, const double* part) {
+  const int P = int(g.M * g.N * g.NB);
+  const int p = threadIdx.x;
+  if (p >= P) return;
+  double v = 0.0;
+  for (int b = 0; b < nblk; ++b) v += part[(long long)b * DOT_MAXP + p];
+  const long long bi = p / (g.M * g.N), mn = p % (g.M * g.N), m = mn / g.N, n = mn % g.N;
+  long long a, b, c0, c1, c2;
+  decomp(g.gb, bi, a, b, c0);
+  decomp(g.gm, m, a, b, c1);
+  decomp(g.gn, n, a, b, c2);
+  double* out = g.C + c0 + c1 + c2;
+  double r = g.alpha * v;
+  if (g.beta != 0.0) r += g.beta * *out;
+  *out = r;
+}
+
 struct Parsed {
   std::string a, b, c;
 };
@@ -290,6 +353,17 @@ void ein(Ctx& cx, const char* spec, const double* A, const Dims& ad, const doubl
   }
   PEPS_REQUIRE(g.NB <= 65535, "batch too large");
 
+  if (g.M * g.N * g.NB <= DOT_MAXP && g.K >= 1024) {
+    const long long kchunk = 2048;
+    const int nblk = int(std::min<long long>((g.K + kchunk - 1) / kchunk, 4 * num_sms()));
+    const long long kc = (g.K + nblk - 1) / nblk;
+    double* part = cx.scratch(size_t(nblk) * DOT_MAXP);
+    Launch L(K_GEMM_F64, cx.st, 2.0 * double(g.M * g.N * g.NB) * double(g.K), 0);
+    k_dot_partial<<<nblk, 256, 0, cx.st>>>(g, kc, part);
+    k_dot_finish<<<1, 32, 0, cx.st>>>(g, nblk, part);
+    PEPS_CHECK_LAUNCH();
+    return;
+  }
   // Tile shape: minimise padded area, prefer square.
   static const int BMs[5] = {16, 32, 64, 128, 256};
   int best = 2;

@@ -1,0 +1,555 @@
+// Tensor-core contractions for the absorb chain (TF32 or BF16 inputs, FP32
+// accumulation) on sm_103a: tcgen05.mma with the accumulator in TMEM, operand
+// tiles staged by TMA (cp.async.bulk.tensor, 128-byte swizzle) through an
+// mbarrier ring, one elected thread issuing the MMAs.
+//
+// C[m, n] = alpha * sum_k A[m, k] B[n, k]: A is [M][K] and B is [N][K], both
+// K-contiguous (rows padded to 16 bytes).  The epilogue reads the accumulator
+// with tcgen05.ld and writes every element through the same row/column offset
+// decomposition as the FP64 gather-GEMM, so the output can be any permutation
+// of the (M, N) indices -- the layout the next contraction wants.
+//
+// Operands that are not already [M][K] / [N][K] are repacked by k_pack (a
+// gather copy that also rounds to TF32 / BF16 and, for the split variants,
+// writes the residual as a second operand: x ~ hi + lo, product ~ hi*hi +
+// hi*lo + lo*hi).
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "ein.cuh"
+#include "linalg.cuh"
+
+namespace peps {
+namespace {
+
+constexpr int TC_BM = 128;            // UMMA M (cta_group::1): accumulator row = TMEM lane
+constexpr int TC_THREADS = 128;       // 4 warps: TMA producer, MMA issuer, all four read TMEM
+constexpr int TC_STAGES = 4;
+constexpr int TC_ROWB = 128;          // bytes per tile row = one 128-byte swizzle row
+constexpr int MAXG = 8;
+
+struct Grp {
+  int n;
+  int dim[MAXG];
+  long long s[MAXG];
+};
+
+struct TcArgs {
+  long long M, N, K;
+  int ktiles;
+  int split;         // 1: A_lo, B_lo present
+  int bf16;          // 0: tf32, 1: bf16
+  int out_f64;       // 1: C is double, else float
+  int out_lo;        // 1: also write C_lo (split residual), C is then the rounded hi part
+  int stages;        // ring depth (<= TC_STAGES), chosen to fit shared memory
+  void* C;
+  void* Clo;
+  Grp gm, gn;        // output offsets of the M and N groups
+  double alpha;
+  int* flag;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait (about 2 s of SM clock at 2 GHz); on timeout sets the status
+// word and returns false so the caller can drain and leave.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* flag) {
+  const long long start = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - start > 4000000000LL) {
+      atomicOr(flag, FLAG_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(smem_u32(dst)), "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory descriptor of a K-major tile laid out by TMA with 128-byte
+// swizzle: 8-row groups 1024 bytes apart (SBO), descriptor version 1, swizzle 2.
+__device__ __forceinline__ uint64_t sdesc(const void* tile) {
+  const uint64_t a = smem_u32(tile);
+  return ((a >> 4) & 0x3FFFull) | (1ull << 16) | (uint64_t(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void decomp(const Grp& g, long long idx, long long& off) {
+  off = 0;
+  for (int i = g.n - 1; i >= 0; --i) {
+    const long long q = idx / g.dim[i];
+    off += (idx - q * g.dim[i]) * g.s[i];
+    idx = q;
+  }
+}
+
+// One 128 x BN output tile per CTA.
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ CUtensorMap ta,
+                                                        const __grid_constant__ CUtensorMap tb,
+                                                        const __grid_constant__ CUtensorMap tal,
+                                                        const __grid_constant__ CUtensorMap tbl,
+                                                        const TcArgs g) {
+  constexpr int A_BYTES = TC_BM * TC_ROWB;
+  constexpr int B_BYTES = BN * TC_ROWB;
+  extern __shared__ __align__(1024) uint8_t dsm[];
+  // 1024-byte aligned stage ring: [A, B, (A_lo, B_lo)] per stage
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
+  const int stage_bytes = g.split ? 2 * (A_BYTES + B_BYTES) : (A_BYTES + B_BYTES);
+  __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ long long offm[TC_BM], offn[BN];
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long tiles_n = (g.N + BN - 1) / BN;
+  const long long m0 = ((long long)blockIdx.x / tiles_n) * TC_BM;
+  const long long n0 = ((long long)blockIdx.x % tiles_n) * BN;
+
+  if (tid == 0) {
+    for (int s = 0; s < g.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    const uint32_t ncols = BN < 32 ? 32 : BN;
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  for (int i = tid; i < TC_BM; i += TC_THREADS) {
+    const long long m = m0 + i;
+    long long o = -1;
+    if (m < g.M) decomp(g.gm, m, o);
+    offm[i] = o;
+  }
+  for (int i = tid; i < BN; i += TC_THREADS) {
+    const long long n = n0 + i;
+    long long o = -1;
+    if (n < g.N) decomp(g.gn, n, o);
+    offn[i] = o;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const int kt_n = g.ktiles;
+  bool ok = true;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    const uint32_t tx = uint32_t(stage_bytes);
+    for (int kt = 0; kt < kt_n && ok; ++kt) {
+      const int s = kt % g.stages;
+      const uint32_t round = uint32_t(kt / g.stages);
+      ok = mbar_wait(&empty[s], (round & 1u) ^ 1u, g.flag);
+      if (!ok) break;
+      uint8_t* st = base + s * stage_bytes;
+      mbar_expect_tx(&full[s], tx);
+      const int kx = kt * (TC_ROWB / (g.bf16 ? 2 : 4));
+      tma_load_2d(st, &ta, &full[s], kx, int(m0));
+      tma_load_2d(st + A_BYTES, &tb, &full[s], kx, int(n0));
+      if (g.split) {
+        tma_load_2d(st + A_BYTES + B_BYTES, &tal, &full[s], kx, int(m0));
+        tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tbl, &full[s], kx, int(n0));
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: 4 instructions of K = 32 bytes cover one 128-byte tile row
+    const uint32_t afmt = g.bf16 ? 1u : 2u;
+    const uint32_t idesc = (1u << 4) | (afmt << 7) | (afmt << 10) | (uint32_t(BN >> 3) << 17) |
+                           (uint32_t(TC_BM >> 4) << 24);
+    for (int kt = 0; kt < kt_n && ok; ++kt) {
+      const int s = kt % g.stages;
+      const uint32_t round = uint32_t(kt / g.stages);
+      ok = mbar_wait(&full[s], round & 1u, g.flag);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint8_t* st = base + s * stage_bytes;
+      const uint64_t da = sdesc(st), db = sdesc(st + A_BYTES);
+      const uint64_t dal = sdesc(st + A_BYTES + B_BYTES), dbl = sdesc(st + 2 * A_BYTES + B_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t o = uint64_t(kk * 2);   // 32 bytes >> 4
+        const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+        if (g.bf16) {
+          mma_f16(tmem, da + o, db + o, idesc, acc);
+          if (g.split) {
+            mma_f16(tmem, da + o, dbl + o, idesc, 1u);
+            mma_f16(tmem, dal + o, db + o, idesc, 1u);
+          }
+        } else {
+          mma_tf32(tmem, da + o, db + o, idesc, acc);
+          if (g.split) {
+            mma_tf32(tmem, da + o, dbl + o, idesc, 1u);
+            mma_tf32(tmem, dal + o, db + o, idesc, 1u);
+          }
+        }
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(&done);
+  }
+  __syncwarp();
+  // Epilogue: every warp waits for the accumulator (bounded), then reads its 32 lanes.
+  const bool waited = mbar_wait(&done, 0u, g.flag);
+  const bool have = __all_sync(0xffffffffu, waited && ok);   // warp-uniform: tcgen05.ld is .sync.aligned
+  __syncwarp();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int row = warp * 32 + lane;
+  const long long om = offm[row];
+  if (have) {
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      uint32_t r[16];
+      tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0), r);
+      if (om < 0) continue;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const long long on = offn[c0 + j];
+        if (on < 0) continue;
+        const float v = __uint_as_float(r[j]) * float(g.alpha);
+        if (g.out_f64) {
+          static_cast<double*>(g.C)[om + on] = double(v);
+        } else if (g.out_lo) {
+          const float h = round_tf32(v);
+          static_cast<float*>(g.C)[om + on] = h;
+          static_cast<float*>(g.Clo)[om + on] = round_tf32(v - h);
+        } else {
+          static_cast<float*>(g.C)[om + on] = v;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t ncols = BN < 32 ? 32 : BN;
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+  }
+}
+
+// Gather-copy into a dense [rows][ld] operand: element (r, k) of the output is
+// src[sum(idx_i * stride_i)] with r, k decomposed over the row / K groups.
+// Rounds to TF32 (or converts to BF16); `lo` receives the rounded residual.
+struct PackArgs {
+  const void* src;
+  int src_f64;
+  Grp gr, gk;        // strides into src
+  long long rows, K, ld;
+  void* hi;
+  void* lo;
+  int bf16;
+};
+
+__global__ void k_pack(const PackArgs p) {
+  const long long total = p.rows * p.K;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long r = t / p.K, k = t - r * p.K;
+    long long o1, o2;
+    decomp(p.gr, r, o1);
+    decomp(p.gk, k, o2);
+    const double v = p.src_f64 ? static_cast<const double*>(p.src)[o1 + o2]
+                               : double(static_cast<const float*>(p.src)[o1 + o2]);
+    const long long d = r * p.ld + k;
+    if (p.bf16) {
+      const __nv_bfloat16 h = __double2bfloat16(v);
+      static_cast<__nv_bfloat16*>(p.hi)[d] = h;
+      if (p.lo) static_cast<__nv_bfloat16*>(p.lo)[d] = __double2bfloat16(v - double(__bfloat162float(h)));
+    } else {
+      const float h = round_tf32(float(v));
+      static_cast<float*>(p.hi)[d] = h;
+      if (p.lo) static_cast<float*>(p.lo)[d] = round_tf32(float(v - double(h)));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encode_fn() {
+  static std::mutex mu;
+  static EncodeFn fn = nullptr;
+  std::lock_guard<std::mutex> g(mu);
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    PEPS_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    PEPS_REQUIRE(p != nullptr && q == cudaDriverEntryPointSuccess, "cuTensorMapEncodeTiled unavailable");
+    fn = reinterpret_cast<EncodeFn>(p);
+  }
+  return fn;
+}
+
+// 2D map of a dense [rows][ld] operand, box = 128 bytes of K x box_rows rows.
+CUtensorMap make_map(const void* ptr, long long rows, long long K, long long ld, int bf16, int box_rows) {
+  CUtensorMap m;
+  std::memset(&m, 0, sizeof(m));
+  const int esz = bf16 ? 2 : 4;
+  PEPS_REQUIRE((reinterpret_cast<uintptr_t>(ptr) & 15) == 0, "TMA operand not 16-byte aligned");
+  PEPS_REQUIRE((ld * esz) % 16 == 0, "TMA row stride not a multiple of 16 bytes");
+  cuuint64_t dims[2] = {cuuint64_t(K), cuuint64_t(rows)};
+  cuuint64_t strides[1] = {cuuint64_t(ld * esz)};
+  cuuint32_t box[2] = {cuuint32_t(TC_ROWB / esz), cuuint32_t(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(&m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                           const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  PEPS_REQUIRE(r == CUDA_SUCCESS, "cuTensorMapEncodeTiled failed: " + std::to_string(int(r)));
+  return m;
+}
+
+struct Parsed {
+  std::string a, b, c;
+};
+
+Parsed parse(const char* spec) {
+  std::string s(spec);
+  auto comma = s.find(','), arrow = s.find("->");
+  PEPS_REQUIRE(comma != std::string::npos && arrow != std::string::npos, std::string("bad spec ") + spec);
+  return {s.substr(0, comma), s.substr(comma + 1, arrow - comma - 1), s.substr(arrow + 2)};
+}
+
+std::vector<long long> strides_of(const Dims& d) {
+  std::vector<long long> s(d.size());
+  long long acc = 1;
+  for (int i = int(d.size()) - 1; i >= 0; --i) {
+    s[i] = acc;
+    acc *= d[i];
+  }
+  return s;
+}
+
+void push(Grp& g, int dim, long long s) {
+  PEPS_REQUIRE(g.n < MAXG, "too many indices in one group");
+  g.dim[g.n] = dim;
+  g.s[g.n] = s;
+  g.n++;
+}
+
+long long prod(const Grp& g) {
+  long long n = 1;
+  for (int i = 0; i < g.n; ++i) n *= g.dim[i];
+  return n;
+}
+
+struct Operand {
+  void* hi = nullptr;
+  void* lo = nullptr;
+  long long rows = 0, K = 0, ld = 0;
+};
+
+// Pack one operand into [rows][ld] (rows over `rowletters`, K over `kletters`).
+Operand pack(Ctx& cx, const void* src, int src_f64, const std::string& letters, const Dims& dims,
+             const std::string& rowletters, const std::string& kletters, int bf16, int split, double* mem) {
+  auto st = strides_of(dims);
+  PackArgs p;
+  std::memset(&p, 0, sizeof(p));
+  for (char ch : rowletters) {
+    auto i = letters.find(ch);
+    push(p.gr, dims[i], st[i]);
+  }
+  for (char ch : kletters) {
+    auto i = letters.find(ch);
+    push(p.gk, dims[i], st[i]);
+  }
+  Operand o;
+  o.rows = prod(p.gr);
+  o.K = prod(p.gk);
+  const int align = bf16 ? 8 : 4;
+  o.ld = (o.K + align - 1) / align * align;
+  const size_t bytes = size_t(o.rows) * o.ld * (bf16 ? 2 : 4);
+  const size_t words = (bytes + 255) / 256 * 32;   // doubles, 256-byte aligned
+  o.hi = mem;
+  o.lo = split ? static_cast<void*>(mem + words) : nullptr;
+  p.src = src;
+  p.src_f64 = src_f64;
+  p.rows = o.rows;
+  p.K = o.K;
+  p.ld = o.ld;
+  p.hi = o.hi;
+  p.lo = o.lo;
+  p.bf16 = bf16;
+  const long long total = o.rows * o.K;
+  Launch L(K_AUX, cx.st);
+  const unsigned blocks = unsigned(std::max<long long>(1, std::min<long long>((total + 255) / 256, 4096)));
+  k_pack<<<blocks, 256, 0, cx.st>>>(p);
+  PEPS_CHECK_LAUNCH();
+  return o;
+}
+
+size_t pack_words(long long rows, long long K, int bf16, int split) {
+  const int align = bf16 ? 8 : 4;
+  const long long ld = (K + align - 1) / align * align;
+  const size_t bytes = size_t(rows) * ld * (bf16 ? 2 : 4);
+  const size_t words = (bytes + 255) / 256 * 32;
+  return split ? 2 * words : words;
+}
+
+template <int BN>
+void launch_tc(Ctx& cx, const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tal,
+               const CUtensorMap& tbl, TcArgs g, long long tiles) {
+  const int a_bytes = TC_BM * TC_ROWB, b_bytes = BN * TC_ROWB;
+  const int stage = g.split ? 2 * (a_bytes + b_bytes) : (a_bytes + b_bytes);
+  const int budget = 200 * 1024;
+  g.stages = std::max(1, std::min(TC_STAGES, (budget - 1024) / stage));
+  const size_t smem = size_t(stage) * g.stages + 1024;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    PEPS_CUDA(cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  });
+  k_gemm_tc<BN><<<unsigned(tiles), TC_THREADS, smem, cx.st>>>(ta, tb, tal, tbl, g);
+  PEPS_CHECK_LAUNCH();
+}
+
+}  // namespace
+
+int tc_available() {
+  static int ok = -1;
+  if (ok < 0) {
+    int dev = 0, major = 0, minor = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    ok = (major == 10 && minor == 3) ? 1 : 0;
+  }
+  return ok;
+}
+
+void ein_tc(Ctx& cx, const char* spec, const void* A, int a_f64, const Dims& ad, const void* B, int b_f64,
+            const Dims& bd, void* C, int c_f64, int prec, double alpha, void* Clo) {
+  PEPS_REQUIRE(tc_available(), "tensor-core path needs an sm_103 device");
+  const Parsed p = parse(spec);
+  const Dims cd = ein_dims(spec, ad, bd);
+  const auto sc = strides_of(cd);
+  std::string mL, nL, kL;
+  TcArgs g;
+  std::memset(&g, 0, sizeof(g));
+  for (size_t i = 0; i < p.c.size(); ++i) {
+    const char ch = p.c[i];
+    const bool inA = p.a.find(ch) != std::string::npos, inB = p.b.find(ch) != std::string::npos;
+    PEPS_REQUIRE(!(inA && inB), std::string("batch index not supported on the tensor-core path: ") + spec);
+    if (inA) {
+      mL += ch;
+      push(g.gm, cd[i], sc[i]);
+    } else {
+      nL += ch;
+      push(g.gn, cd[i], sc[i]);
+    }
+  }
+  for (char ch : p.a)
+    if (p.c.find(ch) == std::string::npos) {
+      PEPS_REQUIRE(p.b.find(ch) != std::string::npos, std::string("unsupported one-sided sum: ") + spec);
+      kL += ch;
+    }
+  const int bf16 = (prec == PEPS_PREC_BF16 || prec == PEPS_PREC_BF16X3) ? 1 : 0;
+  const int split = (prec == PEPS_PREC_TF32X3 || prec == PEPS_PREC_BF16X3) ? 1 : 0;
+  long long M = 1, N = 1, K = 1;
+  for (char ch : mL) M *= ad[p.a.find(ch)];
+  for (char ch : nL) N *= bd[p.b.find(ch)];
+  for (char ch : kL) K *= ad[p.a.find(ch)];
+  if (M == 0 || N == 0) return;
+  const size_t wa = pack_words(M, K, bf16, split), wb = pack_words(N, K, bf16, split);
+  double* mem = cx.scratch(wa + wb);
+  const Operand oa = pack(cx, A, a_f64, p.a, ad, mL, kL, bf16, split, mem);
+  const Operand ob = pack(cx, B, b_f64, p.b, bd, nL, kL, bf16, split, mem + wa);
+  int BN = 16;
+  while (BN < N && BN < 128) BN *= 2;
+  const CUtensorMap ta = make_map(oa.hi, M, K, oa.ld, bf16, TC_BM);
+  const CUtensorMap tb = make_map(ob.hi, N, K, ob.ld, bf16, BN);
+  const CUtensorMap tal = split ? make_map(oa.lo, M, K, oa.ld, bf16, TC_BM) : ta;
+  const CUtensorMap tbl = split ? make_map(ob.lo, N, K, ob.ld, bf16, BN) : tb;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.ktiles = int((K + (TC_ROWB / (bf16 ? 2 : 4)) - 1) / (TC_ROWB / (bf16 ? 2 : 4)));
+  g.split = split;
+  g.bf16 = bf16;
+  g.out_f64 = c_f64;
+  g.out_lo = (Clo != nullptr && !c_f64) ? 1 : 0;
+  g.C = C;
+  g.Clo = Clo;
+  g.alpha = alpha;
+  g.flag = cx.flag;
+  const long long tiles = ((M + TC_BM - 1) / TC_BM) * ((N + BN - 1) / BN);
+  PEPS_REQUIRE(tiles < (1LL << 31), "too many tiles");
+  const double flops = 2.0 * double(M) * double(N) * double(K);
+  Launch L(K_GEMM_TC, cx.st, flops, 0);
+  switch (BN) {
+    case 16: launch_tc<16>(cx, ta, tb, tal, tbl, g, tiles); break;
+    case 32: launch_tc<32>(cx, ta, tb, tal, tbl, g, tiles); break;
+    case 64: launch_tc<64>(cx, ta, tb, tal, tbl, g, tiles); break;
+    default: launch_tc<128>(cx, ta, tb, tal, tbl, g, tiles); break;
+  }
+}
+
+}  // namespace peps

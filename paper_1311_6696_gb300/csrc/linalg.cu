@@ -3,10 +3,18 @@
 // The working copy lives in global memory (column-major) and stays in L2 at
 // the sizes used here (<= a few MB).  Reductions over a column are done by one
 // warp per column; a CTA handles all columns of one matrix.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <mutex>
+#include <vector>
 
 #include "linalg.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace peps {
 namespace {
@@ -131,6 +139,177 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_house(const QrArgs q) {
       q.R[e] = (j >= i) ? W[(long long)j * m + i] : 0.0;
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Householder QR on a thread-block cluster: the rows of one matrix are split
+// over the cluster's CTAs (one SM each); every column reduction (the norm
+// below the diagonal, the reflector's inner products with the trailing
+// columns) is a per-CTA partial sum exchanged through distributed shared
+// memory between hardware cluster barriers.  Same reflectors, same order and
+// same sign convention as the one-CTA kernel; the FP64 work is spread over C
+// SMs instead of one.
+// ---------------------------------------------------------------------------
+constexpr int QRC_THREADS = 256;
+constexpr int QRC_BATCH = 8;   // columns whose remote partials one warp fetches at once
+
+// Sum over the cluster of one double per CTA (at `slot` in each CTA's shared
+// memory): lane r reads rank r, then a warp reduction; every warp gets the sum.
+__device__ __forceinline__ double cluster_sum(cg::cluster_group& cl, double* slot, int C, int lane) {
+  double v = 0.0;
+  for (int r = lane; r < C; r += 32) v += *cl.map_shared_rank(slot, r);
+  return warp_sum(v);
+}
+
+// Each CTA keeps its block of rows of the working matrix and of Q in shared
+// memory when they fit (column-major within the block), else in global scratch.
+__global__ void __launch_bounds__(QRC_THREADS) k_qr_cluster(const QrArgs q, int in_smem) {
+  extern __shared__ double qsm[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = int(cluster.num_blocks());
+  const int rank = int(cluster.block_rank());
+  const int m = q.m, n = q.n, k = min(m, n);
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int chunk = (m + C - 1) / C;
+  const int r0 = min(m, rank * chunk), r1 = min(m, r0 + chunk), rows = r1 - r0;
+  double* wpart = qsm;              // [2][n] per-column partial inner products
+  double* npart = wpart + 2 * n;    // [2]    partial squared norm below the diagonal
+  double* bcast = npart + 2;        // [2]    the diagonal entry, published by its owner
+  double* tau_s = bcast + 2;        // [k]
+  double* W;                        // [n][chunk] my rows, column-major
+  double* Qw;                       // [k][chunk]
+  if (in_smem) {
+    W = tau_s + k;
+    Qw = W + (long long)n * chunk;
+  } else {
+    W = q.W + (long long)rank * chunk * n;
+    Qw = q.Qw + (long long)rank * chunk * k;
+  }
+  for (long long e = tid; e < (long long)rows * n; e += nt) {
+    const int li = int(e % rows), j = int(e / rows);
+    W[(long long)j * chunk + li] = q.A[(r0 + li) * q.rs + j * q.cs];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double part = 0.0;
+    for (int i = max(r0, 1) + lane; i < r1; i += 32) part += W[i - r0] * W[i - r0];
+    part = warp_sum(part);
+    if (lane == 0) {
+      npart[0] = part;
+      if (r0 == 0 && rows > 0) bcast[0] = W[0];
+    }
+  }
+  for (int j = 0; j < k; ++j) {
+    const int b = j & 1;
+    const int owner = j / chunk;
+    const bool own = (owner == rank);
+    cluster.sync();                                   // column j: norm partials and diagonal visible
+    const double alpha_r = *cluster.map_shared_rank(bcast + b, owner);   // issued together with the sum's loads
+    const double sig = cluster_sum(cluster, npart + b, C, lane);
+    const double alpha = alpha_r;
+    double tau = 0.0, scale = 0.0, beta = alpha;
+    if (sig != 0.0) {
+      const double nrm = sqrt(alpha * alpha + sig);
+      beta = alpha >= 0.0 ? -nrm : nrm;
+      tau = (beta - alpha) / beta;
+      scale = 1.0 / (alpha - beta);
+    }
+    if (tid == 0) tau_s[j] = tau;
+    const int i0 = max(r0, j + 1);                    // my rows below the diagonal
+    double* vj = W + (long long)j * chunk - r0;       // vj[i] for global row i
+    if (tau != 0.0) {                                 // uniform across the cluster
+      for (int i = i0 + tid; i < r1; i += nt) vj[i] *= scale;
+      __syncthreads();
+      for (int c = j + 1 + warp; c < n; c += nw) {
+        const double* wc = W + (long long)c * chunk - r0;
+        double w = 0.0;
+        for (int i = i0 + lane; i < r1; i += 32) w += vj[i] * wc[i];
+        w = warp_sum(w);
+        if (lane == 0) wpart[b * n + c] = w + (own ? wc[j] : 0.0);
+      }
+      cluster.sync();                                 // inner products of column j visible
+      for (int cb = j + 1 + warp; cb < n; cb += QRC_BATCH * nw) {
+        double v[QRC_BATCH];                          // all remote loads in flight first
+#pragma unroll
+        for (int u = 0; u < QRC_BATCH; ++u) {
+          const int c = cb + u * nw;
+          v[u] = (c < n && lane < C) ? *cluster.map_shared_rank(wpart + b * n + c, lane) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < QRC_BATCH; ++u) {
+          const int c = cb + u * nw;
+          const double w = tau * warp_sum(v[u]);
+          if (c >= n) continue;
+          double* wc = W + (long long)c * chunk - r0;
+          if (own && lane == 0) wc[j] -= w;
+          for (int i = i0 + lane; i < r1; i += 32) wc[i] -= w * vj[i];
+        }
+      }
+      if (own && tid == 0) vj[j] = beta;
+    }
+    __syncthreads();
+    if (j + 1 < k && warp == 0) {                     // next column: norm partial and diagonal
+      const double* w1 = W + (long long)(j + 1) * chunk - r0;
+      double part = 0.0;
+      for (int i = max(r0, j + 2) + lane; i < r1; i += 32) part += w1[i] * w1[i];
+      part = warp_sum(part);
+      if (lane == 0) {
+        npart[1 - b] = part;
+        if (j + 1 >= r0 && j + 1 < r1) bcast[1 - b] = w1[j + 1];
+      }
+    }
+  }
+  // Q = H_0 ... H_{k-1} [I_k; 0], accumulated backwards on the same row split.
+  for (long long e = tid; e < (long long)rows * k; e += nt) {
+    const int li = int(e % rows), c = int(e / rows);
+    Qw[(long long)c * chunk + li] = (r0 + li == c) ? 1.0 : 0.0;
+  }
+  cluster.sync();
+  for (int j = k - 1, t = 0; j >= 0; --j, ++t) {
+    const double tau = tau_s[j];
+    if (tau == 0.0) continue;
+    const int b = t & 1;
+    const bool own = (j >= r0 && j < r1);
+    const int i0 = max(r0, j + 1);
+    const double* vj = W + (long long)j * chunk - r0;
+    for (int c = j + warp; c < k; c += nw) {
+      const double* qc = Qw + (long long)c * chunk - r0;
+      double w = 0.0;
+      for (int i = i0 + lane; i < r1; i += 32) w += vj[i] * qc[i];
+      w = warp_sum(w);
+      if (lane == 0) wpart[b * n + c] = w + (own ? qc[j] : 0.0);
+    }
+    cluster.sync();
+    for (int cb = j + warp; cb < k; cb += QRC_BATCH * nw) {
+      double v[QRC_BATCH];
+#pragma unroll
+      for (int u = 0; u < QRC_BATCH; ++u) {
+        const int c = cb + u * nw;
+        v[u] = (c < k && lane < C) ? *cluster.map_shared_rank(wpart + b * n + c, lane) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < QRC_BATCH; ++u) {
+        const int c = cb + u * nw;
+        const double w = tau * warp_sum(v[u]);
+        if (c >= k) continue;
+        double* qc = Qw + (long long)c * chunk - r0;
+        if (own && lane == 0) qc[j] -= w;
+        for (int i = i0 + lane; i < r1; i += 32) qc[i] -= w * vj[i];
+      }
+    }
+    __syncthreads();
+  }
+  for (long long e = tid; e < (long long)rows * k; e += nt) {
+    const int li = int(e % rows), c = int(e / rows);
+    q.Q[(r0 + li) * q.qrs + c * q.qcs] = Qw[(long long)c * chunk + li];
+  }
+  if (q.R) {
+    for (long long e = tid; e < (long long)rows * n; e += nt) {
+      const int li = int(e % rows), j = int(e / rows), i = r0 + li;
+      if (i < k) q.R[(long long)i * n + j] = (j >= i) ? W[(long long)j * chunk + li] : 0.0;
+    }
+  }
+  cluster.sync();   // no CTA leaves while others may still read its shared memory
 }
 
 struct SvdArgs {
@@ -262,15 +441,98 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_jacobi(const SvdArgs s) {
 
 }  // namespace
 
+namespace {
+// Largest cluster size (16 non-portable, else 8, 4, 2) launchable with `smem`
+// bytes of dynamic shared memory per CTA; 1 if clusters are unavailable.
+int qr_cluster_size(size_t smem) {
+  static std::mutex mu;
+  static std::vector<std::pair<size_t, int>> cache;
+  static bool attrs = false, attrs_ok = false;
+  std::lock_guard<std::mutex> g(mu);
+  const size_t key = (smem + 4095) / 4096 * 4096;
+  for (auto& e : cache)
+    if (e.first == key) return e.second;
+  if (!attrs) {
+    attrs = true;
+    attrs_ok = cudaFuncSetAttribute(k_qr_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+               cudaFuncSetAttribute(k_qr_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) == cudaSuccess;
+    cudaGetLastError();
+  }
+  int best = 1;
+  if (attrs_ok) {
+    for (int c : {16, 8, 4, 2}) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(c, 1, 1);
+      cfg.blockDim = dim3(QRC_THREADS, 1, 1);
+      cfg.dynamicSmemBytes = key;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = c;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      const cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, k_qr_cluster, &cfg);
+      if (std::getenv("PEPS_VERBOSE"))
+        std::fprintf(stderr, "[peps] qr cluster %d smem %zu: %s, %d active clusters\n", c, key,
+                     cudaGetErrorString(e), nclusters);
+      cudaGetLastError();
+      if (e == cudaSuccess && nclusters > 0) {
+        best = c;
+        break;
+      }
+    }
+  }
+  cache.push_back({key, best});
+  return best;
+}
+}  // namespace
+
 void qr_thin(Ctx& cx, int m, int n, const double* A, long long rs, long long cs, double* Q,
              long long qrs, long long qcs, double* R) {
   PEPS_REQUIRE(m > 0 && n > 0, "qr of an empty matrix");
   const int k = std::min(m, n);
-  double* w = cx.scratch(size_t(m) * n + size_t(m) * k + k);
+  double* w = cx.scratch(size_t(m) * n + size_t(m) * k + k + 64);
   QrArgs a{m, n, A, rs, cs, Q, qrs, qcs, R, w, w + size_t(m) * n, w + size_t(m) * n + size_t(m) * k};
   const double flops = 4.0 * m * double(n) * k - 4.0 / 3.0 * double(k) * k * k;
+  const size_t kQrSmemMax = 200 * 1024;
+  // Rows per CTA >= 32 keeps the per-column barrier cost below the FP64 work.
+  int C = std::max(1, std::min(16, m / 32));
+  while (C > 1 && (C & (C - 1))) --C;
+  const size_t base = sizeof(double) * (2 * size_t(n) + 4 + k);
+  auto full_of = [&](int c) { return base + sizeof(double) * ((size_t(m) + c - 1) / c) * (size_t(n) + k); };
+  if (C > 1) C = std::min(C, qr_cluster_size(full_of(C) <= kQrSmemMax ? full_of(C) : base));
+  while (C > 1 && (C & (C - 1))) --C;
+  if (std::getenv("PEPS_VERBOSE")) std::fprintf(stderr, "[peps] qr %dx%d: cluster %d\n", m, n, C);
   Launch L(K_QR, cx.st, flops, 0);
-  k_qr_house<<<1, QR_THREADS, 0, cx.st>>>(a);
+  if (C <= 1) {
+    k_qr_house<<<1, QR_THREADS, 0, cx.st>>>(a);
+  } else {
+    const size_t chunk = (size_t(m) + C - 1) / C;
+    const size_t full = full_of(C);
+    const int in_smem = full <= kQrSmemMax ? 1 : 0;
+    // the global-memory fallback uses [C][chunk][n] / [C][chunk][k] blocks
+    if (!in_smem) {
+      double* w2 = cx.scratch(size_t(C) * chunk * (size_t(n) + k) + k + 64);
+      a.W = w2;
+      a.Qw = w2 + size_t(C) * chunk * n;
+      a.tau = a.Qw + size_t(C) * chunk * k;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(QRC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = in_smem ? full : base;
+    cfg.stream = cx.st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    PEPS_CUDA(cudaLaunchKernelEx(&cfg, k_qr_cluster, a, in_smem));
+  }
   PEPS_CHECK_LAUNCH();
 }
 

@@ -8,6 +8,7 @@ namespace peps {
 constexpr int FLAG_SVD_NOCONV = 1;
 constexpr int FLAG_CU0_NOCONV = 2;
 constexpr int FLAG_BAD_VALUE = 4;
+constexpr int FLAG_TIMEOUT = 8;
 
 // Thin QR of the m x n matrix with element (i,j) at A[i*rs + j*cs].
 // Writes Q (m x k, k = min(m,n)) to Q[i*qrs + j*qcs] and, if R is not null,

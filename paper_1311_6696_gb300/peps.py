@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libpeps.so")
 OK, EINVAL, ENOMEM, ECUDA, ECONVERGE, ETIMEOUT = range(6)
 F64, F32 = 0, 1
 SVD, VAR = 0, 1
-PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
+PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "tf32x3": 3, "bf16x3": 4}
 KIND = {"site": 0, "hbond": 1, "vbond": 2}
 MODE = {"svd": SVD, "var": VAR}
 
