@@ -151,162 +151,189 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_house(const QrArgs q) {
 // SMs instead of one.
 // ---------------------------------------------------------------------------
 constexpr int QRC_THREADS = 256;
-constexpr int QRC_BATCH = 8;   // columns whose remote partials one warp fetches at once
+// Each CTA keeps its block of rows of the working matrix and of Q in shared
+// memory when they fit (column-major within the block, odd column stride),
+// else in global scratch.  Work per column is split as (column, row quarter)
+// per thread: every thread runs a plain FMA loop over its rows, so the FP64
+// pipe executes the factorisation's own multiply-adds and almost nothing else
+// (a shuffle tree per column would cost more FP64 issue slots than the dot
+// products at 64 rows per CTA).
+constexpr int QS = 4;   // threads per column (rows interleaved mod QS)
 
-// Sum over the cluster of one double per CTA (at `slot` in each CTA's shared
-// memory): lane r reads rank r, then a warp reduction; every warp gets the sum.
-__device__ __forceinline__ double cluster_sum(cg::cluster_group& cl, double* slot, int C, int lane) {
-  double v = 0.0;
-  for (int r = lane; r < C; r += 32) v += *cl.map_shared_rank(slot, r);
-  return warp_sum(v);
+// Sum of one double over the cluster's CTAs, all remote loads issued first.
+__device__ __forceinline__ double remote_sum(cg::cluster_group& cl, double* slot, int C) {
+  double v[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = r < C ? *cl.map_shared_rank(slot, r) : 0.0;
+  double s = 0.0;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) s += v[r];
+  return s;
 }
 
-// Each CTA keeps its block of rows of the working matrix and of Q in shared
-// memory when they fit (column-major within the block), else in global scratch.
-__global__ void __launch_bounds__(QRC_THREADS) k_qr_cluster(const QrArgs q, int in_smem) {
+__global__ void __launch_bounds__(QRC_THREADS) k_qr_cluster(const QrArgs q, int in_smem, int ld) {
   extern __shared__ double qsm[];
   cg::cluster_group cluster = cg::this_cluster();
   const int C = int(cluster.num_blocks());
   const int rank = int(cluster.block_rank());
   const int m = q.m, n = q.n, k = min(m, n);
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int tid = threadIdx.x, nt = blockDim.x;
   const int chunk = (m + C - 1) / C;
   const int r0 = min(m, rank * chunk), r1 = min(m, r0 + chunk), rows = r1 - r0;
-  double* wpart = qsm;              // [2][n] per-column partial inner products
+  double* wpart = qsm;              // [2][n] per-column partial inner products (cluster-visible)
   double* npart = wpart + 2 * n;    // [2]    partial squared norm below the diagonal
   double* bcast = npart + 2;        // [2]    the diagonal entry, published by its owner
   double* tau_s = bcast + 2;        // [k]
-  double* W;                        // [n][chunk] my rows, column-major
-  double* Qw;                       // [k][chunk]
+  double* part4 = tau_s + k;        // [n][QS] quarter sums
+  double* wfin = part4 + (long long)n * QS;   // [n]
+  double* coef = wfin + n;          // [2] scale, beta of the current reflector
+  double* nsq = coef + 2;           // [QS] squares of the next column, by row class
+  double* W;                        // [n][ld] my rows, column-major (row i at i - r0)
+  double* Qw;                       // [k][ld]
   if (in_smem) {
-    W = tau_s + k;
-    Qw = W + (long long)n * chunk;
+    W = nsq + QS;
+    Qw = W + (long long)n * ld;
   } else {
-    W = q.W + (long long)rank * chunk * n;
-    Qw = q.Qw + (long long)rank * chunk * k;
+    W = q.W + (long long)rank * ld * n;
+    Qw = q.Qw + (long long)rank * ld * k;
   }
   for (long long e = tid; e < (long long)rows * n; e += nt) {
     const int li = int(e % rows), j = int(e / rows);
-    W[(long long)j * chunk + li] = q.A[(r0 + li) * q.rs + j * q.cs];
+    W[(long long)j * ld + li] = q.A[(r0 + li) * q.rs + j * q.cs];
   }
   __syncthreads();
-  if (warp == 0) {
+  if (tid == 0) {
     double part = 0.0;
-    for (int i = max(r0, 1) + lane; i < r1; i += 32) part += W[i - r0] * W[i - r0];
-    part = warp_sum(part);
-    if (lane == 0) {
-      npart[0] = part;
-      if (r0 == 0 && rows > 0) bcast[0] = W[0];
-    }
+    for (int i = max(r0, 1); i < r1; ++i) part += W[i - r0] * W[i - r0];
+    npart[0] = part;
+    if (r0 == 0 && rows > 0) bcast[0] = W[0];
   }
   for (int j = 0; j < k; ++j) {
     const int b = j & 1;
     const int owner = j / chunk;
     const bool own = (owner == rank);
     cluster.sync();                                   // column j: norm partials and diagonal visible
-    const double alpha_r = *cluster.map_shared_rank(bcast + b, owner);   // issued together with the sum's loads
-    const double sig = cluster_sum(cluster, npart + b, C, lane);
-    const double alpha = alpha_r;
-    double tau = 0.0, scale = 0.0, beta = alpha;
-    if (sig != 0.0) {
-      const double nrm = sqrt(alpha * alpha + sig);
-      beta = alpha >= 0.0 ? -nrm : nrm;
-      tau = (beta - alpha) / beta;
-      scale = 1.0 / (alpha - beta);
+    if (tid < 32) {
+      const double alpha = *cluster.map_shared_rank(bcast + b, owner);
+      double sig = 0.0;
+      for (int r = tid; r < C; r += 32) sig += *cluster.map_shared_rank(npart + b, r);
+      sig = warp_sum(sig);
+      double tau = 0.0, scale = 0.0, beta = alpha;
+      if (sig != 0.0) {
+        const double nrm = sqrt(alpha * alpha + sig);
+        beta = alpha >= 0.0 ? -nrm : nrm;
+        tau = (beta - alpha) / beta;
+        scale = 1.0 / (alpha - beta);
+      }
+      if (tid == 0) {
+        tau_s[j] = tau;
+        coef[0] = scale;
+        coef[1] = beta;
+      }
     }
-    if (tid == 0) tau_s[j] = tau;
+    __syncthreads();
+    const double tau = tau_s[j], scale = coef[0], beta = coef[1];
     const int i0 = max(r0, j + 1);                    // my rows below the diagonal
-    double* vj = W + (long long)j * chunk - r0;       // vj[i] for global row i
+    double* vj = W + (long long)j * ld - r0;          // vj[i] for global row i
+    const int nc = n - j - 1;                         // trailing columns
     if (tau != 0.0) {                                 // uniform across the cluster
       for (int i = i0 + tid; i < r1; i += nt) vj[i] *= scale;
       __syncthreads();
-      for (int c = j + 1 + warp; c < n; c += nw) {
-        const double* wc = W + (long long)c * chunk - r0;
+      for (int t = tid; t < nc * QS; t += nt) {
+        const int c = j + 1 + t / QS, qq = t % QS;
+        const double* wc = W + (long long)c * ld - r0;
         double w = 0.0;
-        for (int i = i0 + lane; i < r1; i += 32) w += vj[i] * wc[i];
-        w = warp_sum(w);
-        if (lane == 0) wpart[b * n + c] = w + (own ? wc[j] : 0.0);
+        for (int i = i0 + ((qq - i0 % QS + QS) % QS); i < r1; i += QS) w = fma(vj[i], wc[i], w);
+        part4[(long long)c * QS + qq] = w;
+      }
+      __syncthreads();
+      for (int c = j + 1 + tid; c < n; c += nt) {
+        const double* wc = W + (long long)c * ld - r0;
+        double w = own ? wc[j] : 0.0;
+        for (int qq = 0; qq < QS; ++qq) w += part4[(long long)c * QS + qq];
+        wpart[b * n + c] = w;
       }
       cluster.sync();                                 // inner products of column j visible
-      for (int cb = j + 1 + warp; cb < n; cb += QRC_BATCH * nw) {
-        double v[QRC_BATCH];                          // all remote loads in flight first
-#pragma unroll
-        for (int u = 0; u < QRC_BATCH; ++u) {
-          const int c = cb + u * nw;
-          v[u] = (c < n && lane < C) ? *cluster.map_shared_rank(wpart + b * n + c, lane) : 0.0;
+      for (int c = j + 1 + tid; c < n; c += nt) wfin[c] = tau * remote_sum(cluster, wpart + b * n + c, C);
+      __syncthreads();
+      for (int t = tid; t < nc * QS; t += nt) {
+        const int c = j + 1 + t / QS, qq = t % QS;
+        double* wc = W + (long long)c * ld - r0;
+        const double w = wfin[c];
+        if (own && qq == 0) wc[j] -= w;
+        double sq = 0.0;                               // column j+1: squares below its diagonal
+        for (int i = i0 + ((qq - i0 % QS + QS) % QS); i < r1; i += QS) {
+          const double v = fma(-w, vj[i], wc[i]);
+          wc[i] = v;
+          if (i > j + 1) sq = fma(v, v, sq);
         }
-#pragma unroll
-        for (int u = 0; u < QRC_BATCH; ++u) {
-          const int c = cb + u * nw;
-          const double w = tau * warp_sum(v[u]);
-          if (c >= n) continue;
-          double* wc = W + (long long)c * chunk - r0;
-          if (own && lane == 0) wc[j] -= w;
-          for (int i = i0 + lane; i < r1; i += 32) wc[i] -= w * vj[i];
-        }
+        if (c == j + 1) nsq[qq] = sq;
       }
       if (own && tid == 0) vj[j] = beta;
+    } else if (j + 1 < k) {
+      for (int qq = tid; qq < QS; qq += nt) {          // column j+1 untouched: squares as they are
+        const double* w1 = W + (long long)(j + 1) * ld - r0;
+        double sq = 0.0;
+        for (int i = max(r0, j + 2) + ((qq - max(r0, j + 2) % QS + QS) % QS); i < r1; i += QS) sq = fma(w1[i], w1[i], sq);
+        nsq[qq] = sq;
+      }
     }
     __syncthreads();
-    if (j + 1 < k && warp == 0) {                     // next column: norm partial and diagonal
-      const double* w1 = W + (long long)(j + 1) * chunk - r0;
+    if (j + 1 < k && tid == 0) {                      // next column: norm partial and diagonal
       double part = 0.0;
-      for (int i = max(r0, j + 2) + lane; i < r1; i += 32) part += w1[i] * w1[i];
-      part = warp_sum(part);
-      if (lane == 0) {
-        npart[1 - b] = part;
-        if (j + 1 >= r0 && j + 1 < r1) bcast[1 - b] = w1[j + 1];
-      }
+      for (int qq = 0; qq < QS; ++qq) part += nsq[qq];
+      npart[1 - b] = part;
+      if (j + 1 >= r0 && j + 1 < r1) bcast[1 - b] = W[(long long)(j + 1) * ld + (j + 1 - r0)];
     }
   }
   // Q = H_0 ... H_{k-1} [I_k; 0], accumulated backwards on the same row split.
   for (long long e = tid; e < (long long)rows * k; e += nt) {
     const int li = int(e % rows), c = int(e / rows);
-    Qw[(long long)c * chunk + li] = (r0 + li == c) ? 1.0 : 0.0;
+    Qw[(long long)c * ld + li] = (r0 + li == c) ? 1.0 : 0.0;
   }
   cluster.sync();
-  for (int j = k - 1, t = 0; j >= 0; --j, ++t) {
+  for (int j = k - 1, t0 = 0; j >= 0; --j, ++t0) {
     const double tau = tau_s[j];
     if (tau == 0.0) continue;
-    const int b = t & 1;
+    const int b = t0 & 1;
     const bool own = (j >= r0 && j < r1);
     const int i0 = max(r0, j + 1);
-    const double* vj = W + (long long)j * chunk - r0;
-    for (int c = j + warp; c < k; c += nw) {
-      const double* qc = Qw + (long long)c * chunk - r0;
+    const double* vj = W + (long long)j * ld - r0;
+    const int nc = k - j;
+    for (int t = tid; t < nc * QS; t += nt) {
+      const int c = j + t / QS, qq = t % QS;
+      const double* qc = Qw + (long long)c * ld - r0;
       double w = 0.0;
-      for (int i = i0 + lane; i < r1; i += 32) w += vj[i] * qc[i];
-      w = warp_sum(w);
-      if (lane == 0) wpart[b * n + c] = w + (own ? qc[j] : 0.0);
+      for (int i = i0 + ((qq - i0 % QS + QS) % QS); i < r1; i += QS) w = fma(vj[i], qc[i], w);
+      part4[(long long)c * QS + qq] = w;
+    }
+    __syncthreads();
+    for (int c = j + tid; c < k; c += nt) {
+      const double* qc = Qw + (long long)c * ld - r0;
+      double w = own ? qc[j] : 0.0;
+      for (int qq = 0; qq < QS; ++qq) w += part4[(long long)c * QS + qq];
+      wpart[b * n + c] = w;
     }
     cluster.sync();
-    for (int cb = j + warp; cb < k; cb += QRC_BATCH * nw) {
-      double v[QRC_BATCH];
-#pragma unroll
-      for (int u = 0; u < QRC_BATCH; ++u) {
-        const int c = cb + u * nw;
-        v[u] = (c < k && lane < C) ? *cluster.map_shared_rank(wpart + b * n + c, lane) : 0.0;
-      }
-#pragma unroll
-      for (int u = 0; u < QRC_BATCH; ++u) {
-        const int c = cb + u * nw;
-        const double w = tau * warp_sum(v[u]);
-        if (c >= k) continue;
-        double* qc = Qw + (long long)c * chunk - r0;
-        if (own && lane == 0) qc[j] -= w;
-        for (int i = i0 + lane; i < r1; i += 32) qc[i] -= w * vj[i];
-      }
+    for (int c = j + tid; c < k; c += nt) wfin[c] = tau * remote_sum(cluster, wpart + b * n + c, C);
+    __syncthreads();
+    for (int t = tid; t < nc * QS; t += nt) {
+      const int c = j + t / QS, qq = t % QS;
+      double* qc = Qw + (long long)c * ld - r0;
+      const double w = wfin[c];
+      if (own && qq == 0) qc[j] -= w;
+      for (int i = i0 + ((qq - i0 % QS + QS) % QS); i < r1; i += QS) qc[i] = fma(-w, vj[i], qc[i]);
     }
     __syncthreads();
   }
   for (long long e = tid; e < (long long)rows * k; e += nt) {
     const int li = int(e % rows), c = int(e / rows);
-    q.Q[(r0 + li) * q.qrs + c * q.qcs] = Qw[(long long)c * chunk + li];
+    q.Q[(r0 + li) * q.qrs + c * q.qcs] = Qw[(long long)c * ld + li];
   }
   if (q.R) {
     for (long long e = tid; e < (long long)rows * n; e += nt) {
       const int li = int(e % rows), j = int(e / rows), i = r0 + li;
-      if (i < k) q.R[(long long)i * n + j] = (j >= i) ? W[(long long)j * chunk + li] : 0.0;
+      if (i < k) q.R[(long long)i * n + j] = (j >= i) ? W[(long long)j * ld + li] : 0.0;
     }
   }
   cluster.sync();   // no CTA leaves while others may still read its shared memory
@@ -500,8 +527,9 @@ void qr_thin(Ctx& cx, int m, int n, const double* A, long long rs, long long cs,
   // Rows per CTA >= 32 keeps the per-column barrier cost below the FP64 work.
   int C = std::max(1, std::min(16, m / 32));
   while (C > 1 && (C & (C - 1))) --C;
-  const size_t base = sizeof(double) * (2 * size_t(n) + 4 + k);
-  auto full_of = [&](int c) { return base + sizeof(double) * ((size_t(m) + c - 1) / c) * (size_t(n) + k); };
+  const size_t base = sizeof(double) * (2 * size_t(n) + 4 + k + size_t(n) * QS + n + 2 + QS);
+  auto ld_of = [&](int c) { return (((m + c - 1) / c) | 1); };   // odd column stride
+  auto full_of = [&](int c) { return base + sizeof(double) * size_t(ld_of(c)) * (size_t(n) + k); };
   if (C > 1) C = std::min(C, qr_cluster_size(full_of(C) <= kQrSmemMax ? full_of(C) : base));
   while (C > 1 && (C & (C - 1))) --C;
   if (std::getenv("PEPS_VERBOSE")) std::fprintf(stderr, "[peps] qr %dx%d: cluster %d\n", m, n, C);
@@ -509,15 +537,14 @@ void qr_thin(Ctx& cx, int m, int n, const double* A, long long rs, long long cs,
   if (C <= 1) {
     k_qr_house<<<1, QR_THREADS, 0, cx.st>>>(a);
   } else {
-    const size_t chunk = (size_t(m) + C - 1) / C;
+    const int ld = ld_of(C);
     const size_t full = full_of(C);
     const int in_smem = full <= kQrSmemMax ? 1 : 0;
-    // the global-memory fallback uses [C][chunk][n] / [C][chunk][k] blocks
+    // the global-memory fallback uses [C][n][ld] / [C][k][ld] blocks
     if (!in_smem) {
-      double* w2 = cx.scratch(size_t(C) * chunk * (size_t(n) + k) + k + 64);
+      double* w2 = cx.scratch(size_t(C) * ld * (size_t(n) + k) + 64);
       a.W = w2;
-      a.Qw = w2 + size_t(C) * chunk * n;
-      a.tau = a.Qw + size_t(C) * chunk * k;
+      a.Qw = w2 + size_t(C) * ld * n;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
@@ -531,7 +558,7 @@ void qr_thin(Ctx& cx, int m, int n, const double* A, long long rs, long long cs,
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    PEPS_CUDA(cudaLaunchKernelEx(&cfg, k_qr_cluster, a, in_smem));
+    PEPS_CUDA(cudaLaunchKernelEx(&cfg, k_qr_cluster, a, in_smem, ld));
   }
   PEPS_CHECK_LAUNCH();
 }
