@@ -194,15 +194,9 @@ def run_ours(args, rank, world, dist):
         dev = float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-2)))
 
     total_ms = sum(times)
-    ms_step = total_ms / len(times)
-    e_ms = sum(etimes) / len(etimes)
-    if dist:
-        t = torch.tensor([ms_step, e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step, e_ms = float(t[0]), float(t[1])
     envs = WORKLOAD["Ly"] * WORKLOAD["Lx"]
-    value = world * envs / (ms_step * 1e-3)
-    e2e = world * envs / (e_ms * 1e-3)
+    ms_step, e_ms, value, e2e = aggregate(total_ms / len(times), sum(etimes) / len(etimes), envs, world,
+                                          dist, dev)
     if rank != 0:
         return None
 
@@ -265,6 +259,19 @@ def run_ours(args, rank, world, dist):
     if not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_sample(args, budget_s=args.cpu_budget)
     return res
+
+
+def aggregate(ms_step, e_ms, envs_per_rank, world, dist=None, device=None):
+    """Whole-job throughput of weak-scaled replicas: the slowest rank's step
+    time (max over ranks) bounds the job; every rank processed envs_per_rank."""
+    if dist is not None:
+        import torch
+        t = torch.tensor([ms_step, e_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step, e_ms = float(t[0]), float(t[1])
+    value = world * envs_per_rank / (ms_step * 1e-3)
+    e2e = world * envs_per_rank / (e_ms * 1e-3)
+    return ms_step, e_ms, value, e2e
 
 
 def cpu_sample(args, budget_s=20.0):
