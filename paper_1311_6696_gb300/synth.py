@@ -20,6 +20,8 @@ Generators
 * :func:`peps_gauss` -- entries ``0.5 + 0.1*N(0,1)`` by Box-Muller on the same
   stream, unit Frobenius norm (the 10x10 D=4 and 14x14 D=6 workloads).
 * :func:`peps_product` -- a D=1 product state (closed-form test cases).
+* :func:`peps_simple_update` -- a seeded simple-update (Section 3) Heisenberg
+  ground-state approximation (the 20x20 D=8 and 16x16 D=4 workloads).
 
 Tensors are filled in site-row-major order, each in C order over its ragged
 (effective) shape, drawing from one stream that continues across sites.
@@ -129,6 +131,8 @@ WORKLOADS = {
     "14x14_D6": dict(Ly=14, Lx=14, d=2, D=6, gen="gauss", seed=3),
     "20x20_D8": dict(Ly=20, Lx=20, d=2, D=8, gen="gauss", seed=4),
     "16x16_D4": dict(Ly=16, Lx=16, d=2, D=4, gen="gauss", seed=5),
+    "20x20_D8_su": dict(Ly=20, Lx=20, d=2, D=8, gen="su", seed=4),
+    "16x16_D4_su": dict(Ly=16, Lx=16, d=2, D=4, gen="su", seed=5),
 }
 
 
@@ -137,4 +141,144 @@ def workload(name: str, seed: int | None = None) -> np.ndarray:
     s = w["seed"] if seed is None else seed
     if w["gen"] == "uniform":
         return peps_uniform(w["Ly"], w["Lx"], w["d"], w["D"], s)
+    if w["gen"] == "su":
+        return peps_simple_update(w["Ly"], w["Lx"], w["D"], s)
     return peps_gauss(w["Ly"], w["Lx"], w["d"], w["D"], s)
+
+
+# ---------------------------------------------------------------------------
+# Simple-update imaginary-time evolution (input generator for the 20x20 D=8
+# and 16x16 D=4 workloads).  Section 3: tensors Gamma with diagonal bond
+# weights lambda; a nearest-neighbour gate acts on a pair using only the six
+# lambdas around it.  First-order Trotter over four bond sets (horizontal even
+# / odd columns, vertical even / odd rows); lambda normalised to lambda_1 = 1;
+# the start is a Neel product state whose zero entries are replaced by uniform
+# noise in [-0.01, 0.01] (Appendix B).  The PEPS handed out is A = Gamma with
+# sqrt(lambda) absorbed on every bond, each tensor scaled to unit norm.
+# Dense padded storage: outward (OBC) legs carry lambda = (1, 0, ..., 0).
+# ---------------------------------------------------------------------------
+def _heisenberg_gate(tau: float) -> np.ndarray:
+    """exp(-tau S.S) as a 4x4 matrix on (s_1, s_2)."""
+    h = 0.25 * np.array([[1.0, 0, 0, 0], [0, -1.0, 2.0, 0], [0, 2.0, -1.0, 0], [0, 0, 0, 1.0]])
+    w, v = np.linalg.eigh(h)
+    return (v * np.exp(-tau * w)) @ v.T
+
+
+def _su_pair(Ga, Gb, lam_a, lam_b, lam_ab, gate, D):
+    """Batched simple update of horizontal pairs.
+
+    Ga, Gb: (n, d, D, D, D, D) [s, u, l, dn, r]; lam_a = (up, left, down) of the
+    left site, lam_b = (up, down, right) of the right site, each (n, D);
+    lam_ab: (n, D).  Returns new Ga, Gb, lam_ab.
+    """
+    n, d = Ga.shape[0], Ga.shape[1]
+    inv = lambda l: np.where(l > 0, 1.0 / np.where(l > 0, l, 1.0), 0.0)
+    lu, ll, ld = lam_a
+    ru, rd, rr = lam_b
+    A = Ga * lu[:, None, :, None, None, None] * ll[:, None, None, :, None, None] \
+        * ld[:, None, None, None, :, None] * lam_ab[:, None, None, None, None, :]
+    B = Gb * ru[:, None, :, None, None, None] * rd[:, None, None, None, :, None] \
+        * rr[:, None, None, None, None, :]
+    # QR-reduce the outer legs: A -> [(u,l,dn), (s,r)], B -> [(u,dn,r), (t,l)]
+    Am = A.transpose(0, 2, 3, 4, 1, 5).reshape(n, D ** 3, d * D)
+    Bm = B.transpose(0, 2, 4, 5, 1, 3).reshape(n, D ** 3, d * D)
+    Qa, Ra = np.linalg.qr(Am)                         # Ra: (n, k, d*D)
+    Qb, Rb = np.linalg.qr(Bm)
+    k = Ra.shape[1]
+    Ra = Ra.reshape(n, k, d, D)
+    Rb = Rb.reshape(n, k, d, D)
+    th = np.einsum("nasr,nbtr->nasbt", Ra, Rb)        # shared bond contracted
+    G4 = gate.reshape(d, d, d, d)                     # [s', t', s, t]
+    th = np.einsum("pqst,nasbt->napbq", G4, th).reshape(n, k * d, k * d)
+    U, S, Vt = np.linalg.svd(th)
+    S = S[:, :D]
+    lam = S / S[:, :1]
+    Ua = U[:, :, :D].reshape(n, k, d, D)              # [a, s', r]
+    Vb = Vt[:, :D, :].reshape(n, D, k, d)             # [r, b, t']
+    An = np.einsum("nia,nasr->nisr", Qa, Ua).reshape(n, D, D, D, d, D)
+    Bn = np.einsum("nib,nrbt->nitr", Qb, Vb).reshape(n, D, D, D, d, D)
+    Ga = An.transpose(0, 4, 1, 2, 3, 5) * inv(lu)[:, None, :, None, None, None] \
+        * inv(ll)[:, None, None, :, None, None] * inv(ld)[:, None, None, None, :, None]
+    # Bn: [(u, dn, r), t, l] -> [t, u, l, dn, r]
+    Gb = Bn.transpose(0, 4, 1, 5, 2, 3) * inv(ru)[:, None, :, None, None, None] \
+        * inv(rd)[:, None, None, None, :, None] * inv(rr)[:, None, None, None, None, :]
+    return Ga, Gb, lam
+
+
+def peps_simple_update(Ly: int, Lx: int, D: int, seed: int, tau: float = 0.01, steps: int = 400,
+                       d: int = 2) -> np.ndarray:
+    """Seeded simple-update ground-state approximation of the spin-1/2
+    Heisenberg model (eq. 2), returned as dense OBC tensors."""
+    assert d == 2
+    rng_u = uniform01(seed, Ly * Lx * d * D ** 4) * 0.02 - 0.01
+    G = rng_u.reshape(Ly, Lx, d, D, D, D, D).copy()
+    for y in range(Ly):
+        for x in range(Lx):
+            du, dl, dd, dr = site_dims(Ly, Lx, y, x, D)
+            mask = np.zeros((d, D, D, D, D), dtype=bool)
+            mask[:, :du, :dl, :dd, :dr] = True
+            G[y, x][~mask] = 0.0
+            G[y, x, (x + y) % 2, 0, 0, 0, 0] = 1.0        # Neel product state
+    e1 = np.zeros(D)
+    e1[0] = 1.0
+    lh = np.zeros((Ly, max(Lx - 1, 0), D))
+    lh[..., :] = 1.0
+    lv = np.ones((max(Ly - 1, 0), Lx, D))
+    gate = _heisenberg_gate(tau)
+
+    def lam_up(y, x):
+        return lv[y - 1, x] if y > 0 else e1
+
+    def lam_dn(y, x):
+        return lv[y, x] if y < Ly - 1 else e1
+
+    def lam_lt(y, x):
+        return lh[y, x - 1] if x > 0 else e1
+
+    def lam_rt(y, x):
+        return lh[y, x] if x < Lx - 1 else e1
+
+    def hset(par):
+        return [(y, x) for y in range(Ly) for x in range(par, Lx - 1, 2)]
+
+    def vset(par):
+        return [(y, x) for y in range(par, Ly - 1, 2) for x in range(Lx)]
+
+    for _ in range(steps):
+        for par in (0, 1):
+            bonds = hset(par)
+            if bonds:
+                ys, xs = zip(*bonds)
+                ys, xs = np.array(ys), np.array(xs)
+                Ga, Gb = G[ys, xs], G[ys, xs + 1]
+                la = (np.stack([lam_up(y, x) for y, x in bonds]), np.stack([lam_lt(y, x) for y, x in bonds]),
+                      np.stack([lam_dn(y, x) for y, x in bonds]))
+                lb = (np.stack([lam_up(y, x + 1) for y, x in bonds]), np.stack([lam_dn(y, x + 1) for y, x in bonds]),
+                      np.stack([lam_rt(y, x + 1) for y, x in bonds]))
+                Ga, Gb, lam = _su_pair(Ga, Gb, la, lb, lh[ys, xs], gate, D)
+                G[ys, xs], G[ys, xs + 1], lh[ys, xs] = Ga, Gb, lam
+        for par in (0, 1):
+            bonds = vset(par)
+            if bonds:
+                # a vertical pair is a horizontal pair of the transposed lattice:
+                # [s,u,l,dn,r] -> [s,l,u,r,dn]
+                ys, xs = zip(*bonds)
+                ys, xs = np.array(ys), np.array(xs)
+                Ga = G[ys, xs].transpose(0, 1, 3, 2, 5, 4)
+                Gb = G[ys + 1, xs].transpose(0, 1, 3, 2, 5, 4)
+                la = (np.stack([lam_lt(y, x) for y, x in bonds]), np.stack([lam_up(y, x) for y, x in bonds]),
+                      np.stack([lam_rt(y, x) for y, x in bonds]))
+                lb = (np.stack([lam_lt(y + 1, x) for y, x in bonds]), np.stack([lam_rt(y + 1, x) for y, x in bonds]),
+                      np.stack([lam_dn(y + 1, x) for y, x in bonds]))
+                Ga, Gb, lam = _su_pair(Ga, Gb, la, lb, lv[ys, xs], gate, D)
+                G[ys, xs] = Ga.transpose(0, 1, 3, 2, 5, 4)
+                G[ys + 1, xs] = Gb.transpose(0, 1, 3, 2, 5, 4)
+                lv[ys, xs] = lam
+    A = G.copy()
+    for y in range(Ly):
+        for x in range(Lx):
+            t = A[y, x]
+            t = t * np.sqrt(lam_up(y, x))[None, :, None, None, None] * np.sqrt(lam_lt(y, x))[None, None, :, None, None] \
+                * np.sqrt(lam_dn(y, x))[None, None, None, :, None] * np.sqrt(lam_rt(y, x))[None, None, None, None, :]
+            A[y, x] = t / np.linalg.norm(t)
+    return A
