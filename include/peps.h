@@ -74,7 +74,9 @@ extern "C" {
 #define PEPS_VBOND 2        /* rho of bond (y,x)-(y+1,x):    d^2 x d^2, (Ly-1)*Lx values   */
 
 /* cluster closure outside the window */
-#define PEPS_CLOSURE_PLAIN   0   /* CU_0 separable boundaries (Section 4.1) */
+#define PEPS_CLOSURE_PLAIN   0   /* CU_0 separable boundaries (Section 4.1)                 */
+#define PEPS_CLOSURE_LEARNED 1   /* CU_0 matrices replaced by the learned closure's output   */
+#define PEPS_CLOSURE_WIDTH   256 /* hidden width of the learned closure used by peps_env_cluster */
 
 typedef struct {
     int Ly, Lx;          /* lattice size, >= 1 each                                   */
@@ -91,8 +93,9 @@ typedef struct {
     int sweeps;          /* PEPS_VAR half-sweeps; <= 0 selects 2 (L->R then R->L)      */
     int precision;       /* PEPS_PREC_*                                                */
     int n;               /* cluster window edge length (peps_env_cluster), >= 1        */
-    int closure;         /* PEPS_CLOSURE_PLAIN                                         */
-    const void* closure_weights;   /* reserved, must be NULL                           */
+    int closure;         /* PEPS_CLOSURE_PLAIN or PEPS_CLOSURE_LEARNED                 */
+    const void* closure_weights;   /* LEARNED: device float* weights (width 256), see  */
+                                   /* peps_mlp_param_count; else ignored               */
     unsigned long long seed;       /* keys the counter-based noise of the var start    */
 } peps_opts;
 
@@ -192,6 +195,46 @@ int peps_norm(const peps_lattice* lat, const peps_opts* opts,
  */
 int peps_cu0_noalloc(const double* A, int Ly, int Lx, int d, int D, double* sigma,
                      void* cuda_stream);
+
+/*
+ * Learned cluster closure (the paper has no learned part; built on its
+ * cluster scheme, Section 4.2).  A three-layer ReLU network of width W maps,
+ * for one outward leg of a cluster window, the site tensor just above the
+ * cut (d*D^4, zero-padded, legs [s,u,l,n,r] in the sweep's orientation),
+ * the CU_0 matrix sigma0 at that leg (D^2) and its Cholesky factor L0 (D^2)
+ * -- F = d*D^4 + 2*D^2 inputs -- to Y (D x D); the closure matrix is
+ * X X^T / ||X X^T||_F with X = L0 + Y, positive, and sigma0 when Y = 0.
+ * Weights (float32, device): W1[W][F] b1[W] W2[W][W] b2[W] W3[D^2][W] b3[D^2].
+ * The matrix products run on the tensor cores in BF16 with FP32 accumulation.
+ *
+ * peps_closure_data: training examples of one lattice.  Runs the four full
+ *   boundary sweeps at opts->chi and the CU_0 boundaries; for every
+ *   orientation o (top-down, bottom-up, left-right, right-left), cut r >= 1
+ *   and column x it writes the features (row of X, F floats) and the label
+ *   (row of Y, D^2 floats): the site matrix of the best product (D'=1)
+ *   approximation of the full boundary at that cut.  X, Y are device
+ *   pointers; with both NULL only *count is set.  D <= 8.
+ * peps_mlp_param_count: number of floats in the weight vector.
+ * peps_mlp_init: He-uniform hidden layers, zero biases and zero output layer.
+ * peps_mlp_loss_grad: mean over n of ||sigma - label||_F^2 and its gradient
+ *   (device float*, same layout as the weights); loss returned on the host.
+ * peps_mlp_train: AdamW (beta 0.9/0.999, eps 1e-8) on minibatches of `batch`
+ *   examples drawn by a seeded shuffle per epoch; *final_loss = mean
+ *   minibatch loss over the last min(steps, 20) steps.
+ * peps_mlp_predict: closure matrices (n x D^2, device float*).
+ * All synchronise the stream.
+ */
+int peps_closure_data(const peps_lattice* lat, const peps_opts* opts, float* X, float* Y,
+                      long long capacity, long long* count, void* cuda_stream);
+long long peps_mlp_param_count(int d, int D, int width);
+int peps_mlp_init(float* w, int d, int D, int width, unsigned long long seed, void* cuda_stream);
+int peps_mlp_loss_grad(const float* w, const float* X, const float* Y, long long n, int d, int D,
+                       int width, double* loss, float* grad, void* cuda_stream);
+int peps_mlp_train(float* w, const float* X, const float* Y, long long n, int d, int D, int width,
+                   int steps, int batch, float lr, float weight_decay, unsigned long long seed,
+                   double* final_loss, void* cuda_stream);
+int peps_mlp_predict(const float* w, const float* X, long long n, int d, int D, int width,
+                     float* sigma, void* cuda_stream);
 
 /* peps_env_ln_norm -- the norm recorded in a full env (PEPS_EINVAL for cluster envs). */
 int peps_env_ln_norm(const peps_env* env, double* ln_norm, int* sign, void* cuda_stream);

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "aux.cuh"
+#include "closure.cuh"
 #include "engine.cuh"
 #include "linalg.cuh"
 
@@ -178,8 +179,10 @@ Opts check_opts(const peps_opts* o, bool cluster) {
                "precision must be one of PEPS_PREC_FP64, _TF32, _BF16, _TF32X3, _BF16X3");
   if (o->precision != PEPS_PREC_FP64)
     PEPS_REQUIRE(tc_available(), "tensor-core precisions need an sm_103 (GB300) device");
-  PEPS_REQUIRE(o->closure == PEPS_CLOSURE_PLAIN && o->closure_weights == nullptr,
-               "closure must be PEPS_CLOSURE_PLAIN with NULL weights");
+  PEPS_REQUIRE(o->closure == PEPS_CLOSURE_PLAIN || o->closure == PEPS_CLOSURE_LEARNED,
+               "closure must be PEPS_CLOSURE_PLAIN or PEPS_CLOSURE_LEARNED");
+  PEPS_REQUIRE(o->closure == PEPS_CLOSURE_PLAIN || o->closure_weights != nullptr,
+               "PEPS_CLOSURE_LEARNED needs closure_weights (device float*)");
   if (cluster) PEPS_REQUIRE(o->n >= 1, "cluster size n must be >= 1");
   Opts r;
   r.chi = o->chi;
@@ -479,11 +482,10 @@ OLat sub(const OLat& f, int r0, int r1, int c0, int c1) {
   return s;
 }
 
-void cluster_env(Call& c, const peps_lattice* lat, const Opts& opt, int n, peps_env* env, Oriented& ori) {
-  Ctx& cx = c.cx;
+// CU_0 separable boundaries from all four sides (one CTA per side): sig[o] is
+// [L_o][W_o][D*D], matrix (r, x) on the up legs of row r of orientation o.
+void cu0_all_sides(Ctx& cx, const peps_lattice* lat, Oriented& ori, Arena& keep, double* sig[4]) {
   const int Ly = lat->Ly, Lx = lat->Lx, d = lat->d, D = lat->D, DM2 = D * D;
-  // CU_0 boundaries from all four sides (one CTA per side).
-  double* sig[4];
   Cu0Lattice cl[4];
   std::vector<std::vector<long long>> offs(4);
   std::vector<std::vector<int>> dims(4);
@@ -491,7 +493,7 @@ void cluster_env(Call& c, const peps_lattice* lat, const Opts& opt, int n, peps_
   fill(cx, closure_ones, (long long)std::max(Ly, Lx) * DM2, 1.0);   // 1x1 closures read entry 0
   for (int o = 0; o < 4; ++o) {
     const OLat& L = ori.o[o];
-    sig[o] = env->arena->dalloc(size_t(L.Ly) * L.Lx * DM2);
+    sig[o] = keep.dalloc(size_t(L.Ly) * L.Lx * DM2);
     offs[o].resize(size_t(L.Ly) * L.Lx);
     dims[o].resize(size_t(L.Ly) * L.Lx * 4);
     const double* base = L.sites[0].p;
@@ -523,6 +525,44 @@ void cluster_env(Call& c, const peps_lattice* lat, const Opts& opt, int n, peps_
     q.tol = 1e-13;
   }
   cu0_launch(cx, cl, 4);
+}
+
+// Rim positions (orientation o, cut r >= 1, column x), in that order.
+std::vector<RimSite> rim_sites(const Oriented& ori, double* const sig[4], int D) {
+  std::vector<RimSite> v;
+  for (int o = 0; o < 4; ++o) {
+    const OLat& L = ori.o[o];
+    for (int r = 1; r < L.Ly; ++r)
+      for (int x = 0; x < L.Lx; ++x) {
+        const SiteT& t = L.at(r - 1, x);
+        v.push_back(RimSite{t.p, t.du, t.dl, t.dn, t.dr, sig[o] + ((long long)r * L.Lx + x) * D * D});
+      }
+  }
+  return v;
+}
+
+void cluster_env(Call& c, const peps_lattice* lat, const Opts& opt, int n, peps_env* env, Oriented& ori,
+                 const float* closure_w) {
+  Ctx& cx = c.cx;
+  const int Ly = lat->Ly, Lx = lat->Lx, d = lat->d, D = lat->D, DM2 = D * D;
+  double* sig[4];
+  cu0_all_sides(cx, lat, ori, *env->arena, sig);
+  if (closure_w) {
+    // learned closure: predict every rim matrix, keep CU_0 where the prediction is unusable
+    MlpDims m;
+    m.d = d;
+    m.D = D;
+    m.W = PEPS_CLOSURE_WIDTH;
+    const std::vector<RimSite> rs = rim_sites(ori, sig, D);
+    const long long ne = (long long)rs.size();
+    float* X = cx.ws->falloc(size_t(ne) * m.F());
+    float* P = cx.ws->falloc(size_t(ne) * m.out());
+    closure_features(cx, m, rs.data(), ne, X);
+    mlp_predict(cx, m, closure_w, X, ne, P);
+    std::vector<double*> tg(ne);
+    for (long long e = 0; e < ne; ++e) tg[e] = const_cast<double*>(rs[e].sigma);
+    closure_apply(cx, D, P, tg.data(), ne);
+  }
   auto S = [&](int o, int r, int x, int dim) {
     const OLat& L = ori.o[o];
     return Mat{sig[o] + ((long long)r * L.Lx + x) * DM2, dim};
@@ -606,7 +646,8 @@ int run_env(const peps_lattice* lat, const peps_opts* opts, peps_env** out, void
     build_orientations(c.cx, lat, *env->arena, ori);
     const auto t0 = std::chrono::steady_clock::now();
     if (cluster)
-      cluster_env(c, lat, o, opts->n, env.get(), ori);
+      cluster_env(c, lat, o, opts->n, env.get(), ori,
+                  opts->closure == PEPS_CLOSURE_LEARNED ? static_cast<const float*>(opts->closure_weights) : nullptr);
     else
       full_env(c, lat, o, env.get(), ori);
     const auto t1 = std::chrono::steady_clock::now();
@@ -712,6 +753,141 @@ int peps_env_ln_norm(const peps_env* env, double* ln_norm, int* sign, void* cuda
     PEPS_CUDA(cudaStreamSynchronize(st));
     *ln_norm = h[0];
     *sign = int(h[1]);
+  });
+}
+
+int peps_closure_data(const peps_lattice* lat, const peps_opts* opts, float* X, float* Y, long long capacity,
+                      long long* count, void* cuda_stream) {
+  return guard([&] {
+    PEPS_REQUIRE(count != nullptr, "count is NULL");
+    require_device();
+    check_lattice(lat);
+    const Opts o = check_opts(opts, false);
+    PEPS_REQUIRE(lat->D <= 8, "learned closure supports D <= 8");
+    long long ne = 0;
+    ne += (long long)(lat->Ly - 1) * lat->Lx * 2 + (long long)(lat->Lx - 1) * lat->Ly * 2;
+    *count = ne;
+    if (X == nullptr && Y == nullptr) return;
+    PEPS_REQUIRE(X != nullptr && Y != nullptr && capacity >= ne, "X, Y must hold count examples");
+    Call c(cuda_stream);
+    Arena keep(c.st, size_t(64) << 20, false);
+    Oriented ori;
+    build_orientations(c.cx, lat, keep, ori);
+    // full boundaries at bond chi from all four sides
+    Lanes lanes(c, o, lat->d, lat->D, std::max(lat->Ly, lat->Lx));
+    double* lnacc = c.ws.dalloc(4);
+    fill(c.cx, lnacc, 4, 0.0);
+    std::vector<Mps> b[4];
+    lanes.join();
+    lanes.fork();
+    run_lanes(lanes, 4, [&](Lane& L, int oi) {
+      b[oi] = L.eng->sweep(ori.o[oi], oi, ori.o[oi].Ly - 1, lnacc + oi, keep);
+    });
+    lanes.join();
+    double* sig[4];
+    cu0_all_sides(c.cx, lat, ori, keep, sig);
+    MlpDims m;
+    m.d = lat->d;
+    m.D = lat->D;
+    const std::vector<RimSite> rs = rim_sites(ori, sig, lat->D);
+    closure_features(c.cx, m, rs.data(), ne, X);
+    // labels: best product approximation of each full boundary (one job per cut)
+    std::vector<Rank1Job> jobs;
+    std::vector<std::vector<const double*>> ptrs;
+    std::vector<std::vector<int>> bonds;
+    long long e0 = 0;
+    int maxchi = 1, maxL = 1;
+    for (int oi = 0; oi < 4; ++oi) {
+      const OLat& L = ori.o[oi];
+      for (int r = 1; r < L.Ly; ++r) {
+        const Mps& T = b[oi][r];
+        std::vector<const double*> pp(T.p.begin(), T.p.end());
+        std::vector<int> bd;
+        for (int x = 0; x < L.Lx; ++x) bd.push_back(T.dims[x][0]);
+        bd.push_back(T.dims[L.Lx - 1][3]);
+        for (int v : bd) maxchi = std::max(maxchi, v);
+        maxL = std::max(maxL, L.Lx);
+        auto* dp = static_cast<const double**>(c.ws.alloc(sizeof(double*) * pp.size()));
+        auto* db = static_cast<int*>(c.ws.alloc(sizeof(int) * bd.size()));
+        PEPS_CUDA(cudaMemcpyAsync(dp, pp.data(), sizeof(double*) * pp.size(), cudaMemcpyHostToDevice, c.st));
+        PEPS_CUDA(cudaMemcpyAsync(db, bd.data(), sizeof(int) * bd.size(), cudaMemcpyHostToDevice, c.st));
+        PEPS_CUDA(cudaStreamSynchronize(c.st));
+        jobs.push_back(Rank1Job{dp, db, L.Lx, Y + e0 * m.out()});
+        e0 += L.Lx;
+      }
+    }
+    rank1_labels(c.cx, lat->D, maxchi, maxL, jobs.data(), int(jobs.size()));
+    c.finish();
+  });
+}
+
+long long peps_mlp_param_count(int d, int D, int width) {
+  MlpDims m;
+  m.d = d;
+  m.D = D;
+  m.W = width;
+  return m.params();
+}
+
+static MlpDims mlp_dims(int d, int D, int width) {
+  PEPS_REQUIRE(d >= 1 && d <= 4 && D >= 1 && D <= 8 && width >= 16 && width <= 4096, "bad MLP dims");
+  MlpDims m;
+  m.d = d;
+  m.D = D;
+  m.W = width;
+  return m;
+}
+
+int peps_mlp_init(float* w, int d, int D, int width, unsigned long long seed, void* cuda_stream) {
+  return guard([&] {
+    PEPS_REQUIRE(w != nullptr, "w is NULL");
+    require_device();
+    const MlpDims m = mlp_dims(d, D, width);
+    Call c(cuda_stream);
+    mlp_init(c.cx, m, w, seed);
+    c.finish();
+  });
+}
+
+int peps_mlp_loss_grad(const float* w, const float* X, const float* Y, long long n, int d, int D, int width,
+                       double* loss, float* grad, void* cuda_stream) {
+  return guard([&] {
+    PEPS_REQUIRE(w && X && Y && loss && grad && n > 0, "NULL argument or empty batch");
+    require_device();
+    PEPS_REQUIRE(tc_available(), "the learned closure runs on sm_103 tensor cores");
+    const MlpDims m = mlp_dims(d, D, width);
+    Call c(cuda_stream);
+    double* dl = c.ws.dalloc(1);
+    mlp_loss_grad(c.cx, m, w, X, Y, n, dl, grad);
+    PEPS_CUDA(cudaMemcpyAsync(loss, dl, sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    c.finish();
+  });
+}
+
+int peps_mlp_train(float* w, const float* X, const float* Y, long long n, int d, int D, int width, int steps,
+                   int batch, float lr, float weight_decay, unsigned long long seed, double* final_loss,
+                   void* cuda_stream) {
+  return guard([&] {
+    PEPS_REQUIRE(w && X && Y && n > 0, "NULL argument or empty training set");
+    require_device();
+    PEPS_REQUIRE(tc_available(), "the learned closure runs on sm_103 tensor cores");
+    const MlpDims m = mlp_dims(d, D, width);
+    Call c(cuda_stream);
+    mlp_train(c.cx, m, w, X, Y, n, steps, batch, lr, weight_decay, seed, final_loss);
+    c.finish();
+  });
+}
+
+int peps_mlp_predict(const float* w, const float* X, long long n, int d, int D, int width, float* sigma,
+                     void* cuda_stream) {
+  return guard([&] {
+    PEPS_REQUIRE(w && X && sigma, "NULL argument");
+    require_device();
+    PEPS_REQUIRE(tc_available(), "the learned closure runs on sm_103 tensor cores");
+    const MlpDims m = mlp_dims(d, D, width);
+    Call c(cuda_stream);
+    mlp_predict(c.cx, m, w, X, n, sigma);
+    c.finish();
   });
 }
 

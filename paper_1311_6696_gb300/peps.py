@@ -26,8 +26,10 @@ EXPORTS = [
     "peps_env_full", "peps_env_cluster", "peps_expect_local", "peps_env_rho", "peps_norm",
     "peps_env_ln_norm", "peps_env_free", "peps_last_error", "peps_profile_enable",
     "peps_profile_reset", "peps_profile_count", "peps_profile_name", "peps_profile_read",
-    "peps_cu0_noalloc",
+    "peps_cu0_noalloc", "peps_closure_data", "peps_mlp_param_count", "peps_mlp_init",
+    "peps_mlp_loss_grad", "peps_mlp_train", "peps_mlp_predict",
 ]
+CLOSURE_WIDTH = 256
 
 
 class PepsError(RuntimeError):
@@ -69,6 +71,16 @@ def _load():
     lib.peps_profile_read.argtypes = [C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.peps_cu0_noalloc.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P]
+    lib.peps_closure_data.argtypes = [C.POINTER(Lattice), C.POINTER(Opts), P, P, C.c_longlong,
+                                      C.POINTER(C.c_longlong), P]
+    lib.peps_mlp_param_count.argtypes = [C.c_int, C.c_int, C.c_int]
+    lib.peps_mlp_param_count.restype = C.c_longlong
+    lib.peps_mlp_init.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_ulonglong, P]
+    lib.peps_mlp_loss_grad.argtypes = [P, P, P, C.c_longlong, C.c_int, C.c_int, C.c_int,
+                                       C.POINTER(C.c_double), P, P]
+    lib.peps_mlp_train.argtypes = [P, P, P, C.c_longlong, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                   C.c_float, C.c_float, C.c_ulonglong, C.POINTER(C.c_double), P]
+    lib.peps_mlp_predict.argtypes = [P, P, C.c_longlong, C.c_int, C.c_int, C.c_int, P, P]
     return lib
 
 
@@ -114,10 +126,11 @@ class _Input:
         self.lat = Lattice(Ly, Lx, d, D, dt, ptr, dev)
 
 
-def _opts(chi, mode, sweeps, precision, n, seed):
+def _opts(chi, mode, sweeps, precision, n, seed, closure_weights=None):
+    learned = closure_weights is not None
     return Opts(int(chi), MODE[mode] if isinstance(mode, str) else int(mode), int(sweeps),
-                PREC[precision] if isinstance(precision, str) else int(precision), int(n), 0, None,
-                int(seed))
+                PREC[precision] if isinstance(precision, str) else int(precision), int(n),
+                1 if learned else 0, int(closure_weights.data_ptr()) if learned else None, int(seed))
 
 
 class Env:
@@ -181,11 +194,12 @@ def env_full(A, chi: int, mode="svd", sweeps: int = 2, precision="fp64", seed: i
 
 
 def env_cluster(A, n: int, chi: int, mode="svd", sweeps: int = 2, precision="fp64", seed: int = 0,
-                stream=None, device=None) -> Env:
-    """Cluster environments (window n x n around every site); see peps_env_cluster."""
+                stream=None, device=None, closure_weights=None) -> Env:
+    """Cluster environments (window n x n around every site); see peps_env_cluster.
+    closure_weights: a float32 CUDA tensor of learned-closure weights (width 256)."""
     _set_device(device)
     inp = _Input(A)
-    o = _opts(chi, mode, sweeps, precision, n, seed)
+    o = _opts(chi, mode, sweeps, precision, n, seed, closure_weights)
     h = C.c_void_p()
     _check(lib.peps_env_cluster(C.byref(inp.lat), C.byref(o), C.byref(h), _stream_ptr(stream)))
     return Env(h.value, (inp.lat.Ly, inp.lat.Lx, inp.lat.d), stream)
@@ -211,6 +225,59 @@ def cu0_noalloc(A_dev, sigma_dev, stream=None):
     assert A_dev.is_contiguous() and sigma_dev.is_contiguous()
     assert tuple(sigma_dev.shape) == (Ly, Lx, D, D)
     _check(lib.peps_cu0_noalloc(A_dev.data_ptr(), Ly, Lx, d, D, sigma_dev.data_ptr(), _stream_ptr(stream)))
+
+
+# ---------------------------------------------------------------- learned closure
+def closure_data(A, chi: int, mode="svd", precision="fp64", stream=None):
+    """(X, Y) float32 CUDA tensors of closure features and labels for lattice A."""
+    import torch
+    inp = _Input(A)
+    o = _opts(chi, mode, 2, precision, 1, 0)
+    cnt = C.c_longlong()
+    _check(lib.peps_closure_data(C.byref(inp.lat), C.byref(o), None, None, 0, C.byref(cnt), _stream_ptr(stream)))
+    d, D = inp.lat.d, inp.lat.D
+    F = d * D ** 4 + 2 * D * D
+    X = torch.zeros((cnt.value, F), dtype=torch.float32, device="cuda")
+    Y = torch.zeros((cnt.value, D * D), dtype=torch.float32, device="cuda")
+    _check(lib.peps_closure_data(C.byref(inp.lat), C.byref(o), X.data_ptr(), Y.data_ptr(), cnt.value,
+                                 C.byref(cnt), _stream_ptr(stream)))
+    return X, Y
+
+
+def mlp_param_count(d: int, D: int, width: int = CLOSURE_WIDTH) -> int:
+    return int(lib.peps_mlp_param_count(d, D, width))
+
+
+def mlp_init(d: int, D: int, width: int = CLOSURE_WIDTH, seed: int = 0, stream=None):
+    import torch
+    w = torch.zeros(mlp_param_count(d, D, width), dtype=torch.float32, device="cuda")
+    _check(lib.peps_mlp_init(w.data_ptr(), d, D, width, int(seed), _stream_ptr(stream)))
+    return w
+
+
+def mlp_loss_grad(w, X, Y, d: int, D: int, width: int = CLOSURE_WIDTH, stream=None):
+    import torch
+    g = torch.zeros_like(w)
+    loss = C.c_double()
+    _check(lib.peps_mlp_loss_grad(w.data_ptr(), X.data_ptr(), Y.data_ptr(), X.shape[0], d, D, width,
+                                  C.byref(loss), g.data_ptr(), _stream_ptr(stream)))
+    return loss.value, g
+
+
+def mlp_train(w, X, Y, d: int, D: int, width: int = CLOSURE_WIDTH, steps: int = 200, batch: int = 256,
+              lr: float = 1e-3, weight_decay: float = 1e-4, seed: int = 0, stream=None) -> float:
+    loss = C.c_double()
+    _check(lib.peps_mlp_train(w.data_ptr(), X.data_ptr(), Y.data_ptr(), X.shape[0], d, D, width, steps, batch,
+                              lr, weight_decay, int(seed), C.byref(loss), _stream_ptr(stream)))
+    return loss.value
+
+
+def mlp_predict(w, X, d: int, D: int, width: int = CLOSURE_WIDTH, stream=None):
+    import torch
+    out = torch.zeros((X.shape[0], D * D), dtype=torch.float32, device="cuda")
+    _check(lib.peps_mlp_predict(w.data_ptr(), X.data_ptr(), X.shape[0], d, D, width, out.data_ptr(),
+                                _stream_ptr(stream)))
+    return out
 
 
 # ---------------------------------------------------------------- instrumentation
