@@ -247,6 +247,41 @@ void peps_env_free(peps_env* env);
 const char* peps_last_error(void);
 
 /*
+ * Recorded plans.  The paper has no counterpart: a plan is the sweep of
+ * peps_env_full (cluster = 0) or peps_env_cluster (cluster != 0) recorded
+ * once as a CUDA graph and replayed, so that the thousands of small
+ * launches of a call cost one graph launch.  Every bond dimension, window
+ * and launch shape depends on the lattice shape and the options only, and
+ * every data-dependent quantity (norms, log-scales, convergence) stays on
+ * the device, so the recorded graph is valid for any tensor values.
+ *
+ * peps_plan_create: lat->A must be device memory (on_device = 1).  The call
+ *   first runs the plain computation once (validating the input, including
+ *   the OBC rule), then records.  The plan keeps lat->A's address and
+ *   opts->closure_weights' address: the caller keeps both buffers alive and
+ *   may overwrite their contents between runs (same shapes).  Records on an
+ *   internal stream; must not overlap another library call on the same
+ *   device.  *out is NULL on failure.
+ * peps_plan_run: replays the whole computation on cuda_stream, then
+ *   synchronises it and returns the status (PEPS_ECONVERGE, PEPS_ETIMEOUT,
+ *   PEPS_EINVAL for a degenerate state, as the plain calls).
+ * peps_plan_env: the plan's environment handle (owned by the plan, valid
+ *   until peps_plan_free; its contents are those of the last run).  Use it
+ *   with peps_expect_local, peps_env_rho, peps_env_ln_norm; never pass it to
+ *   peps_env_free.
+ * peps_plan_launches: kernel launches in one replay.
+ * peps_plan_free: synchronises the device, releases the graph and its
+ *   memory; NULL is accepted.
+ */
+typedef struct peps_plan peps_plan;
+int peps_plan_create(const peps_lattice* lat, const peps_opts* opts, int cluster, peps_plan** out,
+                     void* cuda_stream);
+int peps_plan_run(peps_plan* plan, void* cuda_stream);
+const peps_env* peps_plan_env(const peps_plan* plan);
+long long peps_plan_launches(const peps_plan* plan);
+void peps_plan_free(peps_plan* plan);
+
+/*
  * Instrumentation (library-wide, not per handle).
  *   peps_profile_enable(mask): bit i of mask enables timing of kernel class
  *   i -- a CUDA event pair is recorded around each launch of that class, on

@@ -2,6 +2,7 @@
 // repacking into the four sweep orientations, the full / cluster / norm
 // drivers, and kernel-class instrumentation.  No exception crosses this file.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -69,6 +70,14 @@ Prof& prof() {
 // Start event of the launch in flight, per class and per host thread.
 thread_local cudaEvent_t t_open_ev[K_NCLASS] = {};
 
+// Counters of the graph being recorded (launch, flop and byte counts per
+// class); while set, launches are counted there and not timed.
+struct Counts {
+  long long launches[K_NCLASS] = {};
+  double flops[K_NCLASS] = {}, bytes[K_NCLASS] = {};
+};
+std::atomic<Counts*> g_recording{nullptr};
+
 thread_local std::string g_err;
 
 int fail(int code, const std::string& msg) {
@@ -98,6 +107,12 @@ int peps_set_error(int code, const std::string& msg) { return fail(code, msg); }
 void prof_launch(KClass c, cudaStream_t st, double flops, double bytes) {
   Prof& p = prof();
   std::lock_guard<std::mutex> g(p.mu);
+  if (Counts* rc = g_recording.load()) {
+    rc->launches[c]++;
+    rc->flops[c] += flops;
+    rc->bytes[c] += bytes;
+    return;
+  }
   p.launches[c]++;
   p.flops[c] += flops;
   p.bytes[c] += bytes;
@@ -110,6 +125,7 @@ void prof_launch(KClass c, cudaStream_t st, double flops, double bytes) {
 void prof_done(KClass c, cudaStream_t st) {
   Prof& p = prof();
   std::lock_guard<std::mutex> g(p.mu);
+  if (g_recording.load()) return;
   if ((p.mask & (1u << c)) && t_open_ev[c]) {
     cudaEvent_t e = p.get();
     cudaEventRecord(e, st);
@@ -136,15 +152,20 @@ struct Call {
   cudaStream_t st;
   Arena ws;
   Ctx cx;
-  explicit Call(void* stream) : st(static_cast<cudaStream_t>(stream)), ws(st), cx(st, &ws) {
-    cx.flag = static_cast<int*>(ws.alloc(sizeof(int)));
+  // persist: set while recording a graph; the status word and staged host
+  // data then live in memory that outlives the recording.
+  explicit Call(void* stream, Arena* persist = nullptr)
+      : st(static_cast<cudaStream_t>(stream)), ws(st), cx(st, &ws) {
+    cx.persist = persist;
+    cx.flag = static_cast<int*>(persist ? persist->alloc(sizeof(int)) : ws.alloc(sizeof(int)));
     PEPS_CUDA(cudaMemsetAsync(cx.flag, 0, sizeof(int), st));
     cx.tmp = ws.dalloc(8);
   }
   // Synchronise and turn the device status word into a status code.
-  void finish() {
+  void finish() { read_status(cx.flag, st); }
+  static void read_status(const int* flag, cudaStream_t st) {
     int h = 0;
-    PEPS_CUDA(cudaMemcpyAsync(&h, cx.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PEPS_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     PEPS_CUDA(cudaStreamSynchronize(st));
     if (h & FLAG_SVD_NOCONV) throw Error(PEPS_ECONVERGE, "Jacobi SVD did not converge within its sweep cap");
     if (h & FLAG_CU0_NOCONV) throw Error(PEPS_ECONVERGE, "CU_0 separable boundary did not converge within 200 half-sweeps");
@@ -242,8 +263,10 @@ void build_orientations(Ctx& cx, const peps_lattice* in, Arena& keep, Oriented& 
     PEPS_CUDA(cudaPointerGetAttributes(&at, in->A));
     PEPS_REQUIRE(at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged,
                  "on_device is set but A is not a device pointer");
-    const long long bad = obc_violations_device(cx, in->A, in->dtype == PEPS_F32, Ly, Lx, d, D);
-    PEPS_REQUIRE(bad == 0, "A has " + std::to_string(bad) + " nonzero entries on outward (OBC) legs");
+    if (!cx.persist) {   // a recorded graph was validated by the plain call made before it
+      const long long bad = obc_violations_device(cx, in->A, in->dtype == PEPS_F32, Ly, Lx, d, D);
+      PEPS_REQUIRE(bad == 0, "A has " + std::to_string(bad) + " nonzero entries on outward (OBC) legs");
+    }
   }
   out.one = keep.dalloc(1);
   fill(cx, out.one, 1, 1.0);
@@ -320,12 +343,12 @@ std::unique_ptr<peps_env> new_env(const peps_lattice* lat, int kind, cudaStream_
 // on a small pool of non-blocking streams, each with its own workspace and
 // engine, forked from and joined back to the caller's stream with events.
 // ---------------------------------------------------------------------------
-// Number of lanes: PEPS_LANES (1..8) if set, else 4.
+// Number of lanes: PEPS_LANES (1..64) if set, else 4.
 int lane_count() {
   static int n = [] {
     const char* e = std::getenv("PEPS_LANES");
     const int v = e ? std::atoi(e) : 4;
-    return v < 1 ? 1 : (v > 8 ? 8 : v);
+    return v < 1 ? 1 : (v > 64 ? 64 : v);
   }();
   return n;
 }
@@ -374,6 +397,7 @@ struct Lanes {
       a.ws = std::make_unique<Arena>(a.st);
       a.cx = std::make_unique<Ctx>(a.st, a.ws.get());
       a.cx->flag = c.cx.flag;
+      a.cx->persist = c.cx.persist;
       a.cx->tmp = a.ws->dalloc(8);
       a.eng = std::make_unique<Engine>(*a.cx, opt, d, D, Lmax);
     }
@@ -387,13 +411,19 @@ struct Lanes {
     for (auto& a : l) stream_after(main, a.st);
   }
   ~Lanes() {
-    // Lane workspaces are freed on their own streams after their work; the
-    // caller's stream already waits for them (join), and the memory returns
-    // to the stream-ordered pool.
+    // Lane workspaces are freed on their own streams after their work, and
+    // the caller's stream waits for those frees too (a recorded graph must
+    // end with every lane joined back).
     for (auto& a : l) {
       a.eng.reset();
       a.cx.reset();
       a.ws.reset();
+      cudaEvent_t e;
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
+        cudaEventRecord(e, a.st);
+        cudaStreamWaitEvent(main, e, 0);
+        cudaEventDestroy(e);
+      }
     }
   }
 };
@@ -504,10 +534,8 @@ void cu0_all_sides(Ctx& cx, const peps_lattice* lat, Oriented& ori, Arena& keep,
       dims[o][4 * i + 2] = L.sites[i].dn;
       dims[o][4 * i + 3] = L.sites[i].dr;
     }
-    auto* doff = static_cast<long long*>(cx.ws->alloc(sizeof(long long) * offs[o].size()));
-    auto* ddim = static_cast<int*>(cx.ws->alloc(sizeof(int) * dims[o].size()));
-    PEPS_CUDA(cudaMemcpyAsync(doff, offs[o].data(), sizeof(long long) * offs[o].size(), cudaMemcpyHostToDevice, cx.st));
-    PEPS_CUDA(cudaMemcpyAsync(ddim, dims[o].data(), sizeof(int) * dims[o].size(), cudaMemcpyHostToDevice, cx.st));
+    auto* doff = static_cast<const long long*>(stage(cx, offs[o].data(), sizeof(long long) * offs[o].size()));
+    auto* ddim = static_cast<const int*>(stage(cx, dims[o].data(), sizeof(int) * dims[o].size()));
     Cu0Lattice& q = cl[o];
     q.Ly = L.Ly;
     q.Lx = L.Lx;
@@ -633,6 +661,17 @@ void cluster_env(Call& c, const peps_lattice* lat, const Opts& opt, int n, peps_
   e.has_norm = false;
 }
 
+// The whole environment computation of one call, enqueued on c's stream.
+void compute(Call& c, const peps_lattice* lat, const peps_opts* opts, const Opts& o, bool cluster, peps_env* env) {
+  Oriented ori;
+  build_orientations(c.cx, lat, *env->arena, ori);
+  if (cluster)
+    cluster_env(c, lat, o, opts->n, env, ori,
+                opts->closure == PEPS_CLOSURE_LEARNED ? static_cast<const float*>(opts->closure_weights) : nullptr);
+  else
+    full_env(c, lat, o, env, ori);
+}
+
 int run_env(const peps_lattice* lat, const peps_opts* opts, peps_env** out, void* stream, bool cluster) {
   if (out) *out = nullptr;
   return guard([&] {
@@ -642,14 +681,8 @@ int run_env(const peps_lattice* lat, const peps_opts* opts, peps_env** out, void
     const Opts o = check_opts(opts, cluster);
     Call c(stream);
     auto env = new_env(lat, cluster ? 1 : 0, c.st);
-    Oriented ori;
-    build_orientations(c.cx, lat, *env->arena, ori);
     const auto t0 = std::chrono::steady_clock::now();
-    if (cluster)
-      cluster_env(c, lat, o, opts->n, env.get(), ori,
-                  opts->closure == PEPS_CLOSURE_LEARNED ? static_cast<const float*>(opts->closure_weights) : nullptr);
-    else
-      full_env(c, lat, o, env.get(), ori);
+    compute(c, lat, opts, o, cluster, env.get());
     const auto t1 = std::chrono::steady_clock::now();
     c.finish();
     if (std::getenv("PEPS_VERBOSE")) {
@@ -663,6 +696,19 @@ int run_env(const peps_lattice* lat, const peps_opts* opts, peps_env** out, void
 }
 
 }  // namespace
+
+// A recorded environment computation: the CUDA graph, the memory it writes
+// its results and status into, and the kernel counts of one replay.
+struct peps_plan {
+  int device = 0;
+  std::unique_ptr<Arena> persist;   // status word and staged shape data (outlives the recording)
+  std::unique_ptr<peps_env> env;    // results, rewritten by every replay
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int* flag = nullptr;
+  long long nodes = 0;
+  Counts counts;                    // kernel launches (and their flops) in one replay
+};
 
 // ---------------------------------------------------------------------------
 // C ABI
@@ -807,11 +853,8 @@ int peps_closure_data(const peps_lattice* lat, const peps_opts* opts, float* X, 
         bd.push_back(T.dims[L.Lx - 1][3]);
         for (int v : bd) maxchi = std::max(maxchi, v);
         maxL = std::max(maxL, L.Lx);
-        auto* dp = static_cast<const double**>(c.ws.alloc(sizeof(double*) * pp.size()));
-        auto* db = static_cast<int*>(c.ws.alloc(sizeof(int) * bd.size()));
-        PEPS_CUDA(cudaMemcpyAsync(dp, pp.data(), sizeof(double*) * pp.size(), cudaMemcpyHostToDevice, c.st));
-        PEPS_CUDA(cudaMemcpyAsync(db, bd.data(), sizeof(int) * bd.size(), cudaMemcpyHostToDevice, c.st));
-        PEPS_CUDA(cudaStreamSynchronize(c.st));
+        auto* dp = static_cast<const double* const*>(stage(c.cx, pp.data(), sizeof(double*) * pp.size()));
+        auto* db = static_cast<const int*>(stage(c.cx, bd.data(), sizeof(int) * bd.size()));
         jobs.push_back(Rank1Job{dp, db, L.Lx, Y + e0 * m.out()});
         e0 += L.Lx;
       }
@@ -904,6 +947,116 @@ void peps_env_free(peps_env* env) {
 }
 
 const char* peps_last_error(void) { return g_err.c_str(); }
+
+// ---------------------------------------------------------------------------
+// Recorded plans (CUDA graphs)
+// ---------------------------------------------------------------------------
+int peps_plan_create(const peps_lattice* lat, const peps_opts* opts, int cluster, peps_plan** out,
+                     void* cuda_stream) {
+  if (out) *out = nullptr;
+  return guard([&] {
+    PEPS_REQUIRE(out != nullptr, "out is NULL");
+    require_device();
+    check_lattice(lat);
+    PEPS_REQUIRE(lat->on_device, "a plan reads its lattice from device memory (on_device = 1)");
+    const bool cl = cluster != 0;
+    const Opts o = check_opts(opts, cl);
+    {
+      // One plain call validates the input and performs every one-time set-up
+      // (kernel attributes, cluster occupancy queries) outside the recording.
+      peps_env* probe = nullptr;
+      const int rc = run_env(lat, opts, &probe, cuda_stream, cl);
+      peps_env_free(probe);
+      if (rc != PEPS_OK) throw Error(rc, g_err);
+    }
+    static std::mutex record_mu;   // one recording at a time (shared lane streams)
+    std::lock_guard<std::mutex> lk(record_mu);
+    auto plan = std::make_unique<peps_plan>();
+    PEPS_CUDA(cudaGetDevice(&plan->device));
+    plan->persist = std::make_unique<Arena>(nullptr, size_t(1) << 20, /*async=*/false);
+    cudaStream_t cs = nullptr;
+    PEPS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    struct Cleanup {
+      cudaStream_t s;
+      ~Cleanup() {
+        g_recording.store(nullptr);
+        cudaStreamDestroy(s);
+      }
+    } cleanup{cs};
+    g_recording.store(&plan->counts);
+    PEPS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    try {
+      Call c(cs, plan->persist.get());
+      plan->flag = c.cx.flag;
+      plan->env = new_env(lat, cl ? 1 : 0, cs);
+      compute(c, lat, opts, o, cl, plan->env.get());
+    } catch (...) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(cs, &g);
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      throw;
+    }
+    PEPS_CUDA(cudaStreamEndCapture(cs, &plan->graph));
+    g_recording.store(nullptr);
+    size_t nodes = 0;
+    PEPS_CUDA(cudaGraphGetNodes(plan->graph, nullptr, &nodes));
+    plan->nodes = (long long)nodes;
+    const auto t0 = std::chrono::steady_clock::now();
+    PEPS_CUDA(cudaGraphInstantiate(&plan->exec, plan->graph, 0));
+    if (std::getenv("PEPS_VERBOSE"))
+      std::fprintf(stderr, "[peps] plan: %zu graph nodes, instantiated in %.1f ms\n", nodes,
+                   std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+    *out = plan.release();
+  });
+}
+
+int peps_plan_run(peps_plan* plan, void* cuda_stream) {
+  return guard([&] {
+    PEPS_REQUIRE(plan != nullptr && plan->exec != nullptr, "plan is NULL");
+    int cur = 0;
+    PEPS_CUDA(cudaGetDevice(&cur));
+    PEPS_REQUIRE(cur == plan->device, "the plan was recorded on another device");
+    const cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    PEPS_CUDA(cudaGraphLaunch(plan->exec, st));
+    {
+      Prof& p = prof();
+      std::lock_guard<std::mutex> g(p.mu);
+      for (int i = 0; i < K_NCLASS; ++i) {
+        p.launches[i] += plan->counts.launches[i];
+        p.flops[i] += plan->counts.flops[i];
+        p.bytes[i] += plan->counts.bytes[i];
+      }
+    }
+    Call::read_status(plan->flag, st);
+  });
+}
+
+const peps_env* peps_plan_env(const peps_plan* plan) { return plan ? plan->env.get() : nullptr; }
+
+long long peps_plan_launches(const peps_plan* plan) {
+  if (!plan) return 0;
+  long long n = 0;
+  for (int i = 0; i < K_NCLASS; ++i) n += plan->counts.launches[i];
+  return n;
+}
+
+void peps_plan_free(peps_plan* plan) {
+  if (!plan) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(plan->device);
+  cudaDeviceSynchronize();
+  if (plan->exec) cudaGraphExecDestroy(plan->exec);
+  if (plan->graph) cudaGraphDestroy(plan->graph);
+  plan->exec = nullptr;
+  plan->graph = nullptr;
+  plan->env.reset();
+  plan->persist.reset();
+  cudaDeviceSynchronize();
+  cudaSetDevice(cur);
+  delete plan;
+}
 
 void peps_profile_enable(int mask) {
   Prof& p = prof();

@@ -459,13 +459,31 @@ __global__ void __launch_bounds__(256) k_cu0(const Cu0Lattice* lats, int* flag) 
 
 void orient_lattice(Ctx& cx, const void* src, int src_f32, int Ly, int Lx, int d, int D,
                     const OrientSite* host_sites, int nsites, double* dst) {
-  auto* dev = static_cast<OrientSite*>(cx.ws->alloc(sizeof(OrientSite) * nsites));
-  PEPS_CUDA(cudaMemcpyAsync(dev, host_sites, sizeof(OrientSite) * nsites, cudaMemcpyHostToDevice, cx.st));
+  auto* dev = static_cast<const OrientSite*>(stage(cx, host_sites, sizeof(OrientSite) * nsites));
   Launch L(K_AUX, cx.st);
   k_orient<<<nsites, 256, 0, cx.st>>>(src, src_f32, Lx, d, D, dev, dst);
   PEPS_CHECK_LAUNCH();
-  // host_sites must stay alive until the copy is done
-  PEPS_CUDA(cudaStreamSynchronize(cx.st));
+}
+
+void* stage(Ctx& cx, const void* host, size_t bytes) {
+  if (!cx.persist) {
+    void* dev = cx.ws->alloc(bytes);
+    PEPS_CUDA(cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, cx.st));
+    PEPS_CUDA(cudaStreamSynchronize(cx.st));   // the host buffer may go out of scope
+    return dev;
+  }
+  // Recording a graph: copy now, on a private stream that takes no part in the capture.
+  static std::mutex mu;
+  static cudaStream_t side[64] = {};
+  int dev_id = 0;
+  PEPS_CUDA(cudaGetDevice(&dev_id));
+  PEPS_REQUIRE(dev_id < 64, "device index above 63");
+  void* dev = cx.persist->alloc(bytes);
+  std::lock_guard<std::mutex> g(mu);
+  if (!side[dev_id]) PEPS_CUDA(cudaStreamCreateWithFlags(&side[dev_id], cudaStreamNonBlocking));
+  PEPS_CUDA(cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, side[dev_id]));
+  PEPS_CUDA(cudaStreamSynchronize(side[dev_id]));
+  return dev;
 }
 
 long long obc_violations_device(Ctx& cx, const void* src, int src_f32, int Ly, int Lx, int d, int D) {
@@ -559,12 +577,10 @@ size_t cu0_work_size(int Lx, int d, int Dmax) {
 }
 
 void cu0_launch(Ctx& cx, const Cu0Lattice* lats, int nlat) {
-  auto* dev = static_cast<Cu0Lattice*>(cx.ws->alloc(sizeof(Cu0Lattice) * nlat));
-  PEPS_CUDA(cudaMemcpyAsync(dev, lats, sizeof(Cu0Lattice) * nlat, cudaMemcpyHostToDevice, cx.st));
+  auto* dev = static_cast<const Cu0Lattice*>(stage(cx, lats, sizeof(Cu0Lattice) * nlat));
   Launch L(K_CU0, cx.st);
   k_cu0<<<nlat, 256, 0, cx.st>>>(dev, cx.flag);
   PEPS_CHECK_LAUNCH();
-  PEPS_CUDA(cudaStreamSynchronize(cx.st));
 }
 
 }  // namespace peps

@@ -342,12 +342,10 @@ void forward(Ctx& cx, const MlpDims& m, const float* w, const float* X, long lon
 void closure_features(Ctx& cx, const MlpDims& m, const RimSite* host_sites, long long n, float* X) {
   if (n == 0) return;
   PEPS_REQUIRE(m.D <= 8, "learned closure supports D <= 8");
-  auto* dev = static_cast<RimSite*>(cx.ws->alloc(sizeof(RimSite) * n));
-  PEPS_CUDA(cudaMemcpyAsync(dev, host_sites, sizeof(RimSite) * n, cudaMemcpyHostToDevice, cx.st));
+  auto* dev = static_cast<const RimSite*>(stage(cx, host_sites, sizeof(RimSite) * n));
   Launch l(K_AUX, cx.st);
   k_features<<<unsigned(n), 256, 0, cx.st>>>(dev, m.d, m.D, m.F(), X);
   PEPS_CHECK_LAUNCH();
-  PEPS_CUDA(cudaStreamSynchronize(cx.st));   // host_sites may go out of scope
 }
 
 void rank1_labels(Ctx& cx, int D, int maxchi, int maxL, const Rank1Job* host_jobs, int njobs) {
@@ -355,14 +353,10 @@ void rank1_labels(Ctx& cx, int D, int maxchi, int maxL, const Rank1Job* host_job
   const long long DD = (long long)D * D;
   const long long wstride = maxL * DD + (long long)maxL * maxchi + maxchi + std::max<long long>(maxchi, DD) + 8;
   double* work = cx.ws->dalloc(size_t(wstride) * njobs);
-  auto* dev = static_cast<Rank1Job*>(cx.ws->alloc(sizeof(Rank1Job) * njobs));
-  PEPS_CUDA(cudaMemcpyAsync(dev, host_jobs, sizeof(Rank1Job) * njobs, cudaMemcpyHostToDevice, cx.st));
-  {
-    Launch l(K_CU0, cx.st);
-    k_rank1<<<njobs, 256, 0, cx.st>>>(dev, D, work, wstride, cx.flag);
-    PEPS_CHECK_LAUNCH();
-  }
-  PEPS_CUDA(cudaStreamSynchronize(cx.st));
+  auto* dev = static_cast<const Rank1Job*>(stage(cx, host_jobs, sizeof(Rank1Job) * njobs));
+  Launch l(K_CU0, cx.st);
+  k_rank1<<<njobs, 256, 0, cx.st>>>(dev, D, work, wstride, cx.flag);
+  PEPS_CHECK_LAUNCH();
 }
 
 void mlp_init(Ctx& cx, const MlpDims& m, float* w, unsigned long long seed) {
@@ -506,12 +500,10 @@ void mlp_train(Ctx& cx, const MlpDims& m, float* w, const float* X, const float*
 
 void closure_apply(Ctx& cx, int D, const float* pred, double* const* host_targets, long long n) {
   if (n == 0) return;
-  auto* dev = static_cast<double**>(cx.ws->alloc(sizeof(double*) * n));
-  PEPS_CUDA(cudaMemcpyAsync(dev, host_targets, sizeof(double*) * n, cudaMemcpyHostToDevice, cx.st));
+  auto* dev = static_cast<double* const*>(stage(cx, host_targets, sizeof(double*) * n));
   Launch l(K_AUX, cx.st);
   k_apply<<<unsigned((n + 127) / 128), 128, 0, cx.st>>>(pred, dev, n, D);
   PEPS_CHECK_LAUNCH();
-  PEPS_CUDA(cudaStreamSynchronize(cx.st));
 }
 
 }  // namespace peps

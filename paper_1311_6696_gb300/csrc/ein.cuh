@@ -16,6 +16,9 @@ struct Ctx {
   size_t scr_n = 0;
   int* flag = nullptr;   // device status word (ECONVERGE / ETIMEOUT), zeroed per call
   double* tmp = nullptr; // 8 device doubles for short-lived scalars (stream ordered)
+  // Set while the call is being recorded into a CUDA graph: memory that host
+  // data is copied into comes from here (allocated once, kept by the graph's owner).
+  Arena* persist = nullptr;
 
   Ctx(cudaStream_t s, Arena* w) : st(s), ws(w) {}
   ~Ctx() {
@@ -39,6 +42,11 @@ struct Ctx {
     return scr;
   }
 };
+
+// Device copy of `bytes` of host data, valid for all later work on cx.st; the
+// host buffer may be released when this returns.  While recording a graph the
+// copy is made once into cx.persist (it is shape data, fixed for the graph).
+void* stage(Ctx& cx, const void* host, size_t bytes);
 
 using Dims = std::vector<int>;
 

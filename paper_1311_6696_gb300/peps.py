@@ -27,7 +27,8 @@ EXPORTS = [
     "peps_env_ln_norm", "peps_env_free", "peps_last_error", "peps_profile_enable",
     "peps_profile_reset", "peps_profile_count", "peps_profile_name", "peps_profile_read",
     "peps_cu0_noalloc", "peps_closure_data", "peps_mlp_param_count", "peps_mlp_init",
-    "peps_mlp_loss_grad", "peps_mlp_train", "peps_mlp_predict",
+    "peps_mlp_loss_grad", "peps_mlp_train", "peps_mlp_predict", "peps_plan_create", "peps_plan_run",
+    "peps_plan_env", "peps_plan_launches", "peps_plan_free",
 ]
 CLOSURE_WIDTH = 256
 
@@ -81,6 +82,14 @@ def _load():
     lib.peps_mlp_train.argtypes = [P, P, P, C.c_longlong, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                    C.c_float, C.c_float, C.c_ulonglong, C.POINTER(C.c_double), P]
     lib.peps_mlp_predict.argtypes = [P, P, C.c_longlong, C.c_int, C.c_int, C.c_int, P, P]
+    lib.peps_plan_create.argtypes = [C.POINTER(Lattice), C.POINTER(Opts), C.c_int, C.POINTER(P), P]
+    lib.peps_plan_run.argtypes = [P, P]
+    lib.peps_plan_env.argtypes = [P]
+    lib.peps_plan_env.restype = P
+    lib.peps_plan_launches.argtypes = [P]
+    lib.peps_plan_launches.restype = C.c_longlong
+    lib.peps_plan_free.argtypes = [P]
+    lib.peps_plan_free.restype = None
     return lib
 
 
@@ -136,16 +145,17 @@ def _opts(chi, mode, sweeps, precision, n, seed, closure_weights=None):
 class Env:
     """A device-resident environment handle (freed with the object)."""
 
-    def __init__(self, handle, shape, stream):
+    def __init__(self, handle, shape, stream, owner=None):
         self._h = handle
         self.Ly, self.Lx, self.d = shape
         self._stream = stream
+        self._owner = owner          # a Plan owns its env handle
 
     def __del__(self):
         h = getattr(self, "_h", None)
-        if h:
+        if h and getattr(self, "_owner", None) is None:
             lib.peps_env_free(h)
-            self._h = None
+        self._h = None
 
     def free(self):
         self.__del__()
@@ -203,6 +213,44 @@ def env_cluster(A, n: int, chi: int, mode="svd", sweeps: int = 2, precision="fp6
     h = C.c_void_p()
     _check(lib.peps_env_cluster(C.byref(inp.lat), C.byref(o), C.byref(h), _stream_ptr(stream)))
     return Env(h.value, (inp.lat.Ly, inp.lat.Lx, inp.lat.d), stream)
+
+
+class Plan:
+    """A recorded environment computation (CUDA graph); see peps_plan_create.
+    A must be a contiguous CUDA tensor; overwrite it in place between runs."""
+
+    def __init__(self, A, chi: int, mode="svd", sweeps: int = 2, precision="fp64", seed: int = 0,
+                 cluster_n: int | None = None, closure_weights=None, stream=None, device=None):
+        _set_device(device)
+        self._inp = _Input(A)
+        assert self._inp.lat.on_device, "a plan needs the lattice on the device"
+        self._w = closure_weights
+        o = _opts(chi, mode, sweeps, precision, cluster_n or 1, seed, closure_weights)
+        self._stream = stream
+        h = C.c_void_p()
+        _check(lib.peps_plan_create(C.byref(self._inp.lat), C.byref(o), int(cluster_n is not None),
+                                    C.byref(h), _stream_ptr(stream)))
+        self._h = h.value
+        self.launches = int(lib.peps_plan_launches(self._h))
+
+    @property
+    def env(self) -> Env:
+        """The plan's environment (contents of the last run); keeps the plan alive."""
+        lat = self._inp.lat
+        return Env(lib.peps_plan_env(self._h), (lat.Ly, lat.Lx, lat.d), self._stream, owner=self)
+
+    def run(self, stream=None) -> Env:
+        _check(lib.peps_plan_run(self._h, _stream_ptr(stream if stream is not None else self._stream)))
+        return self.env
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib.peps_plan_free(h)
+            self._h = None
+
+    def free(self):
+        self.__del__()
 
 
 def norm(A, chi: int, mode="svd", sweeps: int = 2, precision="fp64", seed: int = 0,
