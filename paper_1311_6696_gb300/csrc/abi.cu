@@ -2,6 +2,7 @@
 // repacking into the four sweep orientations, the full / cluster / norm
 // drivers, and kernel-class instrumentation.  No exception crosses this file.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -9,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -157,6 +159,7 @@ struct Call {
   explicit Call(void* stream, Arena* persist = nullptr)
       : st(static_cast<cudaStream_t>(stream)), ws(st), cx(st, &ws) {
     cx.persist = persist;
+    if (const char* e = std::getenv("PEPS_QR_CMAX")) cx.qr_cmax = std::atoi(e);
     cx.flag = static_cast<int*>(persist ? persist->alloc(sizeof(int)) : ws.alloc(sizeof(int)));
     PEPS_CUDA(cudaMemsetAsync(cx.flag, 0, sizeof(int), st));
     cx.tmp = ws.dalloc(8);
@@ -387,7 +390,8 @@ struct Lane {
 struct Lanes {
   cudaStream_t main;
   std::vector<Lane> l;
-  Lanes(Call& c, const Opts& opt, int d, int D, int Lmax) : main(c.st) {
+  // nb: problems each lane's engine runs in lockstep.
+  Lanes(Call& c, const Opts& opt, int d, int D, int Lmax, int nb = 1) : main(c.st) {
     auto& pool = lane_streams();
     l.resize(lane_count());
     for (int i = 0; i < int(l.size()); ++i) {
@@ -398,8 +402,9 @@ struct Lanes {
       a.cx = std::make_unique<Ctx>(a.st, a.ws.get());
       a.cx->flag = c.cx.flag;
       a.cx->persist = c.cx.persist;
+      a.cx->qr_cmax = c.cx.qr_cmax;
       a.cx->tmp = a.ws->dalloc(8);
-      a.eng = std::make_unique<Engine>(*a.cx, opt, d, D, Lmax);
+      a.eng = std::make_unique<Engine>(*a.cx, opt, d, D, Lmax, nb);
     }
   }
   // Fork: every lane waits for the caller's stream.
@@ -526,9 +531,9 @@ void cu0_all_sides(Ctx& cx, const peps_lattice* lat, Oriented& ori, Arena& keep,
     sig[o] = keep.dalloc(size_t(L.Ly) * L.Lx * DM2);
     offs[o].resize(size_t(L.Ly) * L.Lx);
     dims[o].resize(size_t(L.Ly) * L.Lx * 4);
-    const double* base = L.sites[0].p;
+    const double* base = L.sites[0].p.d(0);
     for (size_t i = 0; i < L.sites.size(); ++i) {
-      offs[o][i] = L.sites[i].p - base;
+      offs[o][i] = L.sites[i].p.d(0) - base;
       dims[o][4 * i + 0] = L.sites[i].du;
       dims[o][4 * i + 1] = L.sites[i].dl;
       dims[o][4 * i + 2] = L.sites[i].dn;
@@ -563,7 +568,7 @@ std::vector<RimSite> rim_sites(const Oriented& ori, double* const sig[4], int D)
     for (int r = 1; r < L.Ly; ++r)
       for (int x = 0; x < L.Lx; ++x) {
         const SiteT& t = L.at(r - 1, x);
-        v.push_back(RimSite{t.p, t.du, t.dl, t.dn, t.dr, sig[o] + ((long long)r * L.Lx + x) * D * D});
+        v.push_back(RimSite{t.p.d(0), t.du, t.dl, t.dn, t.dr, sig[o] + ((long long)r * L.Lx + x) * D * D});
       }
   }
   return v;
@@ -593,38 +598,89 @@ void cluster_env(Call& c, const peps_lattice* lat, const Opts& opt, int n, peps_
   }
   auto S = [&](int o, int r, int x, int dim) {
     const OLat& L = ori.o[o];
-    return Mat{sig[o] + ((long long)r * L.Lx + x) * DM2, dim};
+    return Mat{TP(sig[o] + ((long long)r * L.Lx + x) * DM2), dim};
   };
-  Lanes lanes(c, opt, d, D, std::max(Ly, Lx));
-  const int nl = int(lanes.l.size());
-  double* junk = cx.ws->dalloc(4 * nl);
+  // Windows of one shape signature -- size, anchor position inside, and which
+  // lattice edges they touch (which fixes every site's leg dimensions) -- run
+  // as the problems of one engine, in chunks that fit the memory budget.
+  struct Win {
+    int y, x, r0, r1, c0, c1;
+  };
+  std::map<std::array<int, 8>, std::vector<Win>> groups;
+  for (int y = 0; y < Ly; ++y)
+    for (int x = 0; x < Lx; ++x) {
+      const auto rr = window(Ly, y, n), cc = window(Lx, x, n);
+      const Win wv{y, x, rr.first, rr.second, cc.first, cc.second};
+      const std::array<int, 8> key{wv.r1 - wv.r0, wv.c1 - wv.c0, y - wv.r0, x - wv.c0,
+                                   int(wv.r0 == 0), int(wv.r1 == Ly - 1), int(wv.c0 == 0), int(wv.c1 == Lx - 1)};
+      groups[key].push_back(wv);
+    }
+  const int nl = lane_count();
+  const int Lwin = std::min(n, std::max(Ly, Lx));
+  const size_t per = Engine::footprint(opt, d, D, Lwin) * sizeof(double);
+  size_t free_b = 0, total_b = 0;
+  PEPS_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  const size_t budget = std::min<size_t>(free_b * 2 / 5, size_t(96) << 30);
+  const int bmax = int(std::max<size_t>(1, std::min<size_t>(MAXB, budget / (per * nl))));
+  std::vector<std::vector<Win>> chunks;
+  for (auto& kv : groups) {
+    const auto& v = kv.second;
+    const int nch = int((v.size() + bmax - 1) / bmax);
+    const int sz = int((v.size() + nch - 1) / nch);
+    for (size_t i0 = 0; i0 < v.size(); i0 += sz)
+      chunks.emplace_back(v.begin() + i0, v.begin() + std::min(v.size(), i0 + size_t(sz)));
+  }
+  // larger windows first, so the lanes end together
+  std::stable_sort(chunks.begin(), chunks.end(), [](const std::vector<Win>& a, const std::vector<Win>& b) {
+    return (a[0].r1 - a[0].r0 + 1) * (a[0].c1 - a[0].c0 + 1) > (b[0].r1 - b[0].r0 + 1) * (b[0].c1 - b[0].c0 + 1);
+  });
+  int bl = 1;
+  for (auto& c : chunks) bl = std::max(bl, int(c.size()));
+  Lanes lanes(c, opt, d, D, Lwin, bl);
+  double* junk = cx.ws->dalloc(size_t(lanes.l.size()) * 4 * 32 * MAXB);
   EnvData& e = env->data;
   const long long d2 = (long long)d * d, d4 = d2 * d2;
-  std::vector<std::vector<std::unique_ptr<Arena>>> keeps(nl);
-  run_lanes(lanes, Ly * Lx, [&](Lane& lane, int job) {
-      const int y = job / Lx, x = job % Lx;
-      const int li = int(&lane - lanes.l.data());
-      Engine& eng = *lane.eng;
-      double* lj = junk + 4 * li;
-      const auto rr = window(Ly, y, n), cc = window(Lx, x, n);
-      const int r0 = rr.first, r1 = rr.second, c0 = cc.first, c1 = cc.second;
-      const int h = r1 - r0 + 1, w = c1 - c0 + 1, yw = y - r0, xw = x - c0;
+  // Merge per-window lattices (identical shapes) into one lattice of pointer sets.
+  auto merge = [](const std::vector<OLat>& ws) {
+    OLat m = ws[0];
+    const int B = int(ws.size());
+    auto set = [&](TP& t, auto get) {
+      t.n = B;
+      for (int b = 0; b < B; ++b) t.p[b] = get(b).p[0];
+    };
+    for (size_t i = 0; i < m.sites.size(); ++i) set(m.sites[i].p, [&](int b) { return ws[b].sites[i].p; });
+    for (size_t i = 0; i < m.top.size(); ++i) set(m.top[i].p, [&](int b) { return ws[b].top[i].p; });
+    for (size_t i = 0; i < m.bottom.size(); ++i) set(m.bottom[i].p, [&](int b) { return ws[b].bottom[i].p; });
+    for (size_t i = 0; i < m.left.size(); ++i) set(m.left[i].p, [&](int b) { return ws[b].left[i].p; });
+    for (size_t i = 0; i < m.right.size(); ++i) set(m.right[i].p, [&](int b) { return ws[b].right[i].p; });
+    return m;
+  };
+  run_lanes(lanes, int(chunks.size()), [&](Lane& lane, int job) {
+    const std::vector<Win>& ch = chunks[job];
+    const int B = int(ch.size());
+    const int li = int(&lane - lanes.l.data());
+    Engine& eng = *lane.eng;
+    eng.use(B);
+    const TP lj = strided(junk + size_t(li) * 4 * 32 * MAXB, B, 1);
+    std::vector<OLat> w0(B), w1(B), w2(B), w3(B);
+    TP t_site, t_h, t_v;
+    t_site.n = t_h.n = t_v.n = B;
+    for (int b = 0; b < B; ++b) {
+      const Win& wv = ch[b];
+      const int r0 = wv.r0, r1 = wv.r1, c0 = wv.c0, c1 = wv.c1;
+      const int h = r1 - r0 + 1, w = c1 - c0 + 1;
       // window in the four orientations (sub-blocks of the oriented full lattice)
       OLat W0 = sub(ori.o[0], r0, r1, c0, c1);
       OLat W1 = sub(ori.o[1], Ly - 1 - r1, Ly - 1 - r0, c0, c1);
       OLat W2 = sub(ori.o[2], c0, c1, r0, r1);
       OLat W3 = sub(ori.o[3], Lx - 1 - c1, Lx - 1 - c0, r0, r1);
-      auto dimU = [&](const OLat& L, int i, int j) { return L.at(i, j).du; };
-      auto dimN = [&](const OLat& L, int i, int j) { return L.at(i, j).dn; };
-      auto dimL = [&](const OLat& L, int i, int j) { return L.at(i, j).dl; };
-      auto dimR = [&](const OLat& L, int i, int j) { return L.at(i, j).dr; };
       for (int j = 0; j < w; ++j) {
-        W0.top.push_back(S(0, r0, c0 + j, dimU(W0, 0, j)));
-        W0.bottom.push_back(S(1, Ly - 1 - r1, c0 + j, dimN(W0, h - 1, j)));
+        W0.top.push_back(S(0, r0, c0 + j, W0.at(0, j).du));
+        W0.bottom.push_back(S(1, Ly - 1 - r1, c0 + j, W0.at(h - 1, j).dn));
       }
       for (int i = 0; i < h; ++i) {
-        W0.left.push_back(S(2, c0, r0 + i, dimL(W0, i, 0)));
-        W0.right.push_back(S(3, Lx - 1 - c1, r0 + i, dimR(W0, i, w - 1)));
+        W0.left.push_back(S(2, c0, r0 + i, W0.at(i, 0).dl));
+        W0.right.push_back(S(3, Lx - 1 - c1, r0 + i, W0.at(i, w - 1).dr));
       }
       W1.top = W0.bottom;
       W1.bottom = W0.top;
@@ -642,21 +698,47 @@ void cluster_env(Call& c, const peps_lattice* lat, const Opts& opt, int n, peps_
         W3.left.push_back(W0.top[w - 1 - j]);
         W3.right.push_back(W0.bottom[w - 1 - j]);
       }
-      keeps[li].push_back(std::make_unique<Arena>(lane.st));
-      Arena& keep = *keeps[li].back();
-      auto bt = eng.sweep(W0, 0, yw, lj, keep);
-      auto bb = eng.sweep(W1, 1, h - 1 - yw, lj, keep);
-      Engine::Targets ts{{xw, e.rho_site + ((long long)y * Lx + x) * d2}}, tb;
-      if (x + 1 < Lx && xw + 1 < w) tb.push_back({xw, e.rho_h + ((long long)y * (Lx - 1) + x) * d4});
-      eng.row_rhos(W0, bt[yw], bb[h - 1 - yw], yw, ts, tb);
-      if (y + 1 < Ly && yw + 1 < h) {
-        auto bl = eng.sweep(W2, 2, xw, lj, keep);
-        auto br = eng.sweep(W3, 3, w - 1 - xw, lj, keep);
-        eng.row_rhos(W2, bl[xw], br[w - 1 - xw], xw, {}, {{yw, e.rho_v + ((long long)y * Lx + x) * d4}});
-      }
-      if (keeps[li].size() > 2) keeps[li].erase(keeps[li].begin());   // stream-ordered free
+      w0[b] = std::move(W0);
+      w1[b] = std::move(W1);
+      w2[b] = std::move(W2);
+      w3[b] = std::move(W3);
+      t_site.p[b] = e.rho_site + ((long long)wv.y * Lx + wv.x) * d2;
+      t_h.p[b] = e.rho_h + ((long long)wv.y * (Lx - 1) + wv.x) * d4;
+      t_v.p[b] = e.rho_v + ((long long)wv.y * Lx + wv.x) * d4;
+    }
+    const Win& w_ = ch[0];
+    const int h = w_.r1 - w_.r0 + 1, w = w_.c1 - w_.c0 + 1, yw = w_.y - w_.r0, xw = w_.x - w_.c0;
+    const OLat W0 = merge(w0), W1 = merge(w1), W2 = merge(w2), W3 = merge(w3);
+    // PEPS_VERBOSE (plain calls only): device time of every chunk
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    const bool timed = std::getenv("PEPS_VERBOSE") && !cx.persist;
+    if (timed) {
+      PEPS_CUDA(cudaEventCreate(&ev0));
+      PEPS_CUDA(cudaEventCreate(&ev1));
+      PEPS_CUDA(cudaEventRecord(ev0, lane.st));
+    }
+    Arena keep(lane.st);
+    auto bt = eng.sweep(W0, 0, yw, lj, keep);
+    auto bb = eng.sweep(W1, 1, h - 1 - yw, lj, keep);
+    Engine::Targets ts{{xw, t_site}}, tb;
+    if (xw + 1 < w) tb.push_back({xw, t_h});
+    eng.row_rhos(W0, bt[yw], bb[h - 1 - yw], yw, ts, tb);
+    if (yw + 1 < h) {
+      auto bl = eng.sweep(W2, 2, xw, lj, keep);
+      auto br = eng.sweep(W3, 3, w - 1 - xw, lj, keep);
+      eng.row_rhos(W2, bl[xw], br[w - 1 - xw], xw, {}, {{yw, t_v}});
+    }
+    if (timed) {
+      PEPS_CUDA(cudaEventRecord(ev1, lane.st));
+      PEPS_CUDA(cudaEventSynchronize(ev1));
+      float ms = 0.f;
+      PEPS_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+      std::fprintf(stderr, "[peps] chunk %d: %d windows %dx%d anchor (%d,%d), lane %d, %.2f ms\n", job, B, h, w, yw,
+                   xw, li, ms);
+      cudaEventDestroy(ev0);
+      cudaEventDestroy(ev1);
+    }
   });
-  keeps.clear();
   lanes.join();
   e.has_norm = false;
 }
@@ -847,7 +929,8 @@ int peps_closure_data(const peps_lattice* lat, const peps_opts* opts, float* X, 
       const OLat& L = ori.o[oi];
       for (int r = 1; r < L.Ly; ++r) {
         const Mps& T = b[oi][r];
-        std::vector<const double*> pp(T.p.begin(), T.p.end());
+        std::vector<const double*> pp;
+        for (const TP& t : T.p) pp.push_back(t.d(0));
         std::vector<int> bd;
         for (int x = 0; x < L.Lx; ++x) bd.push_back(T.dims[x][0]);
         bd.push_back(T.dims[L.Lx - 1][3]);

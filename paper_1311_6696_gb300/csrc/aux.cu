@@ -85,38 +85,43 @@ __global__ void k_obc_count(const void* src, int f32, int Ly, int Lx, int d, int
   if (c) atomicAdd(count, c);
 }
 
-__global__ void k_sumsq_partial(const double* x, long long n, double* part) {
+// Batched element-wise kernels: grid = (blocks, problems), problem = blockIdx.y.
+__global__ void k_sumsq_partial(const TP x, long long n, double* part) {
   __shared__ double red[32];
+  const double* xp = x.d(blockIdx.y);
   double s = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const double v = x[i];
+    const double v = xp[i];
     s += v * v;
   }
   s = block_sum(s, red);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  if (threadIdx.x == 0) part[(long long)blockIdx.y * gridDim.x + blockIdx.x] = s;
 }
 
-__global__ void k_sumsq_finish(const double* part, int np, double* out) {
+// Grid = problems.
+__global__ void k_sumsq_finish(const double* part, int np, const TP out) {
   __shared__ double red[32];
   double s = 0.0;
-  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[(long long)blockIdx.x * np + i];
   s = block_sum(s, red);
-  if (threadIdx.x == 0) out[0] = sqrt(s);
+  if (threadIdx.x == 0) out.d(blockIdx.x)[0] = sqrt(s);
 }
 
-__global__ void k_rescale(double* x, long long n, const double* nrm, double* lnacc, int* flag) {
-  const double v = nrm[0];
+__global__ void k_rescale(const TP x, long long n, const TP nrm, const TP lnacc, int* flag) {
+  const int pb = blockIdx.y;
+  const double v = nrm.d(pb)[0];
   const bool ok = v > 0.0 && isfinite(v);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (!ok && flag) atomicOr(flag, FLAG_BAD_VALUE);
-    if (lnacc && ok) lnacc[0] += log(v);
+    if (lnacc.n && ok) lnacc.d(pb)[0] += log(v);
   }
   if (!ok) return;
   const double inv = 1.0 / v;
+  double* xp = x.d(pb);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
-    x[i] *= inv;
+    xp[i] *= inv;
 }
 
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
@@ -126,17 +131,20 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
 }
 
 struct VarInitArgs {
-  const double* src;
+  TP src;
   int s0, s1, s2, s3;
-  double* dst;
+  TP dst;
   int d0, d1, d2, d3;
   unsigned long long key;
-  const double* srcnorm;
+  TP srcnorm;
 };
 
 __global__ void k_var_init(const VarInitArgs a) {
+  const int pb = blockIdx.y;
+  const double* src = a.src.d(pb);
+  double* dst = a.dst.d(pb);
   const long long n = (long long)a.d0 * a.d1 * a.d2 * a.d3;
-  const double scale = 1e-3 * a.srcnorm[0] / sqrt(double(n));
+  const double scale = 1e-3 * a.srcnorm.d(pb)[0] / sqrt(double(n));
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
     long long t = e;
@@ -148,11 +156,11 @@ __global__ void k_var_init(const VarInitArgs a) {
     const int i0 = int(t / a.d1);
     const bool inside = i0 < a.s0 && i1 < a.s1 && i2 < a.s1 && i2 < a.s2 && i3 < a.s3;
     if (inside) {
-      a.dst[e] = a.src[(((long long)i0 * a.s1 + i1) * a.s2 + i2) * a.s3 + i3];
+      dst[e] = src[(((long long)i0 * a.s1 + i1) * a.s2 + i2) * a.s3 + i3];
     } else {
       const unsigned long long z = mix64(a.key + (unsigned long long)e + 0x9E3779B97F4A7C15ULL);
       const double u = double(z >> 11) * (1.0 / 4503599627370496.0) - 1.0;   // 2^-52
-      a.dst[e] = scale * u;
+      dst[e] = scale * u;
     }
   }
 }
@@ -179,16 +187,19 @@ __global__ void k_finish_norm(const double* lns, int nl, const double* extra, co
   out_sign[0] = v > 0 ? 1.0 : (v < 0 ? -1.0 : 0.0);
 }
 
-__global__ void k_fill(double* x, long long n, double v) {
+__global__ void k_fill(const TP x, long long n, double v) {
+  double* xp = x.d(blockIdx.y);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
-    x[i] = v;
+    xp[i] = v;
 }
 
-__global__ void k_copy(double* dst, const double* src, long long n) {
+__global__ void k_copy(const TP dst, const TP src, long long n) {
+  double* dp = dst.d(blockIdx.y);
+  const double* sp = src.d(blockIdx.y);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
-    dst[i] = src[i];
+    dp[i] = sp[i];
 }
 
 unsigned grid_for(long long n) {
@@ -500,49 +511,52 @@ long long obc_violations_device(Ctx& cx, const void* src, int src_f32, int Ly, i
   return (long long)h;
 }
 
-void fro_norm(Ctx& cx, const double* x, long long n, double* out) {
-  double* part = cx.scratch(RED_BLOCKS);
+void fro_norm(Ctx& cx, const TP& x, long long n, const TP& out) {
+  const int np = problems({&x, &out});
   const unsigned nb = unsigned(std::max<long long>(1, std::min<long long>(RED_BLOCKS, (n + 255) / 256)));
+  double* part = cx.scratch(size_t(nb) * np);
   Launch L(K_AUX, cx.st);
-  k_sumsq_partial<<<nb, 256, 0, cx.st>>>(x, n, part);
-  k_sumsq_finish<<<1, 256, 0, cx.st>>>(part, int(nb), out);
+  k_sumsq_partial<<<dim3(nb, np), 256, 0, cx.st>>>(x.all(np), n, part);
+  k_sumsq_finish<<<np, 256, 0, cx.st>>>(part, int(nb), out.all(np));
   PEPS_CHECK_LAUNCH();
 }
 
-void rescale(Ctx& cx, double* x, long long n, const double* nrm, double* lnacc) {
+void rescale(Ctx& cx, const TP& x, long long n, const TP& nrm, const TP& lnacc) {
+  const int np = problems({&x, &nrm, &lnacc});
   Launch L(K_AUX, cx.st);
-  k_rescale<<<grid_for(n), 256, 0, cx.st>>>(x, n, nrm, lnacc, cx.flag);
+  k_rescale<<<dim3(grid_for(n), np), 256, 0, cx.st>>>(x.all(np), n, nrm.all(np), lnacc.all(np), cx.flag);
   PEPS_CHECK_LAUNCH();
 }
 
-void normalize(Ctx& cx, double* x, long long n, double* lnacc) {
-  double* t = cx.tmp;
+void normalize(Ctx& cx, const TP& x, long long n, const TP& lnacc, const TP& tmp) {
+  const TP t = tmp.null() ? TP(cx.tmp) : tmp;
   fro_norm(cx, x, n, t);
   rescale(cx, x, n, t, lnacc);
 }
 
-void var_init(Ctx& cx, const double* src, const int sdims[4], double* dst, const int ddims[4],
-              unsigned long long seed, int tag, int y, int x) {
+void var_init(Ctx& cx, const TP& src, const int sdims[4], const TP& dst, const int ddims[4],
+              unsigned long long seed, int tag, int y, int x, const TP& tmp) {
+  const int np = problems({&src, &dst, &tmp});
   const long long ns = (long long)sdims[0] * sdims[1] * sdims[2] * sdims[3];
-  double* sn = cx.tmp + 1;
+  const TP sn = tmp.null() ? TP(cx.tmp + 1) : tmp;
   fro_norm(cx, src, ns, sn);
   VarInitArgs a;
-  a.src = src;
+  a.src = src.all(np);
   a.s0 = sdims[0];
   a.s1 = sdims[1];
   a.s2 = sdims[2];
   a.s3 = sdims[3];
-  a.dst = dst;
+  a.dst = dst.all(np);
   a.d0 = ddims[0];
   a.d1 = ddims[1];
   a.d2 = ddims[2];
   a.d3 = ddims[3];
   a.key = seed * 0x9E3779B97F4A7C15ULL + ((unsigned long long)tag << 56) +
           ((unsigned long long)y << 44) + ((unsigned long long)x << 32);
-  a.srcnorm = sn;
+  a.srcnorm = sn.all(np);
   const long long n = (long long)ddims[0] * ddims[1] * ddims[2] * ddims[3];
   Launch L(K_AUX, cx.st);
-  k_var_init<<<grid_for(n), 256, 0, cx.st>>>(a);
+  k_var_init<<<dim3(grid_for(n), np), 256, 0, cx.st>>>(a);
   PEPS_CHECK_LAUNCH();
 }
 
@@ -559,15 +573,18 @@ void finish_norm(Ctx& cx, const double* lns, int nl, const double* extra, const 
   PEPS_CHECK_LAUNCH();
 }
 
-void fill(Ctx& cx, double* x, long long n, double v) {
+void fill(Ctx& cx, const TP& x, long long n, double v) {
+  const int np = problems({&x});
   Launch L(K_AUX, cx.st);
-  k_fill<<<grid_for(n), 256, 0, cx.st>>>(x, n, v);
+  k_fill<<<dim3(grid_for(n), np), 256, 0, cx.st>>>(x.all(np), n, v);
   PEPS_CHECK_LAUNCH();
 }
 
-void copy(Ctx& cx, double* dst, const double* src, long long n) {
+void copy(Ctx& cx, const TP& dst, const TP& src, long long n) {
+  const int np = problems({&dst, &src});
+  PEPS_REQUIRE(dst.n == np, "internal: copy destination");
   Launch L(K_AUX, cx.st);
-  k_copy<<<grid_for(n), 256, 0, cx.st>>>(dst, src, n);
+  k_copy<<<dim3(grid_for(n), np), 256, 0, cx.st>>>(dst.all(np), src.all(np), n);
   PEPS_CHECK_LAUNCH();
 }
 

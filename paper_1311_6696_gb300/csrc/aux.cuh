@@ -18,18 +18,19 @@ void orient_lattice(Ctx& cx, const void* src, int src_f32, int Ly, int Lx, int d
 // Number of nonzero entries on outward (OBC) legs of the dense device array.
 long long obc_violations_device(Ctx& cx, const void* src, int src_f32, int Ly, int Lx, int d, int D);
 
+// All of these act on every problem of their pointer sets (one launch).
 // out[0] = ||x||_F (device scalar).
-void fro_norm(Ctx& cx, const double* x, long long n, double* out);
+void fro_norm(Ctx& cx, const TP& x, long long n, const TP& out);
 // x /= *nrm; if lnacc: *lnacc += log(*nrm).  Sets FLAG_BAD_VALUE on 0 / inf / nan.
-void rescale(Ctx& cx, double* x, long long n, const double* nrm, double* lnacc);
-// Both in sequence, using a small device temporary.
-void normalize(Ctx& cx, double* x, long long n, double* lnacc);
+void rescale(Ctx& cx, const TP& x, long long n, const TP& nrm, const TP& lnacc);
+// Both in sequence; tmp: one device scalar per problem (absent: cx.tmp, one problem).
+void normalize(Ctx& cx, const TP& x, long long n, const TP& lnacc, const TP& tmp = TP());
 
 // var start: dst[c,n,o,e] = src[c,n,o,e] where inside src's extent, else
 // noise * 1e-3 * ||src|| / sqrt(numel(dst)); noise from SplitMix64 keyed by
-// (seed, tag, y, x, flat index of dst).
-void var_init(Ctx& cx, const double* src, const int sdims[4], double* dst, const int ddims[4],
-              unsigned long long seed, int tag, int y, int x);
+// (seed, tag, y, x, flat index of dst).  tmp as for normalize.
+void var_init(Ctx& cx, const TP& src, const int sdims[4], const TP& dst, const int ddims[4],
+              unsigned long long seed, int tag, int y, int x, const TP& tmp = TP());
 
 // out[i] = sum_ab rho_i[a][b] op[b][a] / sum_a rho_i[a][a] for count matrices k x k.
 void expect_batch(Ctx& cx, const double* rho, int count, int k, const double* op, double* out);
@@ -38,8 +39,8 @@ void expect_batch(Ctx& cx, const double* rho, int count, int k, const double* op
 void finish_norm(Ctx& cx, const double* lns, int nl, const double* extra, const double* s,
                  double* out_ln, double* out_sign);
 
-void fill(Ctx& cx, double* x, long long n, double v);
-void copy(Ctx& cx, double* dst, const double* src, long long n);
+void fill(Ctx& cx, const TP& x, long long n, double v);
+void copy(Ctx& cx, const TP& dst, const TP& src, long long n);
 
 // CU_0 separable boundaries of one oriented lattice (Section 4.1), computed
 // by one CTA.  Site tensors at `sites` (per-site offsets/dims in `meta`),

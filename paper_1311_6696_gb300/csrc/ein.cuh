@@ -1,5 +1,7 @@
 // Pairwise tensor contractions ("einsum" of two operands) on the GPU.
 #pragma once
+#include <cstddef>
+#include <initializer_list>
 #include <string>
 #include <vector>
 
@@ -19,6 +21,8 @@ struct Ctx {
   // Set while the call is being recorded into a CUDA graph: memory that host
   // data is copied into comes from here (allocated once, kept by the graph's owner).
   Arena* persist = nullptr;
+  // Largest thread-block cluster a QR may use (0: no limit beyond 16).
+  int qr_cmax = 0;
 
   Ctx(cudaStream_t s, Arena* w) : st(s), ws(w) {}
   ~Ctx() {
@@ -43,6 +47,41 @@ struct Ctx {
   }
 };
 
+// Independent problems of identical shape that one batched launch serves
+// (e.g. the cluster windows of one shape): every tensor argument is a set of
+// per-problem device pointers, passed by value in the kernel parameters.
+constexpr int MAXB = 64;
+
+struct TP {
+  int n = 0;              // 0: absent, 1: one pointer (shared by every problem), else per problem
+  void* p[MAXB];
+  TP() {}
+  TP(std::nullptr_t) {}
+  TP(const void* q) : n(q ? 1 : 0) { p[0] = const_cast<void*>(q); }   // one problem
+  __host__ __device__ void* v(int b) const { return n == 1 ? p[0] : p[b]; }
+  __host__ __device__ double* d(int b) const { return static_cast<double*>(v(b)); }
+  bool null() const { return n == 0; }
+  // The same element offset (in doubles) into every problem's tensor.
+  TP off(long long e) const {
+    TP r = *this;
+    for (int b = 0; b < n; ++b) r.p[b] = static_cast<double*>(p[b]) + e;
+    return r;
+  }
+  // Every slot filled (a shared pointer repeated), for kernel parameters.
+  TP all(int B) const {
+    TP r = *this;
+    if (n == 1)
+      for (int b = 1; b < B; ++b) r.p[b] = p[0];
+    r.n = n == 0 ? 0 : B;
+    return r;
+  }
+};
+
+// Per-problem blocks of `per` doubles (rounded up to 32) starting at base.
+TP strided(double* base, int count, size_t per);
+// Number of problems of a call: every present argument has 1 or B pointers.
+int problems(std::initializer_list<const TP*> args);
+
 // Device copy of `bytes` of host data, valid for all later work on cx.st; the
 // host buffer may be released when this returns.  While recording a graph the
 // copy is made once into cx.persist (it is shape data, fixed for the graph).
@@ -62,15 +101,15 @@ Dims ein_dims(const char* spec, const Dims& ad, const Dims& bd);
 // C = alpha * sum_{shared} A B + beta * C, all tensors contiguous row-major,
 // in FP64.  Indices present in A, B and C are batch indices; indices in only
 // one operand must appear in C.
-void ein(Ctx& cx, const char* spec, const double* A, const Dims& ad, const double* B,
-         const Dims& bd, double* C, double alpha = 1.0, double beta = 0.0);
+void ein(Ctx& cx, const char* spec, const TP& A, const Dims& ad, const TP& B,
+         const Dims& bd, const TP& C, double alpha = 1.0, double beta = 0.0);
 
 // C = alpha * contract(A, B) on the tensor cores (tcgen05): operands are
 // FP64 (x_f64 = 1) or FP32 tensors, repacked to TF32 / BF16; C is written as
 // FP64 or FP32 in any index order; with Clo (FP32 output only) C receives the
 // TF32-rounded value and Clo the rounded residual.  prec is PEPS_PREC_*.
-void ein_tc(Ctx& cx, const char* spec, const void* A, int a_f64, const Dims& ad, const void* B, int b_f64,
-            const Dims& bd, void* C, int c_f64, int prec, double alpha = 1.0, void* Clo = nullptr);
+void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, const TP& B, int b_f64,
+            const Dims& bd, const TP& C, int c_f64, int prec, double alpha = 1.0, const TP& Clo = TP());
 int tc_available();
 
 }  // namespace peps

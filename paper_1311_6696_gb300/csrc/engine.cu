@@ -27,33 +27,56 @@ std::vector<int> bond_caps(const std::vector<int>& phys, const std::vector<long 
   return caps;
 }
 
-Engine::Engine(Ctx& c, const Opts& o, int d, int Dmax, int Lmax)
-    : cx(c), opt(o), d_(d), Dmax_(Dmax), Lmax_(Lmax) {
+Engine::Engine(Ctx& c, const Opts& o, int d, int Dmax, int Lmax, int nb)
+    : cx(c), opt(o), d_(d), Dmax_(Dmax), Lmax_(Lmax), nb_(nb), cap_(nb) {
+  PEPS_REQUIRE(nb >= 1 && nb <= MAXB, "internal: problems per engine");
   const size_t chi = size_t(o.chi), D2 = size_t(Dmax) * Dmax, dd = size_t(d) * d;
   bigN_ = chi * chi * D2 * D2;
   // X1: chain stage 1 (chi^2 D^4), or bond stage 1 (d^2 chi^2 D^4) / bond stage 4 (d^4 chi^2 D^2)
-  X1_ = cx.ws->dalloc(std::max(bigN_ * dd, chi * chi * D2 * dd * dd));
-  X2_ = cx.ws->dalloc(bigN_ * dd * d);   // ket stage with up to one open pair
-  X3_ = cx.ws->dalloc(bigN_ * dd * dd);  // bra stage with up to two open pairs
+  X1_ = alloc(*cx.ws, std::max(bigN_ * dd, chi * chi * D2 * dd * dd));
+  X2_ = alloc(*cx.ws, bigN_ * dd * d);   // ket stage with up to one open pair
+  X3_ = alloc(*cx.ws, bigN_ * dd * dd);  // bra stage with up to two open pairs
   envN_ = chi * D2 * chi * dd;
-  bb_ = cx.ws->dalloc(envN_);
+  bb_ = alloc(*cx.ws, envN_);
   Lmax = std::max(Lmax, 2);
   Lenv_.resize(Lmax);
   Renv_.resize(Lmax);
   for (int i = 0; i < Lmax; ++i) {
-    Lenv_[i] = cx.ws->dalloc(envN_);
-    Renv_[i] = cx.ws->dalloc(envN_);
+    Lenv_[i] = alloc(*cx.ws, envN_);
+    Renv_[i] = alloc(*cx.ws, envN_);
   }
-  one_ = cx.ws->dalloc(1);
+  one_ = TP(cx.ws->dalloc(1));
   fill(cx, one_, 1, 1.0);
+  tmp0_ = alloc(*cx.ws, 1);
+  tmp1_ = alloc(*cx.ws, 1);
   tc_ = o.precision != PEPS_PREC_FP64;
   x64_ = !tc_;
 }
 
-void Engine::con(const char* spec, const void* A, bool a64, const Dims& ad, const void* B, bool b64,
-                 const Dims& bd, void* C, bool c64) {
+size_t Engine::footprint(const Opts& o, int d, int Dmax, int Lmax) {
+  const size_t chi = size_t(o.chi), D2 = size_t(Dmax) * Dmax, dd = size_t(d) * d;
+  const size_t big = chi * chi * D2 * D2, env = chi * D2 * chi * dd;
+  return std::max(big * dd, chi * chi * D2 * dd * dd) + big * dd * d + big * dd * dd + env +
+         2 * size_t(std::max(Lmax, 2)) * env + 6 * 32;
+}
+
+void Engine::use(int B) {
+  PEPS_REQUIRE(B >= 1 && B <= cap_, "internal: more problems than the engine holds");
+  nb_ = B;
+  for (TP* t : {&X1_, &X2_, &X3_, &bb_, &tmp0_, &tmp1_}) t->n = B;
+  for (auto& t : Lenv_) t.n = B;
+  for (auto& t : Renv_) t.n = B;
+}
+
+TP Engine::alloc(Arena& a, size_t per) const {
+  const size_t stride = (per + 31) / 32 * 32;
+  return strided(a.dalloc(stride * nb_), nb_, per);
+}
+
+void Engine::con(const char* spec, const TP& A, bool a64, const Dims& ad, const TP& B, bool b64,
+                 const Dims& bd, const TP& C, bool c64) {
   if (!tc_) {
-    ein(cx, spec, static_cast<const double*>(A), ad, static_cast<const double*>(B), bd, static_cast<double*>(C));
+    ein(cx, spec, A, ad, B, bd, C);
     return;
   }
   ein_tc(cx, spec, A, a64 ? 1 : 0, ad, B, b64 ? 1 : 0, bd, C, c64 ? 1 : 0, opt.precision);
@@ -62,14 +85,14 @@ void Engine::con(const char* spec, const void* A, bool a64, const Dims& ad, cons
 Mps Engine::closure_mps(const std::vector<Mat>& mats, Arena&) {
   Mps T;
   for (const Mat& m : mats) {
-    T.p.push_back(const_cast<double*>(m.p));
+    T.p.push_back(m.p);
     T.dims.push_back({1, m.n, m.n, 1});
   }
   return T;
 }
 
-Dims Engine::chain_left(const double* L, const Dims& ld, const double* M, const Dims& md,
-                        const SiteT& A, double* X3) {
+Dims Engine::chain_left(const TP& L, const Dims& ld, const TP& M, const Dims& md, const SiteT& A,
+                        const TP& X3) {
   const Dims ad = A.dims();
   const Dims x1 = ein_dims("clma,auvb->clmuvb", ld, md);
   con("clma,auvb->clmuvb", L, true, ld, M, true, md, X1_, x64_);
@@ -80,8 +103,8 @@ Dims Engine::chain_left(const double* L, const Dims& ld, const double* M, const 
   return x3;
 }
 
-Dims Engine::chain_right(const double* R, const Dims& rd, const double* M, const Dims& md,
-                         const SiteT& A, double* Y3) {
+Dims Engine::chain_right(const TP& R, const Dims& rd, const TP& M, const Dims& md, const SiteT& A,
+                         const TP& Y3) {
   const Dims ad = A.dims();
   const Dims y1 = ein_dims("auvb,brqc->auvrqc", md, rd);
   con("auvb,brqc->auvrqc", M, true, md, R, true, rd, X1_, x64_);
@@ -101,13 +124,13 @@ Mps Engine::product_mps(const Mps& T, const OLat& lat, int y, Arena& step) {
     const Dims t1 = ein_dims("auvb,sulnr->avbslnr", T.dims[x], ad);
     con("auvb,sulnr->avbslnr", T.p[x], true, T.dims[x], A.p, true, ad, X2_, x64_);
     const Dims t2 = ein_dims("avbslnr,svmoq->almnobrq", t1, ad);
-    double* cur = step.dalloc(numel(t2));
+    TP cur = alloc(step, numel(t2));
     con("avbslnr,svmoq->almnobrq", X2_, x64_, t1, A.p, true, ad, cur, true);
     Dims cd = t2;
     if (x == 0) {
       const Mat& c = lat.left[y];
       const Dims nd = ein_dims("lm,almnobrq->anobrq", {c.n, c.n}, cd);
-      double* nx = step.dalloc(numel(nd));
+      TP nx = alloc(step, numel(nd));
       ein(cx, "lm,almnobrq->anobrq", c.p, {c.n, c.n}, cur, cd, nx);
       cur = nx;
       cd = nd;
@@ -116,7 +139,7 @@ Mps Engine::product_mps(const Mps& T, const OLat& lat, int y, Arena& step) {
       const Mat& c = lat.right[y];
       const char* spec = (x == 0) ? "anobrq,rq->anob" : "almnobrq,rq->almnob";
       const Dims nd = ein_dims(spec, cd, {c.n, c.n});
-      double* nx = step.dalloc(numel(nd));
+      TP nx = alloc(step, numel(nd));
       ein(cx, spec, cur, cd, c.p, {c.n, c.n}, nx);
       cur = nx;
       cd = nd;
@@ -140,13 +163,13 @@ void Engine::left_canonicalize(Mps& P, Arena& step) {
   for (int x = 0; x + 1 < Lx; ++x) {
     const Dims pd = P.dims[x];
     const int m = pd[0] * pd[1] * pd[2], n = pd[3], k = std::min(m, n);
-    double* Q = step.dalloc(size_t(m) * k);
-    double* R = step.dalloc(size_t(k) * n);
+    TP Q = alloc(step, size_t(m) * k);
+    TP R = alloc(step, size_t(k) * n);
     qr_thin(cx, m, n, P.p[x], n, 1, Q, k, 1, R);
     P.p[x] = Q;
     P.dims[x] = {pd[0], pd[1], pd[2], k};
     const Dims nd = ein_dims("kb,bnoc->knoc", {k, n}, P.dims[x + 1]);
-    double* nx = step.dalloc(numel(nd));
+    TP nx = alloc(step, numel(nd));
     ein(cx, "kb,bnoc->knoc", R, {k, n}, P.p[x + 1], P.dims[x + 1], nx);
     P.p[x + 1] = nx;
     P.dims[x + 1] = nd;
@@ -159,13 +182,13 @@ void Engine::svd_truncate(Mps& P, const std::vector<int>& caps, Arena& step) {
     const Dims pd = P.dims[x];
     const int m = pd[0], n = pd[1] * pd[2] * pd[3];
     const int kk = std::min(caps[x - 1], std::min(m, n));
-    double* US = step.dalloc(size_t(m) * kk);
-    double* Vt = step.dalloc(size_t(kk) * n);
+    TP US = alloc(step, size_t(m) * kk);
+    TP Vt = alloc(step, size_t(kk) * n);
     svd_trunc(cx, m, n, P.p[x], kk, US, Vt);
     P.p[x] = Vt;
     P.dims[x] = {kk, pd[1], pd[2], pd[3]};
     const Dims nd = ein_dims("anob,bk->anok", P.dims[x - 1], {m, kk});
-    double* nx = step.dalloc(numel(nd));
+    TP nx = alloc(step, numel(nd));
     ein(cx, "anob,bk->anok", P.p[x - 1], P.dims[x - 1], US, {m, kk}, nx);
     P.p[x - 1] = nx;
     P.dims[x - 1] = nd;
@@ -183,15 +206,15 @@ Mps Engine::var_compress(const Mps& T, const OLat& lat, int y, const std::vector
     const int e = x == Lx - 1 ? 1 : caps[x];
     const int D = lat.at(y, x).dn;
     N.dims[x] = {c, D, D, e};
-    N.p[x] = step.dalloc(numel(N.dims[x]));
-    var_init(cx, T.p[x], T.dims[x].data(), N.p[x], N.dims[x].data(), opt.seed, tag, y, x);
+    N.p[x] = alloc(step, numel(N.dims[x]));
+    var_init(cx, T.p[x], T.dims[x].data(), N.p[x], N.dims[x].data(), opt.seed, tag, y, x, tmp1_);
   }
   // right-canonicalise the start: N[x] = R^T Q^T (QR of N[x]^T), R^T moves left
   for (int x = Lx - 1; x >= 1; --x) {
     const Dims nd = N.dims[x];
     const int c = nd[0], noe = nd[1] * nd[2] * nd[3];
     PEPS_REQUIRE(c <= noe, "internal: inconsistent bond caps");
-    double* Rt = step.dalloc(size_t(c) * c);
+    TP Rt = alloc(step, size_t(c) * c);
     qr_thin(cx, noe, c, N.p[x], 1, noe, N.p[x], 1, noe, Rt);
     const Dims pd = N.dims[x - 1];
     ein(cx, "anob,kb->anok", N.p[x - 1], pd, Rt, {c, c}, bb_);
@@ -221,7 +244,7 @@ Mps Engine::var_compress(const Mps& T, const OLat& lat, int y, const std::vector
         if (x < Lx - 1) {
           const int m = bd[0] * bd[1] * bd[2], n = bd[3];
           PEPS_REQUIRE(n <= m, "internal: inconsistent bond caps");
-          qr_thin(cx, m, n, bb_, n, 1, N.p[x], n, 1, nullptr);
+          qr_thin(cx, m, n, bb_, n, 1, N.p[x], n, 1, TP());
           ld[x + 1] = ein_dims("cbnroq,cnoe->erqb", x3, N.dims[x]);
           con("cbnroq,cnoe->erqb", X3_, x64_, x3, N.p[x], true, N.dims[x], Lenv_[x + 1], true);
         } else {
@@ -237,7 +260,7 @@ Mps Engine::var_compress(const Mps& T, const OLat& lat, int y, const std::vector
         PEPS_REQUIRE(bd == N.dims[x], "internal: local tensor shape");
         if (x > 0) {
           const int c = bd[0], noe = bd[1] * bd[2] * bd[3];
-          qr_thin(cx, noe, c, bb_, 1, noe, N.p[x], 1, noe, nullptr);
+          qr_thin(cx, noe, c, bb_, 1, noe, N.p[x], 1, noe, TP());
           rd[x - 1] = ein_dims("aelnmo,cnoe->almc", y3, N.dims[x]);
           con("aelnmo,cnoe->almc", X3_, x64_, y3, N.p[x], true, N.dims[x], Renv_[x - 1], true);
         } else {
@@ -250,7 +273,7 @@ Mps Engine::var_compress(const Mps& T, const OLat& lat, int y, const std::vector
   return N;
 }
 
-Mps Engine::absorb_compress(const Mps& T, const OLat& lat, int y, int tag, double* lnacc, Arena& keep) {
+Mps Engine::absorb_compress(const Mps& T, const OLat& lat, int y, int tag, const TP& lnacc, Arena& keep) {
   const int Lx = lat.Lx;
   std::vector<int> phys(Lx);
   std::vector<long long> prod(std::max(0, Lx - 1));
@@ -274,11 +297,11 @@ Mps Engine::absorb_compress(const Mps& T, const OLat& lat, int y, int tag, doubl
   } else {
     P = var_compress(T, lat, y, caps, tag, centre, step);
   }
-  normalize(cx, P.p[centre], (long long)numel(P.dims[centre]), lnacc);
+  normalize(cx, P.p[centre], (long long)numel(P.dims[centre]), lnacc, tmp0_);
   Mps out;
   for (int x = 0; x < Lx; ++x) {
     const size_t n = numel(P.dims[x]);
-    double* q = keep.dalloc(n);
+    TP q = alloc(keep, n);
     copy(cx, q, P.p[x], (long long)n);
     out.p.push_back(q);
     out.dims.push_back(P.dims[x]);
@@ -286,7 +309,7 @@ Mps Engine::absorb_compress(const Mps& T, const OLat& lat, int y, int tag, doubl
   return out;
 }
 
-std::vector<Mps> Engine::sweep(const OLat& lat, int tag, int upto, double* lnacc, Arena& keep) {
+std::vector<Mps> Engine::sweep(const OLat& lat, int tag, int upto, const TP& lnacc, Arena& keep) {
   std::vector<Mps> out;
   out.push_back(closure_mps(lat.top, keep));
   for (int y = 0; y < upto; ++y) out.push_back(absorb_compress(out.back(), lat, y, tag, lnacc, keep));
@@ -316,13 +339,13 @@ void Engine::row_rhos(const OLat& lat, const Mps& T, const Mps& B, int y, const 
     const Dims x3 = chain_left(Lenv_[x], ld[x], T.p[x], T.dims[x], lat.at(y, x), X3_);
     ld[x + 1] = ein_dims("cbnroq,cnoe->erqb", x3, B.dims[x]);
     con("cbnroq,cnoe->erqb", X3_, x64_, x3, B.p[x], true, B.dims[x], Lenv_[x + 1], true);
-    normalize(cx, Lenv_[x + 1], (long long)numel(ld[x + 1]), nullptr);
+    normalize(cx, Lenv_[x + 1], (long long)numel(ld[x + 1]), TP(), tmp0_);
   }
   for (int x = Lx - 1; x >= 1 && x - 1 >= xmin; --x) {
     const Dims y3 = chain_right(Renv_[x], rd[x], T.p[x], T.dims[x], lat.at(y, x), X3_);
     rd[x - 1] = ein_dims("aelnmo,cnoe->almc", y3, B.dims[x]);
     con("aelnmo,cnoe->almc", X3_, x64_, y3, B.p[x], true, B.dims[x], Renv_[x - 1], true);
-    normalize(cx, Renv_[x - 1], (long long)numel(rd[x - 1]), nullptr);
+    normalize(cx, Renv_[x - 1], (long long)numel(rd[x - 1]), TP(), tmp0_);
   }
   auto open_site = [&](int x) -> Dims {
     const SiteT& A = lat.at(y, x);
@@ -360,7 +383,8 @@ void Engine::row_rhos(const OLat& lat, const Mps& T, const Mps& B, int y, const 
   }
 }
 
-void Engine::norm_from_top(const OLat& lat, const Mps& T, const double* lns_acc, double* out) {
+void Engine::norm_from_top(const OLat& lat, const Mps& T, const TP& lns_acc, const TP& out) {
+  PEPS_REQUIRE(nb_ == 1, "internal: the norm is computed for one lattice");
   const int Lx = lat.Lx, y = lat.Ly - 1;
   double* extra = cx.ws->dalloc(1);
   double* s = cx.ws->dalloc(1);
@@ -377,11 +401,11 @@ void Engine::norm_from_top(const OLat& lat, const Mps& T, const double* lns_acc,
     con("cbnroq,cnoe->erqb", X3_, x64_, x3, bc.p, true, bd, Lenv_[1 - cur], true);
     cur = 1 - cur;
     ld = nd;
-    if (x + 1 < Lx) normalize(cx, Lenv_[cur], (long long)numel(ld), extra);
+    if (x + 1 < Lx) normalize(cx, Lenv_[cur], (long long)numel(ld), extra, tmp0_);
   }
   const Mat& rc = lat.right[y];
   ein(cx, "erqb,rq->", Lenv_[cur], ld, rc.p, {rc.n, rc.n}, s);
-  finish_norm(cx, lns_acc, 1, extra, s, out, out + 1);
+  finish_norm(cx, lns_acc.d(0), 1, extra, s, out.d(0), out.d(0) + 1);
 }
 
 }  // namespace peps

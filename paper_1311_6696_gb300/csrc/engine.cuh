@@ -1,4 +1,8 @@
 // Host-side orchestration of the boundary-MPS contraction (device resident).
+// An engine runs nb independent problems of identical shape in lockstep (the
+// cluster windows of one shape; nb = 1 for the full lattice): every tensor is
+// a pointer set (TP) with one pointer per problem, and every step is one
+// batched launch for all of them.
 #pragma once
 #include <memory>
 #include <vector>
@@ -8,13 +12,13 @@
 namespace peps {
 
 struct SiteT {
-  const double* p = nullptr;
+  TP p;
   int d = 0, du = 0, dl = 0, dn = 0, dr = 0;
   Dims dims() const { return {d, du, dl, dn, dr}; }
 };
 
 struct Mat {
-  const double* p = nullptr;   // n x n, row-major (ket leg, bra leg)
+  TP p;                        // n x n, row-major (ket leg, bra leg)
   int n = 0;
 };
 
@@ -27,7 +31,7 @@ struct OLat {
 };
 
 struct Mps {
-  std::vector<double*> p;
+  std::vector<TP> p;
   std::vector<Dims> dims;      // [a, u, v, b]
 };
 
@@ -52,28 +56,34 @@ struct EnvData {
 // Contraction engine bound to one stream/workspace.
 class Engine {
  public:
-  Engine(Ctx& cx, const Opts& o, int d, int Dmax, int Lmax);
+  Engine(Ctx& cx, const Opts& o, int d, int Dmax, int Lmax, int nb = 1);
 
   // Top-down boundaries of `lat`: out[y] = boundary above row y, y = 0..upto.
-  // lnacc (device scalar) accumulates the log of every rescaling factor.
-  std::vector<Mps> sweep(const OLat& lat, int tag, int upto, double* lnacc, Arena& keep);
+  // lnacc (a device scalar per problem) accumulates the log of every rescaling factor.
+  std::vector<Mps> sweep(const OLat& lat, int tag, int upto, const TP& lnacc, Arena& keep);
 
   // Density matrices of row y between top boundary T and bottom boundary B:
   // rho_site of column x into dst for every (x, dst) in `sites`, rho of the
   // bond (x, x+1) into dst for every (x, dst) in `bonds`.
-  using Targets = std::vector<std::pair<int, double*>>;
+  using Targets = std::vector<std::pair<int, TP>>;
   void row_rhos(const OLat& lat, const Mps& T, const Mps& B, int y, const Targets& sites,
                 const Targets& bonds);
 
   // ln|<psi|psi>| from the top boundary above the last row (writes out[0], out[1] = sign).
-  void norm_from_top(const OLat& lat, const Mps& T, const double* lns_acc, double* out);
+  void norm_from_top(const OLat& lat, const Mps& T, const TP& lns_acc, const TP& out);
+
+  int problems() const { return nb_; }
+  // Run the next calls on the first B problems only (B <= the engine's capacity).
+  void use(int B);
+  // Device doubles one problem of an engine with these settings holds.
+  static size_t footprint(const Opts& o, int d, int Dmax, int Lmax);
 
   Ctx& cx;
   Opts opt;
 
  private:
   Mps closure_mps(const std::vector<Mat>& mats, Arena& keep);
-  Mps absorb_compress(const Mps& T, const OLat& lat, int y, int tag, double* lnacc, Arena& keep);
+  Mps absorb_compress(const Mps& T, const OLat& lat, int y, int tag, const TP& lnacc, Arena& keep);
   Mps product_mps(const Mps& T, const OLat& lat, int y, Arena& keep);
   void left_canonicalize(Mps& P, Arena& keep);
   void svd_truncate(Mps& P, const std::vector<int>& caps, Arena& keep);
@@ -82,23 +92,24 @@ class Engine {
 
   // One pairwise contraction.  FP64 mode: FP64 gather-GEMM, every operand FP64.
   // Tensor-core modes: tcgen05 GEMM; a64/b64/c64 tag each tensor FP64 (else FP32).
-  void con(const char* spec, const void* A, bool a64, const Dims& ad, const void* B, bool b64, const Dims& bd,
-           void* C, bool c64);
+  void con(const char* spec, const TP& A, bool a64, const Dims& ad, const TP& B, bool b64, const Dims& bd,
+           const TP& C, bool c64);
+  // `per` doubles for every problem from arena a.
+  TP alloc(Arena& a, size_t per) const;
   bool tc_ = false;   // tensor-core contractions (chain intermediates stored FP32)
   bool x64_ = true;   // dtype of the chain intermediates X1, X2, X3
 
   // absorb chain pieces
-  Dims chain_left(const double* L, const Dims& ld, const double* M, const Dims& md, const SiteT& A,
-                  double* X3);
-  Dims chain_right(const double* R, const Dims& rd, const double* M, const Dims& md,
-                   const SiteT& A, double* Y3);
+  Dims chain_left(const TP& L, const Dims& ld, const TP& M, const Dims& md, const SiteT& A, const TP& X3);
+  Dims chain_right(const TP& R, const Dims& rd, const TP& M, const Dims& md, const SiteT& A, const TP& Y3);
 
-  int d_, Dmax_, Lmax_;
+  int d_, Dmax_, Lmax_, nb_, cap_;
   size_t bigN_;                 // chi^2 * Dmax^4 (elements of the largest chain intermediate / d)
-  double *X1_, *X2_, *X3_, *bb_;
-  std::vector<double*> Lenv_, Renv_;
+  TP X1_, X2_, X3_, bb_;
+  std::vector<TP> Lenv_, Renv_;
   size_t envN_;
-  double* one_;                 // device scalar 1.0
+  TP one_;                      // device scalar 1.0 (shared)
+  TP tmp0_, tmp1_;              // one device scalar per problem each
 };
 
 // Caps of the new boundary (same rule as the documented reading).

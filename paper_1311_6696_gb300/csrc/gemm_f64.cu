@@ -8,8 +8,9 @@
 // On GB300 the FP64 pipe issues about 2 DFMA per clock per SM (~1.2 TFLOP/s
 // for the chip), so this kernel is bound by the FP64 ALU long before memory:
 // a 64x64x16 tile step performs 65,536 DFMA against 2,048 loaded doubles.
-// Grid = (tiles, split-K, batch); split-K partials are reduced by a second
-// kernel in a fixed order, so results are deterministic.
+// Grid = (tiles, split-K, batch x problems); split-K partials are reduced by
+// a second kernel in a fixed order, so results are deterministic.  Independent
+// problems of one shape (TP pointer sets) share a launch.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -30,9 +31,8 @@ struct Grp {
 };
 
 struct GemmArgs {
-  const double* A;
-  const double* B;
-  double* C;
+  TP A, B, C;        // per problem
+  int nprob;
   double* part;
   Grp gm, gn, gk, gb;
   long long M, N, K, NB;
@@ -69,7 +69,11 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const GemmArgs g) {
   const long long tm = (long long)blockIdx.x / tiles_n, tn = (long long)blockIdx.x % tiles_n;
   const long long m0 = tm * BM, n0 = tn * BN;
   const int split = blockIdx.y;
-  const long long bi = blockIdx.z;
+  const long long bz = blockIdx.z;              // problem * NB + batch index
+  const long long bi = bz % g.NB;
+  const int pb = int(bz / g.NB);
+  const double* __restrict__ Ap = static_cast<const double*>(g.A.p[pb]);
+  const double* __restrict__ Bp = static_cast<const double*>(g.B.p[pb]);
   const long long kbeg = split * g.kchunk;
   const long long kend = min(g.K, kbeg + g.kchunk);
 
@@ -110,12 +114,12 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const GemmArgs g) {
     for (int e = tid; e < BK * BM; e += 256) {
       int kk = e / BM, mm = e % BM;
       long long om = oAm[mm], ok = oAk[kk];
-      As[kk][mm] = (om >= 0 && ok >= 0) ? g.A[bA + om + ok] : 0.0;
+      As[kk][mm] = (om >= 0 && ok >= 0) ? Ap[bA + om + ok] : 0.0;
     }
     for (int e = tid; e < BK * BN; e += 256) {
       int kk = e / BN, nn = e % BN;
       long long on = oBn[nn], ok = oBk[kk];
-      Bs[kk][nn] = (on >= 0 && ok >= 0) ? g.B[bB + ok + on] : 0.0;
+      Bs[kk][nn] = (on >= 0 && ok >= 0) ? Bp[bB + ok + on] : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -144,9 +148,9 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const GemmArgs g) {
       const long long n = n0 + c;
       if (n >= g.N) continue;
       if (g.splitk > 1) {
-        g.part[((split * g.NB + bi) * g.M + m) * g.N + n] = acc[i][j];
+        g.part[((split * g.NB * g.nprob + bz) * g.M + m) * g.N + n] = acc[i][j];
       } else {
-        double* p = g.C + bC + oCm[r] + oCn[c];
+        double* p = static_cast<double*>(g.C.p[pb]) + bC + oCm[r] + oCn[c];
         double v = g.alpha * acc[i][j];
         if (g.beta != 0.0) v += g.beta * *p;
         *p = v;
@@ -156,17 +160,18 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const GemmArgs g) {
 }
 
 __global__ void k_splitk_reduce(const GemmArgs g) {
-  const long long total = g.NB * g.M * g.N;
+  const long long nbt = g.NB * g.nprob;
+  const long long total = nbt * g.M * g.N;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
-    long long n = t % g.N, m = (t / g.N) % g.M, bi = t / (g.N * g.M);
+    long long n = t % g.N, m = (t / g.N) % g.M, bz = t / (g.N * g.M);
     double s = 0.0;
-    for (int sp = 0; sp < g.splitk; ++sp) s += g.part[((sp * g.NB + bi) * g.M + m) * g.N + n];
+    for (int sp = 0; sp < g.splitk; ++sp) s += g.part[((sp * nbt + bz) * g.M + m) * g.N + n];
     long long a, b, cb, cm, cn;
-    decomp(g.gb, bi, a, b, cb);
+    decomp(g.gb, bz % g.NB, a, b, cb);
     decomp(g.gm, m, a, b, cm);
     decomp(g.gn, n, a, b, cn);
-    double* p = g.C + cb + cm + cn;
+    double* p = static_cast<double*>(g.C.p[bz / g.NB]) + cb + cm + cn;
     double v = g.alpha * s;
     if (g.beta != 0.0) v += g.beta * *p;
     *p = v;
@@ -177,11 +182,15 @@ __global__ void k_splitk_reduce(const GemmArgs g) {
 // chunk for every output at once; partials are summed in a fixed order.
 constexpr int DOT_MAXP = 16;
 
+// Grid = (K chunks, problems).
 __global__ void __launch_bounds__(256) k_dot_partial(const GemmArgs g, long long kchunk, double* part) {
   __shared__ long long oa[DOT_MAXP], ob[DOT_MAXP];
   __shared__ double red[8][DOT_MAXP];
   const int P = int(g.M * g.N * g.NB);
   const int tid = threadIdx.x;
+  const int pb = blockIdx.y;
+  const double* __restrict__ Ap = static_cast<const double*>(g.A.p[pb]);
+  const double* __restrict__ Bp = static_cast<const double*>(g.B.p[pb]);
   if (tid < P) {
     const long long bi = tid / (g.M * g.N), mn = tid % (g.M * g.N), m = mn / g.N, n = mn % g.N;
     long long a0, b0, c0, a1, b1, c1, a2, b2, c2;
@@ -201,7 +210,7 @@ __global__ void __launch_bounds__(256) k_dot_partial(const GemmArgs g, long long
     decomp(g.gk, k, ka, kb, kc);
 #pragma unroll
     for (int p = 0; p < DOT_MAXP; ++p)
-      if (p < P) acc[p] = fma(g.A[oa[p] + ka], g.B[ob[p] + kb], acc[p]);
+      if (p < P) acc[p] = fma(Ap[oa[p] + ka], Bp[ob[p] + kb], acc[p]);
   }
   const int lane = tid & 31, w = tid >> 5;
 #pragma unroll
@@ -215,22 +224,24 @@ __global__ void __launch_bounds__(256) k_dot_partial(const GemmArgs g, long long
   if (tid < P) {
     double v = 0.0;
     for (int i = 0; i < int(blockDim.x >> 5); ++i) v += red[i][tid];
-    part[(long long)blockIdx.x * DOT_MAXP + tid] = v;
+    part[((long long)pb * gridDim.x + blockIdx.x) * DOT_MAXP + tid] = v;
   }
 }
 
+// Grid = problems.
 __global__ void k_dot_finish(const GemmArgs g, int nblk, const double* part) {
   const int P = int(g.M * g.N * g.NB);
   const int p = threadIdx.x;
+  const int pb = blockIdx.x;
   if (p >= P) return;
   double v = 0.0;
-  for (int b = 0; b < nblk; ++b) v += part[(long long)b * DOT_MAXP + p];
+  for (int b = 0; b < nblk; ++b) v += part[((long long)pb * nblk + b) * DOT_MAXP + p];
   const long long bi = p / (g.M * g.N), mn = p % (g.M * g.N), m = mn / g.N, n = mn % g.N;
   long long a, b, c0, c1, c2;
   decomp(g.gb, bi, a, b, c0);
   decomp(g.gm, m, a, b, c1);
   decomp(g.gn, n, a, b, c2);
-  double* out = g.C + c0 + c1 + c2;
+  double* out = static_cast<double*>(g.C.p[pb]) + c0 + c1 + c2;
   double r = g.alpha * v;
   if (g.beta != 0.0) r += g.beta * *out;
   *out = r;
@@ -287,16 +298,35 @@ Dims ein_dims(const char* spec, const Dims& ad, const Dims& bd) {
   return out;
 }
 
-void ein(Ctx& cx, const char* spec, const double* A, const Dims& ad, const double* B,
-         const Dims& bd, double* C, double alpha, double beta) {
+TP strided(double* base, int count, size_t per) {
+  TP t;
+  t.n = count;
+  const size_t stride = (per + 31) / 32 * 32;
+  for (int b = 0; b < count; ++b) t.p[b] = base + b * stride;
+  return t;
+}
+
+int problems(std::initializer_list<const TP*> args) {
+  int B = 1;
+  for (const TP* t : args) B = std::max(B, t->n);
+  for (const TP* t : args) PEPS_REQUIRE(t->n <= 1 || t->n == B, "internal: problem counts differ");
+  PEPS_REQUIRE(B <= MAXB, "internal: too many problems in one launch");
+  return B;
+}
+
+void ein(Ctx& cx, const char* spec, const TP& A, const Dims& ad, const TP& B,
+         const Dims& bd, const TP& C, double alpha, double beta) {
   Parsed p = parse(spec);
   Dims cd = ein_dims(spec, ad, bd);
   auto sa = strides_of(ad), sb = strides_of(bd), sc = strides_of(cd);
+  const int np = problems({&A, &B, &C});
+  PEPS_REQUIRE(!A.null() && !B.null() && C.n == np, "internal: contraction operands");
   GemmArgs g;
   std::memset(&g, 0, sizeof(g));
-  g.A = A;
-  g.B = B;
-  g.C = C;
+  g.A = A.all(np);
+  g.B = B.all(np);
+  g.C = C.all(np);
+  g.nprob = np;
   g.alpha = alpha;
   g.beta = beta;
   auto push = [&](Grp& gr, int dim, long long a, long long b, long long c) {
@@ -351,16 +381,16 @@ void ein(Ctx& cx, const char* spec, const double* A, const Dims& ad, const doubl
   if (g.K == 0) {
     PEPS_REQUIRE(false, "empty contraction dimension");
   }
-  PEPS_REQUIRE(g.NB <= 65535, "batch too large");
+  PEPS_REQUIRE(g.NB * np <= 65535, "batch too large");
 
   if (g.M * g.N * g.NB <= DOT_MAXP && g.K >= 1024) {
     const long long kchunk = 2048;
-    const int nblk = int(std::min<long long>((g.K + kchunk - 1) / kchunk, 4 * num_sms()));
+    const int nblk = int(std::max<long long>(1, std::min<long long>((g.K + kchunk - 1) / kchunk, 4 * num_sms() / np)));
     const long long kc = (g.K + nblk - 1) / nblk;
-    double* part = cx.scratch(size_t(nblk) * DOT_MAXP);
-    Launch L(K_GEMM_F64, cx.st, 2.0 * double(g.M * g.N * g.NB) * double(g.K), 0);
-    k_dot_partial<<<nblk, 256, 0, cx.st>>>(g, kc, part);
-    k_dot_finish<<<1, 32, 0, cx.st>>>(g, nblk, part);
+    double* part = cx.scratch(size_t(nblk) * np * DOT_MAXP);
+    Launch L(K_GEMM_F64, cx.st, 2.0 * double(g.M * g.N * g.NB) * double(g.K) * np, 0);
+    k_dot_partial<<<dim3(nblk, np), 256, 0, cx.st>>>(g, kc, part);
+    k_dot_finish<<<np, 32, 0, cx.st>>>(g, nblk, part);
     PEPS_CHECK_LAUNCH();
     return;
   }
@@ -379,7 +409,7 @@ void ein(Ctx& cx, const char* spec, const double* A, const Dims& ad, const doubl
   }
   const int BM = BMs[best], BN = 4096 / BM;
   const long long tiles = (long long)cdiv(g.M, BM) * cdiv(g.N, BN);
-  const long long ctas = tiles * g.NB;
+  const long long ctas = tiles * g.NB * np;
   const int target = 2 * num_sms();
   int splitk = 1;
   if (ctas < target) {
@@ -390,13 +420,13 @@ void ein(Ctx& cx, const char* spec, const double* A, const Dims& ad, const doubl
   g.kchunk = ((g.K + splitk - 1) / splitk + BK - 1) / BK * BK;
   splitk = int((g.K + g.kchunk - 1) / g.kchunk);
   g.splitk = splitk;
-  if (splitk > 1) g.part = cx.scratch(size_t(splitk) * g.NB * g.M * g.N);
+  if (splitk > 1) g.part = cx.scratch(size_t(splitk) * g.NB * np * g.M * g.N);
   PEPS_REQUIRE(tiles < (1LL << 31), "too many tiles");
 
-  const double flops = 2.0 * double(g.M) * double(g.N) * double(g.K) * double(g.NB);
+  const double flops = 2.0 * double(g.M) * double(g.N) * double(g.K) * double(g.NB) * np;
   {
     Launch L(K_GEMM_F64, cx.st, flops, 0);
-    dim3 grid(unsigned(tiles), unsigned(splitk), unsigned(g.NB));
+    dim3 grid(unsigned(tiles), unsigned(splitk), unsigned(g.NB * np));
     switch (BM) {
       case 16: k_gemm_f64<16, 256><<<grid, 256, 0, cx.st>>>(g); break;
       case 32: k_gemm_f64<32, 128><<<grid, 256, 0, cx.st>>>(g); break;
@@ -408,7 +438,7 @@ void ein(Ctx& cx, const char* spec, const double* A, const Dims& ad, const doubl
   }
   if (splitk > 1) {
     Launch L(K_AUX, cx.st);
-    long long total = g.NB * g.M * g.N;
+    long long total = g.NB * np * g.M * g.N;
     unsigned blocks = unsigned(std::min<long long>((total + 255) / 256, 4 * 1024));
     k_splitk_reduce<<<blocks, 256, 0, cx.st>>>(g);
     PEPS_CHECK_LAUNCH();

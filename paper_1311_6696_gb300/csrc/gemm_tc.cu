@@ -13,6 +13,11 @@
 // gather copy that also rounds to TF32 / BF16 and, for the split variants,
 // writes the residual as a second operand: x ~ hi + lo, product ~ hi*hi +
 // hi*lo + lo*hi).
+//
+// Independent problems of one shape share a launch: problem p's operands are
+// packed at rows [p * rows_pad, p * rows_pad + M) of one [P * rows_pad][K]
+// array (rows_pad a multiple of the tile height, so no tile straddles two
+// problems), and the epilogue writes through problem p's output pointer.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -47,8 +52,9 @@ struct TcArgs {
   int out_f64;       // 1: C is double, else float
   int out_lo;        // 1: also write C_lo (split residual), C is then the rounded hi part
   int stages;        // ring depth (<= TC_STAGES), chosen to fit shared memory
-  void* C;
-  void* Clo;
+  int nprob;         // problems in this launch
+  long long pad_m, pad_n;   // packed rows per problem (multiples of TC_BM and BN)
+  TP C, Clo;         // per problem
   Grp gm, gn;        // output offsets of the M and N groups
   double alpha;
   int* flag;
@@ -164,8 +170,12 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ 
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long tiles_n = (g.N + BN - 1) / BN;
-  const long long m0 = ((long long)blockIdx.x / tiles_n) * TC_BM;
-  const long long n0 = ((long long)blockIdx.x % tiles_n) * BN;
+  const long long tiles = ((g.M + TC_BM - 1) / TC_BM) * tiles_n;
+  const int pb = int(blockIdx.x / tiles);
+  const long long t = blockIdx.x % tiles;
+  const long long m0 = (t / tiles_n) * TC_BM;
+  const long long n0 = (t % tiles_n) * BN;
+  const int ra = int(pb * g.pad_m + m0), rb = int(pb * g.pad_n + n0);   // packed rows of the tiles
 
   if (tid == 0) {
     for (int s = 0; s < g.stages; ++s) {
@@ -211,11 +221,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ 
       uint8_t* st = base + s * stage_bytes;
       mbar_expect_tx(&full[s], tx);
       const int kx = kt * (TC_ROWB / (g.bf16 ? 2 : 4));
-      tma_load_2d(st, &ta, &full[s], kx, int(m0));
-      tma_load_2d(st + A_BYTES, &tb, &full[s], kx, int(n0));
+      tma_load_2d(st, &ta, &full[s], kx, ra);
+      tma_load_2d(st + A_BYTES, &tb, &full[s], kx, rb);
       if (g.split) {
-        tma_load_2d(st + A_BYTES + B_BYTES, &tal, &full[s], kx, int(m0));
-        tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tbl, &full[s], kx, int(n0));
+        tma_load_2d(st + A_BYTES + B_BYTES, &tal, &full[s], kx, ra);
+        tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tbl, &full[s], kx, rb);
       }
     }
   } else if (warp == 1 && lane == 0) {
@@ -262,6 +272,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ 
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int row = warp * 32 + lane;
   const long long om = offm[row];
+  float* const Cf = static_cast<float*>(g.C.p[pb]);
+  double* const Cd = static_cast<double*>(g.C.p[pb]);
+  float* const Cl = g.out_lo ? static_cast<float*>(g.Clo.p[pb]) : nullptr;
   if (have) {
     for (int c0 = 0; c0 < BN; c0 += 16) {
       uint32_t r[16];
@@ -273,13 +286,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ 
         if (on < 0) continue;
         const float v = __uint_as_float(r[j]) * float(g.alpha);
         if (g.out_f64) {
-          static_cast<double*>(g.C)[om + on] = double(v);
+          Cd[om + on] = double(v);
         } else if (g.out_lo) {
           const float h = round_tf32(v);
-          static_cast<float*>(g.C)[om + on] = h;
-          static_cast<float*>(g.Clo)[om + on] = round_tf32(v - h);
+          Cf[om + on] = h;
+          Cl[om + on] = round_tf32(v - h);
         } else {
-          static_cast<float*>(g.C)[om + on] = v;
+          Cf[om + on] = v;
         }
       }
     }
@@ -296,26 +309,29 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ 
 // src[sum(idx_i * stride_i)] with r, k decomposed over the row / K groups.
 // Rounds to TF32 (or converts to BF16); `lo` receives the rounded residual.
 struct PackArgs {
-  const void* src;
+  TP src;            // per problem
   int src_f64;
   Grp gr, gk;        // strides into src
-  long long rows, K, ld;
+  long long rows, K, ld, pad;   // pad: packed rows per problem
   void* hi;
   void* lo;
   int bf16;
 };
 
+// Grid = (blocks, problems).
 __global__ void k_pack(const PackArgs p) {
   const long long total = p.rows * p.K;
+  const int pb = blockIdx.y;
+  const void* src = p.src.p[pb];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const long long r = t / p.K, k = t - r * p.K;
     long long o1, o2;
     decomp(p.gr, r, o1);
     decomp(p.gk, k, o2);
-    const double v = p.src_f64 ? static_cast<const double*>(p.src)[o1 + o2]
-                               : double(static_cast<const float*>(p.src)[o1 + o2]);
-    const long long d = r * p.ld + k;
+    const double v = p.src_f64 ? static_cast<const double*>(src)[o1 + o2]
+                               : double(static_cast<const float*>(src)[o1 + o2]);
+    const long long d = (pb * p.pad + r) * p.ld + k;
     if (p.bf16) {
       const __nv_bfloat16 h = __double2bfloat16(v);
       static_cast<__nv_bfloat16*>(p.hi)[d] = h;
@@ -408,9 +424,11 @@ struct Operand {
   long long rows = 0, K = 0, ld = 0;
 };
 
-// Pack one operand into [rows][ld] (rows over `rowletters`, K over `kletters`).
-Operand pack(Ctx& cx, const void* src, int src_f64, const std::string& letters, const Dims& dims,
-             const std::string& rowletters, const std::string& kletters, int bf16, int split, double* mem) {
+// Pack one operand of each of np problems into [np * pad][ld] (rows over
+// `rowletters`, K over `kletters`; problem p at rows p * pad ..).
+Operand pack(Ctx& cx, const TP& src, int np, long long pad, int src_f64, const std::string& letters,
+             const Dims& dims, const std::string& rowletters, const std::string& kletters, int bf16, int split,
+             double* mem) {
   auto st = strides_of(dims);
   PackArgs p;
   std::memset(&p, 0, sizeof(p));
@@ -427,22 +445,25 @@ Operand pack(Ctx& cx, const void* src, int src_f64, const std::string& letters, 
   o.K = prod(p.gk);
   const int align = bf16 ? 8 : 4;
   o.ld = (o.K + align - 1) / align * align;
-  const size_t bytes = size_t(o.rows) * o.ld * (bf16 ? 2 : 4);
+  PEPS_REQUIRE(pad >= o.rows, "internal: pack padding");
+  const size_t bytes = size_t(np) * size_t(pad) * o.ld * (bf16 ? 2 : 4);
   const size_t words = (bytes + 255) / 256 * 32;   // doubles, 256-byte aligned
   o.hi = mem;
   o.lo = split ? static_cast<void*>(mem + words) : nullptr;
-  p.src = src;
+  p.src = src.all(np);
   p.src_f64 = src_f64;
   p.rows = o.rows;
   p.K = o.K;
   p.ld = o.ld;
+  p.pad = pad;
   p.hi = o.hi;
   p.lo = o.lo;
   p.bf16 = bf16;
   const long long total = o.rows * o.K;
   Launch L(K_AUX, cx.st);
-  const unsigned blocks = unsigned(std::max<long long>(1, std::min<long long>((total + 255) / 256, 4096)));
-  k_pack<<<blocks, 256, 0, cx.st>>>(p);
+  const long long per = std::max<long long>(1, 4096 / np);
+  const unsigned blocks = unsigned(std::max<long long>(1, std::min<long long>((total + 255) / 256, per)));
+  k_pack<<<dim3(blocks, np), 256, 0, cx.st>>>(p);
   PEPS_CHECK_LAUNCH();
   return o;
 }
@@ -461,7 +482,7 @@ void launch_tc(Ctx& cx, const CUtensorMap& ta, const CUtensorMap& tb, const CUte
   const int a_bytes = TC_BM * TC_ROWB, b_bytes = BN * TC_ROWB;
   const int stage = g.split ? 2 * (a_bytes + b_bytes) : (a_bytes + b_bytes);
   const int budget = 200 * 1024;
-  g.stages = std::max(1, std::min(TC_STAGES, (budget - 1024) / stage));
+  g.stages = std::max(1, std::min({TC_STAGES, (budget - 1024) / stage, g.ktiles}));
   const size_t smem = size_t(stage) * g.stages + 1024;
   static std::once_flag once;
   std::call_once(once, [] {
@@ -485,9 +506,12 @@ int tc_available() {
   return ok;
 }
 
-void ein_tc(Ctx& cx, const char* spec, const void* A, int a_f64, const Dims& ad, const void* B, int b_f64,
-            const Dims& bd, void* C, int c_f64, int prec, double alpha, void* Clo) {
+void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, const TP& B, int b_f64,
+            const Dims& bd, const TP& C, int c_f64, int prec, double alpha, const TP& Clo) {
   PEPS_REQUIRE(tc_available(), "tensor-core path needs an sm_103 device");
+  const int np = problems({&A, &B, &C, &Clo});
+  PEPS_REQUIRE(!A.null() && !B.null() && C.n == np && (Clo.null() || Clo.n == np),
+               "internal: contraction operands");
   const Parsed p = parse(spec);
   const Dims cd = ein_dims(spec, ad, bd);
   const auto sc = strides_of(cd);
@@ -518,16 +542,18 @@ void ein_tc(Ctx& cx, const char* spec, const void* A, int a_f64, const Dims& ad,
   for (char ch : nL) N *= bd[p.b.find(ch)];
   for (char ch : kL) K *= ad[p.a.find(ch)];
   if (M == 0 || N == 0) return;
-  const size_t wa = pack_words(M, K, bf16, split), wb = pack_words(N, K, bf16, split);
-  double* mem = cx.scratch(wa + wb);
-  const Operand oa = pack(cx, A, a_f64, p.a, ad, mL, kL, bf16, split, mem);
-  const Operand ob = pack(cx, B, b_f64, p.b, bd, nL, kL, bf16, split, mem + wa);
   int BN = 16;
   while (BN < N && BN < 128) BN *= 2;
-  const CUtensorMap ta = make_map(oa.hi, M, K, oa.ld, bf16, TC_BM);
-  const CUtensorMap tb = make_map(ob.hi, N, K, ob.ld, bf16, BN);
-  const CUtensorMap tal = split ? make_map(oa.lo, M, K, oa.ld, bf16, TC_BM) : ta;
-  const CUtensorMap tbl = split ? make_map(ob.lo, N, K, ob.ld, bf16, BN) : tb;
+  const long long pad_m = (M + TC_BM - 1) / TC_BM * TC_BM, pad_n = (N + BN - 1) / BN * BN;
+  const size_t wa = pack_words(np * pad_m, K, bf16, split), wb = pack_words(np * pad_n, K, bf16, split);
+  double* mem = cx.scratch(wa + wb);
+  const Operand oa = pack(cx, A, np, pad_m, a_f64, p.a, ad, mL, kL, bf16, split, mem);
+  const Operand ob = pack(cx, B, np, pad_n, b_f64, p.b, bd, nL, kL, bf16, split, mem + wa);
+  PEPS_REQUIRE(np * pad_m < (1LL << 31) && np * pad_n < (1LL << 31), "operand too large for one launch");
+  const CUtensorMap ta = make_map(oa.hi, np * pad_m, K, oa.ld, bf16, TC_BM);
+  const CUtensorMap tb = make_map(ob.hi, np * pad_n, K, ob.ld, bf16, BN);
+  const CUtensorMap tal = split ? make_map(oa.lo, np * pad_m, K, oa.ld, bf16, TC_BM) : ta;
+  const CUtensorMap tbl = split ? make_map(ob.lo, np * pad_n, K, ob.ld, bf16, BN) : tb;
   g.M = M;
   g.N = N;
   g.K = K;
@@ -535,14 +561,17 @@ void ein_tc(Ctx& cx, const char* spec, const void* A, int a_f64, const Dims& ad,
   g.split = split;
   g.bf16 = bf16;
   g.out_f64 = c_f64;
-  g.out_lo = (Clo != nullptr && !c_f64) ? 1 : 0;
-  g.C = C;
-  g.Clo = Clo;
+  g.out_lo = (!Clo.null() && !c_f64) ? 1 : 0;
+  g.nprob = np;
+  g.pad_m = pad_m;
+  g.pad_n = pad_n;
+  g.C = C.all(np);
+  g.Clo = Clo.all(np);
   g.alpha = alpha;
   g.flag = cx.flag;
-  const long long tiles = ((M + TC_BM - 1) / TC_BM) * ((N + BN - 1) / BN);
+  const long long tiles = ((M + TC_BM - 1) / TC_BM) * ((N + BN - 1) / BN) * np;
   PEPS_REQUIRE(tiles < (1LL << 31), "too many tiles");
-  const double flops = 2.0 * double(M) * double(N) * double(K);
+  const double flops = 2.0 * double(M) * double(N) * double(K) * np;
   Launch L(K_GEMM_TC, cx.st, flops, 0);
   switch (BN) {
     case 16: launch_tc<16>(cx, ta, tb, tal, tbl, g, tiles); break;

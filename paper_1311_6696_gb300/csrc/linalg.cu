@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <cstdlib>
 #include <mutex>
 #include <vector>
@@ -49,26 +50,33 @@ __device__ double block_sum(double v, double* red) {
 
 struct QrArgs {
   int m, n;
-  const double* A;
+  TP A;         // per problem
   long long rs, cs;
-  double* Q;
+  TP Q;
   long long qrs, qcs;
-  double* R;
-  double* W;    // m*n work, column-major
-  double* Qw;   // m*k work, column-major
-  double* tau;  // k
+  TP R;         // absent: R not wanted
+  double* W;    // m*n work per problem, column-major (problem p at W + p * wst)
+  double* Qw;   // m*k work per problem, column-major (+ p * qst)
+  double* tau;  // k per problem (+ p * tst)
+  long long wst, qst, tst;
 };
 
+// Grid = problems, one CTA each.
 __global__ void __launch_bounds__(QR_THREADS) k_qr_house(const QrArgs q) {
   __shared__ double red[32];
   __shared__ double s_tau, s_scale;
   const int m = q.m, n = q.n, k = min(m, n);
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  double* W = q.W;
+  const int pb = blockIdx.x;
+  const double* A = q.A.d(pb);
+  double* const Qo = q.Q.d(pb);
+  double* const Ro = q.R.n ? q.R.d(pb) : nullptr;
+  double* const tau_g = q.tau + pb * q.tst;
+  double* W = q.W + pb * q.wst;
   for (long long e = tid; e < (long long)m * n; e += nt) {
     int i = int(e % m), j = int(e / m);
-    W[e] = q.A[i * q.rs + j * q.cs];
+    W[e] = A[i * q.rs + j * q.cs];
   }
   __syncthreads();
   for (int j = 0; j < k; ++j) {
@@ -90,7 +98,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_house(const QrArgs q) {
         s_scale = 1.0 / (alpha - beta);
         W[(long long)j * m + j] = beta;
       }
-      q.tau[j] = s_tau;
+      tau_g[j] = s_tau;
     }
     __syncthreads();
     const double tau = s_tau, scale = s_scale;
@@ -109,14 +117,14 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_house(const QrArgs q) {
     __syncthreads();
   }
   // Q = H_0 ... H_{k-1} [I_k; 0], accumulated backwards.
-  double* Qw = q.Qw;
+  double* Qw = q.Qw + pb * q.qst;
   for (long long e = tid; e < (long long)m * k; e += nt) {
     int i = int(e % m), j = int(e / m);
     Qw[e] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
   for (int j = k - 1; j >= 0; --j) {
-    const double tau = q.tau[j];
+    const double tau = tau_g[j];
     if (tau != 0.0) {
       for (int c = j + warp; c < k; c += nw) {
         double w = 0.0;
@@ -131,12 +139,12 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_house(const QrArgs q) {
   }
   for (long long e = tid; e < (long long)m * k; e += nt) {
     int i = int(e % m), j = int(e / m);
-    q.Q[i * q.qrs + j * q.qcs] = Qw[e];
+    Qo[i * q.qrs + j * q.qcs] = Qw[e];
   }
-  if (q.R) {
+  if (Ro) {
     for (long long e = tid; e < (long long)k * n; e += nt) {
       int i = int(e / n), j = int(e % n);
-      q.R[e] = (j >= i) ? W[(long long)j * m + i] : 0.0;
+      Ro[e] = (j >= i) ? W[(long long)j * m + i] : 0.0;
     }
   }
 }
@@ -176,6 +184,10 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_cluster(const QrArgs q, int 
   cg::cluster_group cluster = cg::this_cluster();
   const int C = int(cluster.num_blocks());
   const int rank = int(cluster.block_rank());
+  const int pb = blockIdx.x / C;               // one cluster per problem
+  const double* A = q.A.d(pb);
+  double* const Qo = q.Q.d(pb);
+  double* const Ro = q.R.n ? q.R.d(pb) : nullptr;
   const int m = q.m, n = q.n, k = min(m, n);
   const int tid = threadIdx.x, nt = blockDim.x;
   const int chunk = (m + C - 1) / C;
@@ -194,12 +206,12 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_cluster(const QrArgs q, int 
     W = nsq + QS;
     Qw = W + (long long)n * ld;
   } else {
-    W = q.W + (long long)rank * ld * n;
-    Qw = q.Qw + (long long)rank * ld * k;
+    W = q.W + pb * q.wst + (long long)rank * ld * n;
+    Qw = q.Qw + pb * q.qst + (long long)rank * ld * k;
   }
   for (long long e = tid; e < (long long)rows * n; e += nt) {
     const int li = int(e % rows), j = int(e / rows);
-    W[(long long)j * ld + li] = q.A[(r0 + li) * q.rs + j * q.cs];
+    W[(long long)j * ld + li] = A[(r0 + li) * q.rs + j * q.cs];
   }
   __syncthreads();
   if (tid == 0) {
@@ -328,12 +340,12 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_cluster(const QrArgs q, int 
   }
   for (long long e = tid; e < (long long)rows * k; e += nt) {
     const int li = int(e % rows), c = int(e / rows);
-    q.Q[(r0 + li) * q.qrs + c * q.qcs] = Qw[(long long)c * ld + li];
+    Qo[(r0 + li) * q.qrs + c * q.qcs] = Qw[(long long)c * ld + li];
   }
-  if (q.R) {
+  if (Ro) {
     for (long long e = tid; e < (long long)rows * n; e += nt) {
       const int li = int(e % rows), j = int(e / rows), i = r0 + li;
-      if (i < k) q.R[(long long)i * n + j] = (j >= i) ? W[(long long)j * ld + li] : 0.0;
+      if (i < k) Ro[(long long)i * n + j] = (j >= i) ? W[(long long)j * ld + li] : 0.0;
     }
   }
   cluster.sync();   // no CTA leaves while others may still read its shared memory
@@ -343,26 +355,31 @@ struct SvdArgs {
   int p, q;          // working matrix G is p x q (p >= q), column-major
   int m, n;          // original A is m x n row-major
   int trans;         // 1: G = A^T (m < n)
-  const double* A;
-  double* G;
-  double* V;         // q x q column-major
-  double* nrm;       // q
-  int* order;        // q
+  TP A;              // per problem
+  double* work;      // per problem (+ problem * wst): G (p x q), V (q x q), nrm (q), order (q ints)
+  long long wst;
   int kk;
-  double* US;        // m x kk row-major
-  double* Vt;        // kk x n row-major
+  TP US;             // m x kk row-major
+  TP Vt;             // kk x n row-major
   int* flag;
 };
 
+// Grid = problems, one CTA each.
 __global__ void __launch_bounds__(SVD_THREADS) k_svd_jacobi(const SvdArgs s) {
   __shared__ int s_rot;
   const int p = s.p, q = s.q;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  double* G = s.G;
-  double* V = s.V;
+  const int pb = blockIdx.x;
+  const double* A = s.A.d(pb);
+  double* const US = s.US.d(pb);
+  double* const Vto = s.Vt.d(pb);
+  double* G = s.work + pb * s.wst;
+  double* V = G + (long long)p * q;
+  double* const nrm = V + (long long)q * q;
+  int* const order = reinterpret_cast<int*>(nrm + q);
   for (long long e = tid; e < (long long)p * q; e += nt) {
     int i = int(e % p), j = int(e / p);   // G(i,j)
-    G[e] = s.trans ? s.A[(long long)j * s.n + i] : s.A[(long long)i * s.n + j];
+    G[e] = s.trans ? A[(long long)j * s.n + i] : A[(long long)i * s.n + j];
   }
   for (long long e = tid; e < (long long)q * q; e += nt) V[e] = ((e % q) == (e / q)) ? 1.0 : 0.0;
   __syncthreads();
@@ -427,17 +444,17 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_jacobi(const SvdArgs s) {
       v += x * x;
     }
     v = warp_sum(v);
-    if (lane == 0) s.nrm[j] = sqrt(v);
+    if (lane == 0) nrm[j] = sqrt(v);
   }
   __syncthreads();
   for (int j = tid; j < q; j += nt) {
-    const double vj = s.nrm[j];
+    const double vj = nrm[j];
     int r = 0;
     for (int i = 0; i < q; ++i) {
-      const double vi = s.nrm[i];
+      const double vi = nrm[i];
       r += (vi > vj) || (vi == vj && i < j);
     }
-    s.order[r] = j;
+    order[r] = j;
   }
   __syncthreads();
   // A V = G  (A = G V^T when trans = 0;  A^T = G V^T  =>  A = V G^T when trans = 1)
@@ -446,22 +463,22 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_jacobi(const SvdArgs s) {
     // US[i][r] = G(i, order[r]);  Vt[r][j] = V(j, order[r])
     for (long long e = tid; e < (long long)s.m * kk; e += nt) {
       int i = int(e / kk), r = int(e % kk);
-      s.US[e] = (r < q) ? G[(long long)s.order[r] * p + i] : 0.0;
+      US[e] = (r < q) ? G[(long long)order[r] * p + i] : 0.0;
     }
     for (long long e = tid; e < (long long)kk * s.n; e += nt) {
       int r = int(e / s.n), j = int(e % s.n);
-      s.Vt[e] = (r < q) ? V[(long long)s.order[r] * q + j] : 0.0;
+      Vto[e] = (r < q) ? V[(long long)order[r] * q + j] : 0.0;
     }
   } else {
     // US[i][r] = V(i, order[r]) * nrm;  Vt[r][j] = G(j, order[r]) / nrm
     for (long long e = tid; e < (long long)s.m * kk; e += nt) {
       int i = int(e / kk), r = int(e % kk);
-      s.US[e] = (r < q) ? V[(long long)s.order[r] * q + i] * s.nrm[s.order[r]] : 0.0;
+      US[e] = (r < q) ? V[(long long)order[r] * q + i] * nrm[order[r]] : 0.0;
     }
     for (long long e = tid; e < (long long)kk * s.n; e += nt) {
       int r = int(e / s.n), j = int(e % s.n);
-      double nr = (r < q) ? s.nrm[s.order[r]] : 0.0;
-      s.Vt[e] = (r < q && nr > 0.0) ? G[(long long)s.order[r] * p + j] / nr : 0.0;
+      double nr = (r < q) ? nrm[order[r]] : 0.0;
+      Vto[e] = (r < q && nr > 0.0) ? G[(long long)order[r] * p + j] / nr : 0.0;
     }
   }
 }
@@ -516,40 +533,71 @@ int qr_cluster_size(size_t smem) {
 }
 }  // namespace
 
-void qr_thin(Ctx& cx, int m, int n, const double* A, long long rs, long long cs, double* Q,
-             long long qrs, long long qcs, double* R) {
+void qr_thin(Ctx& cx, int m, int n, const TP& A, long long rs, long long cs, const TP& Q, long long qrs,
+             long long qcs, const TP& R) {
   PEPS_REQUIRE(m > 0 && n > 0, "qr of an empty matrix");
+  const int np = problems({&A, &Q, &R});
+  PEPS_REQUIRE(!A.null() && Q.n == np && (R.null() || R.n == np), "internal: qr operands");
   const int k = std::min(m, n);
-  double* w = cx.scratch(size_t(m) * n + size_t(m) * k + k + 64);
-  QrArgs a{m, n, A, rs, cs, Q, qrs, qcs, R, w, w + size_t(m) * n, w + size_t(m) * n + size_t(m) * k};
   const double flops = 4.0 * m * double(n) * k - 4.0 / 3.0 * double(k) * k * k;
   const size_t kQrSmemMax = 200 * 1024;
-  // Rows per CTA >= 32 keeps the per-column barrier cost below the FP64 work.
-  int C = std::max(1, std::min(16, m / 32));
-  while (C > 1 && (C & (C - 1))) --C;
   const size_t base = sizeof(double) * (2 * size_t(n) + 4 + k + size_t(n) * QS + n + 2 + QS);
   auto ld_of = [&](int c) { return (((m + c - 1) / c) | 1); };   // odd column stride
   auto full_of = [&](int c) { return base + sizeof(double) * size_t(ld_of(c)) * (size_t(n) + k); };
-  if (C > 1) C = std::min(C, qr_cluster_size(full_of(C) <= kQrSmemMax ? full_of(C) : base));
-  while (C > 1 && (C & (C - 1))) --C;
-  if (std::getenv("PEPS_VERBOSE")) std::fprintf(stderr, "[peps] qr %dx%d: cluster %d\n", m, n, C);
-  Launch L(K_QR, cx.st, flops, 0);
-  if (C <= 1) {
-    k_qr_house<<<1, QR_THREADS, 0, cx.st>>>(a);
-  } else {
-    const int ld = ld_of(C);
-    const size_t full = full_of(C);
-    const int in_smem = full <= kQrSmemMax ? 1 : 0;
-    // the global-memory fallback uses [C][n][ld] / [C][k][ld] blocks
-    if (!in_smem) {
-      double* w2 = cx.scratch(size_t(C) * ld * (size_t(n) + k) + 64);
-      a.W = w2;
-      a.Qw = w2 + size_t(C) * ld * n;
+  // Cluster size: rows per CTA >= 32; among the sizes whose rows fit in shared
+  // memory, the one with the least estimated time for all problems: waves of
+  // clusters over the SMs x (FP64 work per CTA + three cluster barriers per column).
+  int cmax = std::max(1, std::min(cx.qr_cmax > 0 ? cx.qr_cmax : 16, m / 32));
+  while (cmax > 1 && (cmax & (cmax - 1))) --cmax;
+  int C = cmax;
+  if (cmax > 1) {
+    double best = 1e300;
+    for (int c = 2; c <= cmax; c *= 2) {
+      if (full_of(c) > kQrSmemMax && c < cmax) continue;
+      const double waves = std::ceil(double(np) * c / 144.0);
+      const double t = waves * (flops / (c * 8.0e9) + 3.0 * k * 1.5e-6);
+      if (t < best) {
+        best = t;
+        C = c;
+      }
     }
+    C = std::min(C, qr_cluster_size(full_of(C) <= kQrSmemMax ? full_of(C) : base));
+    while (C > 1 && (C & (C - 1))) --C;
+  }
+  if (std::getenv("PEPS_VERBOSE")) std::fprintf(stderr, "[peps] qr %dx%d x%d: cluster %d\n", m, n, np, C);
+  const int ld = ld_of(std::max(C, 1));
+  const bool in_smem = C > 1 && full_of(C) <= kQrSmemMax;
+  QrArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.m = m;
+  a.n = n;
+  a.A = A.all(np);
+  a.rs = rs;
+  a.cs = cs;
+  a.Q = Q.all(np);
+  a.qrs = qrs;
+  a.qcs = qcs;
+  a.R = R.all(np);
+  if (C <= 1) {
+    a.wst = (long long)m * n;
+    a.qst = (long long)m * k;
+  } else {   // the global-memory fallback uses [C][n][ld] / [C][k][ld] blocks per problem
+    a.wst = (long long)C * ld * n;
+    a.qst = (long long)C * ld * k;
+  }
+  a.tst = k;
+  double* w = cx.scratch(size_t(np) * (a.wst + a.qst + a.tst) + 64);
+  a.W = w;
+  a.Qw = w + size_t(np) * a.wst;
+  a.tau = a.Qw + size_t(np) * a.qst;
+  Launch L(K_QR, cx.st, flops * np, 0);
+  if (C <= 1) {
+    k_qr_house<<<np, QR_THREADS, 0, cx.st>>>(a);
+  } else {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(C, 1, 1);
+    cfg.gridDim = dim3(C * np, 1, 1);
     cfg.blockDim = dim3(QRC_THREADS, 1, 1);
-    cfg.dynamicSmemBytes = in_smem ? full : base;
+    cfg.dynamicSmemBytes = in_smem ? full_of(C) : base;
     cfg.stream = cx.st;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -558,33 +606,32 @@ void qr_thin(Ctx& cx, int m, int n, const double* A, long long rs, long long cs,
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    PEPS_CUDA(cudaLaunchKernelEx(&cfg, k_qr_cluster, a, in_smem, ld));
+    PEPS_CUDA(cudaLaunchKernelEx(&cfg, k_qr_cluster, a, in_smem ? 1 : 0, ld));
   }
   PEPS_CHECK_LAUNCH();
 }
 
-void svd_trunc(Ctx& cx, int m, int n, const double* A, int kk, double* US, double* Vt) {
+void svd_trunc(Ctx& cx, int m, int n, const TP& A, int kk, const TP& US, const TP& Vt) {
   PEPS_REQUIRE(m > 0 && n > 0 && kk > 0, "svd of an empty matrix");
+  const int np = problems({&A, &US, &Vt});
+  PEPS_REQUIRE(!A.null() && US.n == np && Vt.n == np, "internal: svd operands");
   SvdArgs s;
+  std::memset(&s, 0, sizeof(s));
   s.trans = (m < n) ? 1 : 0;
   s.p = s.trans ? n : m;
   s.q = s.trans ? m : n;
   s.m = m;
   s.n = n;
-  s.A = A;
+  s.A = A.all(np);
   s.kk = kk;
-  s.US = US;
-  s.Vt = Vt;
+  s.US = US.all(np);
+  s.Vt = Vt.all(np);
   s.flag = cx.flag;
-  const size_t need = size_t(s.p) * s.q + size_t(s.q) * s.q + s.q + s.q;
-  double* w = cx.scratch(need);
-  s.G = w;
-  s.V = w + size_t(s.p) * s.q;
-  s.nrm = s.V + size_t(s.q) * s.q;
-  s.order = reinterpret_cast<int*>(s.nrm + s.q);
+  s.wst = ((long long)s.p * s.q + (long long)s.q * s.q + 2LL * s.q + 31) / 32 * 32;
+  s.work = cx.scratch(size_t(np) * s.wst);
   const double flops = 8.0 * 4.0 * double(s.p) * s.q * s.q;
-  Launch L(K_SVD, cx.st, flops, 0);
-  k_svd_jacobi<<<1, SVD_THREADS, 0, cx.st>>>(s);
+  Launch L(K_SVD, cx.st, flops * np, 0);
+  k_svd_jacobi<<<np, SVD_THREADS, 0, cx.st>>>(s);
   PEPS_CHECK_LAUNCH();
 }
 
