@@ -433,11 +433,12 @@ struct Lanes {
   }
 };
 
-// Runs fn(lane, job) for job = 0..njobs-1, lane i taking jobs i, i+n, ...; one
-// host thread per lane, so every lane's stream is fed while the others block
-// on a full launch queue.  The first exception of any lane is rethrown.
+// Runs fn(lane, job) for every job in plan[lane] (by default lane i takes
+// jobs i, i+n, ...); one host thread per lane, so every lane's stream is fed
+// while the others block on a full launch queue.  The first exception of any
+// lane is rethrown.
 template <class F>
-void run_lanes(Lanes& lanes, int njobs, F fn) {
+void run_lanes(Lanes& lanes, int njobs, F fn, const std::vector<std::vector<int>>* plan = nullptr) {
   const int nl = int(lanes.l.size());
   if (nl == 1) {
     for (int j = 0; j < njobs; ++j) fn(lanes.l[0], j);
@@ -451,7 +452,10 @@ void run_lanes(Lanes& lanes, int njobs, F fn) {
     th.emplace_back([&, i] {
       try {
         PEPS_CUDA(cudaSetDevice(dev));
-        for (int j = i; j < njobs; j += nl) fn(lanes.l[i], j);
+        if (plan)
+          for (int j : (*plan)[i]) fn(lanes.l[i], j);
+        else
+          for (int j = i; j < njobs; j += nl) fn(lanes.l[i], j);
       } catch (...) {
         errs[i] = std::current_exception();
       }
@@ -621,7 +625,9 @@ void cluster_env(Call& c, const peps_lattice* lat, const Opts& opt, int n, peps_
   size_t free_b = 0, total_b = 0;
   PEPS_CUDA(cudaMemGetInfo(&free_b, &total_b));
   const size_t budget = std::min<size_t>(free_b * 2 / 5, size_t(96) << 30);
-  const int bmax = int(std::max<size_t>(1, std::min<size_t>(MAXB, budget / (per * nl))));
+  // Up to 16 windows per chunk: beyond that a launch gains little (its work is
+  // already bandwidth-bound) while smaller chunks balance the lanes.
+  const int bmax = int(std::max<size_t>(1, std::min<size_t>(16, budget / (per * nl))));
   std::vector<std::vector<Win>> chunks;
   for (auto& kv : groups) {
     const auto& v = kv.second;
@@ -630,10 +636,24 @@ void cluster_env(Call& c, const peps_lattice* lat, const Opts& opt, int n, peps_
     for (size_t i0 = 0; i0 < v.size(); i0 += sz)
       chunks.emplace_back(v.begin() + i0, v.begin() + std::min(v.size(), i0 + size_t(sz)));
   }
-  // larger windows first, so the lanes end together
-  std::stable_sort(chunks.begin(), chunks.end(), [](const std::vector<Win>& a, const std::vector<Win>& b) {
-    return (a[0].r1 - a[0].r0 + 1) * (a[0].c1 - a[0].c0 + 1) > (b[0].r1 - b[0].r0 + 1) * (b[0].c1 - b[0].c0 + 1);
-  });
+  // Longest chunk first onto the least-loaded lane.  Estimated device time of
+  // a chunk: (window sites)^1.6 x (3 + B) / 4, fitted to measured chunk times
+  // (one window pays the latency of every step; extra windows ride along).
+  auto cost = [](const std::vector<Win>& v) {
+    const double area = double(v[0].r1 - v[0].r0 + 1) * double(v[0].c1 - v[0].c0 + 1);
+    return std::pow(area, 1.6) * (3.0 + double(v.size())) / 4.0;
+  };
+  std::stable_sort(chunks.begin(), chunks.end(),
+                   [&](const std::vector<Win>& a, const std::vector<Win>& b) { return cost(a) > cost(b); });
+  std::vector<std::vector<int>> plan(nl);
+  {
+    std::vector<double> load(nl, 0.0);
+    for (int j = 0; j < int(chunks.size()); ++j) {
+      const int li = int(std::min_element(load.begin(), load.end()) - load.begin());
+      plan[li].push_back(j);
+      load[li] += cost(chunks[j]);
+    }
+  }
   int bl = 1;
   for (auto& c : chunks) bl = std::max(bl, int(c.size()));
   Lanes lanes(c, opt, d, D, Lwin, bl);
@@ -738,7 +758,7 @@ void cluster_env(Call& c, const peps_lattice* lat, const Opts& opt, int n, peps_
       cudaEventDestroy(ev0);
       cudaEventDestroy(ev1);
     }
-  });
+  }, &plan);
   lanes.join();
   e.has_norm = false;
 }

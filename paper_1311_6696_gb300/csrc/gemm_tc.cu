@@ -53,6 +53,7 @@ struct TcArgs {
   int out_lo;        // 1: also write C_lo (split residual), C is then the rounded hi part
   int stages;        // ring depth (<= TC_STAGES), chosen to fit shared memory
   int nprob;         // problems in this launch
+  int cols_fast;     // 1: the output's unit stride is in the N group (write along columns)
   long long pad_m, pad_n;   // packed rows per problem (multiples of TC_BM and BN)
   TP C, Clo;         // per problem
   Grp gm, gn;        // output offsets of the M and N groups
@@ -167,6 +168,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ 
   __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], done;
   __shared__ uint32_t tmem_base;
   __shared__ long long offm[TC_BM], offn[BN];
+  __shared__ float stage_out[4][32][17];   // per warp: 32 rows x 16 columns of the accumulator
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long tiles_n = (g.N + BN - 1) / BN;
@@ -275,25 +277,42 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ 
   float* const Cf = static_cast<float*>(g.C.p[pb]);
   double* const Cd = static_cast<double*>(g.C.p[pb]);
   float* const Cl = g.out_lo ? static_cast<float*>(g.Clo.p[pb]) : nullptr;
+  auto put = [&](long long o, float v) {
+    if (g.out_f64) {
+      Cd[o] = double(v);
+    } else if (g.out_lo) {
+      const float h = round_tf32(v);
+      Cf[o] = h;
+      Cl[o] = round_tf32(v - h);
+    } else {
+      Cf[o] = v;
+    }
+  };
   if (have) {
     for (int c0 = 0; c0 < BN; c0 += 16) {
       uint32_t r[16];
       tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0), r);
-      if (om < 0) continue;
+      if (!g.cols_fast) {
+        // one row per lane: coalesced when consecutive rows are adjacent in C
+        if (om < 0) continue;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const long long on = offn[c0 + j];
-        if (on < 0) continue;
-        const float v = __uint_as_float(r[j]) * float(g.alpha);
-        if (g.out_f64) {
-          Cd[om + on] = double(v);
-        } else if (g.out_lo) {
-          const float h = round_tf32(v);
-          Cf[om + on] = h;
-          Cl[om + on] = round_tf32(v - h);
-        } else {
-          Cf[om + on] = v;
+        for (int j = 0; j < 16; ++j) {
+          const long long on = offn[c0 + j];
+          if (on >= 0) put(om + on, __uint_as_float(r[j]) * float(g.alpha));
         }
+      } else {
+        // through shared memory: 16 lanes per row along the columns
+#pragma unroll
+        for (int j = 0; j < 16; ++j) stage_out[warp][lane][j] = __uint_as_float(r[j]);
+        __syncwarp();
+        const int j = lane & 15;
+        const long long on = offn[c0 + j];
+#pragma unroll 4
+        for (int i = lane >> 4; i < 32; i += 2) {
+          const long long omi = offm[warp * 32 + i];
+          if (omi >= 0 && on >= 0) put(omi + on, stage_out[warp][i][j] * float(g.alpha));
+        }
+        __syncwarp();
       }
     }
   }
@@ -308,9 +327,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ 
 // Gather-copy into a dense [rows][ld] operand: element (r, k) of the output is
 // src[sum(idx_i * stride_i)] with r, k decomposed over the row / K groups.
 // Rounds to TF32 (or converts to BF16); `lo` receives the rounded residual.
+// Tiled transpose: each CTA moves a 32 x 32 (row, k) tile through shared
+// memory, decomposing its 32 row and 32 k offsets once; reads run along
+// whichever group holds the source's unit stride (rows_fast), writes run along
+// k, so both sides are coalesced whatever the permutation.
 struct PackArgs {
   TP src;            // per problem
   int src_f64;
+  int rows_fast;     // 1: consecutive rows are closer in src than consecutive k
   Grp gr, gk;        // strides into src
   long long rows, K, ld, pad;   // pad: packed rows per problem
   void* hi;
@@ -318,20 +342,46 @@ struct PackArgs {
   int bf16;
 };
 
-// Grid = (blocks, problems).
-__global__ void k_pack(const PackArgs p) {
-  const long long total = p.rows * p.K;
+constexpr int PK_T = 32;
+
+// Grid = (row tiles x k tiles, problems), 256 threads.
+__global__ void __launch_bounds__(256) k_pack(const PackArgs p) {
+  __shared__ double tile[PK_T][PK_T + 1];   // [k][row]
+  __shared__ long long ro[PK_T], ko[PK_T];
   const int pb = blockIdx.y;
-  const void* src = p.src.p[pb];
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const long long r = t / p.K, k = t - r * p.K;
-    long long o1, o2;
-    decomp(p.gr, r, o1);
-    decomp(p.gk, k, o2);
-    const double v = p.src_f64 ? static_cast<const double*>(src)[o1 + o2]
-                               : double(static_cast<const float*>(src)[o1 + o2]);
-    const long long d = (pb * p.pad + r) * p.ld + k;
+  const long long ktiles = (p.K + PK_T - 1) / PK_T;
+  const long long r0 = (blockIdx.x / ktiles) * PK_T, k0 = (blockIdx.x % ktiles) * PK_T;
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  if (tid < PK_T) {
+    long long o = -1;
+    if (r0 + tid < p.rows) decomp(p.gr, r0 + tid, o);
+    ro[tid] = o;
+  } else if (tid < 2 * PK_T) {
+    long long o = -1;
+    if (k0 + tid - PK_T < p.K) decomp(p.gk, k0 + tid - PK_T, o);
+    ko[tid - PK_T] = o;
+  }
+  __syncthreads();
+  const double* sd = static_cast<const double*>(p.src.p[pb]);
+  const float* sf = static_cast<const float*>(p.src.p[pb]);
+#pragma unroll
+  for (int q = 0; q < PK_T / 8; ++q) {
+    const int a = ty + 8 * q;
+    const int r = p.rows_fast ? tx : a, k = p.rows_fast ? a : tx;
+    double v = 0.0;
+    if (ro[r] >= 0 && ko[k] >= 0) {
+      const long long o = ro[r] + ko[k];
+      v = p.src_f64 ? sd[o] : double(sf[o]);
+    }
+    tile[k][r] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < PK_T / 8; ++q) {
+    const int r = ty + 8 * q, k = tx;
+    if (ro[r] < 0 || ko[k] < 0) continue;
+    const double v = tile[k][r];
+    const long long d = (pb * p.pad + r0 + r) * p.ld + k0 + k;
     if (p.bf16) {
       const __nv_bfloat16 h = __double2bfloat16(v);
       static_cast<__nv_bfloat16*>(p.hi)[d] = h;
@@ -459,11 +509,18 @@ Operand pack(Ctx& cx, const TP& src, int np, long long pad, int src_f64, const s
   p.hi = o.hi;
   p.lo = o.lo;
   p.bf16 = bf16;
-  const long long total = o.rows * o.K;
+  // read along whichever group holds the smaller innermost stride
+  auto inner = [](const Grp& g) {
+    long long m = 1LL << 62;
+    for (int i = 0; i < g.n; ++i)
+      if (g.dim[i] > 1) m = std::min(m, g.s[i]);
+    return m;
+  };
+  p.rows_fast = inner(p.gr) < inner(p.gk) ? 1 : 0;
+  const long long tiles = ((o.rows + PK_T - 1) / PK_T) * ((o.K + PK_T - 1) / PK_T);
+  PEPS_REQUIRE(tiles < (1LL << 31), "operand too large to pack");
   Launch L(K_AUX, cx.st);
-  const long long per = std::max<long long>(1, 4096 / np);
-  const unsigned blocks = unsigned(std::max<long long>(1, std::min<long long>((total + 255) / 256, per)));
-  k_pack<<<dim3(blocks, np), 256, 0, cx.st>>>(p);
+  k_pack<<<dim3(unsigned(tiles), np), 256, 0, cx.st>>>(p);
   PEPS_CHECK_LAUNCH();
   return o;
 }
@@ -562,6 +619,15 @@ void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, c
   g.bf16 = bf16;
   g.out_f64 = c_f64;
   g.out_lo = (!Clo.null() && !c_f64) ? 1 : 0;
+  {
+    auto inner = [](const Grp& q) {
+      long long m = 1LL << 62;
+      for (int i = 0; i < q.n; ++i)
+        if (q.dim[i] > 1) m = std::min(m, q.s[i]);
+      return m;
+    };
+    g.cols_fast = inner(g.gn) < inner(g.gm) ? 1 : 0;
+  }
   g.nprob = np;
   g.pad_m = pad_m;
   g.pad_n = pad_n;
