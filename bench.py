@@ -11,7 +11,12 @@ Ly*Lx = 100 site environments; the metric is environments per second.
 The headline path computes the absorb contractions on the tensor cores in
 split TF32 (tf32x3) with FP64 QR / gauge / rescaling; the same line reports
 the plain FP64 GPU path's throughput and the largest relative deviation of
-the 180 bond observables between the two.
+the 180 bond observables between the two.  Each step replays the recorded
+plan (one CUDA graph for the whole environment set) and evaluates <S.S>.
+
+A "cluster" object adds the cluster scheme on the 14x14 D=6 lattice (all 196
+windows at chi=36, n = 2, 4, 6) with its deviation from the full chi=64
+environments.
 
 Launch: ``python bench.py [--gpus N --steps K --warmup W]``; for N > 1 run
 under ``torch.distributed.run`` with one process per GPU.  The full
@@ -91,10 +96,6 @@ def _clock_summary(proc, gpu_index):
             "samples": len(sms)}
 
 
-def _bond_outputs(env, O):
-    return env.expect("hbond", O), env.expect("vbond", O)
-
-
 def run_ours(args, rank, world, dist):
     import numpy as np
     import torch
@@ -108,37 +109,39 @@ def run_ours(args, rank, world, dist):
     A = synth.peps_gauss(WORKLOAD["Ly"], WORKLOAD["Lx"], WORKLOAD["d"], WORKLOAD["D"], WORKLOAD["seed"] + rank)
     At = torch.from_numpy(A).to(dev)
     Ah = torch.from_numpy(A).pin_memory()
-    SD = np.array([[0.25, 0, 0, 0], [0, -0.25, 0.5, 0], [0, 0.5, -0.25, 0], [0, 0, 0, 0.25]])
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     kw = dict(chi=args.chi, mode=args.mode, sweeps=2, precision=args.precision, stream=st)
 
-    def step(inp, precision=None):
-        k = dict(kw)
-        if precision:
-            k["precision"] = precision
-        env = peps.env_full(inp, **k)
-        h, v = _bond_outputs(env, SD)
-        env.free()
-        return h, v
-
-    for _ in range(args.warmup):
-        step(At)
+    # ---- one plain (un-recorded) step with every class timed: the class with
+    # the most device time is the one whose roofline is reported.
+    peps.env_full(At, **kw).free()
     torch.cuda.synchronize()
-
-    # ---- one profiled step: the kernel class with the most device time is the
-    # one whose roofline is reported (timed live below); the absorb class too.
     peps.profile_reset()
     peps.profile_enable(-1)
-    step(At)
+    peps.env_full(At, **kw).free()
     torch.cuda.synchronize()
     prof1 = peps.profile_read()
     peps.profile_enable(0)
     dom = args.dominant or max((k for k in prof1 if prof1[k]["launches"]), key=lambda k: prof1[k]["ms"])
     absorb = "gemm_tc" if args.precision != "fp64" else "gemm_f64"
 
-    # ---- device-resident timed region (per-step events, L2 flushed between steps)
+    # ---- the step as a user runs it repeatedly: the recorded plan (one CUDA
+    # graph launch for the whole environment set), then <S.S> on every bond.
+    # The dominant class is timed inside every replay (event nodes around its
+    # launches); the absorb class's figure comes from the plain step above.
+    peps.profile_enable(1 << peps.class_index(dom))
+    plan = peps.Plan(At, **kw)
+    peps.profile_enable(0)
+    env = plan.env
+
+    def step():
+        plan.run()
+        return env.expect("hbond", SD), env.expect("vbond", SD)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
     peps.profile_reset()
-    peps.profile_enable((1 << peps.class_index(dom)) | (1 << peps.class_index(absorb)))
     clocks = _clock_sampler() if rank == 0 else None
     if dist:
         dist.barrier()
@@ -150,7 +153,7 @@ def run_ours(args, rank, world, dist):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        step(At)
+        h1, v1 = step()
         e1.record(st)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
@@ -160,38 +163,42 @@ def run_ours(args, rank, world, dist):
     t_wall = time.perf_counter() - t_wall
     clk = _clock_summary(clocks, local) if rank == 0 else None
     prof = peps.profile_read()
-    peps.profile_enable(0)
     launches = sum(v["launches"] for v in prof.values())
 
-    # ---- end-to-end through the C ABI with pinned host buffers
+    # ---- end to end: pinned host tensors in (H2D into the plan's lattice), replay, observables out
     etimes = []
     for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        step(Ah)          # host pointer: the library copies A in; expect() copies results out
+        At.copy_(Ah, non_blocking=True)
+        step()
         etimes.append((time.perf_counter() - t0) * 1e3)
 
-    # ---- the plain FP64 GPU path on the same input, and the deviation between the two
-    cmp_ms, dev = None, None
+    # ---- the plain FP64 GPU path (also recorded) on the same input, and the deviation between the two
+    cmp_ms, dev_err = None, None
     if args.precision != "fp64" and not args.no_fp64_compare:
-        h1, v1 = step(At)
-        step(At, "fp64")
-        torch.cuda.synchronize()
+        p64 = peps.Plan(At, **dict(kw, precision="fp64"))
+        e64 = p64.env
+        p64.run()
         tms = []
         for _ in range(max(1, min(3, args.steps))):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(st)
-            h0, v0 = step(At, "fp64")
+            p64.run()
+            h0, v0 = e64.expect("hbond", SD), e64.expect("vbond", SD)
             e1.record(st)
             e1.synchronize()
             tms.append(e0.elapsed_time(e1))
         cmp_ms = sum(tms) / len(tms)
         a = np.concatenate([h1, v1])
         b = np.concatenate([h0, v0])
-        dev = float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-2)))
+        dev_err = float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-2)))
+        del e64, p64
+
+    cluster = None if args.no_cluster else cluster_section(args, peps, synth, torch, st, flush)
 
     total_ms = sum(times)
     envs = WORKLOAD["Ly"] * WORKLOAD["Lx"]
@@ -202,8 +209,17 @@ def run_ours(args, rank, world, dist):
 
     pk = _peaks()
 
-    def roof(cls):
-        d = prof[cls]
+    def roof(cls, src=None):
+        d = (src or prof)[cls]
+        timed = ("CUDA events recorded inside the replayed graph" if src is None else
+                 "CUDA events around each launch of one plain (un-recorded) step")
+        if cls == "pack":
+            achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
+            peak = pk.get("hbm_gbs", 6765.0)
+            return {"bound": "hbm", "kernel": cls, "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 5), "traffic": None, "launches": d["launches"],
+                    "avg_launch_us": round(1e3 * d["ms"] / max(1, d["launches"]), 3),
+                    "peak_source": "of measured HBM copy bandwidth (MEASURED_PEAKS.json)", "timed": timed}
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
         if cls == "gemm_tc":
             bf = pk.get("bf16_tflops_sustained", 1720.0)
@@ -219,7 +235,7 @@ def run_ours(args, rank, world, dist):
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 5), "traffic": None,
                 "launches": d["launches"], "avg_launch_us": round(1e3 * d["ms"] / max(1, d["launches"]), 3),
                 "algorithmic_flops_per_launch": round(d["flops"] / max(1, d["launches"]), 1),
-                "peak_source": note}
+                "peak_source": note, "timed": timed}
 
     h2d = int(A.nbytes)
     d2h = 8 * (WORKLOAD["Ly"] * (WORKLOAD["Lx"] - 1) + (WORKLOAD["Ly"] - 1) * WORKLOAD["Lx"])
@@ -229,7 +245,7 @@ def run_ours(args, rank, world, dist):
         "unit": "envs/s",
         "n_gpus": world,
         "steps": args.steps,
-        "warmup": args.warmup,
+        "warmup": max(3, args.warmup),
         "ms_per_step": round(ms_step, 3),
         "higher_is_better": True,
         "scaling": "weak",
@@ -240,25 +256,72 @@ def run_ours(args, rank, world, dist):
         "config": {"workload": "10x10 OBC PEPS d=2 D=4, entries 0.5+0.1N(0,1), unit-norm tensors",
                    "chi": args.chi, "mode": args.mode, "sweeps": 2, "precision": args.precision,
                    "envs_per_step": envs, "l2": "flushed between steps (256 MiB write)",
+                   "launch": f"recorded plan (CUDA graph of {plan.launches} kernels) replayed per step",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": round(e2e, 3), "unit": "envs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": roof(dom),
-        "roofline_absorb": roof(absorb) if absorb != dom else None,
-        "profiled_step_kernel_ms": {k: round(v["ms"], 3) for k, v in prof1.items() if v["launches"]},
+        "roofline_absorb": roof(absorb, prof1) if absorb != dom else None,
+        "plain_step_kernel_ms": {k: round(v["ms"], 3) for k, v in prof1.items() if v["launches"]},
         "wall_s_timed": round(t_wall, 3),
     }
     if cmp_ms is not None:
         res["fp64_path"] = {"value": round(world * envs / (cmp_ms * 1e-3), 3), "unit": "envs/s",
                             "ms_per_step": round(cmp_ms, 3)}
         res["speedup_vs_fp64_path"] = round(cmp_ms / ms_step, 3)
-        res["accuracy"] = {"max_rel_err_vs_fp64_path": dev, "observables": 180,
+        res["accuracy"] = {"max_rel_err_vs_fp64_path": dev_err, "observables": 180,
                            "metric": "|x-x_ref|/max(|x_ref|,1e-2) over <S.S> on every bond"}
+    if cluster is not None:
+        res["cluster"] = cluster
     if clk:
         res["clocks"] = clk
     if not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_sample(args, budget_s=args.cpu_budget)
     return res
+
+
+SD = [[0.25, 0, 0, 0], [0, -0.25, 0.5, 0], [0, 0.5, -0.25, 0], [0, 0, 0, 0.25]]
+
+
+def cluster_section(args, peps, synth, torch, st, flush):
+    """Cluster environments of the 14x14 D=6 lattice (all 196 windows, chi=36,
+    n in {2, 4, 6}) as recorded plans, with their deviation from the full
+    chi=64 environments on sigma_z and <S.S> (every site and bond)."""
+    import numpy as np
+    A = torch.from_numpy(synth.workload("14x14_D6")).cuda()
+    SZ = np.diag([1.0, -1.0])
+
+    def obs(e):
+        return np.concatenate([e.expect("site", SZ), e.expect("hbond", SD), e.expect("vbond", SD)])
+
+    ref = peps.env_full(A, chi=64, mode="var", precision=args.precision, stream=st)
+    r = obs(ref)
+    ref.free()
+    out = {"workload": "14x14 OBC PEPS d=2 D=6, entries 0.5+0.1N(0,1), 196 windows, chi=36, var, "
+                       f"{args.precision}; reference: full environments at chi=64",
+           "per_n": {}}
+    for n in (2, 4, 6):
+        plan = peps.Plan(A, chi=36, mode="var", precision=args.precision, cluster_n=n, stream=st)
+        env = plan.env
+        plan.run()
+        tms = []
+        for _ in range(2):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            plan.run()
+            o = obs(env)
+            e1.record(st)
+            e1.synchronize()
+            tms.append(e0.elapsed_time(e1))
+        ms = min(tms)
+        err = float(np.max(np.abs(o - r) / np.maximum(np.abs(r), 1e-2)))
+        out["per_n"][str(n)] = {"envs_per_s": round(196 / (ms * 1e-3), 2), "ms": round(ms, 2),
+                                "launches": plan.launches, "max_rel_dev_vs_full_chi64": err}
+        del env
+        plan.free()
+    return out
 
 
 def aggregate(ms_step, e_ms, envs_per_rank, world, dist=None, device=None):
@@ -363,6 +426,7 @@ def main():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--dominant", default=None, help="kernel class timed for the roofline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cluster", action="store_true", help="skip the 14x14 D=6 cluster section")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-budget", type=float, default=10.0)
     args = ap.parse_args()

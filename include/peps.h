@@ -292,6 +292,10 @@ void peps_plan_free(peps_plan* plan);
  *   not timing is enabled; flops / bytes are algorithmic counts (formula,
  *   not hardware counters).  The counters are process-wide and not
  *   thread-safe against concurrent readers.
+ *   Recorded plans: the classes enabled when a plan is recorded are timed
+ *   inside every replay (the event pairs are recorded as external event
+ *   nodes of the graph); each peps_plan_run adds the replay's launches,
+ *   flops, bytes and those times to the counters.
  */
 void        peps_profile_enable(int mask);
 void        peps_profile_reset(void);

@@ -31,7 +31,7 @@ using namespace peps;
 // ---------------------------------------------------------------------------
 namespace {
 
-const char* kClassNames[K_NCLASS] = {"gemm_f64", "gemm_tc", "qr_f64", "svd_f64", "cu0", "observables", "aux"};
+const char* kClassNames[K_NCLASS] = {"gemm_f64", "gemm_tc", "qr_f64", "svd_f64", "cu0", "observables", "aux", "pack"};
 
 struct Prof {
   std::mutex mu;
@@ -77,6 +77,9 @@ thread_local cudaEvent_t t_open_ev[K_NCLASS] = {};
 struct Counts {
   long long launches[K_NCLASS] = {};
   double flops[K_NCLASS] = {}, bytes[K_NCLASS] = {};
+  // Timed classes: event pairs recorded as external event nodes of the graph,
+  // read after every replay.
+  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> events;
 };
 std::atomic<Counts*> g_recording{nullptr};
 
@@ -113,6 +116,11 @@ void prof_launch(KClass c, cudaStream_t st, double flops, double bytes) {
     rc->launches[c]++;
     rc->flops[c] += flops;
     rc->bytes[c] += bytes;
+    if (p.mask & (1u << c)) {
+      cudaEvent_t e = p.get();
+      cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+      t_open_ev[c] = e;
+    }
     return;
   }
   p.launches[c]++;
@@ -127,7 +135,15 @@ void prof_launch(KClass c, cudaStream_t st, double flops, double bytes) {
 void prof_done(KClass c, cudaStream_t st) {
   Prof& p = prof();
   std::lock_guard<std::mutex> g(p.mu);
-  if (g_recording.load()) return;
+  if (Counts* rc = g_recording.load()) {
+    if ((p.mask & (1u << c)) && t_open_ev[c]) {
+      cudaEvent_t e = p.get();
+      cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+      rc->events.emplace_back(int(c), t_open_ev[c], e);
+      t_open_ev[c] = nullptr;
+    }
+    return;
+  }
   if ((p.mask & (1u << c)) && t_open_ev[c]) {
     cudaEvent_t e = p.get();
     cudaEventRecord(e, st);
@@ -1122,16 +1138,19 @@ int peps_plan_run(peps_plan* plan, void* cuda_stream) {
     PEPS_REQUIRE(cur == plan->device, "the plan was recorded on another device");
     const cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     PEPS_CUDA(cudaGraphLaunch(plan->exec, st));
-    {
-      Prof& p = prof();
-      std::lock_guard<std::mutex> g(p.mu);
-      for (int i = 0; i < K_NCLASS; ++i) {
-        p.launches[i] += plan->counts.launches[i];
-        p.flops[i] += plan->counts.flops[i];
-        p.bytes[i] += plan->counts.bytes[i];
-      }
-    }
     Call::read_status(plan->flag, st);
+    Prof& p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    for (int i = 0; i < K_NCLASS; ++i) {
+      p.launches[i] += plan->counts.launches[i];
+      p.flops[i] += plan->counts.flops[i];
+      p.bytes[i] += plan->counts.bytes[i];
+    }
+    for (auto& t : plan->counts.events) {   // classes timed when the plan was recorded
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, std::get<1>(t), std::get<2>(t)) == cudaSuccess) p.ms[std::get<0>(t)] += ms;
+    }
+    cudaGetLastError();
   });
 }
 
@@ -1152,6 +1171,10 @@ void peps_plan_free(peps_plan* plan) {
   cudaDeviceSynchronize();
   if (plan->exec) cudaGraphExecDestroy(plan->exec);
   if (plan->graph) cudaGraphDestroy(plan->graph);
+  for (auto& t : plan->counts.events) {
+    cudaEventDestroy(std::get<1>(t));
+    cudaEventDestroy(std::get<2>(t));
+  }
   plan->exec = nullptr;
   plan->graph = nullptr;
   plan->env.reset();

@@ -45,6 +45,7 @@ enum KClass {
   K_CU0,            // CU_0 separable boundary fixed point
   K_OBS,            // local observables
   K_AUX,            // init noise, norms, rescale, copies, reductions
+  K_PACK,           // operand repacking for the tensor cores (gather + TF32/BF16 split)
   K_NCLASS
 };
 

@@ -54,6 +54,9 @@ struct TcArgs {
   int stages;        // ring depth (<= TC_STAGES), chosen to fit shared memory
   int nprob;         // problems in this launch
   int cols_fast;     // 1: the output's unit stride is in the N group (write along columns)
+  int splitk;        // > 1: blockIdx.y takes k tiles [y * kt_per, ...) and writes FP32 partials
+  int kt_per;
+  float* part;       // [splitk][nprob][M][N] partial sums
   long long pad_m, pad_n;   // packed rows per problem (multiples of TC_BM and BN)
   TP C, Clo;         // per problem
   Grp gm, gn;        // output offsets of the M and N groups
@@ -209,7 +212,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ 
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
-  const int kt_n = g.ktiles;
+  const int kt0 = g.splitk > 1 ? int(blockIdx.y) * g.kt_per : 0;
+  const int kt_n = g.splitk > 1 ? min(g.kt_per, g.ktiles - kt0) : g.ktiles;   // k tiles of this CTA
   bool ok = true;
 
   if (warp == 0 && lane == 0) {
@@ -222,7 +226,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ 
       if (!ok) break;
       uint8_t* st = base + s * stage_bytes;
       mbar_expect_tx(&full[s], tx);
-      const int kx = kt * (TC_ROWB / (g.bf16 ? 2 : 4));
+      const int kx = (kt0 + kt) * (TC_ROWB / (g.bf16 ? 2 : 4));
       tma_load_2d(st, &ta, &full[s], kx, ra);
       tma_load_2d(st + A_BYTES, &tb, &full[s], kx, rb);
       if (g.split) {
@@ -277,6 +281,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ 
   float* const Cf = static_cast<float*>(g.C.p[pb]);
   double* const Cd = static_cast<double*>(g.C.p[pb]);
   float* const Cl = g.out_lo ? static_cast<float*>(g.Clo.p[pb]) : nullptr;
+  const float alpha = float(g.alpha);
   auto put = [&](long long o, float v) {
     if (g.out_f64) {
       Cd[o] = double(v);
@@ -288,7 +293,25 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ 
       Cf[o] = v;
     }
   };
-  if (have) {
+  if (have && g.splitk > 1) {
+    // raw partial sums, dense [M][N] per (split, problem), written along N
+    float* part = g.part + ((long long)blockIdx.y * g.nprob + pb) * g.M * g.N;
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      uint32_t r[16];
+      tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0), r);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) stage_out[warp][lane][j] = __uint_as_float(r[j]);
+      __syncwarp();
+      const int j = lane & 15;
+      const long long n = n0 + c0 + j;
+#pragma unroll 4
+      for (int i = lane >> 4; i < 32; i += 2) {
+        const long long m = m0 + warp * 32 + i;
+        if (m < g.M && n < g.N) part[m * g.N + n] = stage_out[warp][i][j];
+      }
+      __syncwarp();
+    }
+  } else if (have) {
     for (int c0 = 0; c0 < BN; c0 += 16) {
       uint32_t r[16];
       tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0), r);
@@ -298,7 +321,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ 
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const long long on = offn[c0 + j];
-          if (on >= 0) put(om + on, __uint_as_float(r[j]) * float(g.alpha));
+          if (on >= 0) put(om + on, __uint_as_float(r[j]) * alpha);
         }
       } else {
         // through shared memory: 16 lanes per row along the columns
@@ -310,7 +333,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ 
 #pragma unroll 4
         for (int i = lane >> 4; i < 32; i += 2) {
           const long long omi = offm[warp * 32 + i];
-          if (omi >= 0 && on >= 0) put(omi + on, stage_out[warp][i][j] * float(g.alpha));
+          if (omi >= 0 && on >= 0) put(omi + on, stage_out[warp][i][j] * alpha);
         }
         __syncwarp();
       }
@@ -321,6 +344,34 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ 
   if (warp == 0) {
     const uint32_t ncols = BN < 32 ? 32 : BN;
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+  }
+}
+
+// Split-K: out[p][m, n] = alpha * sum_s part[s][p][m][n] (fixed order), through
+// the output offset groups.
+__global__ void k_tc_splitk_reduce(const TcArgs g) {
+  const long long MN = g.M * g.N, total = (long long)g.nprob * MN;
+  const float alpha = float(g.alpha);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int pb = int(t / MN);
+    const long long mn = t - pb * MN, m = mn / g.N, n = mn - m * g.N;
+    float v = 0.f;
+    for (int sp = 0; sp < g.splitk; ++sp) v += g.part[((long long)sp * g.nprob + pb) * MN + mn];
+    v *= alpha;
+    long long om, on;
+    decomp(g.gm, m, om);
+    decomp(g.gn, n, on);
+    const long long o = om + on;
+    if (g.out_f64) {
+      static_cast<double*>(g.C.p[pb])[o] = double(v);
+    } else if (g.out_lo) {
+      const float h = round_tf32(v);
+      static_cast<float*>(g.C.p[pb])[o] = h;
+      static_cast<float*>(g.Clo.p[pb])[o] = round_tf32(v - h);
+    } else {
+      static_cast<float*>(g.C.p[pb])[o] = v;
+    }
   }
 }
 
@@ -344,9 +395,36 @@ struct PackArgs {
 
 constexpr int PK_T = 32;
 
-// Grid = (row tiles x k tiles, problems), 256 threads.
+// hi = v rounded to the operand type; lo = the rounded residual.  For FP32
+// sources everything stays in FP32 (v - tf32(v) is exact there): the FP64
+// pipe of GB300 is ~1/64 of FP32, so FP64 arithmetic here would bound the copy.
+__device__ __forceinline__ void split_store(float v, const PackArgs& p, long long d) {
+  if (p.bf16) {
+    const __nv_bfloat16 h = __float2bfloat16(v);
+    static_cast<__nv_bfloat16*>(p.hi)[d] = h;
+    if (p.lo) static_cast<__nv_bfloat16*>(p.lo)[d] = __float2bfloat16(v - __bfloat162float(h));
+  } else {
+    const float h = round_tf32(v);
+    static_cast<float*>(p.hi)[d] = h;
+    if (p.lo) static_cast<float*>(p.lo)[d] = round_tf32(v - h);
+  }
+}
+__device__ __forceinline__ void split_store(double v, const PackArgs& p, long long d) {
+  if (p.bf16) {
+    const __nv_bfloat16 h = __double2bfloat16(v);
+    static_cast<__nv_bfloat16*>(p.hi)[d] = h;
+    if (p.lo) static_cast<__nv_bfloat16*>(p.lo)[d] = __double2bfloat16(v - double(__bfloat162float(h)));
+  } else {
+    const float h = round_tf32(float(v));
+    static_cast<float*>(p.hi)[d] = h;
+    if (p.lo) static_cast<float*>(p.lo)[d] = round_tf32(float(v - double(h)));
+  }
+}
+
+// Grid = (row tiles x k tiles, problems), 256 threads; T = source element type.
+template <typename T>
 __global__ void __launch_bounds__(256) k_pack(const PackArgs p) {
-  __shared__ double tile[PK_T][PK_T + 1];   // [k][row]
+  __shared__ T tile[PK_T][PK_T + 1];   // [k][row]
   __shared__ long long ro[PK_T], ko[PK_T];
   const int pb = blockIdx.y;
   const long long ktiles = (p.K + PK_T - 1) / PK_T;
@@ -362,17 +440,13 @@ __global__ void __launch_bounds__(256) k_pack(const PackArgs p) {
     ko[tid - PK_T] = o;
   }
   __syncthreads();
-  const double* sd = static_cast<const double*>(p.src.p[pb]);
-  const float* sf = static_cast<const float*>(p.src.p[pb]);
+  const T* src = static_cast<const T*>(p.src.p[pb]);
 #pragma unroll
   for (int q = 0; q < PK_T / 8; ++q) {
     const int a = ty + 8 * q;
     const int r = p.rows_fast ? tx : a, k = p.rows_fast ? a : tx;
-    double v = 0.0;
-    if (ro[r] >= 0 && ko[k] >= 0) {
-      const long long o = ro[r] + ko[k];
-      v = p.src_f64 ? sd[o] : double(sf[o]);
-    }
+    T v = T(0);
+    if (ro[r] >= 0 && ko[k] >= 0) v = src[ro[r] + ko[k]];
     tile[k][r] = v;
   }
   __syncthreads();
@@ -380,17 +454,7 @@ __global__ void __launch_bounds__(256) k_pack(const PackArgs p) {
   for (int q = 0; q < PK_T / 8; ++q) {
     const int r = ty + 8 * q, k = tx;
     if (ro[r] < 0 || ko[k] < 0) continue;
-    const double v = tile[k][r];
-    const long long d = (pb * p.pad + r0 + r) * p.ld + k0 + k;
-    if (p.bf16) {
-      const __nv_bfloat16 h = __double2bfloat16(v);
-      static_cast<__nv_bfloat16*>(p.hi)[d] = h;
-      if (p.lo) static_cast<__nv_bfloat16*>(p.lo)[d] = __double2bfloat16(v - double(__bfloat162float(h)));
-    } else {
-      const float h = round_tf32(float(v));
-      static_cast<float*>(p.hi)[d] = h;
-      if (p.lo) static_cast<float*>(p.lo)[d] = round_tf32(float(v - double(h)));
-    }
+    split_store(tile[k][r], p, (pb * p.pad + r0 + r) * p.ld + k0 + k);
   }
 }
 
@@ -519,8 +583,13 @@ Operand pack(Ctx& cx, const TP& src, int np, long long pad, int src_f64, const s
   p.rows_fast = inner(p.gr) < inner(p.gk) ? 1 : 0;
   const long long tiles = ((o.rows + PK_T - 1) / PK_T) * ((o.K + PK_T - 1) / PK_T);
   PEPS_REQUIRE(tiles < (1LL << 31), "operand too large to pack");
-  Launch L(K_AUX, cx.st);
-  k_pack<<<dim3(unsigned(tiles), np), 256, 0, cx.st>>>(p);
+  const double moved = double(np) * double(o.rows) * double(o.K) *
+                       ((src_f64 ? 8.0 : 4.0) + (split ? 2.0 : 1.0) * (bf16 ? 2.0 : 4.0));
+  Launch L(K_PACK, cx.st, 0, moved);
+  if (src_f64)
+    k_pack<double><<<dim3(unsigned(tiles), np), 256, 0, cx.st>>>(p);
+  else
+    k_pack<float><<<dim3(unsigned(tiles), np), 256, 0, cx.st>>>(p);
   PEPS_CHECK_LAUNCH();
   return o;
 }
@@ -539,13 +608,13 @@ void launch_tc(Ctx& cx, const CUtensorMap& ta, const CUtensorMap& tb, const CUte
   const int a_bytes = TC_BM * TC_ROWB, b_bytes = BN * TC_ROWB;
   const int stage = g.split ? 2 * (a_bytes + b_bytes) : (a_bytes + b_bytes);
   const int budget = 200 * 1024;
-  g.stages = std::max(1, std::min({TC_STAGES, (budget - 1024) / stage, g.ktiles}));
+  g.stages = std::max(1, std::min({TC_STAGES, (budget - 1024) / stage, g.splitk > 1 ? g.kt_per : g.ktiles}));
   const size_t smem = size_t(stage) * g.stages + 1024;
   static std::once_flag once;
   std::call_once(once, [] {
     PEPS_CUDA(cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   });
-  k_gemm_tc<BN><<<unsigned(tiles), TC_THREADS, smem, cx.st>>>(ta, tb, tal, tbl, g);
+  k_gemm_tc<BN><<<dim3(unsigned(tiles), unsigned(std::max(1, g.splitk))), TC_THREADS, smem, cx.st>>>(ta, tb, tal, tbl, g);
   PEPS_CHECK_LAUNCH();
 }
 
@@ -603,7 +672,23 @@ void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, c
   while (BN < N && BN < 128) BN *= 2;
   const long long pad_m = (M + TC_BM - 1) / TC_BM * TC_BM, pad_n = (N + BN - 1) / BN * BN;
   const size_t wa = pack_words(np * pad_m, K, bf16, split), wb = pack_words(np * pad_n, K, bf16, split);
-  double* mem = cx.scratch(wa + wb);
+  const long long tiles = ((M + TC_BM - 1) / TC_BM) * ((N + BN - 1) / BN) * np;
+  PEPS_REQUIRE(tiles < (1LL << 31), "too many tiles");
+  g.ktiles = int((K + (TC_ROWB / (bf16 ? 2 : 4)) - 1) / (TC_ROWB / (bf16 ? 2 : 4)));
+  // Split K when the output tiles would leave most SMs idle: each split runs
+  // at least two k tiles; partials are reduced in a fixed order.
+  g.splitk = 1;
+  g.kt_per = g.ktiles;
+  if (tiles < 152 && g.ktiles >= 4) {
+    const long long want = std::min<long long>((2 * 152 + tiles - 1) / tiles, g.ktiles / 2);
+    if (want > 1) {
+      g.kt_per = int((g.ktiles + want - 1) / want);
+      g.splitk = int((g.ktiles + g.kt_per - 1) / g.kt_per);
+    }
+  }
+  const size_t wp = g.splitk > 1 ? (size_t(g.splitk) * np * M * N + 1) / 2 + 64 : 0;
+  double* mem = cx.scratch(wa + wb + wp);   // one reservation: operands, then split partials
+  if (g.splitk > 1) g.part = reinterpret_cast<float*>(mem + wa + wb);
   const Operand oa = pack(cx, A, np, pad_m, a_f64, p.a, ad, mL, kL, bf16, split, mem);
   const Operand ob = pack(cx, B, np, pad_n, b_f64, p.b, bd, nL, kL, bf16, split, mem + wa);
   PEPS_REQUIRE(np * pad_m < (1LL << 31) && np * pad_n < (1LL << 31), "operand too large for one launch");
@@ -614,7 +699,6 @@ void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, c
   g.M = M;
   g.N = N;
   g.K = K;
-  g.ktiles = int((K + (TC_ROWB / (bf16 ? 2 : 4)) - 1) / (TC_ROWB / (bf16 ? 2 : 4)));
   g.split = split;
   g.bf16 = bf16;
   g.out_f64 = c_f64;
@@ -635,8 +719,6 @@ void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, c
   g.Clo = Clo.all(np);
   g.alpha = alpha;
   g.flag = cx.flag;
-  const long long tiles = ((M + TC_BM - 1) / TC_BM) * ((N + BN - 1) / BN) * np;
-  PEPS_REQUIRE(tiles < (1LL << 31), "too many tiles");
   const double flops = 2.0 * double(M) * double(N) * double(K) * np;
   Launch L(K_GEMM_TC, cx.st, flops, 0);
   switch (BN) {
@@ -644,6 +726,12 @@ void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, c
     case 32: launch_tc<32>(cx, ta, tb, tal, tbl, g, tiles); break;
     case 64: launch_tc<64>(cx, ta, tb, tal, tbl, g, tiles); break;
     default: launch_tc<128>(cx, ta, tb, tal, tbl, g, tiles); break;
+  }
+  if (g.splitk > 1) {
+    const long long total = (long long)np * M * N;
+    const unsigned blocks = unsigned(std::max<long long>(1, std::min<long long>((total + 255) / 256, 4096)));
+    k_tc_splitk_reduce<<<blocks, 256, 0, cx.st>>>(g);
+    PEPS_CHECK_LAUNCH();
   }
 }
 
