@@ -192,18 +192,18 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_cluster(const QrArgs q, int 
   const int tid = threadIdx.x, nt = blockDim.x;
   const int chunk = (m + C - 1) / C;
   const int r0 = min(m, rank * chunk), r1 = min(m, r0 + chunk), rows = r1 - r0;
-  double* wpart = qsm;              // [2][n] per-column partial inner products (cluster-visible)
-  double* npart = wpart + 2 * n;    // [2]    partial squared norm below the diagonal
-  double* bcast = npart + 2;        // [2]    the diagonal entry, published by its owner
-  double* tau_s = bcast + 2;        // [k]
+  // Cluster-visible, double-buffered by column parity:
+  double* wpart = qsm;              // [2][n] my partial raw inner products of column j with columns c > j
+  double* rowj = wpart + 2 * n;     // [2][n] row j of the trailing matrix (valid in the row's owner)
+  double* npart = rowj + 2 * n;     // [2]    my partial squared norm of column j below the diagonal
+  double* tau_s = npart + 2;        // [k]
   double* part4 = tau_s + k;        // [n][QS] quarter sums
   double* wfin = part4 + (long long)n * QS;   // [n]
   double* coef = wfin + n;          // [2] scale, beta of the current reflector
-  double* nsq = coef + 2;           // [QS] squares of the next column, by row class
   double* W;                        // [n][ld] my rows, column-major (row i at i - r0)
   double* Qw;                       // [k][ld]
   if (in_smem) {
-    W = nsq + QS;
+    W = coef + 2 + QS;
     Qw = W + (long long)n * ld;
   } else {
     W = q.W + pb * q.wst + (long long)rank * ld * n;
@@ -214,19 +214,42 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_cluster(const QrArgs q, int 
     W[(long long)j * ld + li] = A[(r0 + li) * q.rs + j * q.cs];
   }
   __syncthreads();
-  if (tid == 0) {
-    double part = 0.0;
-    for (int i = max(r0, 1); i < r1; ++i) part += W[i - r0] * W[i - r0];
-    npart[0] = part;
-    if (r0 == 0 && rows > 0) bcast[0] = W[0];
-  }
+  // My partial sums for column j into buffer b: sum over my rows i > j of
+  // a_ji * a_ci for every c >= j (c = j: the squared norm), and, in the owner
+  // of row j, that row.  The reflector's inner products with the trailing
+  // columns are taken with the unscaled column, w_c = tau (a_cj + scale *
+  // sum_i a_ji a_ci), so one cluster barrier per column carries both the norm
+  // (for tau) and the inner products.
+  auto partials = [&](int j, int b) {
+    const int i0 = max(r0, j + 1);
+    const double* xj = W + (long long)j * ld - r0;
+    for (int t = tid; t < (n - j) * QS; t += nt) {
+      const int c = j + t / QS, qq = t % QS;
+      const double* wc = W + (long long)c * ld - r0;
+      double w = 0.0;
+      for (int i = i0 + ((qq - i0 % QS + QS) % QS); i < r1; i += QS) w = fma(xj[i], wc[i], w);
+      part4[(long long)c * QS + qq] = w;
+    }
+    __syncthreads();
+    const bool has_row = j >= r0 && j < r1;
+    for (int c = j + tid; c < n; c += nt) {
+      double w = 0.0;
+      for (int qq = 0; qq < QS; ++qq) w += part4[(long long)c * QS + qq];
+      if (c == j)
+        npart[b] = w;
+      else
+        wpart[b * n + c] = w;
+      if (has_row) rowj[b * n + c] = W[(long long)c * ld + (j - r0)];
+    }
+  };
+  partials(0, 0);
   for (int j = 0; j < k; ++j) {
     const int b = j & 1;
     const int owner = j / chunk;
     const bool own = (owner == rank);
-    cluster.sync();                                   // column j: norm partials and diagonal visible
+    cluster.sync();                                   // column j: norms, inner products, row j visible
     if (tid < 32) {
-      const double alpha = *cluster.map_shared_rank(bcast + b, owner);
+      const double alpha = *cluster.map_shared_rank(rowj + b * n + j, owner);
       double sig = 0.0;
       for (int r = tid; r < C; r += 32) sig += *cluster.map_shared_rank(npart + b, r);
       sig = warp_sum(sig);
@@ -249,54 +272,22 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_cluster(const QrArgs q, int 
     double* vj = W + (long long)j * ld - r0;          // vj[i] for global row i
     const int nc = n - j - 1;                         // trailing columns
     if (tau != 0.0) {                                 // uniform across the cluster
-      for (int i = i0 + tid; i < r1; i += nt) vj[i] *= scale;
-      __syncthreads();
-      for (int t = tid; t < nc * QS; t += nt) {
-        const int c = j + 1 + t / QS, qq = t % QS;
-        const double* wc = W + (long long)c * ld - r0;
-        double w = 0.0;
-        for (int i = i0 + ((qq - i0 % QS + QS) % QS); i < r1; i += QS) w = fma(vj[i], wc[i], w);
-        part4[(long long)c * QS + qq] = w;
-      }
-      __syncthreads();
-      for (int c = j + 1 + tid; c < n; c += nt) {
-        const double* wc = W + (long long)c * ld - r0;
-        double w = own ? wc[j] : 0.0;
-        for (int qq = 0; qq < QS; ++qq) w += part4[(long long)c * QS + qq];
-        wpart[b * n + c] = w;
-      }
-      cluster.sync();                                 // inner products of column j visible
-      for (int c = j + 1 + tid; c < n; c += nt) wfin[c] = tau * remote_sum(cluster, wpart + b * n + c, C);
+      for (int c = j + 1 + tid; c < n; c += nt)
+        wfin[c] = tau * fma(scale, remote_sum(cluster, wpart + b * n + c, C),
+                            *cluster.map_shared_rank(rowj + b * n + c, owner));
+      for (int i = i0 + tid; i < r1; i += nt) vj[i] *= scale;   // local rows only: no hazard with the loads above
       __syncthreads();
       for (int t = tid; t < nc * QS; t += nt) {
         const int c = j + 1 + t / QS, qq = t % QS;
         double* wc = W + (long long)c * ld - r0;
         const double w = wfin[c];
         if (own && qq == 0) wc[j] -= w;
-        double sq = 0.0;                               // column j+1: squares below its diagonal
-        for (int i = i0 + ((qq - i0 % QS + QS) % QS); i < r1; i += QS) {
-          const double v = fma(-w, vj[i], wc[i]);
-          wc[i] = v;
-          if (i > j + 1) sq = fma(v, v, sq);
-        }
-        if (c == j + 1) nsq[qq] = sq;
+        for (int i = i0 + ((qq - i0 % QS + QS) % QS); i < r1; i += QS) wc[i] = fma(-w, vj[i], wc[i]);
       }
       if (own && tid == 0) vj[j] = beta;
-    } else if (j + 1 < k) {
-      for (int qq = tid; qq < QS; qq += nt) {          // column j+1 untouched: squares as they are
-        const double* w1 = W + (long long)(j + 1) * ld - r0;
-        double sq = 0.0;
-        for (int i = max(r0, j + 2) + ((qq - max(r0, j + 2) % QS + QS) % QS); i < r1; i += QS) sq = fma(w1[i], w1[i], sq);
-        nsq[qq] = sq;
-      }
     }
     __syncthreads();
-    if (j + 1 < k && tid == 0) {                      // next column: norm partial and diagonal
-      double part = 0.0;
-      for (int qq = 0; qq < QS; ++qq) part += nsq[qq];
-      npart[1 - b] = part;
-      if (j + 1 >= r0 && j + 1 < r1) bcast[1 - b] = W[(long long)(j + 1) * ld + (j + 1 - r0)];
-    }
+    if (j + 1 < k) partials(j + 1, 1 - b);
   }
   // Q = H_0 ... H_{k-1} [I_k; 0], accumulated backwards on the same row split.
   for (long long e = tid; e < (long long)rows * k; e += nt) {
@@ -541,7 +532,7 @@ void qr_thin(Ctx& cx, int m, int n, const TP& A, long long rs, long long cs, con
   const int k = std::min(m, n);
   const double flops = 4.0 * m * double(n) * k - 4.0 / 3.0 * double(k) * k * k;
   const size_t kQrSmemMax = 200 * 1024;
-  const size_t base = sizeof(double) * (2 * size_t(n) + 4 + k + size_t(n) * QS + n + 2 + QS);
+  const size_t base = sizeof(double) * (4 * size_t(n) + 2 + k + size_t(n) * QS + n + 2 + QS);
   auto ld_of = [&](int c) { return (((m + c - 1) / c) | 1); };   // odd column stride
   auto full_of = [&](int c) { return base + sizeof(double) * size_t(ld_of(c)) * (size_t(n) + k); };
   // Cluster size: rows per CTA >= 32; among the sizes whose rows fit in shared
