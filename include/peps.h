@@ -8,8 +8,8 @@
  *
  *   - the norm <psi|psi>                                     (Section 2, Fig. 2)
  *   - the environment of every site, in factored form        (Section 2: N_l, b_l)
- *   - local expectation values <O> = Tr(rho O)/Tr(rho)       (Section 4.3)
- *   - the same environments in the cluster scheme CU         (Section 4, 4.2, 4.3)
+ *   - local expectation values <O> = Tr(rho O)/Tr(rho)       (Section 5.3)
+ *   - the same environments in the cluster scheme CU         (Section 5, 5.2, 5.3)
  *
  * Every step runs in the library's CUDA kernels; there is no CPU fallback.
  * A call made without a usable CUDA device fails with PEPS_ECUDA.
@@ -74,7 +74,7 @@ extern "C" {
 #define PEPS_VBOND 2        /* rho of bond (y,x)-(y+1,x):    d^2 x d^2, (Ly-1)*Lx values   */
 
 /* cluster closure outside the window */
-#define PEPS_CLOSURE_PLAIN   0   /* CU_0 separable boundaries (Section 4.1)                 */
+#define PEPS_CLOSURE_PLAIN   0   /* CU_0 separable boundaries (Section 5.1)                 */
 #define PEPS_CLOSURE_LEARNED 1   /* CU_0 matrices replaced by the learned closure's output   */
 #define PEPS_CLOSURE_WIDTH   256 /* hidden width of the learned closure used by peps_env_cluster */
 
@@ -118,16 +118,16 @@ int peps_env_full(const peps_lattice* lat, const peps_opts* opts,
 
 /*
  * peps_env_cluster -- cluster (CU) environments of every site.
- *   Section 4 / 4.2: outside a window around each site the environment is
- *   the product of CU_0 separable boundaries (Section 4.1: D'=1 boundary
+ *   Section 5 / 5.2: outside a window around each site the environment is
+ *   the product of CU_0 separable boundaries (Section 5.1: D'=1 boundary
  *   found by ALS whose local solution is proportional to b_l); inside the
- *   window the contraction is the full one at bond chi.  Section 4.3 forms
+ *   window the contraction is the full one at bond chi.  Section 5.3 forms
  *   the cluster around the local term itself: the window is opts->n x
  *   opts->n with rows y-ceil(n/2)+1 .. (same for columns), clipped at the
  *   lattice edge, so edge windows are smaller.  Site (y,x) yields its own
  *   density matrix and those of the bonds to (y,x+1) and (y+1,x).  With
  *   n >= 2*max(Ly,Lx) every window is the lattice and the result equals
- *   peps_env_full's (Section 4: CU_{L-1} is the full update).
+ *   peps_env_full's (Section 5: CU_{L-1} is the full update).
  *   Fails with PEPS_ECONVERGE if a CU_0 iteration does not converge.
  */
 int peps_env_cluster(const peps_lattice* lat, const peps_opts* opts,
@@ -135,7 +135,7 @@ int peps_env_cluster(const peps_lattice* lat, const peps_opts* opts,
 
 /*
  * peps_expect_local -- <O> = Tr(rho O) / Tr(rho) at every site or bond.
- *   Section 4.3 (local expectation values from local reduced density matrices).
+ *   Section 5.3 (local expectation values from local reduced density matrices).
  *   kind: PEPS_SITE / PEPS_HBOND / PEPS_VBOND.
  *   op:   host array, real, row-major, d x d (site) or d^2 x d^2 (bond, rows
  *         and columns ordered (s_first, s_second) with the first site the left
@@ -198,7 +198,7 @@ int peps_cu0_noalloc(const double* A, int Ly, int Lx, int d, int D, double* sigm
 
 /*
  * Learned cluster closure (the paper has no learned part; built on its
- * cluster scheme, Section 4.2).  A three-layer ReLU network of width W maps,
+ * cluster scheme, Section 5.2).  A three-layer ReLU network of width W maps,
  * for one outward leg of a cluster window, the site tensor just above the
  * cut (d*D^4, zero-padded, legs [s,u,l,n,r] in the sweep's orientation),
  * the CU_0 matrix sigma0 at that leg (D^2) and its Cholesky factor L0 (D^2)

@@ -9,7 +9,7 @@ MPS, truncation or environments, so it pins the boundary-MPS oracle
 independently.
 
 Closures (a window's outward legs closed by positive matrices C = X X^T,
-Section 4.2) are handled by absorbing X into the ket and the bra: the
+Section 5.2) are handled by absorbing X into the ket and the bra: the
 column index of X becomes an extra physical index of that site.
 """
 from __future__ import annotations

@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY (see the oracle package header).
 
 The closure replaces the CU_0 matrix on one outward leg of a cluster window
-(Section 4.1, 4.2) by a positive matrix predicted from local data.  The paper
+(Section 5.1, 5.2) by a positive matrix predicted from local data.  The paper
 has no learned part; this is the build's reading of it:
 
 * label at (direction, cut, column): the site matrix of the best D'=1 product

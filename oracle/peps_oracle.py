@@ -17,10 +17,10 @@ What it computes (Lubasch, Cirac, Banuls, "Unifying PEPS contractions"):
   alternating least squares with the local equation N_l A_l = b_l of
   Section 2, where the orthonormal gauge makes N_l the identity.
 * Environments and local reduced density matrices (Section 2: environment of
-  a site; Section 4.3: local expectation values).
-* CU_0 separable boundaries (Section 4.1, Figs. 7-8): a D'=1 boundary whose
+  a site; Section 5.3: local expectation values).
+* CU_0 separable boundaries (Section 5.1, Figs. 7-8): a D'=1 boundary whose
   local ALS update is proportional to b_l, and stays positive.
-* Cluster environments (Section 4, 4.2, 4.3): inside a window around a site
+* Cluster environments (Section 5, 5.2, 5.3): inside a window around a site
   the contraction is done as in the full method; outside it the environment
   is the product of CU_0 matrices.
 
@@ -75,7 +75,7 @@ class Lat:
     For the full lattice the outward legs have dimension 1 and the closures
     are [[1]] (open boundary conditions, Section 2).  A cluster window keeps
     the real dimension D on its outward legs and closes them with CU_0
-    matrices (Section 4.2).
+    matrices (Section 5.2).
     """
 
     def __init__(self, A, top, bottom, left, right):
@@ -549,7 +549,7 @@ def norm(Ad_or_lat, chi: int, mode: str = "svd", sweeps: int = 2, seed: int = 0)
 
 
 # ---------------------------------------------------------------------------
-# CU_0: separable (D'=1) boundaries (Section 4.1)
+# CU_0: separable (D'=1) boundaries (Section 5.1)
 # ---------------------------------------------------------------------------
 def cu0_local(Lm, S, A, Rm):
     """b[n,o] = sum Lm[l,m] S[u,v] A[s,u,l,n,r] A[s,v,m,o,q] Rm[r,q]; O(dD^5)."""
@@ -589,7 +589,7 @@ def cu0_sweep(lat: Lat, tol: float = 1e-13, max_half: int = 200,
     unit Frobenius norm; half-sweeps alternate L->R and R->L until the
     largest change of any matrix is below ``tol``.  Initial matrices are the
     identity (or X X^T with X from ``init_seed`` when init='random'), so they
-    are positive and stay positive (Section 4.1).
+    are positive and stay positive (Section 5.1).
     """
     Ly, Lx = lat.Ly, lat.Lx
     sig = [np.array(m, dtype=np.float64) for m in lat.top]
@@ -644,7 +644,7 @@ def cu0_all(lat: Lat, tol: float = 1e-13, max_half: int = 200):
 
 
 # ---------------------------------------------------------------------------
-# Cluster environments (Section 4; window shape per Section 4.3 "around the
+# Cluster environments (Section 5; window shape per Section 5.3 "around the
 # individual terms"; n x n window clipped at the lattice edge)
 # ---------------------------------------------------------------------------
 def window_bounds(L: int, i: int, n: int):

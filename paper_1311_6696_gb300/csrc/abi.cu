@@ -520,7 +520,7 @@ void full_env(Call& c, const peps_lattice* lat, const Opts& opt, peps_env* env, 
   e.has_norm = true;
 }
 
-// Window of the cluster scheme (Section 4.3): n x n around (i) clipped at [0, L).
+// Window of the cluster scheme (Section 5.3): n x n around (i) clipped at [0, L).
 std::pair<int, int> window(int L, int i, int n) {
   const int h = (n + 1) / 2;
   const int lo = i - h + 1;

@@ -207,7 +207,7 @@ unsigned grid_for(long long n) {
 }
 
 // ----------------------------------------------------------------------------
-// CU_0 (Section 4.1): one CTA per oriented lattice.
+// CU_0 (Section 5.1): one CTA per oriented lattice.
 // ----------------------------------------------------------------------------
 struct SiteDims {
   int du, dl, dn, dr;

@@ -42,7 +42,7 @@ void finish_norm(Ctx& cx, const double* lns, int nl, const double* extra, const 
 void fill(Ctx& cx, const TP& x, long long n, double v);
 void copy(Ctx& cx, const TP& dst, const TP& src, long long n);
 
-// CU_0 separable boundaries of one oriented lattice (Section 4.1), computed
+// CU_0 separable boundaries of one oriented lattice (Section 5.1), computed
 // by one CTA.  Site tensors at `sites` (per-site offsets/dims in `meta`),
 // closures as device matrices.  Output: out[r][x] = D x D matrix (stride
 // out_stride per row, mat_stride per site) on the up legs of row r, r = 1..Ly-1.

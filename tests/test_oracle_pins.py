@@ -3,9 +3,9 @@
 * brute-force state vectors (the PEPS definition, Section 2) on 4x4 and 4x5;
 * exactness: chi >= (D^2)^(Lx/2) reproduces the exact contraction;
 * closed forms for D=1 product states;
-* a cluster covering the lattice is the full method (Section 4: CU_{L-1});
+* a cluster covering the lattice is the full method (Section 5: CU_{L-1});
 * cluster windows with CU_0 closures vs brute force of the closed window;
-* CU_0 positivity (Section 4.1) and its fixed point checked as a stationary
+* CU_0 positivity (Section 5.1) and its fixed point checked as a stationary
   point of the overlap, computed with dense vectors;
 * the var local update vs a dense least-squares solve (Section 2, N A = b);
 * gauge invariance, and top-down vs bottom-up norms;

@@ -1,4 +1,4 @@
-"""The simple-update input generator against the paper's Table ESU (Appendix A),
+"""The simple-update input generator against the paper's Table 2 (Appendix A),
 evaluated by exact (brute-force) contraction of the generated 4x4 states."""
 import os
 
@@ -9,7 +9,7 @@ from oracle import bruteforce as BF
 from oracle import peps_oracle as O
 from paper_1311_6696_gb300 import synth
 
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "su_heisenberg_4x4_table_esu.txt")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "su_heisenberg_4x4_table2.txt")
 
 
 def _rows():
@@ -22,7 +22,7 @@ def _rows():
 
 
 @pytest.mark.parametrize("D,e_paper,tol", _rows())
-def test_su_energy_matches_table_esu(D, e_paper, tol):
+def test_su_energy_matches_table2(D, e_paper, tol):
     A = synth.peps_simple_update(4, 4, D, seed=3, tau=0.01, steps=400)
     psi = BF.state_vector(BF.dense_lattice(A))
     dims = [2] * 16
