@@ -52,6 +52,14 @@ def _peaks():
         return {}
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
+# stands (profiles/<kernel>_bench_10x10_D4_chi64.md); update or drop an entry
+# whenever that kernel changes.
+TRAFFIC = {
+    "qr_f64": (592128, "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 1024x64 k_qr_cluster "
+                       "launch (profiles/k_qr_cluster_bench_10x10_D4_chi64.md); the matrix read once"),
+}
+
 # FP64 ALU peak of GB300 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -236,8 +244,10 @@ def run_ours(args, rank, world, dist):
         else:
             peak, bound = FP64_PEAK_TFLOPS, "alu"
             note = "FP64 ALU peak derived from 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"
+        tr = TRAFFIC.get(cls) if src is None else None
         return {"bound": bound, "kernel": cls, "achieved": round(achieved, 4), "peak": round(peak, 4),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 5), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 5), "traffic": tr[0] if tr else None,
+                "traffic_source": tr[1] if tr else None,
                 "launches": d["launches"], "avg_launch_us": round(1e3 * d["ms"] / max(1, d["launches"]), 3),
                 "algorithmic_flops_per_launch": round(d["flops"] / max(1, d["launches"]), 1),
                 "peak_source": note, "timed": timed}
