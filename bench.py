@@ -143,7 +143,7 @@ def run_ours(args, rank, world, dist):
     # The dominant class is timed inside every replay (event nodes around its
     # launches); the absorb class's figure comes from the probe replay above.
     peps.profile_enable(1 << peps.class_index(dom))
-    plan = peps.Plan(At, **kw)
+    plan = peps.Plan(At, **kw, tune=not args.no_tune)
     peps.profile_enable(0)
     env = plan.env
 
@@ -272,6 +272,7 @@ def run_ours(args, rank, world, dist):
                    "chi": args.chi, "mode": args.mode, "sweeps": 2, "precision": args.precision,
                    "envs_per_step": envs, "l2": "flushed between steps (256 MiB write)",
                    "launch": f"recorded plan (CUDA graph of {plan.launches} kernels) replayed per step",
+                   "tuned": {"lanes": plan.lanes, "qr_cluster_max": plan.qr_cluster} if not args.no_tune else None,
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": round(e2e, 3), "unit": "envs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
@@ -442,6 +443,7 @@ def main():
     ap.add_argument("--dominant", default=None, help="kernel class timed for the roofline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cluster", action="store_true", help="skip the 14x14 D=6 cluster section")
+    ap.add_argument("--no-tune", action="store_true", help="record the plan with the default launch configuration")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-budget", type=float, default=10.0)
     args = ap.parse_args()

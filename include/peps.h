@@ -269,6 +269,14 @@ const char* peps_last_error(void);
  *   until peps_plan_free; its contents are those of the last run).  Use it
  *   with peps_expect_local, peps_env_rho, peps_env_ln_norm; never pass it to
  *   peps_env_free.
+ * peps_plan_tune: as peps_plan_create, with the launch configuration chosen
+ *   by measurement (a project-written autotuner).  It records one plan per
+ *   candidate and times one warm plus two timed replays of each with CUDA
+ *   events on cuda_stream, keeping the fastest.  The search is over host
+ *   lanes {2, 4, 8} first (QR cluster size by the library's model), then over
+ *   the largest QR cluster {8, 4} with the best lane count.  *lanes and
+ *   *qr_cluster (either may be NULL) receive the choice.  Costs five
+ *   recordings and fifteen replays.
  * peps_plan_launches: kernel launches in one replay.
  * peps_plan_free: synchronises the device, releases the graph and its
  *   memory; NULL is accepted.
@@ -277,6 +285,8 @@ typedef struct peps_plan peps_plan;
 int peps_plan_create(const peps_lattice* lat, const peps_opts* opts, int cluster, peps_plan** out,
                      void* cuda_stream);
 int peps_plan_run(peps_plan* plan, void* cuda_stream);
+int peps_plan_tune(const peps_lattice* lat, const peps_opts* opts, int cluster, peps_plan** out,
+                   int* lanes, int* qr_cluster, void* cuda_stream);
 const peps_env* peps_plan_env(const peps_plan* plan);
 long long peps_plan_launches(const peps_plan* plan);
 void peps_plan_free(peps_plan* plan);

@@ -166,16 +166,25 @@ struct peps_env {
 
 namespace {
 
+// Launch configuration of one call: host lanes (0: PEPS_LANES or 4) and the
+// largest thread-block cluster of a QR (0: PEPS_QR_CMAX or 16).
+struct Tune {
+  int lanes = 0;
+  int qr_cmax = 0;
+};
+
 struct Call {
   cudaStream_t st;
   Arena ws;
   Ctx cx;
+  Tune tune;
   // persist: set while recording a graph; the status word and staged host
   // data then live in memory that outlives the recording.
-  explicit Call(void* stream, Arena* persist = nullptr)
-      : st(static_cast<cudaStream_t>(stream)), ws(st), cx(st, &ws) {
+  explicit Call(void* stream, Arena* persist = nullptr, Tune t = Tune())
+      : st(static_cast<cudaStream_t>(stream)), ws(st), cx(st, &ws), tune(t) {
     cx.persist = persist;
     if (const char* e = std::getenv("PEPS_QR_CMAX")) cx.qr_cmax = std::atoi(e);
+    if (tune.qr_cmax > 0) cx.qr_cmax = tune.qr_cmax;
     cx.flag = static_cast<int*>(persist ? persist->alloc(sizeof(int)) : ws.alloc(sizeof(int)));
     PEPS_CUDA(cudaMemsetAsync(cx.flag, 0, sizeof(int), st));
     cx.tmp = ws.dalloc(8);
@@ -372,7 +381,9 @@ int lane_count() {
   return n;
 }
 
-std::vector<cudaStream_t>& lane_streams() {
+int lanes_of(const Tune& t) { return t.lanes > 0 ? std::min(t.lanes, 64) : lane_count(); }
+
+std::vector<cudaStream_t>& lane_streams(int n) {
   static std::mutex mu;
   static std::vector<std::vector<cudaStream_t>> pool;
   std::lock_guard<std::mutex> g(mu);
@@ -380,7 +391,7 @@ std::vector<cudaStream_t>& lane_streams() {
   PEPS_CUDA(cudaGetDevice(&dev));
   if (int(pool.size()) <= dev) pool.resize(dev + 1);
   auto& v = pool[dev];
-  while (int(v.size()) < lane_count()) {
+  while (int(v.size()) < n) {
     cudaStream_t s;
     PEPS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     v.push_back(s);
@@ -408,8 +419,9 @@ struct Lanes {
   std::vector<Lane> l;
   // nb: problems each lane's engine runs in lockstep.
   Lanes(Call& c, const Opts& opt, int d, int D, int Lmax, int nb = 1) : main(c.st) {
-    auto& pool = lane_streams();
-    l.resize(lane_count());
+    const int nl = lanes_of(c.tune);
+    auto& pool = lane_streams(nl);
+    l.resize(nl);
     for (int i = 0; i < int(l.size()); ++i) {
       Lane& a = l[i];
       a.st = pool[i];
@@ -635,7 +647,7 @@ void cluster_env(Call& c, const peps_lattice* lat, const Opts& opt, int n, peps_
                                    int(wv.r0 == 0), int(wv.r1 == Ly - 1), int(wv.c0 == 0), int(wv.c1 == Lx - 1)};
       groups[key].push_back(wv);
     }
-  const int nl = lane_count();
+  const int nl = lanes_of(c.tune);
   const int Lwin = std::min(n, std::max(Ly, Lx));
   const size_t per = Engine::footprint(opt, d, D, Lwin) * sizeof(double);
   size_t free_b = 0, total_b = 0;
@@ -825,8 +837,101 @@ struct peps_plan {
   cudaGraphExec_t exec = nullptr;
   int* flag = nullptr;
   long long nodes = 0;
+  int lanes = 0, qr_cmax = 0;       // launch configuration it was recorded with
   Counts counts;                    // kernel launches (and their flops) in one replay
 };
+
+namespace {
+
+struct PlanDel {
+  void operator()(peps_plan* p) const { peps_plan_free(p); }
+};
+using PlanPtr = std::unique_ptr<peps_plan, PlanDel>;
+
+Opts plan_checks(const peps_lattice* lat, const peps_opts* opts, bool cl) {
+  require_device();
+  check_lattice(lat);
+  PEPS_REQUIRE(lat->on_device, "a plan reads its lattice from device memory (on_device = 1)");
+  return check_opts(opts, cl);
+}
+
+// One plain call validates the input and performs every one-time set-up
+// (kernel attributes, cluster occupancy queries) outside any recording.
+void validate_by_running(const peps_lattice* lat, const peps_opts* opts, bool cl, void* stream) {
+  peps_env* probe = nullptr;
+  const int rc = run_env(lat, opts, &probe, stream, cl);
+  peps_env_free(probe);
+  if (rc != PEPS_OK) throw Error(rc, g_err);
+}
+
+// Records the whole computation of one call, with launch configuration t, as a CUDA graph.
+PlanPtr record_plan(const peps_lattice* lat, const peps_opts* opts, const Opts& o, bool cl, const Tune& t) {
+  static std::mutex record_mu;   // one recording at a time (shared lane streams)
+  std::lock_guard<std::mutex> lk(record_mu);
+  PlanPtr plan(new peps_plan());
+  PEPS_CUDA(cudaGetDevice(&plan->device));
+  plan->lanes = lanes_of(t);
+  plan->qr_cmax = t.qr_cmax;
+  plan->persist = std::make_unique<Arena>(nullptr, size_t(1) << 20, /*async=*/false);
+  cudaStream_t cs = nullptr;
+  PEPS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  struct Cleanup {
+    cudaStream_t s;
+    ~Cleanup() {
+      g_recording.store(nullptr);
+      cudaStreamDestroy(s);
+    }
+  } cleanup{cs};
+  g_recording.store(&plan->counts);
+  PEPS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+  try {
+    Call c(cs, plan->persist.get(), t);
+    plan->flag = c.cx.flag;
+    plan->env = new_env(lat, cl ? 1 : 0, cs);
+    compute(c, lat, opts, o, cl, plan->env.get());
+  } catch (...) {
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(cs, &g);
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    throw;
+  }
+  PEPS_CUDA(cudaStreamEndCapture(cs, &plan->graph));
+  g_recording.store(nullptr);
+  size_t nodes = 0;
+  PEPS_CUDA(cudaGraphGetNodes(plan->graph, nullptr, &nodes));
+  plan->nodes = (long long)nodes;
+  const auto t0 = std::chrono::steady_clock::now();
+  PEPS_CUDA(cudaGraphInstantiate(&plan->exec, plan->graph, 0));
+  if (std::getenv("PEPS_VERBOSE"))
+    std::fprintf(stderr, "[peps] plan: %zu graph nodes, instantiated in %.1f ms\n", nodes,
+                 std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+  return plan;
+}
+
+// Device time of one replay: one warm replay, then the best of `reps` (CUDA events on st).
+double time_plan(peps_plan* p, cudaStream_t st, int reps) {
+  cudaEvent_t e0, e1;
+  PEPS_CUDA(cudaEventCreate(&e0));
+  PEPS_CUDA(cudaEventCreate(&e1));
+  double best = 1e300;
+  cudaError_t err = cudaGraphLaunch(p->exec, st);
+  for (int r = 0; r < reps && err == cudaSuccess; ++r) {
+    cudaEventRecord(e0, st);
+    err = cudaGraphLaunch(p->exec, st);
+    cudaEventRecord(e1, st);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) best = std::min(best, double(ms));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  PEPS_CUDA(err);
+  Call::read_status(p->flag, st);
+  return best;
+}
+
+}  // namespace
 
 // ---------------------------------------------------------------------------
 // C ABI
@@ -1075,58 +1180,43 @@ int peps_plan_create(const peps_lattice* lat, const peps_opts* opts, int cluster
   if (out) *out = nullptr;
   return guard([&] {
     PEPS_REQUIRE(out != nullptr, "out is NULL");
-    require_device();
-    check_lattice(lat);
-    PEPS_REQUIRE(lat->on_device, "a plan reads its lattice from device memory (on_device = 1)");
+    const Opts o = plan_checks(lat, opts, cluster != 0);
+    validate_by_running(lat, opts, cluster != 0, cuda_stream);
+    *out = record_plan(lat, opts, o, cluster != 0, Tune()).release();
+  });
+}
+
+int peps_plan_tune(const peps_lattice* lat, const peps_opts* opts, int cluster, peps_plan** out, int* lanes,
+                   int* qr_cluster, void* cuda_stream) {
+  if (out) *out = nullptr;
+  return guard([&] {
+    PEPS_REQUIRE(out != nullptr, "out is NULL");
     const bool cl = cluster != 0;
-    const Opts o = check_opts(opts, cl);
-    {
-      // One plain call validates the input and performs every one-time set-up
-      // (kernel attributes, cluster occupancy queries) outside the recording.
-      peps_env* probe = nullptr;
-      const int rc = run_env(lat, opts, &probe, cuda_stream, cl);
-      peps_env_free(probe);
-      if (rc != PEPS_OK) throw Error(rc, g_err);
-    }
-    static std::mutex record_mu;   // one recording at a time (shared lane streams)
-    std::lock_guard<std::mutex> lk(record_mu);
-    auto plan = std::make_unique<peps_plan>();
-    PEPS_CUDA(cudaGetDevice(&plan->device));
-    plan->persist = std::make_unique<Arena>(nullptr, size_t(1) << 20, /*async=*/false);
-    cudaStream_t cs = nullptr;
-    PEPS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    struct Cleanup {
-      cudaStream_t s;
-      ~Cleanup() {
-        g_recording.store(nullptr);
-        cudaStreamDestroy(s);
+    const Opts o = plan_checks(lat, opts, cl);
+    validate_by_running(lat, opts, cl, cuda_stream);
+    const cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    PlanPtr best;
+    double tbest = 1e300;
+    Tune tb;
+    auto consider = [&](const Tune& t) {
+      PlanPtr p(record_plan(lat, opts, o, cl, t).release());
+      const double ms = time_plan(p.get(), st, 2);
+      if (std::getenv("PEPS_VERBOSE"))
+        std::fprintf(stderr, "[peps] tune: lanes %d, qr cluster <= %d: %.3f ms\n", lanes_of(t),
+                     t.qr_cmax > 0 ? t.qr_cmax : 16, ms);
+      if (ms < tbest) {
+        tbest = ms;
+        tb = t;
+        best.swap(p);
       }
-    } cleanup{cs};
-    g_recording.store(&plan->counts);
-    PEPS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
-    try {
-      Call c(cs, plan->persist.get());
-      plan->flag = c.cx.flag;
-      plan->env = new_env(lat, cl ? 1 : 0, cs);
-      compute(c, lat, opts, o, cl, plan->env.get());
-    } catch (...) {
-      cudaGraph_t g = nullptr;
-      cudaStreamEndCapture(cs, &g);
-      if (g) cudaGraphDestroy(g);
-      cudaGetLastError();
-      throw;
-    }
-    PEPS_CUDA(cudaStreamEndCapture(cs, &plan->graph));
-    g_recording.store(nullptr);
-    size_t nodes = 0;
-    PEPS_CUDA(cudaGraphGetNodes(plan->graph, nullptr, &nodes));
-    plan->nodes = (long long)nodes;
-    const auto t0 = std::chrono::steady_clock::now();
-    PEPS_CUDA(cudaGraphInstantiate(&plan->exec, plan->graph, 0));
-    if (std::getenv("PEPS_VERBOSE"))
-      std::fprintf(stderr, "[peps] plan: %zu graph nodes, instantiated in %.1f ms\n", nodes,
-                   std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
-    *out = plan.release();
+    };
+    // Coordinate search: lanes first (QR clusters by the model), then the QR cluster cap.
+    for (int nl : {2, 4, 8}) consider(Tune{nl, 0});
+    const int bl = tb.lanes;
+    for (int qc : {8, 4}) consider(Tune{bl, qc});
+    if (lanes) *lanes = lanes_of(tb);
+    if (qr_cluster) *qr_cluster = tb.qr_cmax > 0 ? tb.qr_cmax : 16;
+    *out = best.release();
   });
 }
 

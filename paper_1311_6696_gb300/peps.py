@@ -28,7 +28,7 @@ EXPORTS = [
     "peps_profile_reset", "peps_profile_count", "peps_profile_name", "peps_profile_read",
     "peps_cu0_noalloc", "peps_closure_data", "peps_mlp_param_count", "peps_mlp_init",
     "peps_mlp_loss_grad", "peps_mlp_train", "peps_mlp_predict", "peps_plan_create", "peps_plan_run",
-    "peps_plan_env", "peps_plan_launches", "peps_plan_free",
+    "peps_plan_env", "peps_plan_launches", "peps_plan_free", "peps_plan_tune",
 ]
 CLOSURE_WIDTH = 256
 
@@ -83,6 +83,8 @@ def _load():
                                    C.c_float, C.c_float, C.c_ulonglong, C.POINTER(C.c_double), P]
     lib.peps_mlp_predict.argtypes = [P, P, C.c_longlong, C.c_int, C.c_int, C.c_int, P, P]
     lib.peps_plan_create.argtypes = [C.POINTER(Lattice), C.POINTER(Opts), C.c_int, C.POINTER(P), P]
+    lib.peps_plan_tune.argtypes = [C.POINTER(Lattice), C.POINTER(Opts), C.c_int, C.POINTER(P),
+                                   C.POINTER(C.c_int), C.POINTER(C.c_int), P]
     lib.peps_plan_run.argtypes = [P, P]
     lib.peps_plan_env.argtypes = [P]
     lib.peps_plan_env.restype = P
@@ -220,7 +222,8 @@ class Plan:
     A must be a contiguous CUDA tensor; overwrite it in place between runs."""
 
     def __init__(self, A, chi: int, mode="svd", sweeps: int = 2, precision="fp64", seed: int = 0,
-                 cluster_n: int | None = None, closure_weights=None, stream=None, device=None):
+                 cluster_n: int | None = None, closure_weights=None, stream=None, device=None,
+                 tune: bool = False):
         _set_device(device)
         self._inp = _Input(A)
         assert self._inp.lat.on_device, "a plan needs the lattice on the device"
@@ -228,8 +231,15 @@ class Plan:
         o = _opts(chi, mode, sweeps, precision, cluster_n or 1, seed, closure_weights)
         self._stream = stream
         h = C.c_void_p()
-        _check(lib.peps_plan_create(C.byref(self._inp.lat), C.byref(o), int(cluster_n is not None),
-                                    C.byref(h), _stream_ptr(stream)))
+        self.lanes = self.qr_cluster = None
+        if tune:      # launch configuration chosen by measurement (peps_plan_tune)
+            nl, qc = C.c_int(), C.c_int()
+            _check(lib.peps_plan_tune(C.byref(self._inp.lat), C.byref(o), int(cluster_n is not None),
+                                      C.byref(h), C.byref(nl), C.byref(qc), _stream_ptr(stream)))
+            self.lanes, self.qr_cluster = nl.value, qc.value
+        else:
+            _check(lib.peps_plan_create(C.byref(self._inp.lat), C.byref(o), int(cluster_n is not None),
+                                        C.byref(h), _stream_ptr(stream)))
         self._h = h.value
         self.launches = int(lib.peps_plan_launches(self._h))
 

@@ -113,3 +113,15 @@ def test_plan_rejects_obc_violation(peps):
     with pytest.raises(peps.PepsError) as e:
         peps.Plan(torch.from_numpy(A).cuda(), chi=4)
     assert e.value.code == peps.EINVAL
+
+
+def test_tuned_plan_matches_oracle(peps):
+    """The autotuner's choice changes only the launch configuration."""
+    import torch
+    from paper_1311_6696_gb300 import synth
+    A = synth.peps_gauss(5, 5, 2, 2, seed=91)
+    At = torch.from_numpy(A).cuda()
+    plan = peps.Plan(At, chi=8, mode="var", seed=3, tune=True)
+    assert plan.lanes in (2, 4, 8) and plan.qr_cluster in (4, 8, 16)
+    env = plan.run()
+    _close(_obs(env), _oracle_obs(O.env_full(A, chi=8, mode="var", seed=3)), TOL)
