@@ -5,6 +5,7 @@
 #include <array>
 #include <atomic>
 #include <chrono>
+#include <condition_variable>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -493,6 +494,45 @@ void run_lanes(Lanes& lanes, int njobs, F fn, const std::vector<std::vector<int>
     if (e) std::rethrow_exception(e);
 }
 
+// Boundaries published by the sweeps as they are produced: the host waits on
+// the condition variable for the Mps, the device on the event recorded after it.
+struct Published {
+  std::mutex mu;
+  std::condition_variable cv;
+  std::vector<Mps> b[4];
+  std::vector<cudaEvent_t> ev[4];
+  std::vector<char> ready[4];
+  std::exception_ptr failed;
+  ~Published() {
+    for (auto& v : ev)
+      for (cudaEvent_t e : v)
+        if (e) cudaEventDestroy(e);
+  }
+  void put(int o, int y, const Mps& m, cudaStream_t st) {
+    cudaEvent_t e;
+    PEPS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    PEPS_CUDA(cudaEventRecord(e, st));
+    std::lock_guard<std::mutex> g(mu);
+    b[o][y] = m;
+    ev[o][y] = e;
+    ready[o][y] = 1;
+    cv.notify_all();
+  }
+  void fail(std::exception_ptr p) {
+    std::lock_guard<std::mutex> g(mu);
+    if (!failed) failed = p;
+    cv.notify_all();
+  }
+  // Host: block until boundary (o, y) exists; device: make st wait for it.
+  const Mps& get(int o, int y, cudaStream_t st) {
+    std::unique_lock<std::mutex> g(mu);
+    cv.wait(g, [&] { return ready[o][y] || failed; });
+    if (!ready[o][y]) throw Error(PEPS_ECUDA, "a boundary sweep failed");
+    PEPS_CUDA(cudaStreamWaitEvent(st, ev[o][y], 0));
+    return b[o][y];
+  }
+};
+
 void full_env(Call& c, const peps_lattice* lat, const Opts& opt, peps_env* env, Oriented& ori) {
   Ctx& cx = c.cx;
   Arena& keep = *env->arena;
@@ -500,35 +540,101 @@ void full_env(Call& c, const peps_lattice* lat, const Opts& opt, peps_env* env, 
   double* lnacc = cx.ws->dalloc(4);
   fill(cx, lnacc, 4, 0.0);
   Lanes lanes(c, opt, d, lat->D, std::max(Ly, Lx));
-  // Four independent directional sweeps, one per lane.
-  std::vector<Mps> b[4];
-  run_lanes(lanes, 4, [&](Lane& L, int o) {
-    b[o] = L.eng->sweep(ori.o[o], o, (o < 2 ? Ly : Lx) - 1, lnacc + o, keep);
-  });
-  lanes.join();
-  lanes.fork();
+  const int nl = int(lanes.l.size());
+  // PEPS_VERBOSE (plain calls only): device time of the whole set
+  cudaEvent_t ph[2] = {};
+  const bool timed = std::getenv("PEPS_VERBOSE") && !cx.persist;
+  if (timed) {
+    for (auto& e : ph) PEPS_CUDA(cudaEventCreate(&e));
+    PEPS_CUDA(cudaEventRecord(ph[0], c.st));
+  }
   EnvData& e = env->data;
   const long long d2 = (long long)d * d, d4 = d2 * d2;
   const int ncol = Ly > 1 ? Lx : 0;
-  // Row passes, then column passes (vertical bonds), then the norm.
-  run_lanes(lanes, Ly + ncol + 1, [&](Lane& L, int job) {
-    if (job < Ly) {
-      const int y = job;
+  // Jobs: 0..3 the four directional sweeps; then row passes (Ly), column
+  // passes (ncol) and the norm.  A pass starts as soon as its two boundaries
+  // exist (a wavefront: the middle rows first), overlapping the sweeps.
+  Published pub;
+  for (int o = 0; o < 4; ++o) {
+    const int n = (o < 2 ? Ly : Lx);
+    pub.b[o].resize(n);
+    pub.ev[o].assign(n, nullptr);
+    pub.ready[o].assign(n, 0);
+  }
+  const int njobs = 4 + Ly + ncol + 1;
+  std::vector<std::vector<int>> plan(nl);
+  {
+    // Static plan: every lane runs its sweeps before any pass (so no pass
+    // waits on work queued behind it).  Passes go, in order of readiness, to
+    // the lane free earliest; a sweep costs ~8 passes, a pass is ready when
+    // the later of its two boundaries is (fraction of a sweep).
+    const double S = 8.0;
+    std::vector<double> avail(nl, 0.0);
+    for (int o = 0; o < 4; ++o) {
+      plan[o % nl].push_back(o);
+      avail[o % nl] += S;
+    }
+    std::vector<std::pair<double, int>> passes;
+    for (int y = 0; y < Ly; ++y)
+      passes.push_back({S * std::max(y, Ly - 1 - y) / std::max(1, Ly - 1), 4 + y});
+    for (int x = 0; x < ncol; ++x)
+      passes.push_back({S * std::max(x, Lx - 1 - x) / std::max(1, Lx - 1), 4 + Ly + x});
+    passes.push_back({S, 4 + Ly + ncol});
+    std::stable_sort(passes.begin(), passes.end());
+    for (auto& pj : passes) {
+      int best = 0;
+      double bt = 1e300;
+      for (int li = 0; li < nl; ++li) {
+        const double t = std::max(avail[li], pj.first) + 1.0;
+        if (t < bt) {
+          bt = t;
+          best = li;
+        }
+      }
+      plan[best].push_back(pj.second);
+      avail[best] = bt;
+    }
+  }
+  run_lanes(lanes, njobs, [&](Lane& L, int job) {
+    if (job < 4) {
+      const int o = job;
+      try {
+        L.eng->sweep(ori.o[o], o, (o < 2 ? Ly : Lx) - 1, lnacc + o, keep,
+                     [&](int y, const Mps& m) { pub.put(o, y, m, L.st); });
+      } catch (...) {
+        pub.fail(std::current_exception());
+        throw;
+      }
+    } else if (job < 4 + Ly) {
+      const int y = job - 4;
+      const Mps& T = pub.get(0, y, L.st);
+      const Mps& B = pub.get(1, Ly - 1 - y, L.st);
       Engine::Targets ts, tb;
       for (int x = 0; x < Lx; ++x) ts.push_back({x, e.rho_site + ((long long)y * Lx + x) * d2});
       for (int x = 0; x + 1 < Lx; ++x) tb.push_back({x, e.rho_h + ((long long)y * (Lx - 1) + x) * d4});
-      L.eng->row_rhos(ori.o[0], b[0][y], b[1][Ly - 1 - y], y, ts, tb);
-    } else if (job < Ly + ncol) {
+      L.eng->row_rhos(ori.o[0], T, B, y, ts, tb);
+    } else if (job < 4 + Ly + ncol) {
       // row x of the transposed lattice holds the vertical bonds (y,x)-(y+1,x) at its column y
-      const int x = job - Ly;
+      const int x = job - 4 - Ly;
+      const Mps& T = pub.get(2, x, L.st);
+      const Mps& B = pub.get(3, Lx - 1 - x, L.st);
       Engine::Targets tb;
       for (int y = 0; y + 1 < Ly; ++y) tb.push_back({y, e.rho_v + ((long long)y * Lx + x) * d4});
-      L.eng->row_rhos(ori.o[2], b[2][x], b[3][Lx - 1 - x], x, {}, tb);
+      L.eng->row_rhos(ori.o[2], T, B, x, {}, tb);
     } else {
-      L.eng->norm_from_top(ori.o[0], b[0][Ly - 1], lnacc, e.lnnorm);
+      const Mps& T = pub.get(0, Ly - 1, L.st);
+      L.eng->norm_from_top(ori.o[0], T, lnacc, e.lnnorm);
     }
-  });
+  }, &plan);
   lanes.join();
+  if (timed) {
+    PEPS_CUDA(cudaEventRecord(ph[1], c.st));
+    PEPS_CUDA(cudaEventSynchronize(ph[1]));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ph[0], ph[1]);
+    std::fprintf(stderr, "[peps] full env: %.2f ms on the device\n", ms);
+    for (auto& ev : ph) cudaEventDestroy(ev);
+  }
   e.has_norm = true;
 }
 

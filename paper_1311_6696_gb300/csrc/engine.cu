@@ -309,10 +309,15 @@ Mps Engine::absorb_compress(const Mps& T, const OLat& lat, int y, int tag, const
   return out;
 }
 
-std::vector<Mps> Engine::sweep(const OLat& lat, int tag, int upto, const TP& lnacc, Arena& keep) {
+std::vector<Mps> Engine::sweep(const OLat& lat, int tag, int upto, const TP& lnacc, Arena& keep,
+                               const std::function<void(int, const Mps&)>& on_boundary) {
   std::vector<Mps> out;
   out.push_back(closure_mps(lat.top, keep));
-  for (int y = 0; y < upto; ++y) out.push_back(absorb_compress(out.back(), lat, y, tag, lnacc, keep));
+  if (on_boundary) on_boundary(0, out.back());
+  for (int y = 0; y < upto; ++y) {
+    out.push_back(absorb_compress(out.back(), lat, y, tag, lnacc, keep));
+    if (on_boundary) on_boundary(y + 1, out.back());
+  }
   return out;
 }
 

@@ -4,6 +4,7 @@
 // a pointer set (TP) with one pointer per problem, and every step is one
 // batched launch for all of them.
 #pragma once
+#include <functional>
 #include <memory>
 #include <vector>
 
@@ -60,7 +61,9 @@ class Engine {
 
   // Top-down boundaries of `lat`: out[y] = boundary above row y, y = 0..upto.
   // lnacc (a device scalar per problem) accumulates the log of every rescaling factor.
-  std::vector<Mps> sweep(const OLat& lat, int tag, int upto, const TP& lnacc, Arena& keep);
+  // on_boundary(y, out[y]), if given, is called as soon as out[y] is enqueued.
+  std::vector<Mps> sweep(const OLat& lat, int tag, int upto, const TP& lnacc, Arena& keep,
+                         const std::function<void(int, const Mps&)>& on_boundary = nullptr);
 
   // Density matrices of row y between top boundary T and bottom boundary B:
   // rho_site of column x into dst for every (x, dst) in `sites`, rho of the
