@@ -2,6 +2,7 @@
 #pragma once
 #include <cstddef>
 #include <initializer_list>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -108,8 +109,24 @@ void ein(Ctx& cx, const char* spec, const TP& A, const Dims& ad, const TP& B,
 // FP64 (x_f64 = 1) or FP32 tensors, repacked to TF32 / BF16; C is written as
 // FP64 or FP32 in any index order; with Clo (FP32 output only) C receives the
 // TF32-rounded value and Clo the rounded residual.  prec is PEPS_PREC_*.
+// Packed tensor-core copies of B operands that stay unchanged for the cache's
+// lifetime (the site tensors of a call), keyed by contraction, precision and
+// the operand's pointers; memory from `mem`.
+struct PackCache {
+  explicit PackCache(Arena* a) : mem(a) {}
+  struct Entry {
+    void* hi;
+    void* lo;
+    long long ld;
+  };
+  Arena* mem;
+  std::map<std::string, Entry> entries;
+};
+
+// bcache: B is packed once per cache and reused (B must not change meanwhile).
 void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, const TP& B, int b_f64,
-            const Dims& bd, const TP& C, int c_f64, int prec, double alpha = 1.0, const TP& Clo = TP());
+            const Dims& bd, const TP& C, int c_f64, int prec, double alpha = 1.0, const TP& Clo = TP(),
+            PackCache* bcache = nullptr);
 int tc_available();
 
 }  // namespace peps

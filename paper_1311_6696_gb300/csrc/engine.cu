@@ -51,6 +51,7 @@ Engine::Engine(Ctx& c, const Opts& o, int d, int Dmax, int Lmax, int nb)
   tmp1_ = alloc(*cx.ws, 1);
   tc_ = o.precision != PEPS_PREC_FP64;
   x64_ = !tc_;
+  site_packs_ = std::make_unique<PackCache>(cx.ws);
 }
 
 size_t Engine::footprint(const Opts& o, int d, int Dmax, int Lmax) {
@@ -74,12 +75,13 @@ TP Engine::alloc(Arena& a, size_t per) const {
 }
 
 void Engine::con(const char* spec, const TP& A, bool a64, const Dims& ad, const TP& B, bool b64,
-                 const Dims& bd, const TP& C, bool c64) {
+                 const Dims& bd, const TP& C, bool c64, bool b_site) {
   if (!tc_) {
     ein(cx, spec, A, ad, B, bd, C);
     return;
   }
-  ein_tc(cx, spec, A, a64 ? 1 : 0, ad, B, b64 ? 1 : 0, bd, C, c64 ? 1 : 0, opt.precision);
+  ein_tc(cx, spec, A, a64 ? 1 : 0, ad, B, b64 ? 1 : 0, bd, C, c64 ? 1 : 0, opt.precision, 1.0, TP(),
+         b_site ? site_packs_.get() : nullptr);
 }
 
 Mps Engine::closure_mps(const std::vector<Mat>& mats, Arena&) {
@@ -97,9 +99,9 @@ Dims Engine::chain_left(const TP& L, const Dims& ld, const TP& M, const Dims& md
   const Dims x1 = ein_dims("clma,auvb->clmuvb", ld, md);
   con("clma,auvb->clmuvb", L, true, ld, M, true, md, X1_, x64_);
   const Dims x2 = ein_dims("clmuvb,sulnr->cmvbsnr", x1, ad);
-  con("clmuvb,sulnr->cmvbsnr", X1_, x64_, x1, A.p, true, ad, X2_, x64_);
+  con("clmuvb,sulnr->cmvbsnr", X1_, x64_, x1, A.p, true, ad, X2_, x64_, true);
   const Dims x3 = ein_dims("cmvbsnr,svmoq->cbnroq", x2, ad);
-  con("cmvbsnr,svmoq->cbnroq", X2_, x64_, x2, A.p, true, ad, X3, x64_);
+  con("cmvbsnr,svmoq->cbnroq", X2_, x64_, x2, A.p, true, ad, X3, x64_, true);
   return x3;
 }
 
@@ -109,9 +111,9 @@ Dims Engine::chain_right(const TP& R, const Dims& rd, const TP& M, const Dims& m
   const Dims y1 = ein_dims("auvb,brqc->auvrqc", md, rd);
   con("auvb,brqc->auvrqc", M, true, md, R, true, rd, X1_, x64_);
   const Dims y2 = ein_dims("auvrqc,sulnr->avqcsln", y1, ad);
-  con("auvrqc,sulnr->avqcsln", X1_, x64_, y1, A.p, true, ad, X2_, x64_);
+  con("auvrqc,sulnr->avqcsln", X1_, x64_, y1, A.p, true, ad, X2_, x64_, true);
   const Dims y3 = ein_dims("avqcsln,svmoq->aclnmo", y2, ad);
-  con("avqcsln,svmoq->aclnmo", X2_, x64_, y2, A.p, true, ad, Y3, x64_);
+  con("avqcsln,svmoq->aclnmo", X2_, x64_, y2, A.p, true, ad, Y3, x64_, true);
   return y3;
 }
 
@@ -122,10 +124,10 @@ Mps Engine::product_mps(const Mps& T, const OLat& lat, int y, Arena& step) {
     const SiteT& A = lat.at(y, x);
     const Dims ad = A.dims();
     const Dims t1 = ein_dims("auvb,sulnr->avbslnr", T.dims[x], ad);
-    con("auvb,sulnr->avbslnr", T.p[x], true, T.dims[x], A.p, true, ad, X2_, x64_);
+    con("auvb,sulnr->avbslnr", T.p[x], true, T.dims[x], A.p, true, ad, X2_, x64_, true);
     const Dims t2 = ein_dims("avbslnr,svmoq->almnobrq", t1, ad);
     TP cur = alloc(step, numel(t2));
-    con("avbslnr,svmoq->almnobrq", X2_, x64_, t1, A.p, true, ad, cur, true);
+    con("avbslnr,svmoq->almnobrq", X2_, x64_, t1, A.p, true, ad, cur, true, true);
     Dims cd = t2;
     if (x == 0) {
       const Mat& c = lat.left[y];
@@ -358,9 +360,9 @@ void Engine::row_rhos(const OLat& lat, const Mps& T, const Mps& B, int y, const 
     const Dims x1 = ein_dims("clma,auvb->clmuvb", ld[x], T.dims[x]);
     con("clma,auvb->clmuvb", Lenv_[x], true, ld[x], T.p[x], true, T.dims[x], X1_, x64_);
     const Dims x2 = ein_dims("clmuvb,sulnr->cmvbsnr", x1, ad);
-    con("clmuvb,sulnr->cmvbsnr", X1_, x64_, x1, A.p, true, ad, X2_, x64_);
+    con("clmuvb,sulnr->cmvbsnr", X1_, x64_, x1, A.p, true, ad, X2_, x64_, true);
     const Dims x3 = ein_dims("cmvbsnr,tvmoq->cbsnrtoq", x2, ad);
-    con("cmvbsnr,tvmoq->cbsnrtoq", X2_, x64_, x2, A.p, true, ad, X3_, x64_);
+    con("cmvbsnr,tvmoq->cbsnrtoq", X2_, x64_, x2, A.p, true, ad, X3_, x64_, true);
     const Dims w = ein_dims("cbsnrtoq,cnoe->erqbst", x3, B.dims[x]);
     con("cbsnrtoq,cnoe->erqbst", X3_, x64_, x3, B.p[x], true, B.dims[x], bb_, true);
     return w;
@@ -379,9 +381,9 @@ void Engine::row_rhos(const OLat& lat, const Mps& T, const Mps& B, int y, const 
     const Dims x1 = ein_dims("clmaij,auvb->clmuvbij", w, T.dims[x + 1]);
     con("clmaij,auvb->clmuvbij", bb_, true, w, T.p[x + 1], true, T.dims[x + 1], X1_, x64_);
     const Dims x2 = ein_dims("clmuvbij,sulnr->cmvbsnrij", x1, ad);
-    con("clmuvbij,sulnr->cmvbsnrij", X1_, x64_, x1, A2.p, true, ad, X2_, x64_);
+    con("clmuvbij,sulnr->cmvbsnrij", X1_, x64_, x1, A2.p, true, ad, X2_, x64_, true);
     const Dims x3 = ein_dims("cmvbsnrij,tvmoq->cbsnrtoqij", x2, ad);
-    con("cmvbsnrij,tvmoq->cbsnrtoqij", X2_, x64_, x2, A2.p, true, ad, X3_, x64_);
+    con("cmvbsnrij,tvmoq->cbsnrtoqij", X2_, x64_, x2, A2.p, true, ad, X3_, x64_, true);
     const Dims x4 = ein_dims("cbsnrtoqij,cnoe->erqbstij", x3, B.dims[x + 1]);
     con("cbsnrtoqij,cnoe->erqbstij", X3_, x64_, x3, B.p[x + 1], true, B.dims[x + 1], X1_, true);
     ein(cx, "erqbstij,brqe->isjt", X1_, x4, Renv_[x + 1], rd[x + 1], t.second);

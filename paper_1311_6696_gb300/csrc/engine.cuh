@@ -95,8 +95,10 @@ class Engine {
 
   // One pairwise contraction.  FP64 mode: FP64 gather-GEMM, every operand FP64.
   // Tensor-core modes: tcgen05 GEMM; a64/b64/c64 tag each tensor FP64 (else FP32).
+  // b_site: B is a site tensor (unchanged during the call): its packed copy is cached.
   void con(const char* spec, const TP& A, bool a64, const Dims& ad, const TP& B, bool b64, const Dims& bd,
-           const TP& C, bool c64);
+           const TP& C, bool c64, bool b_site = false);
+  std::unique_ptr<PackCache> site_packs_;
   // `per` doubles for every problem from arena a.
   TP alloc(Arena& a, size_t per) const;
   bool tc_ = false;   // tensor-core contractions (chain intermediates stored FP32)

@@ -633,7 +633,7 @@ int tc_available() {
 }
 
 void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, const TP& B, int b_f64,
-            const Dims& bd, const TP& C, int c_f64, int prec, double alpha, const TP& Clo) {
+            const Dims& bd, const TP& C, int c_f64, int prec, double alpha, const TP& Clo, PackCache* bcache) {
   PEPS_REQUIRE(tc_available(), "tensor-core path needs an sm_103 device");
   const int np = problems({&A, &B, &C, &Clo});
   PEPS_REQUIRE(!A.null() && !B.null() && C.n == np && (Clo.null() || Clo.n == np),
@@ -671,7 +671,25 @@ void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, c
   int BN = 16;
   while (BN < N && BN < 128) BN *= 2;
   const long long pad_m = (M + TC_BM - 1) / TC_BM * TC_BM, pad_n = (N + BN - 1) / BN * BN;
-  const size_t wa = pack_words(np * pad_m, K, bf16, split), wb = pack_words(np * pad_n, K, bf16, split);
+  const size_t wa = pack_words(np * pad_m, K, bf16, split);
+  const size_t wb_need = pack_words(np * pad_n, K, bf16, split);
+  // a cached B operand: packed once into the cache's memory
+  PackCache::Entry* cached = nullptr;
+  bool fresh = false;
+  if (bcache) {
+    std::string key = std::string(spec) + '|' + std::to_string(np) + '|' + std::to_string(bf16) +
+                      std::to_string(split) + '|' + std::to_string(BN);
+    for (int b = 0; b < np; ++b) key += '|' + std::to_string(reinterpret_cast<uintptr_t>(B.v(b)));
+    auto it = bcache->entries.find(key);
+    if (it == bcache->entries.end()) {
+      double* m = bcache->mem->dalloc(wb_need);
+      const size_t words = wb_need / (split ? 2 : 1);
+      it = bcache->entries.emplace(key, PackCache::Entry{m, split ? static_cast<void*>(m + words) : nullptr, 0}).first;
+      fresh = true;
+    }
+    cached = &it->second;
+  }
+  const size_t wb = cached ? 0 : wb_need;
   const long long tiles = ((M + TC_BM - 1) / TC_BM) * ((N + BN - 1) / BN) * np;
   PEPS_REQUIRE(tiles < (1LL << 31), "too many tiles");
   g.ktiles = int((K + (TC_ROWB / (bf16 ? 2 : 4)) - 1) / (TC_ROWB / (bf16 ? 2 : 4)));
@@ -690,7 +708,18 @@ void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, c
   double* mem = cx.scratch(wa + wb + wp);   // one reservation: operands, then split partials
   if (g.splitk > 1) g.part = reinterpret_cast<float*>(mem + wa + wb);
   const Operand oa = pack(cx, A, np, pad_m, a_f64, p.a, ad, mL, kL, bf16, split, mem);
-  const Operand ob = pack(cx, B, np, pad_n, b_f64, p.b, bd, nL, kL, bf16, split, mem + wa);
+  Operand ob;
+  if (!cached || fresh) {
+    ob = pack(cx, B, np, pad_n, b_f64, p.b, bd, nL, kL, bf16, split,
+              cached ? static_cast<double*>(cached->hi) : mem + wa);
+    if (cached) cached->ld = ob.ld;
+  } else {
+    ob.hi = cached->hi;
+    ob.lo = cached->lo;
+    ob.rows = N;
+    ob.K = K;
+    ob.ld = cached->ld;
+  }
   PEPS_REQUIRE(np * pad_m < (1LL << 31) && np * pad_n < (1LL << 31), "operand too large for one launch");
   const CUtensorMap ta = make_map(oa.hi, np * pad_m, K, oa.ld, bf16, TC_BM);
   const CUtensorMap tb = make_map(ob.hi, np * pad_n, K, ob.ld, bf16, BN);
