@@ -11,6 +11,7 @@
 #include <cstring>
 #include <cstdlib>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "linalg.cuh"
@@ -474,31 +475,227 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_jacobi(const SvdArgs s) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// One-sided Jacobi on a thread-block cluster: the rows of the working matrix G
+// (p x q) and of V (q x q) are split over the cluster's CTAs.  A round of the
+// round-robin schedule is one cluster barrier: every CTA publishes its partial
+// (alpha, beta, gamma) of every pair, then sums all CTAs' partials in the same
+// order -- so every CTA forms the same rotations -- and rotates its own rows.
+// Same rotations, threshold, ordering and output as the one-CTA kernel.
+// ---------------------------------------------------------------------------
+constexpr int SVC_THREADS = 256;
+
+__global__ void __launch_bounds__(SVC_THREADS) k_svd_cluster(const SvdArgs s, double* work, long long wst) {
+  extern __shared__ double ssm[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = int(cluster.num_blocks()), rank = int(cluster.block_rank());
+  const int pb = blockIdx.x / C;
+  const int p = s.p, q = s.q, tid = threadIdx.x, nt = blockDim.x;
+  const int qq = q + (q & 1), npair = qq / 2;
+  const int cp = (p + C - 1) / C, cv = (q + C - 1) / C;
+  const int g0 = min(p, rank * cp), g1 = min(p, g0 + cp), gr = g1 - g0;   // my rows of G
+  const int v0 = min(q, rank * cv), v1 = min(q, v0 + cv), vr = v1 - v0;   // my rows of V
+  double* part = ssm;                         // [2][3][npair] my partial sums (cluster-visible)
+  double* cs = part + 6 * npair;              // [2][2][npair] rotation (c, s) of this round
+  double* nrm = cs + 4 * npair;               // [q]
+  int* order = reinterpret_cast<int*>(nrm + q);   // [q]
+  __shared__ int s_rot;
+  double* G = work + pb * wst + (long long)rank * cp * q;                   // [q][cp] column-major block
+  double* V = work + pb * wst + (long long)C * cp * q + (long long)rank * cv * q;   // [q][cv]
+  const double* A = s.A.d(pb);
+  for (long long e = tid; e < (long long)gr * q; e += nt) {
+    const int li = int(e % gr), j = int(e / gr), i = g0 + li;
+    G[(long long)j * cp + li] = s.trans ? A[(long long)j * s.n + i] : A[(long long)i * s.n + j];
+  }
+  for (long long e = tid; e < (long long)vr * q; e += nt) {
+    const int li = int(e % vr), j = int(e / vr);
+    V[(long long)j * cv + li] = (v0 + li == j) ? 1.0 : 0.0;
+  }
+  const double tol = 1e-15;
+  int sweep = 0, t = 0;
+  for (; sweep < SVD_MAX_SWEEPS; ++sweep) {
+    int rotated = 0;
+    for (int round = 0; round < qq - 1; ++round, ++t) {
+      const int b = t & 1;
+      __syncthreads();
+      for (int pr = tid; pr < npair; pr += nt) {
+        int a = (pr == 0) ? 0 : 1 + (pr - 1 + round) % (qq - 1);
+        int c = 1 + (qq - 2 - pr + round) % (qq - 1);
+        if (a > c) {
+          const int tmp = a;
+          a = c;
+          c = tmp;
+        }
+        double al = 0.0, be = 0.0, ga = 0.0;
+        if (a < q && c < q) {
+          const double* xa = G + (long long)a * cp;
+          const double* xc = G + (long long)c * cp;
+          for (int i = 0; i < gr; ++i) {
+            const double x = xa[i], y = xc[i];
+            al = fma(x, x, al);
+            be = fma(y, y, be);
+            ga = fma(x, y, ga);
+          }
+        }
+        part[(b * 3 + 0) * npair + pr] = al;
+        part[(b * 3 + 1) * npair + pr] = be;
+        part[(b * 3 + 2) * npair + pr] = ga;
+      }
+      cluster.sync();
+      for (int pr = tid; pr < npair; pr += nt) {
+        int a = (pr == 0) ? 0 : 1 + (pr - 1 + round) % (qq - 1);
+        int c = 1 + (qq - 2 - pr + round) % (qq - 1);
+        double cc = 1.0, sn = 0.0;
+        if (a < q && c < q) {
+          if (a > c) {
+            const int tmp = a;
+            a = c;
+            c = tmp;
+          }
+          double al = 0.0, be = 0.0, ga = 0.0;
+          for (int r = 0; r < C; ++r) {
+            al += *cluster.map_shared_rank(part + (b * 3 + 0) * npair + pr, r);
+            be += *cluster.map_shared_rank(part + (b * 3 + 1) * npair + pr, r);
+            ga += *cluster.map_shared_rank(part + (b * 3 + 2) * npair + pr, r);
+          }
+          if (ga != 0.0 && fabs(ga) > tol * sqrt(al * be)) {
+            const double zeta = (be - al) / (2.0 * ga);
+            const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            cc = 1.0 / sqrt(1.0 + tt * tt);
+            sn = cc * tt;
+            rotated = 1;
+          }
+        }
+        cs[(b * 2 + 0) * npair + pr] = cc;
+        cs[(b * 2 + 1) * npair + pr] = sn;
+      }
+      __syncthreads();
+      // rotate my rows of G and V: consecutive threads take consecutive rows of one pair
+      for (long long e = tid; e < (long long)npair * (gr + vr); e += nt) {
+        const int row = int(e % (gr + vr)), pr = int(e / (gr + vr));
+        const double cc = cs[(b * 2 + 0) * npair + pr], sn = cs[(b * 2 + 1) * npair + pr];
+        if (sn == 0.0) continue;
+        int a = (pr == 0) ? 0 : 1 + (pr - 1 + round) % (qq - 1);
+        int c = 1 + (qq - 2 - pr + round) % (qq - 1);
+        if (a > c) {
+          const int tmp = a;
+          a = c;
+          c = tmp;
+        }
+        double* X;
+        int ld, li;
+        if (row < gr) {
+          X = G;
+          ld = cp;
+          li = row;
+        } else {
+          X = V;
+          ld = cv;
+          li = row - gr;
+        }
+        const double x = X[(long long)a * ld + li], y = X[(long long)c * ld + li];
+        X[(long long)a * ld + li] = cc * x - sn * y;
+        X[(long long)c * ld + li] = sn * x + cc * y;
+      }
+    }
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    if (rotated) s_rot = 1;   // benign race: every writer stores 1
+    __syncthreads();
+    if (!s_rot) break;        // identical in every CTA (same sums, same decisions)
+  }
+  if (sweep >= SVD_MAX_SWEEPS && tid == 0 && rank == 0) atomicOr(s.flag, FLAG_SVD_NOCONV);
+  // column norms of G over all rows, then a stable descending order
+  cluster.sync();
+  const int b = t & 1;
+  for (int j = tid; j < q; j += nt) {
+    const double* x = G + (long long)j * cp;
+    double v = 0.0;
+    for (int i = 0; i < gr; ++i) v = fma(x[i], x[i], v);
+    nrm[j] = v;
+  }
+  __syncthreads();
+  // publish squared norms through the part buffer (size 3*npair >= q)
+  for (int j = tid; j < q; j += nt) part[b * 3 * npair + j] = nrm[j];
+  cluster.sync();
+  for (int j = tid; j < q; j += nt) {
+    double v = 0.0;
+    for (int r = 0; r < C; ++r) v += *cluster.map_shared_rank(part + b * 3 * npair + j, r);
+    nrm[j] = sqrt(v);
+  }
+  __syncthreads();
+  for (int j = tid; j < q; j += nt) {
+    const double vj = nrm[j];
+    int r = 0;
+    for (int i = 0; i < q; ++i) {
+      const double vi = nrm[i];
+      r += (vi > vj) || (vi == vj && i < j);
+    }
+    order[r] = j;
+  }
+  __syncthreads();
+  const int kk = s.kk;
+  double* const US = s.US.d(pb);
+  double* const Vt = s.Vt.d(pb);
+  if (!s.trans) {
+    // US[i][r] = G(i, order[r]) for my G rows; Vt[r][j] = V(j, order[r]) for my V rows
+    for (long long e = tid; e < (long long)gr * kk; e += nt) {
+      const int li = int(e / kk), r = int(e % kk);
+      US[(long long)(g0 + li) * kk + r] = (r < q) ? G[(long long)order[r] * cp + li] : 0.0;
+    }
+    for (long long e = tid; e < (long long)vr * kk; e += nt) {
+      const int li = int(e / kk), r = int(e % kk);
+      if (r < kk) Vt[(long long)r * s.n + (v0 + li)] = (r < q) ? V[(long long)order[r] * cv + li] : 0.0;
+    }
+  } else {
+    // US[i][r] = V(i, order[r]) * nrm for my V rows; Vt[r][j] = G(j, order[r]) / nrm for my G rows
+    for (long long e = tid; e < (long long)vr * kk; e += nt) {
+      const int li = int(e / kk), r = int(e % kk);
+      US[(long long)(v0 + li) * kk + r] = (r < q) ? V[(long long)order[r] * cv + li] * nrm[order[r]] : 0.0;
+    }
+    for (long long e = tid; e < (long long)gr * kk; e += nt) {
+      const int li = int(e / kk), r = int(e % kk);
+      const double nr = (r < q) ? nrm[order[r]] : 0.0;
+      Vt[(long long)r * s.n + (g0 + li)] = (r < q && nr > 0.0) ? G[(long long)order[r] * cp + li] / nr : 0.0;
+    }
+  }
+  cluster.sync();   // no CTA leaves while others may still read its shared memory
+}
+
 }  // namespace
 
 namespace {
-// Largest cluster size (16 non-portable, else 8, 4, 2) launchable with `smem`
-// bytes of dynamic shared memory per CTA; 1 if clusters are unavailable.
-int qr_cluster_size(size_t smem) {
+// Largest cluster size (16 non-portable, else 8, 4, 2) with which `kern` can be
+// launched with `smem` bytes of dynamic shared memory per CTA; 1 if clusters
+// are unavailable.  Cached per kernel and size.
+template <class K>
+int cluster_size_for(K kern, int threads, size_t smem) {
   static std::mutex mu;
-  static std::vector<std::pair<size_t, int>> cache;
-  static bool attrs = false, attrs_ok = false;
+  static std::vector<std::tuple<const void*, size_t, int>> cache;
+  static std::vector<std::pair<const void*, bool>> attrs;
   std::lock_guard<std::mutex> g(mu);
+  const void* id = reinterpret_cast<const void*>(kern);
   const size_t key = (smem + 4095) / 4096 * 4096;
   for (auto& e : cache)
-    if (e.first == key) return e.second;
-  if (!attrs) {
-    attrs = true;
-    attrs_ok = cudaFuncSetAttribute(k_qr_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
-               cudaFuncSetAttribute(k_qr_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) == cudaSuccess;
+    if (std::get<0>(e) == id && std::get<1>(e) == key) return std::get<2>(e);
+  bool attrs_ok = false, seen = false;
+  for (auto& a : attrs)
+    if (a.first == id) {
+      attrs_ok = a.second;
+      seen = true;
+    }
+  if (!seen) {
+    attrs_ok = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+               cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) == cudaSuccess;
     cudaGetLastError();
+    attrs.push_back({id, attrs_ok});
   }
   int best = 1;
   if (attrs_ok) {
     for (int c : {16, 8, 4, 2}) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(c, 1, 1);
-      cfg.blockDim = dim3(QRC_THREADS, 1, 1);
+      cfg.blockDim = dim3(threads, 1, 1);
       cfg.dynamicSmemBytes = key;
       cudaLaunchAttribute at[1];
       at[0].id = cudaLaunchAttributeClusterDimension;
@@ -508,7 +705,7 @@ int qr_cluster_size(size_t smem) {
       cfg.attrs = at;
       cfg.numAttrs = 1;
       int nclusters = 0;
-      const cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, k_qr_cluster, &cfg);
+      const cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
       if (std::getenv("PEPS_VERBOSE"))
         std::fprintf(stderr, "[peps] qr cluster %d smem %zu: %s, %d active clusters\n", c, key,
                      cudaGetErrorString(e), nclusters);
@@ -519,9 +716,11 @@ int qr_cluster_size(size_t smem) {
       }
     }
   }
-  cache.push_back({key, best});
+  cache.push_back(std::make_tuple(id, key, best));
   return best;
 }
+
+int qr_cluster_size(size_t smem) { return cluster_size_for(k_qr_cluster, QRC_THREADS, smem); }
 }  // namespace
 
 void qr_thin(Ctx& cx, int m, int n, const TP& A, long long rs, long long cs, const TP& Q, long long qrs,
@@ -621,8 +820,37 @@ void svd_trunc(Ctx& cx, int m, int n, const TP& A, int kk, const TP& US, const T
   s.wst = ((long long)s.p * s.q + (long long)s.q * s.q + 2LL * s.q + 31) / 32 * 32;
   s.work = cx.scratch(size_t(np) * s.wst);
   const double flops = 8.0 * 4.0 * double(s.p) * s.q * s.q;
+  // Matrices of 4096+ entries: rows split over a thread-block cluster (16 rows per CTA or more).
+  int C = 1;
+  if (double(s.p) * s.q >= 4096.0) {
+    C = std::max(1, std::min(16, s.p / 16));
+    while (C > 1 && (C & (C - 1))) --C;
+  }
+  const int npair = (s.q + (s.q & 1)) / 2;
+  const size_t smem = sizeof(double) * (10 * size_t(npair) + s.q + (s.q + 1) / 2 + 8);
+  if (C > 1) C = std::min(C, cluster_size_for(k_svd_cluster, SVC_THREADS, smem));
+  while (C > 1 && (C & (C - 1))) --C;
   Launch L(K_SVD, cx.st, flops * np, 0);
-  k_svd_jacobi<<<np, SVD_THREADS, 0, cx.st>>>(s);
+  if (C <= 1) {
+    k_svd_jacobi<<<np, SVD_THREADS, 0, cx.st>>>(s);
+  } else {
+    const int cp = (s.p + C - 1) / C, cv = (s.q + C - 1) / C;
+    const long long cwst = (long long)C * cp * s.q + (long long)C * cv * s.q;
+    double* cwork = cx.scratch(size_t(np) * cwst + 64);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C * np, 1, 1);
+    cfg.blockDim = dim3(SVC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = cx.st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    PEPS_CUDA(cudaLaunchKernelEx(&cfg, k_svd_cluster, s, cwork, cwst));
+  }
   PEPS_CHECK_LAUNCH();
 }
 

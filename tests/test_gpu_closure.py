@@ -119,3 +119,17 @@ def test_training_lowers_the_loss_and_reports_the_gain(env):
     print(f"closure: loss {l0:.3e} -> {l1:.3e} (train tail {lf:.3e}); mean |d<S.S>| plain "
           f"{errs['plain']:.3e} learned {errs['learned']:.3e} ratio {errs['learned'] / errs['plain']:.3f}")
     assert errs["learned"] <= 1.5 * errs["plain"]
+
+
+def test_recorded_plan_with_learned_closure(env):
+    """A plan records the learned-closure inference too; replays match the plain call."""
+    torch, peps = env
+    from paper_1311_6696_gb300 import synth
+    A = torch.from_numpy(synth.peps_simple_update(5, 5, 2, seed=23, steps=100)).cuda()
+    w = peps.mlp_init(2, 2, peps.CLOSURE_WIDTH, seed=5)
+    w += torch.randn_like(w) * 0.01
+    plain = peps.env_cluster(A, n=2, chi=8, mode="svd", closure_weights=w)
+    plan = peps.Plan(A, chi=8, mode="svd", cluster_n=2, closure_weights=w)
+    e = plan.run()
+    for kind, op in (("site", O.SZ), ("hbond", O.SDOTS), ("vbond", O.SDOTS)):
+        assert np.max(np.abs(plain.expect(kind, op) - e.expect(kind, op))) < 1e-12

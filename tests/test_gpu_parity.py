@@ -152,3 +152,19 @@ def test_bad_args_are_einval(peps):
     with pytest.raises(peps.PepsError) as e:
         peps.env_cluster(A, n=0, chi=4)
     assert e.value.code == peps.EINVAL
+
+
+def test_cluster_svd_mode_parity(peps):
+    """svd compression inside batched windows (batched QR sweep + Jacobi SVD)."""
+    from paper_1311_6696_gb300 import synth
+    A = synth.peps_gauss(5, 5, 2, 2, seed=57)
+    _compare(peps.env_cluster(A, n=2, chi=4, mode="svd"),
+             O.env_cluster(A, n=2, chi=4, mode="svd"), with_norm=False)
+
+
+def test_cluster_large_batched_group(peps):
+    """8x8 lattice, n=3: 36 interior windows share one shape and run as one batch."""
+    from paper_1311_6696_gb300 import synth
+    A = synth.peps_gauss(8, 8, 2, 2, seed=58)
+    _compare(peps.env_cluster(A, n=3, chi=6, mode="var", seed=4),
+             O.env_cluster(A, n=3, chi=6, mode="var", seed=4), with_norm=False)
