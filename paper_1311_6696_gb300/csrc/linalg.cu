@@ -552,11 +552,20 @@ __global__ void __launch_bounds__(SVC_THREADS) k_svd_cluster(const SvdArgs s, do
             a = c;
             c = tmp;
           }
+          // all 3C remote loads in flight before any add (one round trip), summed in rank order
+          double va[16], vb[16], vg[16];
+#pragma unroll
+          for (int r = 0; r < 16; ++r) {
+            va[r] = r < C ? *cluster.map_shared_rank(part + (b * 3 + 0) * npair + pr, r) : 0.0;
+            vb[r] = r < C ? *cluster.map_shared_rank(part + (b * 3 + 1) * npair + pr, r) : 0.0;
+            vg[r] = r < C ? *cluster.map_shared_rank(part + (b * 3 + 2) * npair + pr, r) : 0.0;
+          }
           double al = 0.0, be = 0.0, ga = 0.0;
-          for (int r = 0; r < C; ++r) {
-            al += *cluster.map_shared_rank(part + (b * 3 + 0) * npair + pr, r);
-            be += *cluster.map_shared_rank(part + (b * 3 + 1) * npair + pr, r);
-            ga += *cluster.map_shared_rank(part + (b * 3 + 2) * npair + pr, r);
+#pragma unroll
+          for (int r = 0; r < 16; ++r) {
+            al += va[r];
+            be += vb[r];
+            ga += vg[r];
           }
           if (ga != 0.0 && fabs(ga) > tol * sqrt(al * be)) {
             const double zeta = (be - al) / (2.0 * ga);
@@ -620,7 +629,7 @@ __global__ void __launch_bounds__(SVC_THREADS) k_svd_cluster(const SvdArgs s, do
   cluster.sync();
   for (int j = tid; j < q; j += nt) {
     double v = 0.0;
-    for (int r = 0; r < C; ++r) v += *cluster.map_shared_rank(part + b * 3 * npair + j, r);
+    v = remote_sum(cluster, part + b * 3 * npair + j, C);
     nrm[j] = sqrt(v);
   }
   __syncthreads();
