@@ -317,7 +317,10 @@ def cluster_section(args, peps, synth, torch, st, flush):
                        f"{args.precision}; reference: full environments at chi=64",
            "per_n": {}}
     for n in (2, 4, 6):
-        plan = peps.Plan(A, chi=36, mode="var", precision=args.precision, cluster_n=n, stream=st)
+        t0 = time.perf_counter()
+        plan = peps.Plan(A, chi=36, mode="var", precision=args.precision, cluster_n=n, stream=st,
+                         tune=not args.no_tune)
+        t_create = time.perf_counter() - t0
         env = plan.env
         plan.run()
         tms = []
@@ -334,7 +337,9 @@ def cluster_section(args, peps, synth, torch, st, flush):
         ms = min(tms)
         err = float(np.max(np.abs(o - r) / np.maximum(np.abs(r), 1e-2)))
         out["per_n"][str(n)] = {"envs_per_s": round(196 / (ms * 1e-3), 2), "ms": round(ms, 2),
-                                "launches": plan.launches, "max_rel_dev_vs_full_chi64": err}
+                                "launches": plan.launches, "max_rel_dev_vs_full_chi64": err,
+                                "tuned": {"lanes": plan.lanes, "qr_cluster_max": plan.qr_cluster}
+                                if not args.no_tune else None, "plan_create_s": round(t_create, 1)}
         del env
         plan.free()
     return out

@@ -273,10 +273,11 @@ const char* peps_last_error(void);
  *   by measurement (a project-written autotuner).  It records one plan per
  *   candidate and times one warm plus two timed replays of each with CUDA
  *   events on cuda_stream, keeping the fastest.  The search is over host
- *   lanes {2, 4, 8} first (QR cluster size by the library's model), then over
- *   the largest QR cluster {8, 4} with the best lane count.  *lanes and
- *   *qr_cluster (either may be NULL) receive the choice.  Costs five
- *   recordings and fifteen replays.
+ *   lanes {2, 4, 8} first (QR cluster size by the library's model), then,
+ *   for the cluster scheme, over the windows per batched launch {8, 16, 32},
+ *   then over the largest QR cluster {8, 4}.  *lanes and *qr_cluster (either
+ *   may be NULL) receive the choice.  Costs five recordings (seven for the
+ *   cluster scheme), each timed over three replays.
  * peps_plan_launches: kernel launches in one replay.
  * peps_plan_free: synchronises the device, releases the graph and its
  *   memory; NULL is accepted.

@@ -172,6 +172,7 @@ namespace {
 struct Tune {
   int lanes = 0;
   int qr_cmax = 0;
+  int chunk = 0;   // cluster windows per batched chunk (0: 16)
 };
 
 struct Call {
@@ -759,9 +760,11 @@ void cluster_env(Call& c, const peps_lattice* lat, const Opts& opt, int n, peps_
   size_t free_b = 0, total_b = 0;
   PEPS_CUDA(cudaMemGetInfo(&free_b, &total_b));
   const size_t budget = std::min<size_t>(free_b * 2 / 5, size_t(96) << 30);
-  // Up to 16 windows per chunk: beyond that a launch gains little (its work is
-  // already bandwidth-bound) while smaller chunks balance the lanes.
-  const int bmax = int(std::max<size_t>(1, std::min<size_t>(16, budget / (per * nl))));
+  // Up to 16 windows per chunk by default (the autotuner also tries 8 and 32):
+  // beyond that a launch gains little (its work is already bandwidth-bound)
+  // while smaller chunks balance the lanes.
+  const int cap = c.tune.chunk > 0 ? std::min(c.tune.chunk, MAXB) : 16;
+  const int bmax = int(std::max<size_t>(1, std::min<size_t>(size_t(cap), budget / (per * nl))));
   std::vector<std::vector<Win>> chunks;
   for (auto& kv : groups) {
     const auto& v = kv.second;
@@ -1308,18 +1311,21 @@ int peps_plan_tune(const peps_lattice* lat, const peps_opts* opts, int cluster, 
       PlanPtr p(record_plan(lat, opts, o, cl, t).release());
       const double ms = time_plan(p.get(), st, 2);
       if (std::getenv("PEPS_VERBOSE"))
-        std::fprintf(stderr, "[peps] tune: lanes %d, qr cluster <= %d: %.3f ms\n", lanes_of(t),
-                     t.qr_cmax > 0 ? t.qr_cmax : 16, ms);
+        std::fprintf(stderr, "[peps] tune: lanes %d, qr cluster <= %d, chunk %d: %.3f ms\n", lanes_of(t),
+                     t.qr_cmax > 0 ? t.qr_cmax : 16, t.chunk > 0 ? t.chunk : 16, ms);
       if (ms < tbest) {
         tbest = ms;
         tb = t;
         best.swap(p);
       }
     };
-    // Coordinate search: lanes first (QR clusters by the model), then the QR cluster cap.
-    for (int nl : {2, 4, 8}) consider(Tune{nl, 0});
-    const int bl = tb.lanes;
-    for (int qc : {8, 4}) consider(Tune{bl, qc});
+    // Coordinate search: lanes first (QR clusters by the model), then (cluster
+    // scheme) the windows per batched chunk, then the QR cluster cap.
+    for (int nl : {2, 4, 8}) consider(Tune{nl, 0, 0});
+    if (cl)
+      for (int ch : {8, 32}) consider(Tune{tb.lanes, 0, ch});
+    const Tune base = tb;
+    for (int qc : {8, 4}) consider(Tune{base.lanes, qc, base.chunk});
     if (lanes) *lanes = lanes_of(tb);
     if (qr_cluster) *qr_cluster = tb.qr_cmax > 0 ? tb.qr_cmax : 16;
     *out = best.release();
