@@ -189,7 +189,7 @@ def run_ours(args, rank, world, dist):
         etimes.append((time.perf_counter() - t0) * 1e3)
 
     # ---- the plain FP64 GPU path (also recorded) on the same input, and the deviation between the two
-    cmp_ms, dev_err = None, None
+    cmp_ms, dev_err, others = None, None, {}
     if args.precision != "fp64" and not args.no_fp64_compare:
         p64 = peps.Plan(At, **dict(kw, precision="fp64"))
         e64 = p64.env
@@ -210,6 +210,30 @@ def run_ours(args, rank, world, dist):
         b = np.concatenate([h0, v0])
         dev_err = float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-2)))
         del e64, p64
+        # every other tensor-core precision on the same input, against the FP64 path
+        for prec in ("bf16x3", "tf32", "bf16"):
+            if prec == args.precision:
+                continue
+            pp = peps.Plan(At, **dict(kw, precision=prec), tune=not args.no_tune)
+            ep = pp.env
+            pp.run()
+            tms = []
+            for _ in range(max(1, min(3, args.steps))):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                pp.run()
+                hp, vp = ep.expect("hbond", SD), ep.expect("vbond", SD)
+                e1.record(st)
+                e1.synchronize()
+                tms.append(e0.elapsed_time(e1))
+            ms_p = min(tms)
+            c = np.concatenate([hp, vp])
+            others[prec] = {"value": round(world * WORKLOAD["Ly"] * WORKLOAD["Lx"] / (ms_p * 1e-3), 2),
+                            "ms_per_step": round(ms_p, 2),
+                            "max_rel_err_vs_fp64_path": float(np.max(np.abs(c - b) / np.maximum(np.abs(b), 1e-2)))}
+            del ep, pp
 
     cluster = None if args.no_cluster else cluster_section(args, peps, synth, torch, st, flush)
 
@@ -287,6 +311,7 @@ def run_ours(args, rank, world, dist):
         res["speedup_vs_fp64_path"] = round(cmp_ms / ms_step, 3)
         res["accuracy"] = {"max_rel_err_vs_fp64_path": dev_err, "observables": 180,
                            "metric": "|x-x_ref|/max(|x_ref|,1e-2) over <S.S> on every bond"}
+        res["other_precisions"] = others
     if cluster is not None:
         res["cluster"] = cluster
     if clk:

@@ -125,3 +125,14 @@ def test_tuned_plan_matches_oracle(peps):
     assert plan.lanes in (2, 4, 8) and plan.qr_cluster in (4, 8, 16)
     env = plan.run()
     _close(_obs(env), _oracle_obs(O.env_full(A, chi=8, mode="var", seed=3)), TOL)
+
+
+def test_tuned_cluster_plan_matches_oracle(peps):
+    """Tuning a cluster plan (lanes, windows per batch, QR cluster cap) keeps the results."""
+    import torch
+    from paper_1311_6696_gb300 import synth
+    A = synth.peps_gauss(6, 6, 2, 2, seed=93)
+    At = torch.from_numpy(A).cuda()
+    plan = peps.Plan(At, chi=6, mode="var", cluster_n=3, tune=True)
+    env = plan.run()
+    _close(_obs(env), _oracle_obs(O.env_cluster(A, n=3, chi=6, mode="var")), TOL)
