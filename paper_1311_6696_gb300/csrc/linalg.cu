@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_house(const QrArgs q) {
 // same sign convention as the one-CTA kernel; the FP64 work is spread over C
 // SMs instead of one.
 // ---------------------------------------------------------------------------
-constexpr int QRC_THREADS = 256;
+constexpr int QRC_THREADS = 512;
 // Each CTA keeps its block of rows of the working matrix and of Q in shared
 // memory when they fit (column-major within the block, odd column stride),
 // else in global scratch.  Work per column is split as (column, row quarter)
@@ -167,7 +167,7 @@ constexpr int QRC_THREADS = 256;
 // pipe executes the factorisation's own multiply-adds and almost nothing else
 // (a shuffle tree per column would cost more FP64 issue slots than the dot
 // products at 64 rows per CTA).
-constexpr int QS = 4;   // threads per column (rows interleaved mod QS)
+constexpr int QS = 8;   // threads per column (rows interleaved mod QS)
 
 // Sum of one double over the cluster's CTAs, all remote loads issued first.
 __device__ __forceinline__ double remote_sum(cg::cluster_group& cl, double* slot, int C) {
