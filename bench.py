@@ -56,7 +56,7 @@ def _peaks():
 # stands (profiles/<kernel>_bench_10x10_D4_chi64.md); update or drop an entry
 # whenever that kernel changes.
 TRAFFIC = {
-    "qr_f64": (592128, "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 1024x64 k_qr_cluster "
+    "qr_f64": (595456, "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 1024x64 k_qr_cluster "
                        "launch (profiles/k_qr_cluster_bench_10x10_D4_chi64.md); the matrix read once"),
 }
 
