@@ -348,3 +348,22 @@ def test_planted_mistake_in_noise_free_cu0_is_caught(monkeypatch):
     monkeypatch.setattr(O, "cu0_local", good)
     ok = O.cu0_sweep(lat)
     assert max(np.max(np.abs(a - b)) for ra, rb in zip(ok[1:], bad[1:]) for a, b in zip(ra, rb)) > 1e-6
+
+
+def test_cluster_error_shrinks_with_window_size():
+    """Section 5.2: the cluster scheme interpolates between CU_0 and the full
+    update -- on a simple-update state the deviation of every bond's <S.S>
+    from the full environments falls as the window grows and vanishes once
+    the window covers the lattice (same chi, svd mode)."""
+    from paper_1311_6696_gb300 import synth
+    A = synth.peps_simple_update(6, 6, 2, seed=31, steps=150)
+    full = O.env_full(A, chi=16, mode="svd")
+
+    def bonds(e):
+        return np.concatenate([np.ravel(O.expect_all(e, "hbond", O.SDOTS)),
+                               np.ravel(O.expect_all(e, "vbond", O.SDOTS))])
+
+    ref = bonds(full)
+    errs = [float(np.mean(np.abs(bonds(O.env_cluster(A, n=n, chi=16, mode="svd")) - ref))) for n in (2, 3, 4, 6)]
+    assert all(a > 2 * b for a, b in zip(errs, errs[1:])), errs
+    assert float(np.max(np.abs(bonds(O.env_cluster(A, n=12, chi=16, mode="svd")) - ref))) == 0.0
