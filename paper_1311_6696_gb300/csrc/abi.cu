@@ -385,9 +385,12 @@ int lane_count() {
 
 int lanes_of(const Tune& t) { return t.lanes > 0 ? std::min(t.lanes, 64) : lane_count(); }
 
-std::vector<cudaStream_t>& lane_streams(int n) {
+// Non-blocking streams of the lanes (set 0) and their second streams (set 1),
+// created once per device and kept: a recorded graph may have used them.
+std::vector<cudaStream_t>& lane_streams(int n, int set = 0) {
   static std::mutex mu;
-  static std::vector<std::vector<cudaStream_t>> pool;
+  static std::vector<std::vector<cudaStream_t>> pool_sets[2];
+  auto& pool = pool_sets[set];
   std::lock_guard<std::mutex> g(mu);
   int dev = 0;
   PEPS_CUDA(cudaGetDevice(&dev));
@@ -435,6 +438,7 @@ struct Lanes {
       a.cx->qr_cmax = c.cx.qr_cmax;
       a.cx->tmp = a.ws->dalloc(8);
       a.eng = std::make_unique<Engine>(*a.cx, opt, d, D, Lmax, nb);
+      if (nb == 1) a.eng->enable_dual(lane_streams(nl, 1)[i]);
     }
   }
   // Fork: every lane waits for the caller's stream.

@@ -52,6 +52,48 @@ Engine::Engine(Ctx& c, const Opts& o, int d, int Dmax, int Lmax, int nb)
   tc_ = o.precision != PEPS_PREC_FP64;
   x64_ = !tc_;
   site_packs_ = std::make_unique<PackCache>(cx.ws);
+  main_ = Side{&cx, X1_, X2_, X3_, tmp0_, site_packs_.get()};
+}
+
+Engine::~Engine() {
+  if (!dual_) return;
+  aux_.cx = nullptr;
+  cache2_.reset();
+  cx2_.reset();
+  ws2_.reset();   // frees on the second stream ...
+  cudaEvent_t e;   // ... which the main stream then waits for (required while recording a graph)
+  if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
+    cudaEventRecord(e, ws2_stream_);
+    cudaStreamWaitEvent(cx.st, e, 0);
+    cudaEventDestroy(e);
+  }
+}
+
+void Engine::enable_dual(cudaStream_t st2) {
+  const size_t chi = size_t(opt.chi), D2 = size_t(Dmax_) * Dmax_, dd = size_t(d_) * d_;
+  const size_t set = (std::max(bigN_ * dd, chi * chi * D2 * dd * dd) + bigN_ * dd * d_ + bigN_ * dd * dd) * 8;
+  if (dual_ || nb_ != 1 || set > (size_t(512) << 20)) return;
+  ws2_stream_ = st2;
+  {
+    cudaEvent_t e;   // the second stream starts after everything enqueued so far
+    PEPS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    PEPS_CUDA(cudaEventRecord(e, cx.st));
+    PEPS_CUDA(cudaStreamWaitEvent(st2, e, 0));
+    PEPS_CUDA(cudaEventDestroy(e));
+  }
+  ws2_ = std::make_unique<Arena>(st2);
+  cx2_ = std::make_unique<Ctx>(st2, ws2_.get());
+  cx2_->flag = cx.flag;
+  cx2_->persist = cx.persist;
+  cx2_->qr_cmax = cx.qr_cmax;
+  cx2_->tmp = ws2_->dalloc(8);
+  cache2_ = std::make_unique<PackCache>(ws2_.get());
+  const size_t x1 = std::max(bigN_ * dd, chi * chi * D2 * dd * dd);
+  aux_ = Side{cx2_.get(), strided(ws2_->dalloc((x1 + 31) / 32 * 32), 1, x1),
+              strided(ws2_->dalloc((bigN_ * dd * d_ + 31) / 32 * 32), 1, bigN_ * dd * d_),
+              strided(ws2_->dalloc((bigN_ * dd * dd + 31) / 32 * 32), 1, bigN_ * dd * dd),
+              strided(ws2_->dalloc(32), 1, 1), cache2_.get()};
+  dual_ = true;
 }
 
 size_t Engine::footprint(const Opts& o, int d, int Dmax, int Lmax) {
@@ -67,6 +109,7 @@ void Engine::use(int B) {
   for (TP* t : {&X1_, &X2_, &X3_, &bb_, &tmp0_, &tmp1_}) t->n = B;
   for (auto& t : Lenv_) t.n = B;
   for (auto& t : Renv_) t.n = B;
+  main_ = Side{&cx, X1_, X2_, X3_, tmp0_, site_packs_.get()};   // the helpers' view of the buffers
 }
 
 TP Engine::alloc(Arena& a, size_t per) const {
@@ -76,12 +119,13 @@ TP Engine::alloc(Arena& a, size_t per) const {
 
 void Engine::con(const char* spec, const TP& A, bool a64, const Dims& ad, const TP& B, bool b64,
                  const Dims& bd, const TP& C, bool c64, bool b_site) {
+  Ctx& c = *side_->cx;
   if (!tc_) {
-    ein(cx, spec, A, ad, B, bd, C);
+    ein(c, spec, A, ad, B, bd, C);
     return;
   }
-  ein_tc(cx, spec, A, a64 ? 1 : 0, ad, B, b64 ? 1 : 0, bd, C, c64 ? 1 : 0, opt.precision, 1.0, TP(),
-         b_site ? site_packs_.get() : nullptr);
+  ein_tc(c, spec, A, a64 ? 1 : 0, ad, B, b64 ? 1 : 0, bd, C, c64 ? 1 : 0, opt.precision, 1.0, TP(),
+         b_site ? side_->cache : nullptr);
 }
 
 Mps Engine::closure_mps(const std::vector<Mat>& mats, Arena&) {
@@ -97,11 +141,11 @@ Dims Engine::chain_left(const TP& L, const Dims& ld, const TP& M, const Dims& md
                         const TP& X3) {
   const Dims ad = A.dims();
   const Dims x1 = ein_dims("clma,auvb->clmuvb", ld, md);
-  con("clma,auvb->clmuvb", L, true, ld, M, true, md, X1_, x64_);
+  con("clma,auvb->clmuvb", L, true, ld, M, true, md, side_->X1, x64_);
   const Dims x2 = ein_dims("clmuvb,sulnr->cmvbsnr", x1, ad);
-  con("clmuvb,sulnr->cmvbsnr", X1_, x64_, x1, A.p, true, ad, X2_, x64_, true);
+  con("clmuvb,sulnr->cmvbsnr", side_->X1, x64_, x1, A.p, true, ad, side_->X2, x64_, true);
   const Dims x3 = ein_dims("cmvbsnr,svmoq->cbnroq", x2, ad);
-  con("cmvbsnr,svmoq->cbnroq", X2_, x64_, x2, A.p, true, ad, X3, x64_, true);
+  con("cmvbsnr,svmoq->cbnroq", side_->X2, x64_, x2, A.p, true, ad, X3, x64_, true);
   return x3;
 }
 
@@ -109,11 +153,11 @@ Dims Engine::chain_right(const TP& R, const Dims& rd, const TP& M, const Dims& m
                          const TP& Y3) {
   const Dims ad = A.dims();
   const Dims y1 = ein_dims("auvb,brqc->auvrqc", md, rd);
-  con("auvb,brqc->auvrqc", M, true, md, R, true, rd, X1_, x64_);
+  con("auvb,brqc->auvrqc", M, true, md, R, true, rd, side_->X1, x64_);
   const Dims y2 = ein_dims("auvrqc,sulnr->avqcsln", y1, ad);
-  con("auvrqc,sulnr->avqcsln", X1_, x64_, y1, A.p, true, ad, X2_, x64_, true);
+  con("auvrqc,sulnr->avqcsln", side_->X1, x64_, y1, A.p, true, ad, side_->X2, x64_, true);
   const Dims y3 = ein_dims("avqcsln,svmoq->aclnmo", y2, ad);
-  con("avqcsln,svmoq->aclnmo", X2_, x64_, y2, A.p, true, ad, Y3, x64_, true);
+  con("avqcsln,svmoq->aclnmo", side_->X2, x64_, y2, A.p, true, ad, Y3, x64_, true);
   return y3;
 }
 
@@ -332,7 +376,6 @@ void Engine::row_rhos(const OLat& lat, const Mps& T, const Mps& B, int y, const 
   ld[0] = {1, lc.n, lc.n, 1};
   copy(cx, Lenv_[0], lc.p, (long long)lc.n * lc.n);
   rd[Lx - 1] = {1, rc.n, rc.n, 1};
-  copy(cx, Renv_[Lx - 1], rc.p, (long long)rc.n * rc.n);
   int xmax = 0, xmin = lat.Lx;
   for (const auto& t : sites) {
     xmax = std::max(xmax, t.first + 1);
@@ -348,11 +391,30 @@ void Engine::row_rhos(const OLat& lat, const Mps& T, const Mps& B, int y, const 
     con("cbnroq,cnoe->erqb", X3_, x64_, x3, B.p[x], true, B.dims[x], Lenv_[x + 1], true);
     normalize(cx, Lenv_[x + 1], (long long)numel(ld[x + 1]), TP(), tmp0_);
   }
+  // Right environments: on the second stream when there is one (they depend
+  // only on T, B and the row, like the left ones).
+  if (dual_) {
+    cudaEvent_t e;
+    PEPS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    PEPS_CUDA(cudaEventRecord(e, cx.st));
+    PEPS_CUDA(cudaStreamWaitEvent(aux_.cx->st, e, 0));
+    PEPS_CUDA(cudaEventDestroy(e));
+    side_ = &aux_;
+  }
+  copy(*side_->cx, Renv_[Lx - 1], rc.p, (long long)rc.n * rc.n);
   for (int x = Lx - 1; x >= 1 && x - 1 >= xmin; --x) {
-    const Dims y3 = chain_right(Renv_[x], rd[x], T.p[x], T.dims[x], lat.at(y, x), X3_);
+    const Dims y3 = chain_right(Renv_[x], rd[x], T.p[x], T.dims[x], lat.at(y, x), side_->X3);
     rd[x - 1] = ein_dims("aelnmo,cnoe->almc", y3, B.dims[x]);
-    con("aelnmo,cnoe->almc", X3_, x64_, y3, B.p[x], true, B.dims[x], Renv_[x - 1], true);
-    normalize(cx, Renv_[x - 1], (long long)numel(rd[x - 1]), TP(), tmp0_);
+    con("aelnmo,cnoe->almc", side_->X3, x64_, y3, B.p[x], true, B.dims[x], Renv_[x - 1], true);
+    normalize(*side_->cx, Renv_[x - 1], (long long)numel(rd[x - 1]), TP(), side_->tmp);
+  }
+  if (dual_) {
+    side_ = &main_;
+    cudaEvent_t e;
+    PEPS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    PEPS_CUDA(cudaEventRecord(e, aux_.cx->st));
+    PEPS_CUDA(cudaStreamWaitEvent(cx.st, e, 0));
+    PEPS_CUDA(cudaEventDestroy(e));
   }
   auto open_site = [&](int x) -> Dims {
     const SiteT& A = lat.at(y, x);

@@ -58,6 +58,11 @@ struct EnvData {
 class Engine {
  public:
   Engine(Ctx& cx, const Opts& o, int d, int Dmax, int Lmax, int nb = 1);
+  ~Engine();
+  // A second stream (and its own chain buffers) on which row_rhos builds the
+  // right environments while the left ones are built on the main stream.
+  // Taken only when one more buffer set is small (single problem, < 512 MB).
+  void enable_dual(cudaStream_t st2);
 
   // Top-down boundaries of `lat`: out[y] = boundary above row y, y = 0..upto.
   // lnacc (a device scalar per problem) accumulates the log of every rescaling factor.
@@ -107,6 +112,20 @@ class Engine {
   // absorb chain pieces
   Dims chain_left(const TP& L, const Dims& ld, const TP& M, const Dims& md, const SiteT& A, const TP& X3);
   Dims chain_right(const TP& R, const Dims& rd, const TP& M, const Dims& md, const SiteT& A, const TP& Y3);
+
+  // The stream, scratch, chain buffers and pack cache the contraction helpers use.
+  struct Side {
+    Ctx* cx;
+    TP X1, X2, X3, tmp;
+    PackCache* cache;
+  };
+  Side main_, aux_;
+  Side* side_ = &main_;
+  bool dual_ = false;
+  std::unique_ptr<Arena> ws2_;
+  std::unique_ptr<Ctx> cx2_;
+  std::unique_ptr<PackCache> cache2_;
+  cudaStream_t ws2_stream_ = nullptr;
 
   int d_, Dmax_, Lmax_, nb_, cap_;
   size_t bigN_;                 // chi^2 * Dmax^4 (elements of the largest chain intermediate / d)
