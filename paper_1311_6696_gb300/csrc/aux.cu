@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(256) k_cu0(const Cu0Lattice* lats, int* flag) 
 
 }  // namespace
 
-void orient_lattice(Ctx& cx, const void* src, int src_f32, int Ly, int Lx, int d, int D,
+void orient_lattice(Ctx& cx, const void* src, int src_f32, int /*Ly*/, int Lx, int d, int D,
                     const OrientSite* host_sites, int nsites, double* dst) {
   auto* dev = static_cast<const OrientSite*>(stage(cx, host_sites, sizeof(OrientSite) * nsites));
   Launch L(K_AUX, cx.st);

@@ -322,7 +322,7 @@ void ein(Ctx& cx, const char* spec, const TP& A, const Dims& ad, const TP& B,
   const int np = problems({&A, &B, &C});
   PEPS_REQUIRE(!A.null() && !B.null() && C.n == np, "internal: contraction operands");
   GemmArgs g;
-  std::memset(&g, 0, sizeof(g));
+  std::memset(static_cast<void*>(&g), 0, sizeof(g));
   g.A = A.all(np);
   g.B = B.all(np);
   g.C = C.all(np);

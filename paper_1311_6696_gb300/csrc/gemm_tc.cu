@@ -545,7 +545,7 @@ Operand pack(Ctx& cx, const TP& src, int np, long long pad, int src_f64, const s
              double* mem) {
   auto st = strides_of(dims);
   PackArgs p;
-  std::memset(&p, 0, sizeof(p));
+  std::memset(static_cast<void*>(&p), 0, sizeof(p));
   for (char ch : rowletters) {
     auto i = letters.find(ch);
     push(p.gr, dims[i], st[i]);
@@ -643,7 +643,7 @@ void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, c
   const auto sc = strides_of(cd);
   std::string mL, nL, kL;
   TcArgs g;
-  std::memset(&g, 0, sizeof(g));
+  std::memset(static_cast<void*>(&g), 0, sizeof(g));
   for (size_t i = 0; i < p.c.size(); ++i) {
     const char ch = p.c[i];
     const bool inA = p.a.find(ch) != std::string::npos, inB = p.b.find(ch) != std::string::npos;

@@ -767,7 +767,7 @@ void qr_thin(Ctx& cx, int m, int n, const TP& A, long long rs, long long cs, con
   const int ld = ld_of(std::max(C, 1));
   const bool in_smem = C > 1 && full_of(C) <= kQrSmemMax;
   QrArgs a;
-  std::memset(&a, 0, sizeof(a));
+  std::memset(static_cast<void*>(&a), 0, sizeof(a));
   a.m = m;
   a.n = n;
   a.A = A.all(np);
@@ -815,7 +815,7 @@ void svd_trunc(Ctx& cx, int m, int n, const TP& A, int kk, const TP& US, const T
   const int np = problems({&A, &US, &Vt});
   PEPS_REQUIRE(!A.null() && US.n == np && Vt.n == np, "internal: svd operands");
   SvdArgs s;
-  std::memset(&s, 0, sizeof(s));
+  std::memset(static_cast<void*>(&s), 0, sizeof(s));
   s.trans = (m < n) ? 1 : 0;
   s.p = s.trans ? n : m;
   s.q = s.trans ? m : n;
