@@ -1,6 +1,9 @@
 // The extern "C" boundary of the library: argument validation, lattice
 // repacking into the four sweep orientations, the full / cluster / norm
-// drivers, and kernel-class instrumentation.  No exception crosses this file.
+// drivers (host-threaded lanes of streams; row passes that start as soon as
+// their boundaries exist; cluster windows batched by shape), recorded plans
+// (CUDA graphs) and their autotuner, the learned-closure calls, and
+// kernel-class instrumentation.  No exception crosses this file.
 #include <algorithm>
 #include <array>
 #include <atomic>

@@ -1,5 +1,5 @@
 // Boundary-MPS sweeps, one-site ALS compression, row environments and local
-// density matrices (Sections 2, 4.1-4.3), orchestrated on the host, executed
+// density matrices (Sections 2, 5.1-5.3), orchestrated on the host, executed
 // on the device.  No host synchronisation happens inside a sweep: bond
 // dimensions depend on shapes only, and every data-dependent quantity (norms,
 // log-scales, convergence) stays on the device.

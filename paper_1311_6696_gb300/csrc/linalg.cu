@@ -1,8 +1,11 @@
-// FP64 Householder QR and one-sided Jacobi SVD, one CTA per matrix.
+// FP64 Householder QR and one-sided Jacobi SVD, batched over independent
+// problems of one shape.
 //
-// The working copy lives in global memory (column-major) and stays in L2 at
-// the sizes used here (<= a few MB).  Reductions over a column are done by one
-// warp per column; a CTA handles all columns of one matrix.
+// Small matrices take one CTA each (working copy in global memory, L2
+// resident; one warp per column reduction).  Larger ones are split by rows
+// over a thread-block cluster of 2-16 CTAs that exchange partial sums through
+// distributed shared memory: the QR with one cluster barrier per Householder
+// column, the SVD with one per round of the round-robin Jacobi schedule.
 #include <cooperative_groups.h>
 
 #include <algorithm>
