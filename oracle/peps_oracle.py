@@ -419,7 +419,7 @@ def boundary_sweep(lat: Lat, chi: int, mode: str = "svd", sweeps: int = 2,
 
 
 # ---------------------------------------------------------------------------
-# Row environments and local reduced density matrices (Sections 2 and 4.3)
+# Row environments and local reduced density matrices (Sections 2 and 5.3)
 # ---------------------------------------------------------------------------
 def row_envs(T, B, lat: Lat, y: int):
     """Left/right environments along row y between top boundary T and bottom
