@@ -255,8 +255,15 @@ Mps Engine::var_compress(const Mps& T, const OLat& lat, int y, const std::vector
     N.p[x] = alloc(step, numel(N.dims[x]));
     var_init(cx, T.p[x], T.dims[x].data(), N.p[x], N.dims[x].data(), opt.seed, tag, y, x, tmp1_);
   }
-  // right-canonicalise the start: N[x] = R^T Q^T (QR of N[x]^T), R^T moves left
-  for (int x = Lx - 1; x >= 1; --x) {
+  // Right-canonicalise the start: N[x] = R^T Q^T (QR of N[x]^T), R^T moves left.
+  // A start that is a plain copy of a right-canonical boundary (the previous
+  // fit ended on a right-to-left half-sweep and no bond grew) is already in
+  // that form: there each QR would return N[x]^T up to column signs and
+  // rounding, so the pass is skipped.  The skipped pass changes only the sign
+  // gauge of the bonds, which no contracted quantity sees.
+  bool copy_of_canonical = T.right_canonical;
+  for (int x = 0; x < Lx; ++x) copy_of_canonical = copy_of_canonical && N.dims[x] == T.dims[x];
+  for (int x = Lx - 1; x >= 1 && !copy_of_canonical; --x) {
     const Dims nd = N.dims[x];
     const int c = nd[0], noe = nd[1] * nd[2] * nd[3];
     PEPS_REQUIRE(c <= noe, "internal: inconsistent bond caps");
@@ -316,6 +323,7 @@ Mps Engine::var_compress(const Mps& T, const OLat& lat, int y, const std::vector
       centre = 0;
     }
   }
+  N.right_canonical = centre == 0;
   return N;
 }
 
@@ -345,6 +353,7 @@ Mps Engine::absorb_compress(const Mps& T, const OLat& lat, int y, int tag, const
   }
   normalize(cx, P.p[centre], (long long)numel(P.dims[centre]), lnacc, tmp0_);
   Mps out;
+  out.right_canonical = P.right_canonical;
   for (int x = 0; x < Lx; ++x) {
     const size_t n = numel(P.dims[x]);
     TP q = alloc(keep, n);

@@ -34,6 +34,7 @@ struct OLat {
 struct Mps {
   std::vector<TP> p;
   std::vector<Dims> dims;      // [a, u, v, b]
+  bool right_canonical = false;   // sites 1..L-1 right-orthonormal, centre at site 0
 };
 
 struct Opts {
