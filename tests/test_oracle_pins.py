@@ -278,6 +278,42 @@ def test_var_local_update_is_dense_least_squares():
     assert np.max(np.abs(sol.reshape(b0.shape) - b0)) < 1e-12 * max(1.0, np.max(np.abs(b0)))
 
 
+def test_var_fit_start_from_canonical_boundary_needs_no_gauge_pass():
+    """A var fit that ends on a right-to-left half-sweep leaves sites 1..L-1
+    right-orthonormal (Section 2, orthonormal gauge).  When the next row's
+    bond caps equal its bonds, the next fit starts from a plain copy of it,
+    and the start's right-canonicalisation changes only the signs of the bond
+    bases: every entry keeps its magnitude and the state is the same."""
+    A = synth.peps_gauss(5, 5, 2, 2, seed=41)
+    lat = O.lattice_from_dense(A)
+    bounds, _ = O.boundary_sweep(lat, chi=8, mode="var", upto=3)
+    T = bounds[3]
+    Lx = 5
+    for x in range(1, Lx):
+        M = T[x].reshape(T[x].shape[0], -1)
+        assert np.max(np.abs(M @ M.T - np.eye(M.shape[0]))) < 1e-12
+    y = 3
+    A3 = lat.A[y]
+    phys = [A3[x].shape[3] ** 2 for x in range(Lx)]
+    prod = [T[k].shape[3] * A3[k].shape[4] ** 2 for k in range(Lx - 1)]
+    caps = O.bond_caps(phys, prod, 8)
+    assert caps == [T[k].shape[3] for k in range(Lx - 1)] and max(caps) == 8
+    N0 = O.var_init(T, caps, [A3[x].shape[3] for x in range(Lx)], 0, 0, y)
+    assert all(np.array_equal(N0[x], T[x]) for x in range(Lx))
+    N1 = O.right_canonicalize(N0)
+
+    def dense(N):
+        v = N[0]
+        for k in range(1, Lx):
+            v = np.tensordot(v, N[k], axes=([v.ndim - 1], [0]))
+        return v.reshape(-1)
+
+    for x in range(Lx):
+        assert np.max(np.abs(np.abs(N1[x]) - np.abs(N0[x]))) < 1e-12
+    v0, v1 = dense(N0), dense(N1)
+    assert np.max(np.abs(v1 - v0)) < 1e-12 * np.max(np.abs(v0))
+
+
 # ---------------------------------------------------------------- consistency
 def test_top_down_and_bottom_up_norms_agree_at_exact_chi():
     A = synth.peps_gauss(4, 4, 2, 2, seed=15)
