@@ -278,7 +278,8 @@ const char* peps_last_error(void);
  *   then over the largest QR cluster {8, 4}.  *lanes and *qr_cluster (either
  *   may be NULL) receive the choice.  Costs five recordings (seven for the
  *   cluster scheme), each timed over three replays.
- * peps_plan_launches: kernel launches in one replay.
+ * peps_plan_launches: kernel launches in one replay (the kernel nodes of the
+ *   recorded graph; 0 for NULL).
  * peps_plan_free: synchronises the device, releases the graph and its
  *   memory; NULL is accepted.
  */

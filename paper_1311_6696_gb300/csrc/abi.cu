@@ -136,6 +136,14 @@ void prof_launch(KClass c, cudaStream_t st, double flops, double bytes) {
     t_open_ev[c] = e;
   }
 }
+void prof_more(KClass c, int kernels) {
+  Prof& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  if (Counts* rc = g_recording.load())
+    rc->launches[c] += kernels;
+  else
+    p.launches[c] += kernels;
+}
 void prof_done(KClass c, cudaStream_t st) {
   Prof& p = prof();
   std::lock_guard<std::mutex> g(p.mu);
@@ -953,6 +961,7 @@ struct peps_plan {
   cudaGraphExec_t exec = nullptr;
   int* flag = nullptr;
   long long nodes = 0;
+  long long kernels = 0;            // kernel nodes of the graph: kernels one replay launches
   int lanes = 0, qr_cmax = 0;       // launch configuration it was recorded with
   Counts counts;                    // kernel launches (and their flops) in one replay
 };
@@ -1017,10 +1026,21 @@ PlanPtr record_plan(const peps_lattice* lat, const peps_opts* opts, const Opts& 
   size_t nodes = 0;
   PEPS_CUDA(cudaGraphGetNodes(plan->graph, nullptr, &nodes));
   plan->nodes = (long long)nodes;
+  {
+    std::vector<cudaGraphNode_t> all(nodes);
+    size_t got = nodes;
+    if (nodes) PEPS_CUDA(cudaGraphGetNodes(plan->graph, all.data(), &got));
+    for (size_t i = 0; i < got; ++i) {
+      cudaGraphNodeType ty;
+      PEPS_CUDA(cudaGraphNodeGetType(all[i], &ty));
+      if (ty == cudaGraphNodeTypeKernel) ++plan->kernels;
+    }
+  }
   const auto t0 = std::chrono::steady_clock::now();
   PEPS_CUDA(cudaGraphInstantiate(&plan->exec, plan->graph, 0));
   if (std::getenv("PEPS_VERBOSE"))
-    std::fprintf(stderr, "[peps] plan: %zu graph nodes, instantiated in %.1f ms\n", nodes,
+    std::fprintf(stderr, "[peps] plan: %zu graph nodes (%lld kernels), instantiated in %.1f ms\n", nodes,
+                 plan->kernels,
                  std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
   return plan;
 }
@@ -1365,12 +1385,7 @@ int peps_plan_run(peps_plan* plan, void* cuda_stream) {
 
 const peps_env* peps_plan_env(const peps_plan* plan) { return plan ? plan->env.get() : nullptr; }
 
-long long peps_plan_launches(const peps_plan* plan) {
-  if (!plan) return 0;
-  long long n = 0;
-  for (int i = 0; i < K_NCLASS; ++i) n += plan->counts.launches[i];
-  return n;
-}
+long long peps_plan_launches(const peps_plan* plan) { return plan ? plan->kernels : 0; }
 
 void peps_plan_free(peps_plan* plan) {
   if (!plan) return;

@@ -518,6 +518,7 @@ void fro_norm(Ctx& cx, const TP& x, long long n, const TP& out) {
   Launch L(K_AUX, cx.st);
   k_sumsq_partial<<<dim3(nb, np), 256, 0, cx.st>>>(x.all(np), n, part);
   k_sumsq_finish<<<np, 256, 0, cx.st>>>(part, int(nb), out.all(np));
+  L.more();
   PEPS_CHECK_LAUNCH();
 }
 

@@ -391,6 +391,7 @@ void loss_grad_buf(Ctx& cx, const MlpDims& m, const float* w, const float* X, co
     k_sigma<<<gs, 256, 0, cx.st>>>(X, F, Yo, Y, n, m.D, nullptr, dYo, part);
     k_sum_loss<<<1, 32, 0, cx.st>>>(part, int(gs), n, loss_dev, accumulate);
     PEPS_CHECK_LAUNCH();
+    l.more();
   }
   float* gW1 = grad;
   float* gb1 = gW1 + (long long)W * F;
@@ -406,6 +407,7 @@ void loss_grad_buf(Ctx& cx, const MlpDims& m, const float* w, const float* X, co
     k_relu_bwd<<<grid_for(n * W), 256, 0, cx.st>>>(dH2, H2, n * W);
     k_colsum<<<std::min(W, 1024), 256, 0, cx.st>>>(dH2, n, W, gb2);
     PEPS_CHECK_LAUNCH();
+    l.more(2);
   }
   ein_tc(cx, "bv,bw->vw", dH2, 0, {nn, W}, H1, 0, {nn, W}, gW2, 0, kMlpPrec);
   ein_tc(cx, "bv,vw->bw", dH2, 0, {nn, W}, L.W2, 0, {W, W}, dH1, 0, kMlpPrec);
@@ -414,6 +416,7 @@ void loss_grad_buf(Ctx& cx, const MlpDims& m, const float* w, const float* X, co
     k_relu_bwd<<<grid_for(n * W), 256, 0, cx.st>>>(dH1, H1, n * W);
     k_colsum<<<std::min(W, 1024), 256, 0, cx.st>>>(dH1, n, W, gb1);
     PEPS_CHECK_LAUNCH();
+    l.more();
   }
   ein_tc(cx, "bw,bi->wi", dH1, 0, {nn, W}, X, 0, {nn, F}, gW1, 0, kMlpPrec);
 }
@@ -483,6 +486,7 @@ void mlp_train(Ctx& cx, const MlpDims& m, float* w, const float* X, const float*
       k_gather_rows<<<grid_for(B * F), 256, 0, cx.st>>>(X, didx + (long long)t * B, B, int(F), Xb);
       k_gather_rows<<<grid_for(B * o), 256, 0, cx.st>>>(Y, didx + (long long)t * B, B, int(o), Yb);
       PEPS_CHECK_LAUNCH();
+      l.more();
     }
     const bool rec = t >= steps - tail;
     loss_grad_buf(cx, m, w, Xb, Yb, B, rec ? loss_acc : part + grid_for(B), rec ? 1 : 0, grad, H1, H2, Yo, dYo,

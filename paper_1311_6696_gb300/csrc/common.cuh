@@ -51,6 +51,7 @@ enum KClass {
 
 void prof_launch(KClass c, cudaStream_t st, double flops, double bytes);
 void prof_done(KClass c, cudaStream_t st);
+void prof_more(KClass c, int kernels);
 bool prof_timing();
 
 // RAII helper: record around one launch.
@@ -61,6 +62,9 @@ struct Launch {
     prof_launch(c, st, flops, bytes);
   }
   ~Launch() { prof_done(c, st); }
+  // The scope counts as one kernel launch; a scope that launches more kernels
+  // adds them here, so the counters hold kernel launches, not scopes.
+  void more(int kernels = 1) { prof_more(c, kernels); }
 };
 
 // ---------------------------------------------------------------------------

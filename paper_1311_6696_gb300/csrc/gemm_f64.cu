@@ -391,6 +391,7 @@ void ein(Ctx& cx, const char* spec, const TP& A, const Dims& ad, const TP& B,
     Launch L(K_GEMM_F64, cx.st, 2.0 * double(g.M * g.N * g.NB) * double(g.K) * np, 0);
     k_dot_partial<<<dim3(nblk, np), 256, 0, cx.st>>>(g, kc, part);
     k_dot_finish<<<np, 32, 0, cx.st>>>(g, nblk, part);
+    L.more();
     PEPS_CHECK_LAUNCH();
     return;
   }

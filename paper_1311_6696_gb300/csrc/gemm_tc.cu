@@ -761,6 +761,7 @@ void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, c
     const unsigned blocks = unsigned(std::max<long long>(1, std::min<long long>((total + 255) / 256, 4096)));
     k_tc_splitk_reduce<<<blocks, 256, 0, cx.st>>>(g);
     PEPS_CHECK_LAUNCH();
+    L.more();
   }
 }
 

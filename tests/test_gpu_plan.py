@@ -136,3 +136,23 @@ def test_tuned_cluster_plan_matches_oracle(peps):
     plan = peps.Plan(At, chi=6, mode="var", cluster_n=3, tune=True)
     env = plan.run()
     _close(_obs(env), _oracle_obs(O.env_cluster(A, n=3, chi=6, mode="var")), TOL)
+
+
+@pytest.mark.parametrize("precision,cluster_n", [("fp64", 0), ("tf32x3", 0), ("tf32x3", 3)])
+def test_profiler_counts_every_kernel_of_a_replay(peps, precision, cluster_n):
+    """One replay adds to the per-class launch counters exactly the kernel
+    nodes of the recorded graph: every kernel is counted once."""
+    import torch
+    from paper_1311_6696_gb300 import synth
+    A = torch.from_numpy(synth.peps_gauss(6, 6, 2, 3, seed=95)).cuda()
+    kw = dict(chi=12, mode="var", precision=precision)
+    if cluster_n:
+        kw["cluster_n"] = cluster_n
+    plan = peps.Plan(A, **kw)
+    assert plan.launches > 0
+    torch.cuda.synchronize()
+    peps.profile_reset()
+    plan.run()
+    torch.cuda.synchronize()
+    counted = sum(v["launches"] for v in peps.profile_read().values())
+    assert counted == plan.launches
