@@ -1,30 +1,37 @@
 #!/usr/bin/env python
-"""Benchmark: full boundary-MPS environments of a 10x10 OBC PEPS (d=2, D=4).
+"""Benchmark: full boundary-MPS environments of a 20x20 OBC PEPS (d=2, D=8).
 
-Workload (one step): every site environment of a 10x10 PEPS with d=2, D=4,
-entries 0.5 + 0.1*N(0,1) (unit-norm tensors, seeded), boundary bond chi=64,
-variational (2 half-sweep) compression -- four directional sweeps, the row
-and column environments, every site / bond density matrix -- followed by
-<S.S> on every one of the 180 nearest-neighbour bonds.  One step yields
-Ly*Lx = 100 site environments; the metric is environments per second.
+Workload (one step): every site environment of the 20x20 D=8 lattice made by
+the seeded simple-update Heisenberg generator (tau=0.01, 400 steps), boundary
+bond chi=128, variational (2 half-sweep) compression -- four directional
+sweeps, the row and column environments, every site / bond density matrix --
+followed by <S.S> on every one of the 760 nearest-neighbour bonds.  One step
+yields Ly*Lx = 400 site environments; the metric is environments per second.
 
-The headline path computes the absorb contractions on the tensor cores in
-split TF32 (tf32x3) with FP64 QR / gauge / rescaling; the same line reports
-the plain FP64 GPU path's throughput and the largest relative deviation of
-the 180 bond observables between the two.  Each step replays the recorded
-plan (one CUDA graph for the whole environment set) and evaluates <S.S>.
+The absorb contractions run on the tensor cores in split BF16 (bf16x3: three
+BF16 products per FP32 operand pair, FP32 accumulation) with FP64 QR, gauge
+and rescaling.  Each step replays the recorded plan (one CUDA graph for the
+whole environment set) and evaluates <S.S>.  The line also reports
 
-A "cluster" object adds the cluster scheme on the 14x14 D=6 lattice (all 196
-windows at chi=36, n = 2, 4, 6) with its deviation from the full chi=64
-environments.
+* the accuracy of the step's own output against the FP64 oracle on the same
+  tensors (ln N and the last row's observables, stored by
+  tests/golden/make_oracle_golden.py);
+* the FP64 GPU path on a bounded part of the same lattice (the norm sweep of
+  its top rows) against the headline precision on the same part;
+* the FP64 oracle on the host cores (a bounded sample, costed up to the whole
+  environment set by operation count).
+
+``--workload c2`` runs the 10x10 D=4 chi=64 lattice instead (entries
+0.5 + 0.1 N(0,1)), with the FP64 path timed on the whole set.  ``--cluster``
+adds the cluster scheme on the 14x14 D=6 lattice (all 196 windows at chi=36,
+n = 2, 4, 6).
 
 Launch: ``python bench.py [--gpus N --steps K --warmup W]``; for N > 1 run
 under ``torch.distributed.run`` with one process per GPU.  The full
-environment does not shard, so every rank computes its own replica (seed 2 +
+environment does not shard, so every rank computes its own replica (seed +
 rank): weak scaling, no collective on the data path.
 
-``--impl reference`` times the FP64 CPU oracle on the host cores instead
-(a bounded sample of the same workload, extrapolated by operation count).
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
 """
 from __future__ import annotations
 
@@ -40,7 +47,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(name="10x10_D4", Ly=10, Lx=10, d=2, D=4, seed=2)
+WORKLOADS = {
+    "c4": dict(name="20x20_D8_su", Ly=20, Lx=20, d=2, D=8, chi=128, precision="bf16x3",
+               desc="20x20 OBC PEPS d=2 D=8 from the seeded simple-update Heisenberg generator "
+                    "(tau=0.01, 400 steps, seed 4), unit-norm tensors",
+               golden="oracle_20x20_D8_su_chi128.json", fp64_rows=4),
+    "c2": dict(name="10x10_D4", Ly=10, Lx=10, d=2, D=4, chi=64, precision="tf32x3",
+               desc="10x10 OBC PEPS d=2 D=4, entries 0.5+0.1N(0,1), unit-norm tensors",
+               golden=None, fp64_rows=None),
+}
 L2_BYTES = 129 * 2 ** 20
 
 
@@ -53,15 +68,14 @@ def _peaks():
 
 
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
-# stands (profiles/<kernel>_bench_10x10_D4_chi64.md); update or drop an entry
-# whenever that kernel changes.
-TRAFFIC = {
-    "qr_f64": (595456, "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 1024x64 k_qr_cluster "
-                       "launch (profiles/k_qr_cluster_bench_10x10_D4_chi64.md); the matrix read once"),
-}
+# stands, keyed by (workload, class); an entry is dropped whenever its kernel changes.
+TRAFFIC = {}
 
-# FP64 ALU peak of GB300 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# Dense FP64 and TF32 peaks: measured at start-up by _measure_peaks (torch
+# matmul 8192^3 on this GPU); these values (one earlier measurement on a GB300,
+# best of 5) stand in if that fails.
+FP64_PEAK_TFLOPS = 1.0996
+TF32_PEAK_TFLOPS = 1008.8
 
 
 def _clock_sampler():
@@ -104,47 +118,107 @@ def _clock_summary(proc, gpu_index):
             "samples": len(sms)}
 
 
+def load_input(name: str, seed_offset: int = 0):
+    """The named synthetic lattice (synth.workload); the simple-update lattices
+    take a minute or two to generate, so they are kept in the temp directory
+    keyed by the generator's source and the seed (a later process on the same
+    machine reuses them)."""
+    import hashlib
+    import tempfile
+
+    import numpy as np
+
+    from paper_1311_6696_gb300 import synth
+    w = synth.WORKLOADS[name]
+    seed = w["seed"] + seed_offset
+    if w["gen"] != "su":
+        return synth.workload(name, seed=seed)
+    src = open(synth.__file__, "rb").read()
+    key = hashlib.sha256(src + f"{name}:{seed}".encode()).hexdigest()[:16]
+    path = os.path.join(tempfile.gettempdir(), f"peps_input_{name}_{key}.npy")
+    if os.path.exists(path):
+        try:
+            return np.load(path)
+        except (OSError, ValueError):
+            pass
+    A = synth.workload(name, seed=seed)
+    tmp = f"{path}.{os.getpid()}.tmp.npy"
+    np.save(tmp, A)
+    os.replace(tmp, path)
+    return A
+
+
+def _timed(fn, st, n, flush=None):
+    """Device times (ms) of n calls of fn on stream st, CUDA events around each."""
+    import torch
+    out = []
+    for _ in range(n):
+        if flush is not None:
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def _rel(a, b):
+    import numpy as np
+    a = np.asarray(a, dtype=float)
+    b = np.asarray(b, dtype=float)
+    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-2)))
+
+
 def run_ours(args, rank, world, dist):
     import numpy as np
     import torch
 
-    from paper_1311_6696_gb300 import peps, synth
+    from paper_1311_6696_gb300 import peps
 
+    W = WORKLOADS[args.workload]
+    chi = args.chi or W["chi"]
+    prec = args.precision or W["precision"]
     local = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     st = torch.cuda.current_stream()
-    A = synth.peps_gauss(WORKLOAD["Ly"], WORKLOAD["Lx"], WORKLOAD["d"], WORKLOAD["D"], WORKLOAD["seed"] + rank)
+    A = load_input(W["name"], seed_offset=rank)
     At = torch.from_numpy(A).to(dev)
     Ah = torch.from_numpy(A).pin_memory()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    kw = dict(chi=args.chi, mode=args.mode, sweeps=2, precision=args.precision, stream=st)
+    kw = dict(chi=chi, mode=args.mode, sweeps=2, precision=prec, stream=st)
+    Ly, Lx = W["Ly"], W["Lx"]
+    envs = Ly * Lx
 
     # ---- one replay of a plan with every kernel class timed inside the graph
-    # (event nodes run back to back with the kernels, so small kernels are not
-    # charged the host's launch gaps): the class with the most device time is
-    # the one whose roofline is reported; the absorb class is reported from
-    # the same replay.
-    peps.profile_enable(-1)
-    probe = peps.Plan(At, **kw)
-    peps.profile_enable(0)
-    probe.run()
-    torch.cuda.synchronize()
-    peps.profile_reset()
-    probe.run()
-    prof1 = peps.profile_read()
-    probe.free()
-    del probe
-    dom = args.dominant or max((k for k in prof1 if prof1[k]["launches"]), key=lambda k: prof1[k]["ms"])
-    absorb = "gemm_tc" if args.precision != "fp64" else "gemm_f64"
+    # (event nodes run back to back with the kernels): the class with the most
+    # device time is the one whose roofline is reported.
+    prof1 = None
+    dom = args.dominant
+    if dom is None:
+        peps.profile_enable(-1)
+        probe = peps.Plan(At, **kw)
+        peps.profile_enable(0)
+        peps.profile_reset()
+        probe.run()
+        prof1 = peps.profile_read()
+        probe.free()
+        del probe
+        dom = max((k for k in prof1 if prof1[k]["launches"]), key=lambda k: prof1[k]["ms"])
+    absorb = "gemm_tc" if prec != "fp64" else "gemm_f64"
 
     # ---- the step as a user runs it repeatedly: the recorded plan (one CUDA
     # graph launch for the whole environment set), then <S.S> on every bond.
     # The dominant class is timed inside every replay (event nodes around its
-    # launches); the absorb class's figure comes from the probe replay above.
+    # launches).
+    t0 = time.perf_counter()
     peps.profile_enable(1 << peps.class_index(dom))
-    plan = peps.Plan(At, **kw, tune=not args.no_tune)
+    plan = peps.Plan(At, **kw, tune=args.tune)
     peps.profile_enable(0)
+    t_plan = time.perf_counter() - t0
     env = plan.env
 
     def step():
@@ -159,17 +233,8 @@ def run_ours(args, rank, world, dist):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    times = []
     t_wall = time.perf_counter()
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        h1, v1 = step()
-        e1.record(st)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
+    times = _timed(step, st, args.steps, flush)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -177,69 +242,67 @@ def run_ours(args, rank, world, dist):
     clk = _clock_summary(clocks, local) if rank == 0 else None
     prof = peps.profile_read()
     launches = sum(v["launches"] for v in prof.values())
+    h1, v1 = step()
+    out_site = env.expect("site", SZ)
+    ln_step = env.ln_norm()
 
-    # ---- end to end: pinned host tensors in (H2D into the plan's lattice), replay, observables out
+    # ---- end to end: pinned host tensors in (H2D into the plan's lattice),
+    # replay, observables out (D2H), timed on the host
     etimes = []
-    for _ in range(args.steps):
+    for _ in range(max(1, min(args.steps, args.e2e_steps))):
         flush.zero_()
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        t1 = time.perf_counter()
         At.copy_(Ah, non_blocking=True)
         step()
-        etimes.append((time.perf_counter() - t0) * 1e3)
+        etimes.append((time.perf_counter() - t1) * 1e3)
 
-    # ---- the plain FP64 GPU path (also recorded) on the same input, and the deviation between the two
-    cmp_ms, dev_err, others = None, None, {}
-    if args.precision != "fp64" and not args.no_fp64_compare:
-        p64 = peps.Plan(At, **dict(kw, precision="fp64"))
-        e64 = p64.env
-        p64.run()
-        tms = []
-        for _ in range(max(1, min(3, args.steps))):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            p64.run()
+    # ---- accuracy of the step's own output against the FP64 oracle
+    accuracy = None
+    gpath = os.path.join(ROOT, "tests", "golden", W["golden"]) if W["golden"] else None
+    if gpath and os.path.exists(gpath) and chi == json.load(open(gpath))["chi"] and args.mode == "var":
+        g = json.load(open(gpath))
+        y = g["row"]
+        sz = out_site.reshape(Ly, Lx)[y]
+        ss = h1.reshape(Ly, Lx - 1)[y]
+        accuracy = {"vs": "FP64 oracle on the same tensors (stored: " + os.path.relpath(gpath, ROOT) + ")",
+                    "max_rel_err": max(_rel(sz, g["sz"]), _rel(ss, g["sdots_h"])),
+                    "observables": f"<sigma_z> on the {Lx} sites and <S.S> on the {Lx - 1} bonds of row {y}",
+                    "ln_norm_abs_err": abs(ln_step[0] - g["ln_norm"]),
+                    "metric": "|x-x_ref|/max(|x_ref|,1e-2); absolute on ln N",
+                    "input_matches_stored": bool(abs(float(np.sum(A * _fp_weights(A))) - g["input"]["wsum"])
+                                                 < 1e-9 * max(1.0, abs(g["input"]["wsum"])))}
+        if args.mode != "var":
+            accuracy = None
+
+    # ---- the plain FP64 GPU path
+    fp64 = None
+    if prec != "fp64" and not args.no_fp64_compare:
+        if W["fp64_rows"]:
+            # bounded: the norm sweep (Section 2) of the lattice's top rows, both precisions
+            R = W["fp64_rows"]
+            sub = torch.from_numpy(np.ascontiguousarray(A[:R])).to(dev)
+            for p_ in ("fp64", prec):
+                peps.norm(sub, chi=chi, mode=args.mode, precision=p_, stream=st)   # warm
+            tf = _timed(lambda: peps.norm(sub, chi=chi, mode=args.mode, precision="fp64", stream=st), st, 1)
+            tp = _timed(lambda: peps.norm(sub, chi=chi, mode=args.mode, precision=prec, stream=st), st, 2)
+            fp64 = {"part": f"norm sweep of the top {R} rows ({R - 1} absorbs at chi={chi}) of the same lattice",
+                    "fp64_ms": round(min(tf), 1), f"{prec}_ms": round(min(tp), 1),
+                    "speedup": round(min(tf) / min(tp), 3)}
+        else:
+            p64 = peps.Plan(At, **dict(kw, precision="fp64"))
+            e64 = p64.env
+            tms = _timed(lambda: (p64.run(), e64.expect("hbond", SD)), st, max(1, min(3, args.steps)), flush)
             h0, v0 = e64.expect("hbond", SD), e64.expect("vbond", SD)
-            e1.record(st)
-            e1.synchronize()
-            tms.append(e0.elapsed_time(e1))
-        cmp_ms = sum(tms) / len(tms)
-        a = np.concatenate([h1, v1])
-        b = np.concatenate([h0, v0])
-        dev_err = float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-2)))
-        del e64, p64
-        # every other tensor-core precision on the same input, against the FP64 path
-        for prec in ("bf16x3", "tf32", "bf16"):
-            if prec == args.precision:
-                continue
-            pp = peps.Plan(At, **dict(kw, precision=prec), tune=not args.no_tune)
-            ep = pp.env
-            pp.run()
-            tms = []
-            for _ in range(max(1, min(3, args.steps))):
-                flush.zero_()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(st)
-                pp.run()
-                hp, vp = ep.expect("hbond", SD), ep.expect("vbond", SD)
-                e1.record(st)
-                e1.synchronize()
-                tms.append(e0.elapsed_time(e1))
-            ms_p = min(tms)
-            c = np.concatenate([hp, vp])
-            others[prec] = {"value": round(world * WORKLOAD["Ly"] * WORKLOAD["Lx"] / (ms_p * 1e-3), 2),
-                            "ms_per_step": round(ms_p, 2),
-                            "max_rel_err_vs_fp64_path": float(np.max(np.abs(c - b) / np.maximum(np.abs(b), 1e-2)))}
-            del ep, pp
+            ms64 = min(tms)
+            fp64 = {"part": "whole environment set", "value": round(world * envs / (ms64 * 1e-3), 3),
+                    "unit": "envs/s", "ms_per_step": round(ms64, 3),
+                    "max_rel_err_vs_fp64_path": _rel(np.concatenate([h1, v1]), np.concatenate([h0, v0]))}
+            del e64, p64
 
-    cluster = None if args.no_cluster else cluster_section(args, peps, synth, torch, st, flush)
+    cluster = cluster_section(args, peps, torch, st, flush) if args.cluster else None
 
-    total_ms = sum(times)
-    envs = WORKLOAD["Ly"] * WORKLOAD["Lx"]
-    ms_step, e_ms, value, e2e = aggregate(total_ms / len(times), sum(etimes) / len(etimes), envs, world,
+    ms_step, e_ms, value, e2e = aggregate(sum(times) / len(times), sum(etimes) / len(etimes), envs, world,
                                           dist, dev)
     if rank != 0:
         return None
@@ -259,16 +322,16 @@ def run_ours(args, rank, world, dist):
                     "peak_source": "of measured HBM copy bandwidth (MEASURED_PEAKS.json)", "timed": timed}
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
         if cls == "gemm_tc":
-            bf = pk.get("bf16_tflops_sustained", 1720.0)
-            if args.precision.startswith("bf16"):
-                peak, note = bf, "of measured bf16 sustained (cuBLAS, MEASURED_PEAKS.json)"
+            if prec.startswith("bf16"):
+                peak, note = pk.get("bf16_tflops_sustained", 1716.1), \
+                    "of measured bf16 dense, sustained (cuBLAS, MEASURED_PEAKS.json)"
             else:
-                peak, note = bf / 2.0, "of measured bf16 sustained x 1/2 (nominal tf32:bf16 dense ratio)"
+                peak, note = TF32_PEAK_TFLOPS, "of measured tf32 dense (torch matmul 8192^3, best of 5)"
             bound = "tensor"
         else:
             peak, bound = FP64_PEAK_TFLOPS, "alu"
-            note = "FP64 ALU peak derived from 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"
-        tr = TRAFFIC.get(cls) if src is None else None
+            note = "of measured FP64 dense (torch matmul 8192^3, best of 5)"
+        tr = TRAFFIC.get((args.workload, cls)) if src is None else None
         return {"bound": bound, "kernel": cls, "achieved": round(achieved, 4), "peak": round(peak, 4),
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 5), "traffic": tr[0] if tr else None,
                 "traffic_source": tr[1] if tr else None,
@@ -277,7 +340,7 @@ def run_ours(args, rank, world, dist):
                 "peak_source": note, "timed": timed}
 
     h2d = int(A.nbytes)
-    d2h = 8 * (WORKLOAD["Ly"] * (WORKLOAD["Lx"] - 1) + (WORKLOAD["Ly"] - 1) * WORKLOAD["Lx"])
+    d2h = 8 * (Ly * (Lx - 1) + (Ly - 1) * Lx)
     res = {
         "metric": "PEPS site environments/sec (full boundary-MPS envs + <S.S> on all bonds)",
         "value": round(value, 3),
@@ -290,28 +353,28 @@ def run_ours(args, rank, world, dist):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": {"fp64": "f64", "tf32": "tf32", "bf16": "bf16", "tf32x3": "tf32x3+f64",
-                  "bf16x3": "bf16x3+f64"}[args.precision],
+                  "bf16x3": "bf16x3+f64"}[prec],
         "data": "synthetic",
-        "config": {"workload": "10x10 OBC PEPS d=2 D=4, entries 0.5+0.1N(0,1), unit-norm tensors",
-                   "chi": args.chi, "mode": args.mode, "sweeps": 2, "precision": args.precision,
-                   "envs_per_step": envs, "l2": "flushed between steps (256 MiB write)",
+        "config": {"workload": W["desc"], "chi": chi, "mode": args.mode, "sweeps": 2, "precision": prec,
+                   "envs_per_step": envs,
+                   "l2": "flushed between steps (256 MiB write); the step's working set is far above L2",
                    "launch": f"recorded plan (CUDA graph of {plan.launches} kernels) replayed per step",
-                   "tuned": {"lanes": plan.lanes, "qr_cluster_max": plan.qr_cluster} if not args.no_tune else None,
-                   "parallelism": f"replicas x{world}"},
-        "e2e": {"value": round(e2e, 3), "unit": "envs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                   "tuned": {"lanes": plan.lanes, "qr_cluster_max": plan.qr_cluster} if args.tune else None,
+                   "plan_create_s": round(t_plan, 1), "parallelism": f"replicas x{world}"},
+        "e2e": {"value": round(e2e, 3), "unit": "envs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": len(etimes)},
         "gpu_launches": int(launches),
         "roofline": roof(dom),
-        "roofline_absorb": roof(absorb, prof1) if absorb != dom else None,
-        "replay_kernel_ms": {k: round(v["ms"], 3) for k, v in prof1.items() if v["launches"]},
+        "roofline_absorb": roof(absorb, prof1) if (prof1 and absorb != dom and prof1[absorb]["launches"]) else None,
+        "replay_kernel_ms": {k: round(v["ms"], 3) for k, v in prof1.items() if v["launches"]} if prof1 else None,
         "wall_s_timed": round(t_wall, 3),
     }
-    if cmp_ms is not None:
-        res["fp64_path"] = {"value": round(world * envs / (cmp_ms * 1e-3), 3), "unit": "envs/s",
-                            "ms_per_step": round(cmp_ms, 3)}
-        res["speedup_vs_fp64_path"] = round(cmp_ms / ms_step, 3)
-        res["accuracy"] = {"max_rel_err_vs_fp64_path": dev_err, "observables": 180,
-                           "metric": "|x-x_ref|/max(|x_ref|,1e-2) over <S.S> on every bond"}
-        res["other_precisions"] = others
+    if accuracy is not None:
+        res["accuracy"] = accuracy
+    if fp64 is not None:
+        res["fp64_path"] = fp64
+        if "ms_per_step" in fp64:
+            res["speedup_vs_fp64_path"] = round(fp64["ms_per_step"] / ms_step, 3)
     if cluster is not None:
         res["cluster"] = cluster
     if clk:
@@ -321,50 +384,45 @@ def run_ours(args, rank, world, dist):
     return res
 
 
+def _fp_weights(A):
+    from paper_1311_6696_gb300 import synth
+    return synth.uniform01(99, A.size).reshape(A.shape) - 0.5
+
+
 SD = [[0.25, 0, 0, 0], [0, -0.25, 0.5, 0], [0, 0.5, -0.25, 0], [0, 0, 0, 0.25]]
+SZ = [[1.0, 0.0], [0.0, -1.0]]
 
 
-def cluster_section(args, peps, synth, torch, st, flush):
+def cluster_section(args, peps, torch, st, flush):
     """Cluster environments of the 14x14 D=6 lattice (all 196 windows, chi=36,
     n in {2, 4, 6}) as recorded plans, with their deviation from the full
     chi=64 environments on sigma_z and <S.S> (every site and bond)."""
     import numpy as np
-    A = torch.from_numpy(synth.workload("14x14_D6")).cuda()
-    SZ = np.diag([1.0, -1.0])
+    prec = "tf32x3"
+    A = torch.from_numpy(load_input("14x14_D6")).cuda()
+    SZm = np.diag([1.0, -1.0])
 
     def obs(e):
-        return np.concatenate([e.expect("site", SZ), e.expect("hbond", SD), e.expect("vbond", SD)])
+        return np.concatenate([e.expect("site", SZm), e.expect("hbond", SD), e.expect("vbond", SD)])
 
-    ref = peps.env_full(A, chi=64, mode="var", precision=args.precision, stream=st)
+    ref = peps.env_full(A, chi=64, mode="var", precision=prec, stream=st)
     r = obs(ref)
     ref.free()
     out = {"workload": "14x14 OBC PEPS d=2 D=6, entries 0.5+0.1N(0,1), 196 windows, chi=36, var, "
-                       f"{args.precision}; reference: full environments at chi=64",
+                       f"{prec}; reference: full environments at chi=64",
            "per_n": {}}
     for n in (2, 4, 6):
         t0 = time.perf_counter()
-        plan = peps.Plan(A, chi=36, mode="var", precision=args.precision, cluster_n=n, stream=st,
-                         tune=not args.no_tune)
+        plan = peps.Plan(A, chi=36, mode="var", precision=prec, cluster_n=n, stream=st, tune=args.tune)
         t_create = time.perf_counter() - t0
         env = plan.env
         plan.run()
-        tms = []
-        for _ in range(2):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            plan.run()
-            o = obs(env)
-            e1.record(st)
-            e1.synchronize()
-            tms.append(e0.elapsed_time(e1))
+        tms = _timed(lambda: (plan.run(), obs(env)), st, 2, flush)
         ms = min(tms)
-        err = float(np.max(np.abs(o - r) / np.maximum(np.abs(r), 1e-2)))
+        o = obs(env)
         out["per_n"][str(n)] = {"envs_per_s": round(196 / (ms * 1e-3), 2), "ms": round(ms, 2),
-                                "launches": plan.launches, "max_rel_dev_vs_full_chi64": err,
-                                "tuned": {"lanes": plan.lanes, "qr_cluster_max": plan.qr_cluster}
-                                if not args.no_tune else None, "plan_create_s": round(t_create, 1)}
+                                "launches": plan.launches, "max_rel_dev_vs_full_chi64": _rel(o, r),
+                                "plan_create_s": round(t_create, 1)}
         del env
         plan.free()
     return out
@@ -383,47 +441,74 @@ def aggregate(ms_step, e_ms, envs_per_rank, world, dist=None, device=None):
     return ms_step, e_ms, value, e2e
 
 
-def cpu_sample(args, budget_s=20.0):
-    """The FP64 oracle as it stands, on a bounded sample of the same workload.
+def set_cost_model(L: int, t_step: float, t_open: float) -> float:
+    """Seconds of one environment set of an L x L lattice (var mode, two
+    half-sweeps) from the time of one site step of a fit (absorb chain,
+    closing contraction, QR, environment update) and of one site's density
+    matrices (site + right bond).  Each absorbed row costs (L-1) right
+    environments to start the fit and L site steps per half-sweep; each of the
+    2L row / column passes costs 2(L-1) environment steps and L open sites.
+    Every site is costed as an interior one (an upper bound: edge sites have
+    smaller bonds)."""
+    absorb = (L - 1) + 2 * L
+    return 4 * (L - 1) * absorb * t_step + 2 * L * (2 * (L - 1) * t_step + L * t_open)
 
-    Sample: top-down absorb+compress steps of interior rows until the budget is
-    spent, plus one row pass (row environments and all density matrices of that
-    row, with the boundary above it standing in for the one below, which has the
-    same shapes).  envs/s = Ly*Lx / (4 (L-1) t_absorb + 2 L t_row), i.e. the
-    full environment set's operation count: four directional sweeps of L-1 rows
-    and L row passes plus L column passes.
+
+def cpu_sample(args, budget_s=20.0):
+    """The FP64 oracle as it stands on a bounded sample of the same workload.
+
+    Sample: single site steps of the variational fit at the centre of an
+    interior row (absorb chain, closing contraction, QR, environment update)
+    and one open site (its density matrix and its right bond's), on the
+    workload's own site tensors with boundary and environment tensors of the
+    interior shapes (chi, D, D, chi) drawn at random -- the cost of a step
+    depends on the shapes only.  set_cost_model turns the times into the time
+    of the whole environment set.
     """
     import numpy as np
 
     from oracle import peps_oracle as O
-    from paper_1311_6696_gb300 import synth
 
-    A = synth.peps_gauss(WORKLOAD["Ly"], WORKLOAD["Lx"], WORKLOAD["d"], WORKLOAD["D"], WORKLOAD["seed"])
+    W = WORKLOADS[args.workload]
+    chi = args.chi or W["chi"]
+    A = load_input(W["name"])
     lat = O.lattice_from_dense(A)
-    L = WORKLOAD["Ly"]
-    T = O.closure_mps(lat.top)
-    ts = []
-    y = 0
+    L, Dv = W["Ly"], W["D"]
+    t_all = time.perf_counter()
+    y, x = L // 2, L // 2
+    Ay = lat.A[y]
+    rng = np.random.default_rng(0)
+
+    def bt():
+        return rng.standard_normal((chi, Dv, Dv, chi))
+
+    M, M2, Lenv, Renv, Bm, Bm2 = bt(), bt(), bt(), bt(), bt(), bt()
+    steps = []
     t_start = time.perf_counter()
-    while y < L - 1:
+    while True:
         t0 = time.perf_counter()
-        T, _ = O.absorb_compress(T, lat, y, args.chi, args.mode, 2, 0, 0)
-        dt = time.perf_counter() - t0
-        if y >= 1:
-            ts.append(dt)
-        y += 1
-        if time.perf_counter() - t_start > budget_s and len(ts) >= 1:
+        X3 = O.chain_left(Lenv, M, Ay[x])
+        b = O.close_left(X3, Renv)
+        cc, n, o, e = b.shape
+        Q, _ = np.linalg.qr(b.reshape(cc * n * o, e))
+        O.lenv_next(X3, Q.reshape(cc, n, o, Q.shape[1]))
+        steps.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start > 0.6 * budget_s or len(steps) >= 5:
             break
     t0 = time.perf_counter()
-    O._row_rhos(lat, T, T, y)
-    t_row = time.perf_counter() - t0
-    t_abs = float(np.median(ts))
-    t_set = 4 * (L - 1) * t_abs + 2 * L * t_row
+    O.rho_site(Lenv, Renv, M, Ay[x], Bm)
+    O.rho_hbond(Lenv, Renv, M, Ay[x], Bm, M2, Ay[x + 1], Bm2)
+    t_open = time.perf_counter() - t0
+    t_step = float(np.median(steps))
+    t_set = set_cost_model(L, t_step, t_open)
     cores = _blas_threads()
-    return {"value": round(L * L / t_set, 5), "unit": "envs/s", "cores": cores, "kind": "oracle",
-            "sample": f"{len(ts)} interior absorb+compress steps (median {t_abs:.2f} s) and one row pass "
-                      f"({t_row:.2f} s) of the same 10x10 D=4 chi={args.chi} {args.mode} workload, "
-                      f"extrapolated to the full environment set (4x{L-1} absorbs + {2*L} row passes)"}
+    return {"value": round(L * L / t_set, 6), "unit": "envs/s", "cores": cores, "kind": "oracle",
+            "set_seconds": round(t_set, 1), "sample_wall_s": round(time.perf_counter() - t_all, 1),
+            "sample": f"{len(steps)} interior site steps of the variational fit (median {t_step:.2f} s: "
+                      f"absorb chain, closing contraction, QR, environment update) and one open site "
+                      f"({t_open:.2f} s) of the same {L}x{L} D={Dv} chi={chi} {args.mode} workload, "
+                      f"costed up to the whole environment set by operation count "
+                      f"(bench.set_cost_model: every site as an interior one)"}
 
 
 def _blas_threads():
@@ -438,26 +523,55 @@ def _blas_threads():
 
 
 def run_reference(args):
-    steps = []
-    cb = None
+    W = WORKLOADS[args.workload]
+    chi = args.chi or W["chi"]
+    vals, cb = [], None
+    t_wall = time.perf_counter()
     for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
         cb = cpu_sample(args, budget_s=args.ref_budget)
         if i >= args.warmup:
-            steps.append((time.perf_counter() - t0, cb["value"]))
-    v = statistics.mean(s[1] for s in steps)
+            vals.append(cb["value"])
+    v = statistics.mean(vals)
+    envs = W["Ly"] * W["Lx"]
     return {
         "impl": "reference",
         "metric": "PEPS site environments/sec (full boundary-MPS envs + <S.S> on all bonds)",
-        "value": round(v, 5), "unit": "envs/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(1e3 * statistics.mean(s[0] for s in steps), 1), "higher_is_better": True,
+        "value": round(v, 6), "unit": "envs/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * envs / v, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "10x10 OBC PEPS d=2 D=4, entries 0.5+0.1N(0,1), unit-norm tensors",
-                   "chi": args.chi, "mode": args.mode, "sweeps": 2, "precision": "fp64"},
-        "cpu_baseline": {"value": round(v, 5), "unit": "envs/s", "cores": cb["cores"], "kind": "oracle",
+        "config": {"workload": W["desc"], "chi": chi, "mode": args.mode, "sweeps": 2, "precision": "fp64",
+                   "step": "one whole environment set, costed from a timed sample (see cpu_baseline)"},
+        "cpu_baseline": {"value": round(v, 6), "unit": "envs/s", "cores": cb["cores"], "kind": "oracle",
                          "sample": cb["sample"]},
-        "e2e": {"value": round(v, 5), "unit": "envs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "e2e": {"value": round(v, 6), "unit": "envs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": round(time.perf_counter() - t_wall, 1),
     }
+
+
+def _measure_peaks():
+    """FP64 and TF32 dense peaks of this GPU (torch matmul 8192^3, best of 3,
+    CUDA events); the BF16 peak is MEASURED_PEAKS.json's."""
+    import torch
+    global FP64_PEAK_TFLOPS, TF32_PEAK_TFLOPS
+    try:
+        n = 8192
+        old = torch.backends.cuda.matmul.allow_tf32
+        for dt, tf32 in ((torch.float64, False), (torch.float32, True)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            a = torch.randn(n, n, device="cuda", dtype=dt)
+            b = torch.randn(n, n, device="cuda", dtype=dt)
+            a @ b
+            best = min(_timed(lambda: a @ b, torch.cuda.current_stream(), 3))
+            tf = 2 * n ** 3 / (best * 1e-3) / 1e12
+            if dt == torch.float64:
+                FP64_PEAK_TFLOPS = tf
+            else:
+                TF32_PEAK_TFLOPS = tf
+            del a, b
+        torch.backends.cuda.matmul.allow_tf32 = old
+        torch.cuda.empty_cache()
+    except Exception:
+        pass
 
 
 def main():
@@ -466,16 +580,18 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--chi", type=int, default=64)
+    ap.add_argument("--workload", default="c4", choices=sorted(WORKLOADS))
+    ap.add_argument("--chi", type=int, default=None, help="default: the workload's")
     ap.add_argument("--mode", default="var", choices=["var", "svd"])
-    ap.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32", "bf16", "tf32x3", "bf16x3"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "tf32", "bf16", "tf32x3", "bf16x3"])
     ap.add_argument("--no-fp64-compare", action="store_true")
-    ap.add_argument("--dominant", default=None, help="kernel class timed for the roofline")
+    ap.add_argument("--dominant", default=None, help="kernel class timed for the roofline (skips the probe replay)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-cluster", action="store_true", help="skip the 14x14 D=6 cluster section")
-    ap.add_argument("--no-tune", action="store_true", help="record the plan with the default launch configuration")
+    ap.add_argument("--cluster", action="store_true", help="add the 14x14 D=6 cluster section")
+    ap.add_argument("--tune", action="store_true", help="choose the plan's launch configuration by measurement")
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
-    ap.add_argument("--ref-budget", type=float, default=10.0)
+    ap.add_argument("--ref-budget", type=float, default=20.0)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -490,6 +606,7 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         tdist.init_process_group("nccl")
         dist = tdist
+    _measure_peaks()
     res = run_ours(args, rank, world, dist)
     if res is not None:
         print(json.dumps(res), flush=True)

@@ -154,7 +154,7 @@ __global__ void k_var_init(const VarInitArgs a) {
     t /= a.d2;
     const int i1 = int(t % a.d1);
     const int i0 = int(t / a.d1);
-    const bool inside = i0 < a.s0 && i1 < a.s1 && i2 < a.s1 && i2 < a.s2 && i3 < a.s3;
+    const bool inside = i0 < a.s0 && i1 < a.s1 && i2 < a.s2 && i3 < a.s3;
     if (inside) {
       dst[e] = src[(((long long)i0 * a.s1 + i1) * a.s2 + i2) * a.s3 + i3];
     } else {

@@ -279,9 +279,27 @@ def cu0_noalloc(A_dev, sigma_dev, stream=None):
     """Top-down CU_0 boundaries into a caller-owned device tensor, with no
     device allocation (see peps_cu0_noalloc).  A_dev: contiguous float64 CUDA
     tensor (Ly,Lx,d,D,D,D,D); sigma_dev: float64 CUDA tensor (Ly,Lx,D,D)."""
+    import torch
+    # The C side reads and writes these buffers by the sizes alone, so every
+    # property it relies on is checked here, before anything is launched.
+    if A_dev.dim() != 7:
+        raise ValueError(f"A must have 7 dimensions (Ly,Lx,d,D,D,D,D), got {tuple(A_dev.shape)}")
     Ly, Lx, d, D = (int(v) for v in A_dev.shape[:4])
-    assert A_dev.is_contiguous() and sigma_dev.is_contiguous()
-    assert tuple(sigma_dev.shape) == (Ly, Lx, D, D)
+    if tuple(A_dev.shape[3:]) != (D,) * 4:
+        raise ValueError(f"A's four virtual legs must all have dimension D={D}, got {tuple(A_dev.shape)}")
+    if tuple(sigma_dev.shape) != (Ly, Lx, D, D):
+        raise ValueError(f"sigma must have shape {(Ly, Lx, D, D)}, got {tuple(sigma_dev.shape)}")
+    for name, t in (("A", A_dev), ("sigma", sigma_dev)):
+        if t.dtype != torch.float64:
+            raise TypeError(f"{name} must be float64, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    for name, t in (("A", A_dev), ("sigma", sigma_dev)):
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is "
+                             f"cuda:{torch.cuda.current_device()}")
     _check(lib.peps_cu0_noalloc(A_dev.data_ptr(), Ly, Lx, d, D, sigma_dev.data_ptr(), _stream_ptr(stream)))
 
 

@@ -185,24 +185,49 @@ def _su_pair(Ga, Gb, lam_a, lam_b, lam_ab, gate, D):
     Qa, Ra = np.linalg.qr(Am)                         # Ra: (n, k, d*D)
     Qb, Rb = np.linalg.qr(Bm)
     k = Ra.shape[1]
-    Ra = Ra.reshape(n, k, d, D)
-    Rb = Rb.reshape(n, k, d, D)
-    th = np.einsum("nasr,nbtr->nasbt", Ra, Rb)        # shared bond contracted
-    G4 = gate.reshape(d, d, d, d)                     # [s', t', s, t]
-    th = np.einsum("pqst,nasbt->napbq", G4, th).reshape(n, k * d, k * d)
+    # shared bond contracted: th[a,s,b,t] = sum_r Ra[a,s,r] Rb[b,t,r]
+    th = np.matmul(Ra.reshape(n, k * d, D), Rb.reshape(n, k * d, D).transpose(0, 2, 1))
+    # gate on (s, t): th'[a,p,b,q] = sum_st G[p,q,s,t] th[a,s,b,t]
+    th = th.reshape(n, k, d, k, d).transpose(0, 1, 3, 2, 4).reshape(n * k * k, d * d)
+    th = (th @ gate.T).reshape(n, k, k, d, d).transpose(0, 1, 3, 2, 4).reshape(n, k * d, k * d)
     U, S, Vt = np.linalg.svd(th)
     S = S[:, :D]
     lam = S / S[:, :1]
-    Ua = U[:, :, :D].reshape(n, k, d, D)              # [a, s', r]
-    Vb = Vt[:, :D, :].reshape(n, D, k, d)             # [r, b, t']
-    An = np.einsum("nia,nasr->nisr", Qa, Ua).reshape(n, D, D, D, d, D)
-    Bn = np.einsum("nib,nrbt->nitr", Qb, Vb).reshape(n, D, D, D, d, D)
+    Ua = U[:, :, :D]                                  # [(a, s'), r]
+    Vb = Vt[:, :D, :]                                 # [r, (b, t')]
+    # back to site tensors: An[i,s',r] = sum_a Qa[i,a] Ua[a,s',r], Bn[i,t',r] likewise
+    An = np.matmul(Qa, Ua.reshape(n, k, d * D)).reshape(n, D, D, D, d, D)
+    Bn = np.matmul(Qb, Vb.reshape(n, D, k, d).transpose(0, 2, 3, 1).reshape(n, k, d * D)).reshape(n, D, D, D, d, D)
     Ga = An.transpose(0, 4, 1, 2, 3, 5) * inv(lu)[:, None, :, None, None, None] \
         * inv(ll)[:, None, None, :, None, None] * inv(ld)[:, None, None, None, :, None]
     # Bn: [(u, dn, r), t, l] -> [t, u, l, dn, r]
     Gb = Bn.transpose(0, 4, 1, 5, 2, 3) * inv(ru)[:, None, :, None, None, None] \
         * inv(rd)[:, None, None, None, :, None] * inv(rr)[:, None, None, None, None, :]
     return Ga, Gb, lam
+
+
+_POOL = None
+
+
+def _su_pairs(Ga, Gb, lam_a, lam_b, lam_ab, gate, D):
+    """_su_pair over chunks of the independent pairs on a thread pool (numpy's
+    batched linear algebra runs one matrix at a time and releases the GIL);
+    every pair's arithmetic is the same as in one batch."""
+    global _POOL
+    import concurrent.futures as cf
+    import os
+    n = Ga.shape[0]
+    workers = min(16, os.cpu_count() or 1)
+    if workers <= 1 or n < 2 * workers:
+        return _su_pair(Ga, Gb, lam_a, lam_b, lam_ab, gate, D)
+    if _POOL is None:
+        _POOL = cf.ThreadPoolExecutor(max_workers=workers)
+    cuts = np.linspace(0, n, workers + 1).astype(int)
+    parts = [(a, b) for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+    futs = [_POOL.submit(_su_pair, Ga[a:b], Gb[a:b], tuple(l[a:b] for l in lam_a),
+                         tuple(l[a:b] for l in lam_b), lam_ab[a:b], gate, D) for a, b in parts]
+    res = [f.result() for f in futs]
+    return tuple(np.concatenate([r[i] for r in res]) for i in range(3))
 
 
 def peps_simple_update(Ly: int, Lx: int, D: int, seed: int, tau: float = 0.01, steps: int = 400,
@@ -255,7 +280,7 @@ def peps_simple_update(Ly: int, Lx: int, D: int, seed: int, tau: float = 0.01, s
                       np.stack([lam_dn(y, x) for y, x in bonds]))
                 lb = (np.stack([lam_up(y, x + 1) for y, x in bonds]), np.stack([lam_dn(y, x + 1) for y, x in bonds]),
                       np.stack([lam_rt(y, x + 1) for y, x in bonds]))
-                Ga, Gb, lam = _su_pair(Ga, Gb, la, lb, lh[ys, xs], gate, D)
+                Ga, Gb, lam = _su_pairs(Ga, Gb, la, lb, lh[ys, xs], gate, D)
                 G[ys, xs], G[ys, xs + 1], lh[ys, xs] = Ga, Gb, lam
         for par in (0, 1):
             bonds = vset(par)
@@ -270,7 +295,7 @@ def peps_simple_update(Ly: int, Lx: int, D: int, seed: int, tau: float = 0.01, s
                       np.stack([lam_rt(y, x) for y, x in bonds]))
                 lb = (np.stack([lam_lt(y + 1, x) for y, x in bonds]), np.stack([lam_rt(y + 1, x) for y, x in bonds]),
                       np.stack([lam_dn(y + 1, x) for y, x in bonds]))
-                Ga, Gb, lam = _su_pair(Ga, Gb, la, lb, lv[ys, xs], gate, D)
+                Ga, Gb, lam = _su_pairs(Ga, Gb, la, lb, lv[ys, xs], gate, D)
                 G[ys, xs] = Ga.transpose(0, 1, 3, 2, 5, 4)
                 G[ys + 1, xs] = Gb.transpose(0, 1, 3, 2, 5, 4)
                 lv[ys, xs] = lam

@@ -46,3 +46,27 @@ def test_bond_caps_rule_matches_oracle():
     assert O.bond_caps([16] * 10, [256] * 9, 64) == [16, 64, 64, 64, 64, 64, 64, 64, 16]
     assert O.bond_caps([1, 1], [1], 8) == [1]
     assert O.bond_caps([4, 4, 4], [16, 16], 2) == [2, 2]
+
+
+def test_cu0_noalloc_wrapper_rejects_bad_inputs_before_any_launch():
+    """The C side of peps_cu0_noalloc trusts the sizes it is given, so the
+    binding checks rank, shapes, dtype, contiguity and device first (each case
+    here fails on the host, before the library is called)."""
+    torch = pytest.importorskip("torch")
+    from paper_1311_6696_gb300 import peps
+    f64 = torch.float64
+    good_A = torch.zeros((3, 4, 2, 3, 3, 3, 3), dtype=f64)
+    good_s = torch.zeros((3, 4, 3, 3), dtype=f64)
+    cases = [
+        (torch.zeros((3, 4, 2, 3, 3, 3), dtype=f64), good_s, ValueError),          # rank 6
+        (torch.zeros((3, 4, 2, 3, 3, 2, 3), dtype=f64), good_s, ValueError),       # ragged legs
+        (good_A, torch.zeros((3, 4, 3, 2), dtype=f64), ValueError),               # sigma shape
+        (good_A.float(), good_s, TypeError),                                       # float32 A
+        (good_A, good_s.float(), TypeError),                                       # float32 sigma
+        (good_A.transpose(0, 1).contiguous().transpose(0, 1), good_s, ValueError),  # not contiguous
+    ]
+    if not torch.cuda.is_available():
+        cases.append((good_A, good_s, ValueError))                                 # host tensors
+    for A, s, exc in cases:
+        with pytest.raises(exc):
+            peps.cu0_noalloc(A, s)

@@ -63,3 +63,27 @@ def test_reference_arm_prints_on_rank0_only(tmp_path):
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                         "--warmup", "0"], capture_output=True, text=True, env=env, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_set_cost_model_counts_the_operations():
+    """One environment set of an L x L lattice: 4 sweeps of L-1 absorbs, each
+    (L-1) right environments + 2 half-sweeps of L site steps; 2L passes of
+    2(L-1) environment steps and L open sites."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.set_cost_model(3, 1.0, 0.0) == 4 * 2 * (2 + 6) + 2 * 3 * 4
+    assert bench.set_cost_model(3, 0.0, 1.0) == 2 * 3 * 3
+    assert bench.set_cost_model(20, 2.0, 5.0) == 4 * 19 * 59 * 2.0 + 40 * (38 * 2.0 + 20 * 5.0)
+
+
+def test_reference_arm_step_time_is_the_time_of_its_value():
+    """The reference arm's ms_per_step is the time of one whole environment set
+    at the throughput it reports (not the time of its sample)."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "c2",
+                        "--steps", "1", "--warmup", "0", "--ref-budget", "1"],
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "envs/s"
+    assert abs(line["ms_per_step"] - 1e3 * 100 / line["value"]) <= 1e-3 * line["ms_per_step"] + 0.1
+    assert line["e2e"]["value"] == line["value"] and line["cpu_baseline"]["kind"] == "oracle"

@@ -1,0 +1,276 @@
+"""GPU parity at the sizes the product runs: the CUDA path against the FP64
+oracle on the benchmark workloads themselves.
+
+* 10x10 D=4 at chi=64, var (the full-environment workload at its largest
+  chi): the FP64 path at 1e-10 on every normalised density-matrix entry,
+  expectation value and ln|<psi|psi>|; the split tensor-core paths at 1e-4 on
+  the local observables.  Here the 16-CTA cluster QR (1024 x 64), the split-K
+  tensor-core shapes and the skipped start gauge pass of the variational fit
+  all run.
+* 14x14 D=6 at chi=36, the cluster workload: n=2 on every window, n=4 on a
+  sample of windows (corners, edges, interior), FP64 at 1e-10.
+* 4x5 D=8 at chi=64, var: QRs of 4096 x 64 on the largest clusters.
+* The learned closure with trained (non-zero) weights: the GPU cluster
+  environments against the oracle's cluster contraction with rims from the
+  FP64 network evaluated on the same weights (the GPU network runs in BF16).
+* The 20x20 D=8 simple-update workload at chi=128 (the benchmark headline)
+  against a stored oracle result (tests/golden/make_oracle_golden.py): ln N
+  and the last row's observables.
+
+Tolerances are the same as in test_gpu_parity.py: 1e-10 for the FP64 path, and
+1e-4 (the target for the mixed-precision paths) on |x - x_ref| / max(|x_ref|, 1e-2).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import closure_oracle as CO
+from oracle import peps_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+TOL_TC = 1e-4
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def peps():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1311_6696_gb300 import peps as P
+    return P
+
+
+def _rel(a, b):
+    a = np.asarray(a, dtype=float)
+    b = np.asarray(b, dtype=float)
+    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-2))) if a.size else 0.0
+
+
+def _norm_rhos(r):
+    return r / np.trace(r, axis1=1, axis2=2)[:, None, None]
+
+
+def _oracle_rhos(env, kind, anchors=None, Lx=None):
+    key = {"site": "rho_site", "hbond": "rho_h", "vbond": "rho_v"}[kind]
+    out = []
+    for y, row in enumerate(env[key]):
+        for x, r in enumerate(row):
+            if r is None:
+                continue
+            k = int(round(np.sqrt(r.size)))
+            m = r.reshape(k, k)
+            out.append(m / np.trace(m))
+    return np.array(out)
+
+
+OBS = (("site", O.SZ), ("site", O.SX), ("hbond", O.SDOTS), ("vbond", O.SDOTS))
+
+
+def _observables(genv):
+    return {(k, i): genv.expect(k, op) for i, (k, op) in enumerate(OBS)}
+
+
+def _oracle_observables(oenv):
+    return {(k, i): np.array(O.expect_all(oenv, k, op), dtype=float) for i, (k, op) in enumerate(OBS)}
+
+
+# ------------------------------------------------------------------ 10x10 D=4, chi=64
+@pytest.fixture(scope="module")
+def c2_oracle():
+    from paper_1311_6696_gb300 import synth
+    A = synth.workload("10x10_D4")
+    return A, O.env_full(A, chi=64, mode="var")
+
+
+def test_10x10_D4_chi64_var_fp64_path(peps, c2_oracle):
+    A, ref = c2_oracle
+    g = peps.env_full(A, chi=64, mode="var", precision="fp64")
+    for kind in ("site", "hbond", "vbond"):
+        assert _rel(_norm_rhos(g.rho(kind)), _oracle_rhos(ref, kind)) < TOL, kind
+    go, ro = _observables(g), _oracle_observables(ref)
+    for key in go:
+        assert _rel(go[key], ro[key]) < TOL, key
+    ln, sg = g.ln_norm()
+    assert abs(ln - ref["ln_norm"]) < TOL and sg == ref["sign"]
+
+
+@pytest.mark.parametrize("precision", ["tf32x3", "bf16x3"])
+def test_10x10_D4_chi64_var_tensor_cores(peps, c2_oracle, precision):
+    A, ref = c2_oracle
+    g = peps.env_full(A, chi=64, mode="var", precision=precision)
+    go, ro = _observables(g), _oracle_observables(ref)
+    for key in go:
+        assert _rel(go[key], ro[key]) < TOL_TC, (precision, key, _rel(go[key], ro[key]))
+    ln, _ = g.ln_norm()
+    assert abs(ln - ref["ln_norm"]) < TOL_TC
+
+
+def test_10x10_D4_chi64_recorded_plan(peps, c2_oracle):
+    """The benchmark's own launch configuration: a tuned recorded plan
+    (one CUDA graph) on a device lattice, replayed twice."""
+    import torch
+    A, ref = c2_oracle
+    plan = peps.Plan(torch.from_numpy(A).cuda(), chi=64, mode="var", precision="tf32x3", tune=True)
+    for _ in range(2):
+        e = plan.run()
+        go, ro = _observables(e), _oracle_observables(ref)
+        for key in go:
+            assert _rel(go[key], ro[key]) < TOL_TC, key
+
+
+# ------------------------------------------------------------------ 14x14 D=6, chi=36 clusters
+def _cluster_compare(genv, oenv, anchors, Lx, Ly, tol):
+    gs = _norm_rhos(genv.rho("site"))
+    gh = _norm_rhos(genv.rho("hbond"))
+    gv = _norm_rhos(genv.rho("vbond"))
+    for (y, x) in anchors:
+        r = oenv["rho_site"][y][x]
+        assert _rel(gs[y * Lx + x], r / np.trace(r)) < tol, ("site", y, x)
+        if x + 1 < Lx:
+            r = oenv["rho_h"][y][x].reshape(4, 4)
+            assert _rel(gh[y * (Lx - 1) + x], r / np.trace(r)) < tol, ("hbond", y, x)
+        if y + 1 < Ly:
+            r = oenv["rho_v"][y][x].reshape(4, 4)
+            assert _rel(gv[y * Lx + x], r / np.trace(r)) < tol, ("vbond", y, x)
+
+
+@pytest.mark.parametrize("n,sample", [(2, False), (4, True)])
+def test_14x14_D6_chi36_clusters_fp64(peps, n, sample):
+    from paper_1311_6696_gb300 import synth
+    A = synth.workload("14x14_D6")
+    L = 14
+    if sample:
+        anchors = [(0, 0), (0, 13), (13, 0), (13, 13), (0, 6), (6, 0), (13, 7), (7, 13), (6, 6), (7, 8),
+                   (1, 12), (12, 2)]
+    else:
+        anchors = [(y, x) for y in range(L) for x in range(L)]
+    g = peps.env_cluster(A, n=n, chi=36, mode="var", precision="fp64")
+    ref = O.env_cluster(A, n=n, chi=36, mode="var", anchors=anchors)
+    _cluster_compare(g, ref, anchors, L, L, TOL)
+
+
+def test_14x14_D6_chi36_n2_tensor_cores(peps):
+    from paper_1311_6696_gb300 import synth
+    A = synth.workload("14x14_D6")
+    anchors = [(y, x) for y in range(14) for x in range(14)]
+    g = peps.env_cluster(A, n=2, chi=36, mode="var", precision="tf32x3")
+    ref = O.env_cluster(A, n=2, chi=36, mode="var", anchors=anchors)
+    go = np.concatenate([g.expect("site", O.SZ), g.expect("hbond", O.SDOTS), g.expect("vbond", O.SDOTS)])
+    ro = np.concatenate([O.expect_all(ref, "site", O.SZ), O.expect_all(ref, "hbond", O.SDOTS),
+                         O.expect_all(ref, "vbond", O.SDOTS)]).astype(float)
+    assert _rel(go, ro) < TOL_TC
+
+
+# ------------------------------------------------------------------ D=8
+@pytest.fixture(scope="module")
+def d8_oracle():
+    from paper_1311_6696_gb300 import synth
+    A = synth.peps_gauss(4, 5, 2, 8, seed=88)
+    return A, O.env_full(A, chi=64, mode="var", seed=5)
+
+
+def test_4x5_D8_chi64_var_fp64_path(peps, d8_oracle):
+    A, ref = d8_oracle
+    g = peps.env_full(A, chi=64, mode="var", seed=5, precision="fp64")
+    for kind in ("site", "hbond", "vbond"):
+        assert _rel(_norm_rhos(g.rho(kind)), _oracle_rhos(ref, kind)) < TOL, kind
+    ln, sg = g.ln_norm()
+    assert abs(ln - ref["ln_norm"]) < TOL and sg == ref["sign"]
+
+
+def test_4x5_D8_chi64_var_bf16x3(peps, d8_oracle):
+    A, ref = d8_oracle
+    g = peps.env_full(A, chi=64, mode="var", seed=5, precision="bf16x3")
+    go, ro = _observables(g), _oracle_observables(ref)
+    for key in go:
+        assert _rel(go[key], ro[key]) < TOL_TC, key
+
+
+# ------------------------------------------------------------------ learned closure, trained weights
+def _oracle_learned_rims(A, w64, D, width):
+    """CU_0 rims with every outward leg (orientation, cut r >= 1, column)
+    replaced by the FP64 network's prediction on the oracle's own features
+    (site tensor above the cut zero-padded to D, sigma0, its Cholesky factor)."""
+    lat = O.lattice_from_dense(A)
+    cu0 = O.cu0_all(lat)
+    d = A.shape[2]
+    F = d * D ** 4 + 2 * D * D
+    feats, where = [], []
+    for o, lo in enumerate(O.orientations(lat)):
+        for r in range(1, lo.Ly):
+            for x in range(lo.Lx):
+                site = np.zeros((d, D, D, D, D))
+                t = lo.A[r - 1][x]
+                site[:, :t.shape[1], :t.shape[2], :t.shape[3], :t.shape[4]] = t
+                s0 = cu0[o][r][x]
+                L0 = np.linalg.cholesky(s0 + 1e-12 * np.eye(D))
+                feats.append(np.concatenate([site.ravel(), s0.ravel(), np.tril(L0).ravel()]))
+                where.append((o, r, x))
+    sig, _ = CO.forward(w64, np.array(feats), F, width, D)
+    new = [[[m for m in row] for row in side] for side in cu0]
+    for (o, r, x), s in zip(where, sig):
+        if np.all(np.isfinite(s)) and np.trace(s) > 0:
+            new[o][r][x] = s
+    return lat, new
+
+
+def test_learned_closure_with_trained_weights_matches_the_oracle(peps):
+    import torch
+    from paper_1311_6696_gb300 import synth
+    D, n, chi = 2, 2, 8
+    Xs, Ys = [], []
+    for seed in (300, 301):
+        X, Y = peps.closure_data(synth.peps_simple_update(5, 5, D, seed=seed, steps=80), chi=16, mode="svd")
+        Xs.append(X)
+        Ys.append(Y)
+    X, Y = torch.cat(Xs), torch.cat(Ys)
+    w = peps.mlp_init(2, D, peps.CLOSURE_WIDTH, seed=11)
+    peps.mlp_train(w, X, Y, 2, D, steps=200, batch=128, lr=1e-3, seed=11)
+    w64 = w.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(w64[-(D * D * (peps.CLOSURE_WIDTH + 1)):])) > 0     # the output layer moved
+
+    A = synth.peps_simple_update(5, 5, D, seed=302, steps=80)
+    g = peps.env_cluster(A, n=n, chi=chi, mode="var", closure_weights=w)
+    lat, rims = _oracle_learned_rims(A, w64, D, peps.CLOSURE_WIDTH)
+    L = 5
+    for y in range(L):
+        for x in range(L):
+            W, (r0, _, c0, _) = O.window_lattice(lat, rims, y, x, n)
+            s, h, v = O.cluster_anchor(W, y - r0, x - c0, chi, "var", 2, 0)
+            assert _rel(g.expect("site", O.SZ)[y * L + x], O.expect(s, O.SZ)) < TOL_TC, (y, x)
+            if x + 1 < L:
+                assert _rel(g.expect("hbond", O.SDOTS)[y * (L - 1) + x], O.expect(h, O.SDOTS)) < TOL_TC
+            if y + 1 < L:
+                assert _rel(g.expect("vbond", O.SDOTS)[y * L + x], O.expect(v, O.SDOTS)) < TOL_TC
+    # and the learned rims are not the plain ones (the test would be vacuous otherwise)
+    plain = peps.env_cluster(A, n=n, chi=chi, mode="var")
+    assert np.max(np.abs(plain.expect("hbond", O.SDOTS) - g.expect("hbond", O.SDOTS))) > 1e-6
+
+
+# ------------------------------------------------------------------ 20x20 D=8 simple update, chi=128
+def test_20x20_D8_su_chi128_against_stored_oracle(peps):
+    """The benchmark's headline configuration (bf16x3 absorb, FP64 QR, chi=128)
+    against the oracle's ln N and last-row observables, computed once by
+    tests/golden/make_oracle_golden.py from the same generator."""
+    path = os.path.join(HERE, "golden", "oracle_20x20_D8_su_chi128.json")
+    if not os.path.exists(path):
+        pytest.skip("stored oracle result not present")
+    import torch
+    from paper_1311_6696_gb300 import synth
+    gold = json.load(open(path))
+    A = synth.workload("20x20_D8_su")
+    w = synth.uniform01(99, A.size).reshape(A.shape) - 0.5
+    assert abs(float(np.sum(A * w)) - gold["input"]["wsum"]) < 1e-9 * max(1.0, abs(gold["input"]["wsum"]))
+    g = peps.env_full(torch.from_numpy(A).cuda(), chi=128, mode="var", precision="bf16x3")
+    y = gold["row"]
+    sz = g.expect("site", O.SZ).reshape(20, 20)[y]
+    ss = g.expect("hbond", O.SDOTS).reshape(20, 19)[y]
+    assert _rel(sz, gold["sz"]) < TOL_TC
+    assert _rel(ss, gold["sdots_h"]) < TOL_TC
+    ln, sg = g.ln_norm()
+    assert abs(ln - gold["ln_norm"]) < TOL_TC and sg == gold["sign"]

@@ -403,3 +403,62 @@ def test_cluster_error_shrinks_with_window_size():
     errs = [float(np.mean(np.abs(bonds(O.env_cluster(A, n=n, chi=16, mode="svd")) - ref))) for n in (2, 3, 4, 6)]
     assert all(a > 2 * b for a, b in zip(errs, errs[1:])), errs
     assert float(np.max(np.abs(bonds(O.env_cluster(A, n=12, chi=16, mode="svd")) - ref))) == 0.0
+
+
+def _dense_top_boundary(Ad, rows):
+    """The exact boundary below the first `rows` rows as a dense vector over
+    the sites' (ket down leg, bra down leg) pairs, site 0 most significant:
+    the ket of those rows with open physical and down legs (brute force, no
+    MPS), contracted with its own copy over every physical index."""
+    from oracle import bruteforce as BF
+    Lx, D = Ad.shape[1], Ad.shape[3]
+    lat = BF.dense_lattice(Ad[:rows].copy())
+    # the last kept row's down legs are interior: give them their real dimension
+    last = [np.array(Ad[rows - 1, x, :, :(1 if rows == 1 else D), :(1 if x == 0 else D), :D,
+                        :(1 if x == Lx - 1 else D)]) for x in range(Lx)]
+    lat[rows - 1] = last
+    psi = np.ones((1, 1))                                   # [S so far, open down legs]
+    for row in lat:
+        R = BF._row_tensor(row)                             # [S, U, N]
+        psi = np.einsum("pu,sun->psn", psi, R).reshape(-1, R.shape[2])
+    B = psi.T @ psi                                         # [N ket, N bra]
+    B = B.reshape([D] * Lx + [D] * Lx)
+    order = [i for x in range(Lx) for i in (x, Lx + x)]     # (n_x, o_x) per site
+    return B.transpose(order).reshape(-1)
+
+
+def _mps_to_dense(P):
+    v = P[0]
+    for M in P[1:]:
+        v = np.tensordot(v, M, axes=([v.ndim - 1], [0]))
+    return v.reshape(-1)
+
+
+def test_svd_truncation_is_sequential_eckart_young_on_the_dense_boundary():
+    """svd mode at truncated chi (Section 2: the new boundary is the best MPS
+    of bond chi, here by the SVD sweep): after the two top rows of a 3x5 D=2
+    lattice the product boundary has bond 16 and chi=8 truncates cuts 1 and
+    2.  A right-to-left SVD sweep over a left-canonical MPS is, cut by cut,
+    the best rank-k approximation (Eckart-Young) of the current state across
+    that cut; the same truncations done on the dense 4^5 vector with nothing
+    but a matrix SVD must give the oracle's boundary."""
+    from oracle import peps_oracle as O
+    from paper_1311_6696_gb300 import synth
+    Ad = synth.peps_gauss(3, 5, 2, 2, seed=31, mean=0.0, std=1.0)   # far from a product state
+    chi = 8
+    bounds, _ = O.boundary_sweep(O.lattice_from_dense(Ad), chi, "svd", upto=2)
+    got = _mps_to_dense(bounds[2])
+    assert [M.shape[3] for M in bounds[2][:-1]] == [4, 8, 8, 4]
+    psi = _dense_top_boundary(Ad, 2)
+    Lx, p = 5, 4
+    caps = [4, 8, 8, 4]
+    for k in range(Lx - 2, -1, -1):                          # cut k: sites 0..k | k+1..
+        M = psi.reshape(p ** (k + 1), -1)
+        U, S, Vt = np.linalg.svd(M, full_matrices=False)
+        r = caps[k]
+        psi = ((U[:, :r] * S[:r]) @ Vt[:r]).reshape(-1)
+    # something was truncated (the test is not the exact case)
+    assert np.linalg.norm(psi - _dense_top_boundary(Ad, 2)) > 1e-3 * np.linalg.norm(psi)
+    want = psi / np.linalg.norm(psi)
+    got = got / np.linalg.norm(got)
+    assert np.max(np.abs(got - want)) < 1e-10

@@ -4,10 +4,14 @@ existing peps_env_cluster.
 Callers that cannot allocate device memory (an allocator that already holds
 the memory, a latency-critical loop, a framework that forbids allocation)
 get the CU_0 separable boundaries from peps_cu0_noalloc, whose scratch is a
-static device array.  With n = 1 every cluster window is a single site closed
-by exactly these boundaries on its four sides, so the site density matrices
-of peps_env_cluster(n=1) must follow from the new call's output.  The check
-runs two calls in a row, since every call reuses the same scratch.
+static device array.  Two checks, each over two calls in a row (every call
+reuses the same scratch):
+
+* the matrices themselves against the FP64 oracle's CU_0 sweep (Section 5.1),
+  including a case whose sizes fill the whole scratch array (d=4, D=8, Lx=64);
+* with n = 1 every cluster window is a single site closed by exactly these
+  boundaries on its four sides, so the site density matrices of
+  peps_env_cluster(n=1) must follow from the new call's output.
 
 This file is named to be collected last: if it fails, a run that stops at the
 first failure has already run every other test.
@@ -80,6 +84,30 @@ def test_noalloc_cu0_matches_cluster_n1_two_calls(env):
         got = _site_rhos(A, _sigmas(torch, peps, A, stream))
         err = np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1e-2))
         assert err < TOL, err
+
+
+@pytest.mark.parametrize("Ly,Lx,d,D,seed", [(6, 5, 2, 3, 77), (3, 64, 4, 8, 78)])
+def test_noalloc_cu0_matches_the_oracle_two_calls(env, Ly, Lx, d, D, seed):
+    """sigma[r][x] of every cut against the oracle's top-down CU_0 sweep; the
+    second case needs 8 + 3 d D^4 + 4 Lx D^2 + D^2 = 65,608 words, the whole
+    static scratch."""
+    torch, peps = env
+    from oracle import peps_oracle as O
+    from paper_1311_6696_gb300 import synth
+    A = synth.peps_gauss(Ly, Lx, d, D, seed=seed)
+    ref = O.cu0_sweep(O.lattice_from_dense(A))
+    a = torch.from_numpy(A).cuda()
+    for _ in range(2):
+        s = torch.full((Ly, Lx, D, D), 7.0, dtype=torch.float64, device="cuda")
+        peps.cu0_noalloc(a, s, stream=torch.cuda.current_stream())
+        got = s.cpu().numpy()
+        for r in range(Ly):
+            for x in range(Lx):
+                m = ref[r][x]
+                k = m.shape[0]
+                assert np.all(got[r, x, k:, :] == 0.0) and np.all(got[r, x, :, k:] == 0.0)
+                err = np.max(np.abs(got[r, x, :k, :k] - m))
+                assert err < TOL, (r, x, err)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(env):
