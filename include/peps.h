@@ -33,7 +33,7 @@
  *   Open boundary conditions: a leg that points out of the lattice has
  *   dimension 1 (Section 2, footnote on OBC tensors); in the dense array it
  *   uses index 0 only and every other entry on it must be 0, otherwise the
- *   call fails with PEPS_EINVAL.
+ *   call fails with PEPS_EINVAL.  Every entry must be finite (PEPS_EINVAL).
  */
 #ifndef PEPS_H
 #define PEPS_H
@@ -235,6 +235,36 @@ int peps_mlp_train(float* w, const float* X, const float* Y, long long n, int d,
                    double* final_loss, void* cuda_stream);
 int peps_mlp_predict(const float* w, const float* X, long long n, int d, int D, int width,
                      float* sigma, void* cuda_stream);
+
+/*
+ * Failure detection (the paper has no counterpart).
+ *
+ * peps_set_iteration_caps -- caps of the library's iterations: the
+ *   half-sweeps of a CU_0 fixed point (Section 5.1; default 200) and the
+ *   sweeps of a one-sided Jacobi SVD (svd mode; default 60).  A computation
+ *   that reaches a cap fails with PEPS_ECONVERGE.  0 restores a default;
+ *   values above 1e6 fail with PEPS_EINVAL.  Process-wide, for calls made
+ *   afterwards; a recorded plan keeps the caps it was recorded with.  Needs
+ *   no GPU.
+ * peps_wait_selftest -- one kernel that spins on a device flag nothing sets,
+ *   with the same bounded-wait shape as the library's device-side waits, for
+ *   budget_us microseconds (1..1e6) of the GPU's global timer; it returns
+ *   PEPS_ETIMEOUT through the device status word, and the context stays
+ *   usable.  For tests of the timeout path.  Synchronises the stream.
+ *
+ * Host-side fault injection: the environment variable PEPS_FAULT, read at
+ * the start of every call, forces an error path of that call without
+ * touching the GPU's state:
+ *   PEPS_FAULT=alloc     every device allocation of the call fails  -> PEPS_ENOMEM
+ *   PEPS_FAULT=nan       a NaN is planted in the call's own device copy of the
+ *                        lattice before its validation              -> PEPS_EINVAL
+ *   PEPS_FAULT=converge  both iteration caps are 1 for the call     -> PEPS_ECONVERGE
+ *                        (where an iteration does not stop after one step)
+ * Inputs with non-finite entries fail with PEPS_EINVAL in every call that
+ * takes a lattice.
+ */
+int peps_set_iteration_caps(int cu0_half_sweeps, int jacobi_sweeps);
+int peps_wait_selftest(int budget_us, void* cuda_stream);
 
 /* peps_env_ln_norm -- the norm recorded in a full env (PEPS_EINVAL for cluster envs). */
 int peps_env_ln_norm(const peps_env* env, double* ln_norm, int* sign, void* cuda_stream);

@@ -89,6 +89,7 @@ std::atomic<Counts*> g_recording{nullptr};
 
 thread_local std::string g_err;
 
+
 int fail(int code, const std::string& msg) {
   g_err = msg;
   return code;
@@ -111,6 +112,21 @@ int guard(F&& f) {
 }  // namespace
 
 namespace peps {
+std::atomic<int> g_fault_alloc{0};
+std::atomic<int> g_cap_cu0{200}, g_cap_jacobi{60};
+
+int fault_from_env() {
+  const char* e = std::getenv("PEPS_FAULT");
+  if (!e || !*e) return FAULT_NONE;
+  const std::string v(e);
+  if (v == "alloc") return FAULT_ALLOC;
+  if (v == "nan") return FAULT_NAN;
+  if (v == "converge") return FAULT_CONVERGE;
+  return FAULT_NONE;
+}
+int cap_cu0_half_sweeps() { return g_cap_cu0.load(); }
+int cap_jacobi_sweeps() { return g_cap_jacobi.load(); }
+
 int peps_set_error(int code, const std::string& msg) { return fail(code, msg); }
 
 void prof_launch(KClass c, cudaStream_t st, double flops, double bytes) {
@@ -186,7 +202,20 @@ struct Tune {
   int chunk = 0;   // cluster windows per batched chunk (0: 16)
 };
 
+// PEPS_FAULT=alloc for the lifetime of one call (set before the call's first
+// allocation, cleared when the call ends, also by an exception).
+struct FaultScope {
+  int mode;
+  FaultScope() : mode(fault_from_env()) {
+    if (mode == FAULT_ALLOC) g_fault_alloc.fetch_add(1);
+  }
+  ~FaultScope() {
+    if (mode == FAULT_ALLOC) g_fault_alloc.fetch_sub(1);
+  }
+};
+
 struct Call {
+  FaultScope fault;
   cudaStream_t st;
   Arena ws;
   Ctx cx;
@@ -196,6 +225,8 @@ struct Call {
   explicit Call(void* stream, Arena* persist = nullptr, Tune t = Tune())
       : st(static_cast<cudaStream_t>(stream)), ws(st), cx(st, &ws), tune(t) {
     cx.persist = persist;
+    cx.svd_cap = fault.mode == FAULT_CONVERGE ? 1 : cap_jacobi_sweeps();
+    cx.cu0_cap = fault.mode == FAULT_CONVERGE ? 1 : cap_cu0_half_sweeps();
     if (const char* e = std::getenv("PEPS_QR_CMAX")) cx.qr_cmax = std::atoi(e);
     if (tune.qr_cmax > 0) cx.qr_cmax = tune.qr_cmax;
     cx.flag = static_cast<int*>(persist ? persist->alloc(sizeof(int)) : ws.alloc(sizeof(int)));
@@ -209,7 +240,7 @@ struct Call {
     PEPS_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     PEPS_CUDA(cudaStreamSynchronize(st));
     if (h & FLAG_SVD_NOCONV) throw Error(PEPS_ECONVERGE, "Jacobi SVD did not converge within its sweep cap");
-    if (h & FLAG_CU0_NOCONV) throw Error(PEPS_ECONVERGE, "CU_0 separable boundary did not converge within 200 half-sweeps");
+    if (h & FLAG_CU0_NOCONV) throw Error(PEPS_ECONVERGE, "CU_0 separable boundary did not converge within its half-sweep cap");
     if (h & FLAG_BAD_VALUE) throw Error(PEPS_EINVAL, "zero or non-finite norm encountered (degenerate state)");
     if (h & FLAG_TIMEOUT) throw Error(PEPS_ETIMEOUT, "a device-side bounded wait ran out");
   }
@@ -293,6 +324,7 @@ void build_orientations(Ctx& cx, const peps_lattice* in, Arena& keep, Oriented& 
   const size_t elems = size_t(Ly) * Lx * d * D * D * D * D;
   const size_t esz = in->dtype == PEPS_F32 ? 4 : 8;
   const void* src = in->A;
+  const bool plant_nan = fault_from_env() == FAULT_NAN && !cx.persist;
   if (!in->on_device) {
     const long long bad = obc_violations_host(in);
     PEPS_REQUIRE(bad == 0, "A has " + std::to_string(bad) + " nonzero entries on outward (OBC) legs");
@@ -304,10 +336,17 @@ void build_orientations(Ctx& cx, const peps_lattice* in, Arena& keep, Oriented& 
     PEPS_CUDA(cudaPointerGetAttributes(&at, in->A));
     PEPS_REQUIRE(at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged,
                  "on_device is set but A is not a device pointer");
-    if (!cx.persist) {   // a recorded graph was validated by the plain call made before it
-      const long long bad = obc_violations_device(cx, in->A, in->dtype == PEPS_F32, Ly, Lx, d, D);
-      PEPS_REQUIRE(bad == 0, "A has " + std::to_string(bad) + " nonzero entries on outward (OBC) legs");
+    if (plant_nan) {   // never write into the caller's buffer: plant into a copy
+      void* dsrc = cx.ws->alloc(elems * esz);
+      PEPS_CUDA(cudaMemcpyAsync(dsrc, in->A, elems * esz, cudaMemcpyDeviceToDevice, cx.st));
+      src = dsrc;
     }
+  }
+  if (plant_nan) plant_nan_value(cx, const_cast<void*>(src), in->dtype == PEPS_F32);
+  if (!cx.persist) {   // a recorded graph was validated by the plain call made before it
+    const auto bad = input_violations_device(cx, src, in->dtype == PEPS_F32, Ly, Lx, d, D);
+    PEPS_REQUIRE(bad.first == 0, "A has " + std::to_string(bad.first) + " nonzero entries on outward (OBC) legs");
+    PEPS_REQUIRE(bad.second == 0, "A has " + std::to_string(bad.second) + " non-finite entries");
   }
   out.one = keep.dalloc(1);
   fill(cx, out.one, 1, 1.0);
@@ -447,6 +486,8 @@ struct Lanes {
       a.cx->flag = c.cx.flag;
       a.cx->persist = c.cx.persist;
       a.cx->qr_cmax = c.cx.qr_cmax;
+      a.cx->svd_cap = c.cx.svd_cap;
+      a.cx->cu0_cap = c.cx.cu0_cap;
       a.cx->tmp = a.ws->dalloc(8);
       a.eng = std::make_unique<Engine>(*a.cx, opt, d, D, Lmax, nb);
       if (nb == 1) a.eng->enable_dual(lane_streams(nl, 1)[i]);
@@ -708,7 +749,7 @@ void cu0_all_sides(Ctx& cx, const peps_lattice* lat, Oriented& ori, Arena& keep,
     q.right = closure_ones;
     q.out = sig[o];
     q.work = cx.ws->dalloc(cu0_work_size(L.Lx, d, D));
-    q.max_half = 200;
+    q.max_half = std::max(1, cx.cu0_cap);
     q.tol = 1e-13;
   }
   cu0_launch(cx, cl, 4);
@@ -1080,6 +1121,26 @@ int peps_env_full(const peps_lattice* lat, const peps_opts* opts, peps_env** out
 
 int peps_env_cluster(const peps_lattice* lat, const peps_opts* opts, peps_env** out, void* cuda_stream) {
   return run_env(lat, opts, out, cuda_stream, true);
+}
+
+int peps_set_iteration_caps(int cu0_half_sweeps, int jacobi_sweeps) {
+  return guard([&] {
+    PEPS_REQUIRE(cu0_half_sweeps >= 0 && cu0_half_sweeps <= 1000000 && jacobi_sweeps >= 0 &&
+                     jacobi_sweeps <= 1000000,
+                 "iteration caps must be in [0, 1e6] (0 restores the default)");
+    g_cap_cu0.store(cu0_half_sweeps == 0 ? 200 : cu0_half_sweeps);
+    g_cap_jacobi.store(jacobi_sweeps == 0 ? 60 : jacobi_sweeps);
+  });
+}
+
+int peps_wait_selftest(int budget_us, void* cuda_stream) {
+  return guard([&] {
+    PEPS_REQUIRE(budget_us >= 1 && budget_us <= 1000000, "budget_us must be in [1, 1e6]");
+    require_device();
+    Call c(cuda_stream);
+    wait_unset_flag(c.cx, (long long)budget_us * 1000);
+    c.finish();
+  });
 }
 
 static int count_of(const EnvData& e, int kind) {

@@ -59,13 +59,16 @@ __global__ void k_orient(const void* src, int f32, int Lx, int d, int D, const O
   }
 }
 
+// count[0]: nonzero entries on outward (OBC) legs; count[1]: non-finite entries.
 __global__ void k_obc_count(const void* src, int f32, int Ly, int Lx, int d, int D,
                             unsigned long long* count) {
   const long long per = (long long)d * D * D * D * D;
   const long long total = (long long)Ly * Lx * per;
-  unsigned long long c = 0;
+  unsigned long long c = 0, nf = 0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
+    const double ve = f32 ? double(static_cast<const float*>(src)[e]) : static_cast<const double*>(src)[e];
+    if (!isfinite(ve)) ++nf;
     const long long site = e / per;
     const int y = int(site / Lx), x = int(site % Lx);
     long long r = e % per;
@@ -83,6 +86,29 @@ __global__ void k_obc_count(const void* src, int f32, int Ly, int Lx, int d, int
     }
   }
   if (c) atomicAdd(count, c);
+  if (nf) atomicAdd(count + 1, nf);
+}
+
+__global__ void k_plant_nan(void* p, int f32) {
+  if (f32)
+    static_cast<float*>(p)[0] = __int_as_float(0x7fc00000);
+  else
+    static_cast<double*>(p)[0] = __longlong_as_double(0x7ff8000000000000LL);
+}
+
+// Spins on a flag nothing sets, for at most budget_ns of the global timer,
+// then records a timeout in the status word: the same bounded-wait shape as
+// the library's other device-side waits, with a wait that is certain to run out.
+__global__ void k_wait_unset(const volatile int* never, long long budget_ns, int* status) {
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  while (*never == 0) {
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if ((long long)(t - t0) > budget_ns) {
+      atomicOr(status, FLAG_TIMEOUT);
+      return;
+    }
+  }
 }
 
 // Batched element-wise kernels: grid = (blocks, problems), problem = blockIdx.y.
@@ -497,18 +523,33 @@ void* stage(Ctx& cx, const void* host, size_t bytes) {
   return dev;
 }
 
-long long obc_violations_device(Ctx& cx, const void* src, int src_f32, int Ly, int Lx, int d, int D) {
-  auto* cnt = static_cast<unsigned long long*>(cx.ws->alloc(sizeof(unsigned long long)));
-  PEPS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), cx.st));
+std::pair<long long, long long> input_violations_device(Ctx& cx, const void* src, int src_f32, int Ly, int Lx,
+                                                        int d, int D) {
+  auto* cnt = static_cast<unsigned long long*>(cx.ws->alloc(2 * sizeof(unsigned long long)));
+  PEPS_CUDA(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), cx.st));
   {
     Launch L(K_AUX, cx.st);
     k_obc_count<<<1024, 256, 0, cx.st>>>(src, src_f32, Ly, Lx, d, D, cnt);
     PEPS_CHECK_LAUNCH();
   }
-  unsigned long long h = 0;
-  PEPS_CUDA(cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, cx.st));
+  unsigned long long h[2] = {0, 0};
+  PEPS_CUDA(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, cx.st));
   PEPS_CUDA(cudaStreamSynchronize(cx.st));
-  return (long long)h;
+  return {(long long)h[0], (long long)h[1]};
+}
+
+void plant_nan_value(Ctx& cx, void* p, int f32) {
+  Launch L(K_AUX, cx.st);
+  k_plant_nan<<<1, 1, 0, cx.st>>>(p, f32);
+  PEPS_CHECK_LAUNCH();
+}
+
+void wait_unset_flag(Ctx& cx, long long budget_ns) {
+  int* never = static_cast<int*>(cx.ws->alloc(sizeof(int)));
+  PEPS_CUDA(cudaMemsetAsync(never, 0, sizeof(int), cx.st));
+  Launch L(K_AUX, cx.st);
+  k_wait_unset<<<1, 1, 0, cx.st>>>(never, budget_ns, cx.flag);
+  PEPS_CHECK_LAUNCH();
 }
 
 void fro_norm(Ctx& cx, const TP& x, long long n, const TP& out) {

@@ -1,5 +1,6 @@
 // Auxiliary kernels: lattice repacking, norms, var initialisation, observables, CU_0.
 #pragma once
+#include <utility>
 #include "ein.cuh"
 
 namespace peps {
@@ -15,8 +16,13 @@ struct OrientSite {
 void orient_lattice(Ctx& cx, const void* src, int src_f32, int Ly, int Lx, int d, int D,
                     const OrientSite* host_sites, int nsites, double* dst);
 
-// Number of nonzero entries on outward (OBC) legs of the dense device array.
-long long obc_violations_device(Ctx& cx, const void* src, int src_f32, int Ly, int Lx, int d, int D);
+// (nonzero entries on outward legs, non-finite entries) of a device lattice.
+std::pair<long long, long long> input_violations_device(Ctx& cx, const void* src, int src_f32, int Ly, int Lx,
+                                                        int d, int D);
+// Writes a NaN into element 0 (PEPS_FAULT=nan).
+void plant_nan_value(Ctx& cx, void* p, int f32);
+// A bounded wait on a flag nothing sets: records FLAG_TIMEOUT in cx.flag after budget_ns.
+void wait_unset_flag(Ctx& cx, long long budget_ns);
 
 // All of these act on every problem of their pointer sets (one launch).
 // out[0] = ||x||_F (device scalar).

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <mutex>
@@ -68,6 +69,26 @@ struct Launch {
 };
 
 // ---------------------------------------------------------------------------
+// Iteration caps and host-side fault injection.
+//   Caps (peps_set_iteration_caps): half-sweeps of a CU_0 fixed point and
+//   sweeps of a one-sided Jacobi SVD; a computation that hits one fails with
+//   PEPS_ECONVERGE.  Process-wide; a recorded plan keeps the caps it was
+//   recorded with.
+//   Faults (environment variable PEPS_FAULT, read at the start of every call;
+//   for tests of the error paths, nothing here touches the GPU's state):
+//     alloc     every device allocation of the call fails   -> PEPS_ENOMEM
+//     nan       a NaN is planted in the call's device copy of the lattice
+//               before validation                           -> PEPS_EINVAL
+//     converge  both caps are 1 for the call                -> PEPS_ECONVERGE
+//               (wherever an iteration does not stop in one step)
+// ---------------------------------------------------------------------------
+enum Fault { FAULT_NONE = 0, FAULT_ALLOC = 1, FAULT_NAN = 2, FAULT_CONVERGE = 3 };
+int fault_from_env();
+int cap_cu0_half_sweeps();
+int cap_jacobi_sweeps();
+extern std::atomic<int> g_fault_alloc;      // > 0 while a PEPS_FAULT=alloc call runs
+
+// ---------------------------------------------------------------------------
 // Stream-ordered bump arena (cudaMallocAsync chunks, freed together).
 // ---------------------------------------------------------------------------
 class Arena {
@@ -84,6 +105,8 @@ class Arena {
     std::lock_guard<std::mutex> g(mu_);   // shared by lane threads when it owns an env
     bytes = (bytes + 255) & ~size_t(255);
     if (bytes == 0) bytes = 256;
+    if (g_fault_alloc.load(std::memory_order_relaxed) > 0)
+      throw Error(PEPS_ENOMEM, "device allocation failed (injected: PEPS_FAULT=alloc)");
     if (bytes > left_) {
       size_t n = bytes > chunk_ ? bytes : chunk_;
       void* p = nullptr;

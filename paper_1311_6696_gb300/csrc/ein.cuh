@@ -24,6 +24,9 @@ struct Ctx {
   Arena* persist = nullptr;
   // Largest thread-block cluster a QR may use (0: no limit beyond 16).
   int qr_cmax = 0;
+  // Iteration caps of this call (Jacobi SVD sweeps, CU_0 half-sweeps).
+  int svd_cap = 60;
+  int cu0_cap = 200;
 
   Ctx(cudaStream_t s, Arena* w) : st(s), ws(w) {}
   ~Ctx() {
@@ -123,10 +126,41 @@ struct PackCache {
   std::map<std::string, Entry> entries;
 };
 
+// An operand in the tensor-core layout of one contraction: [np * pad][ld]
+// (rows over the contraction's M letters, K contiguous), hi part and, for the
+// split precisions, the rounded residual.
+struct TcOperand {
+  void* hi = nullptr;
+  void* lo = nullptr;
+  long long ld = 0, pad = 0;
+  int np = 0;
+};
+
+// Chained contractions without a repack in between.
+//   a_pre:    operand A is already in this contraction's layout (written by
+//             the previous contraction's epilogue).
+//   next:     write C not as a tensor but as operand A of the contraction
+//             `next` (whose B operand has dims next_bd), into next_mem
+//             (next_cap doubles, contiguous over the problems); next_out
+//             receives its description.  C and Clo are then ignored.
+// K is ordered as in a plain call, so the result is the same as packing the
+// FP32 output of a plain call.
+struct TcChain {
+  const TcOperand* a_pre = nullptr;
+  const char* next = nullptr;
+  Dims next_bd;
+  double* next_mem = nullptr;
+  size_t next_cap = 0;
+  TcOperand* next_out = nullptr;
+};
+
+// Doubles a TcChain target needs for operand A of `spec` (hi and lo parts).
+size_t tc_operand_words(const char* spec, const Dims& ad, const Dims& bd, int np, int prec);
+
 // bcache: B is packed once per cache and reused (B must not change meanwhile).
 void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, const TP& B, int b_f64,
             const Dims& bd, const TP& C, int c_f64, int prec, double alpha = 1.0, const TP& Clo = TP(),
-            PackCache* bcache = nullptr);
+            PackCache* bcache = nullptr, const TcChain* chain = nullptr);
 int tc_available();
 
 }  // namespace peps

@@ -35,6 +35,8 @@ Engine::Engine(Ctx& c, const Opts& o, int d, int Dmax, int Lmax, int nb)
   // X1: chain stage 1 (chi^2 D^4), or bond stage 1 (d^2 chi^2 D^4) / bond stage 4 (d^4 chi^2 D^2)
   X1_ = alloc(*cx.ws, std::max(bigN_ * dd, chi * chi * D2 * dd * dd));
   X2_ = alloc(*cx.ws, bigN_ * dd * d);   // ket stage with up to one open pair
+  x1per_ = (std::max(bigN_ * dd, chi * chi * D2 * dd * dd) + 31) / 32 * 32;
+  x2per_ = (bigN_ * dd * d + 31) / 32 * 32;
   X3_ = alloc(*cx.ws, bigN_ * dd * dd);  // bra stage with up to two open pairs
   envN_ = chi * D2 * chi * dd;
   bb_ = alloc(*cx.ws, envN_);
@@ -52,7 +54,7 @@ Engine::Engine(Ctx& c, const Opts& o, int d, int Dmax, int Lmax, int nb)
   tc_ = o.precision != PEPS_PREC_FP64;
   x64_ = !tc_;
   site_packs_ = std::make_unique<PackCache>(cx.ws);
-  main_ = Side{&cx, X1_, X2_, X3_, tmp0_, site_packs_.get()};
+  main_ = Side{&cx, X1_, X2_, X3_, tmp0_, site_packs_.get(), x1per_ * nb_, x2per_ * nb_};
 }
 
 Engine::~Engine() {
@@ -86,13 +88,16 @@ void Engine::enable_dual(cudaStream_t st2) {
   cx2_->flag = cx.flag;
   cx2_->persist = cx.persist;
   cx2_->qr_cmax = cx.qr_cmax;
+  cx2_->svd_cap = cx.svd_cap;
+  cx2_->cu0_cap = cx.cu0_cap;
   cx2_->tmp = ws2_->dalloc(8);
   cache2_ = std::make_unique<PackCache>(ws2_.get());
   const size_t x1 = std::max(bigN_ * dd, chi * chi * D2 * dd * dd);
   aux_ = Side{cx2_.get(), strided(ws2_->dalloc((x1 + 31) / 32 * 32), 1, x1),
               strided(ws2_->dalloc((bigN_ * dd * d_ + 31) / 32 * 32), 1, bigN_ * dd * d_),
               strided(ws2_->dalloc((bigN_ * dd * dd + 31) / 32 * 32), 1, bigN_ * dd * dd),
-              strided(ws2_->dalloc(32), 1, 1), cache2_.get()};
+              strided(ws2_->dalloc(32), 1, 1), cache2_.get(), (x1 + 31) / 32 * 32,
+              (bigN_ * dd * d_ + 31) / 32 * 32};
   dual_ = true;
 }
 
@@ -109,7 +114,7 @@ void Engine::use(int B) {
   for (TP* t : {&X1_, &X2_, &X3_, &bb_, &tmp0_, &tmp1_}) t->n = B;
   for (auto& t : Lenv_) t.n = B;
   for (auto& t : Renv_) t.n = B;
-  main_ = Side{&cx, X1_, X2_, X3_, tmp0_, site_packs_.get()};   // the helpers' view of the buffers
+  main_ = Side{&cx, X1_, X2_, X3_, tmp0_, site_packs_.get(), x1per_ * B, x2per_ * B};   // the helpers' view
 }
 
 TP Engine::alloc(Arena& a, size_t per) const {
@@ -137,8 +142,86 @@ Mps Engine::closure_mps(const std::vector<Mat>& mats, Arena&) {
   return T;
 }
 
+// Tensor-core chains.  The three GEMMs of an absorb chain hand their results
+// over in the next GEMM's operand layout (TcChain), so the intermediates are
+// written once, already rounded and split, and never repacked.  The output
+// letter orders of the first two contractions are chosen for that hand-over:
+// the next contraction's K letters are contiguous in its operand, so the
+// epilogue writes runs along them.  The first two contractions sum over the same
+// letters as the plain form; the third one takes its K letters in the order
+// (s, then the bra leg pair) so that the second GEMM's rows write contiguous
+// runs, which changes only the FP32 summation order.  Falls back to the plain
+// form where the chain buffers are too small for a padded operand (tiny bonds).
+Dims Engine::chain_left_tc(const TP& L, const Dims& ld, const TP& M, const Dims& md, const SiteT& A,
+                           const TP& X3) {
+  static const char* s1 = "clma,auvb->clmbvu";
+  static const char* s2 = "clmbvu,sulnr->cbsmvnr";
+  static const char* s3 = "cbsmvnr,svmoq->cbnroq";
+  Ctx& c = *side_->cx;
+  const Dims ad = A.dims();
+  const Dims x1 = ein_dims(s1, ld, md), x2 = ein_dims(s2, x1, ad), x3 = ein_dims(s3, x2, ad);
+  const int np = ::peps::problems({&L, &M, &A.p, &X3});
+  if (tc_operand_words(s2, x1, ad, np, opt.precision) > side_->x1n ||
+      tc_operand_words(s3, x2, ad, np, opt.precision) > side_->x2n)
+    return Dims();
+  TcOperand o1, o2;
+  TcChain c1, c2, c3;
+  c1.next = s2;
+  c1.next_bd = ad;
+  c1.next_mem = side_->X1.d(0);
+  c1.next_cap = side_->x1n;
+  c1.next_out = &o1;
+  ein_tc(c, s1, L, 1, ld, M, 1, md, TP(), 0, opt.precision, 1.0, TP(), nullptr, &c1);
+  c2.a_pre = &o1;
+  c2.next = s3;
+  c2.next_bd = ad;
+  c2.next_mem = side_->X2.d(0);
+  c2.next_cap = side_->x2n;
+  c2.next_out = &o2;
+  ein_tc(c, s2, TP(), 0, x1, A.p, 1, ad, TP(), 0, opt.precision, 1.0, TP(), side_->cache, &c2);
+  c3.a_pre = &o2;
+  ein_tc(c, s3, TP(), 0, x2, A.p, 1, ad, X3, 0, opt.precision, 1.0, TP(), side_->cache, &c3);
+  return x3;
+}
+
+Dims Engine::chain_right_tc(const TP& R, const Dims& rd, const TP& M, const Dims& md, const SiteT& A,
+                            const TP& Y3) {
+  static const char* s1 = "auvb,brqc->auvcqr";
+  static const char* s2 = "auvcqr,sulnr->acsvqln";
+  static const char* s3 = "acsvqln,svmoq->aclnmo";
+  Ctx& c = *side_->cx;
+  const Dims ad = A.dims();
+  const Dims y1 = ein_dims(s1, md, rd), y2 = ein_dims(s2, y1, ad), y3 = ein_dims(s3, y2, ad);
+  const int np = ::peps::problems({&R, &M, &A.p, &Y3});
+  if (tc_operand_words(s2, y1, ad, np, opt.precision) > side_->x1n ||
+      tc_operand_words(s3, y2, ad, np, opt.precision) > side_->x2n)
+    return Dims();
+  TcOperand o1, o2;
+  TcChain c1, c2, c3;
+  c1.next = s2;
+  c1.next_bd = ad;
+  c1.next_mem = side_->X1.d(0);
+  c1.next_cap = side_->x1n;
+  c1.next_out = &o1;
+  ein_tc(c, s1, M, 1, md, R, 1, rd, TP(), 0, opt.precision, 1.0, TP(), nullptr, &c1);
+  c2.a_pre = &o1;
+  c2.next = s3;
+  c2.next_bd = ad;
+  c2.next_mem = side_->X2.d(0);
+  c2.next_cap = side_->x2n;
+  c2.next_out = &o2;
+  ein_tc(c, s2, TP(), 0, y1, A.p, 1, ad, TP(), 0, opt.precision, 1.0, TP(), side_->cache, &c2);
+  c3.a_pre = &o2;
+  ein_tc(c, s3, TP(), 0, y2, A.p, 1, ad, Y3, 0, opt.precision, 1.0, TP(), side_->cache, &c3);
+  return y3;
+}
+
 Dims Engine::chain_left(const TP& L, const Dims& ld, const TP& M, const Dims& md, const SiteT& A,
                         const TP& X3) {
+  if (tc_) {
+    const Dims r = chain_left_tc(L, ld, M, md, A, X3);
+    if (!r.empty()) return r;
+  }
   const Dims ad = A.dims();
   const Dims x1 = ein_dims("clma,auvb->clmuvb", ld, md);
   con("clma,auvb->clmuvb", L, true, ld, M, true, md, side_->X1, x64_);
@@ -151,6 +234,10 @@ Dims Engine::chain_left(const TP& L, const Dims& ld, const TP& M, const Dims& md
 
 Dims Engine::chain_right(const TP& R, const Dims& rd, const TP& M, const Dims& md, const SiteT& A,
                          const TP& Y3) {
+  if (tc_) {
+    const Dims r = chain_right_tc(R, rd, M, md, A, Y3);
+    if (!r.empty()) return r;
+  }
   const Dims ad = A.dims();
   const Dims y1 = ein_dims("auvb,brqc->auvrqc", md, rd);
   con("auvb,brqc->auvrqc", M, true, md, R, true, rd, side_->X1, x64_);

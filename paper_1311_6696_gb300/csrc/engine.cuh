@@ -119,7 +119,11 @@ class Engine {
     Ctx* cx;
     TP X1, X2, X3, tmp;
     PackCache* cache;
+    size_t x1n, x2n;   // doubles from X1.p[0] / X2.p[0] (contiguous over the problems)
   };
+  // Tensor-core absorb chains: each GEMM writes the next one's operand.
+  Dims chain_left_tc(const TP& L, const Dims& ld, const TP& M, const Dims& md, const SiteT& A, const TP& X3);
+  Dims chain_right_tc(const TP& R, const Dims& rd, const TP& M, const Dims& md, const SiteT& A, const TP& Y3);
   Side main_, aux_;
   Side* side_ = &main_;
   bool dual_ = false;
@@ -129,6 +133,7 @@ class Engine {
   cudaStream_t ws2_stream_ = nullptr;
 
   int d_, Dmax_, Lmax_, nb_, cap_;
+  size_t x1per_ = 0, x2per_ = 0;   // doubles per problem of X1_ / X2_ (their stride)
   size_t bigN_;                 // chi^2 * Dmax^4 (elements of the largest chain intermediate / d)
   TP X1_, X2_, X3_, bb_;
   std::vector<TP> Lenv_, Renv_;

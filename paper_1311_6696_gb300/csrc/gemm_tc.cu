@@ -25,6 +25,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "ein.cuh"
 #include "linalg.cuh"
@@ -51,6 +52,8 @@ struct TcArgs {
   int bf16;          // 0: tf32, 1: bf16
   int out_f64;       // 1: C is double, else float
   int out_lo;        // 1: also write C_lo (split residual), C is then the rounded hi part
+  int out_tc;        // C is a tensor-core operand of the next contraction: 1 = TF32 (float,
+                     // rounded), 2 = BF16; with out_lo the rounded residual goes to C_lo
   int stages;        // ring depth (<= TC_STAGES), chosen to fit shared memory
   int nprob;         // problems in this launch
   int cols_fast;     // 1: the output's unit stride is in the N group (write along columns)
@@ -152,6 +155,26 @@ __device__ __forceinline__ void decomp(const Grp& g, long long idx, long long& o
     const long long q = idx / g.dim[i];
     off += (idx - q * g.dim[i]) * g.s[i];
     idx = q;
+  }
+}
+
+// Element o of problem pb's output: FP64, FP32, or a tensor-core operand of
+// the next contraction (TF32 or BF16, rounded, with the rounded residual in
+// C_lo for the split precisions) -- the values the operand pack would make
+// from the FP32 result.
+__device__ __forceinline__ void put_out(const TcArgs& g, int pb, long long o, float v) {
+  if (g.out_f64) {
+    static_cast<double*>(g.C.p[pb])[o] = double(v);
+  } else if (g.out_tc == 2) {
+    const __nv_bfloat16 h = __float2bfloat16(v);
+    static_cast<__nv_bfloat16*>(g.C.p[pb])[o] = h;
+    if (g.out_lo) static_cast<__nv_bfloat16*>(g.Clo.p[pb])[o] = __float2bfloat16(v - __bfloat162float(h));
+  } else if (g.out_tc == 1 || g.out_lo) {
+    const float h = round_tf32(v);
+    static_cast<float*>(g.C.p[pb])[o] = h;
+    if (g.out_lo) static_cast<float*>(g.Clo.p[pb])[o] = round_tf32(v - h);
+  } else {
+    static_cast<float*>(g.C.p[pb])[o] = v;
   }
 }
 
@@ -278,21 +301,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ 
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int row = warp * 32 + lane;
   const long long om = offm[row];
-  float* const Cf = static_cast<float*>(g.C.p[pb]);
-  double* const Cd = static_cast<double*>(g.C.p[pb]);
-  float* const Cl = g.out_lo ? static_cast<float*>(g.Clo.p[pb]) : nullptr;
   const float alpha = float(g.alpha);
-  auto put = [&](long long o, float v) {
-    if (g.out_f64) {
-      Cd[o] = double(v);
-    } else if (g.out_lo) {
-      const float h = round_tf32(v);
-      Cf[o] = h;
-      Cl[o] = round_tf32(v - h);
-    } else {
-      Cf[o] = v;
-    }
-  };
+  auto put = [&](long long o, float v) { put_out(g, pb, o, v); };
   if (have && g.splitk > 1) {
     // raw partial sums, dense [M][N] per (split, problem), written along N
     float* part = g.part + ((long long)blockIdx.y * g.nprob + pb) * g.M * g.N;
@@ -362,16 +372,7 @@ __global__ void k_tc_splitk_reduce(const TcArgs g) {
     long long om, on;
     decomp(g.gm, m, om);
     decomp(g.gn, n, on);
-    const long long o = om + on;
-    if (g.out_f64) {
-      static_cast<double*>(g.C.p[pb])[o] = double(v);
-    } else if (g.out_lo) {
-      const float h = round_tf32(v);
-      static_cast<float*>(g.C.p[pb])[o] = h;
-      static_cast<float*>(g.Clo.p[pb])[o] = round_tf32(v - h);
-    } else {
-      static_cast<float*>(g.C.p[pb])[o] = v;
-    }
+    put_out(g, pb, om + on, v);
   }
 }
 
@@ -632,15 +633,86 @@ int tc_available() {
   return ok;
 }
 
+// Operand A of `spec` as ein_tc lays it out: M rows over the output letters
+// taken from A (in the output's order), K over A's summed letters (in A's
+// order), rows padded to the tile height per problem, K padded to 16 bytes.
+struct LayoutA {
+  std::string rows, ks;
+  std::vector<long long> rdim, kdim;
+  long long M = 1, K = 1, pad = 0, ld = 0;
+  size_t words = 0;   // doubles of the hi array; the lo array follows
+};
+
+LayoutA layout_a(const char* spec, const Dims& ad, const Dims& bd, int np, int prec) {
+  const Parsed p = parse(spec);
+  (void)bd;
+  LayoutA L;
+  for (char ch : p.c)
+    if (p.a.find(ch) != std::string::npos) {
+      L.rows += ch;
+      L.rdim.push_back(ad[p.a.find(ch)]);
+      L.M *= ad[p.a.find(ch)];
+    }
+  for (char ch : p.a)
+    if (p.c.find(ch) == std::string::npos) {
+      L.ks += ch;
+      L.kdim.push_back(ad[p.a.find(ch)]);
+      L.K *= ad[p.a.find(ch)];
+    }
+  const int bf16 = (prec == PEPS_PREC_BF16 || prec == PEPS_PREC_BF16X3) ? 1 : 0;
+  const int align = bf16 ? 8 : 4;
+  L.pad = (L.M + TC_BM - 1) / TC_BM * TC_BM;
+  L.ld = (L.K + align - 1) / align * align;
+  L.words = pack_words(np * L.pad, L.K, bf16, 0);
+  return L;
+}
+
+size_t tc_operand_words(const char* spec, const Dims& ad, const Dims& bd, int np, int prec) {
+  const int split = (prec == PEPS_PREC_TF32X3 || prec == PEPS_PREC_BF16X3) ? 1 : 0;
+  return (split ? 2 : 1) * layout_a(spec, ad, bd, np, prec).words;
+}
+
 void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, const TP& B, int b_f64,
-            const Dims& bd, const TP& C, int c_f64, int prec, double alpha, const TP& Clo, PackCache* bcache) {
+            const Dims& bd, const TP& C, int c_f64, int prec, double alpha, const TP& Clo, PackCache* bcache,
+            const TcChain* chain) {
   PEPS_REQUIRE(tc_available(), "tensor-core path needs an sm_103 device");
-  const int np = problems({&A, &B, &C, &Clo});
-  PEPS_REQUIRE(!A.null() && !B.null() && C.n == np && (Clo.null() || Clo.n == np),
+  const bool to_next = chain && chain->next;
+  const TcOperand* a_pre = chain ? chain->a_pre : nullptr;
+  int np = to_next ? problems({&A, &B}) : problems({&A, &B, &C, &Clo});
+  if (a_pre) {
+    PEPS_REQUIRE(np == 1 || np == a_pre->np, "internal: pre-packed operand for another problem count");
+    np = a_pre->np;
+  }
+  PEPS_REQUIRE(!B.null() && (a_pre || !A.null()) && (to_next || (C.n == np && (Clo.null() || Clo.n == np))),
                "internal: contraction operands");
   const Parsed p = parse(spec);
   const Dims cd = ein_dims(spec, ad, bd);
   const auto sc = strides_of(cd);
+  const int bf16 = (prec == PEPS_PREC_BF16 || prec == PEPS_PREC_BF16X3) ? 1 : 0;
+  const int split = (prec == PEPS_PREC_TF32X3 || prec == PEPS_PREC_BF16X3) ? 1 : 0;
+  // Output strides: C's own (row-major over the output letters), or those of
+  // operand A of the next contraction.
+  std::vector<long long> ostr(sc.begin(), sc.end());
+  LayoutA nx;
+  if (to_next) {
+    nx = layout_a(chain->next, cd, chain->next_bd, np, prec);
+    PEPS_REQUIRE(nx.rows.size() + nx.ks.size() == p.c.size(), "internal: chained operand letters");
+    for (size_t i = 0; i < p.c.size(); ++i) {
+      const char ch = p.c[i];
+      long long st = 1;
+      auto r = nx.rows.find(ch), k = nx.ks.find(ch);
+      if (r != std::string::npos) {
+        st = nx.ld;
+        for (size_t j = r + 1; j < nx.rows.size(); ++j) st *= nx.rdim[j];
+        PEPS_REQUIRE(nx.rdim[r] == cd[i], "internal: chained operand dims");
+      } else {
+        PEPS_REQUIRE(k != std::string::npos && nx.kdim[k] == cd[i], "internal: chained operand letters");
+        for (size_t j = k + 1; j < nx.ks.size(); ++j) st *= nx.kdim[j];
+      }
+      ostr[i] = st;
+    }
+    PEPS_REQUIRE((split ? 2 : 1) * nx.words <= chain->next_cap, "internal: chained operand buffer too small");
+  }
   std::string mL, nL, kL;
   TcArgs g;
   std::memset(static_cast<void*>(&g), 0, sizeof(g));
@@ -650,10 +722,10 @@ void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, c
     PEPS_REQUIRE(!(inA && inB), std::string("batch index not supported on the tensor-core path: ") + spec);
     if (inA) {
       mL += ch;
-      push(g.gm, cd[i], sc[i]);
+      push(g.gm, cd[i], ostr[i]);
     } else {
       nL += ch;
-      push(g.gn, cd[i], sc[i]);
+      push(g.gn, cd[i], ostr[i]);
     }
   }
   for (char ch : p.a)
@@ -661,8 +733,6 @@ void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, c
       PEPS_REQUIRE(p.b.find(ch) != std::string::npos, std::string("unsupported one-sided sum: ") + spec);
       kL += ch;
     }
-  const int bf16 = (prec == PEPS_PREC_BF16 || prec == PEPS_PREC_BF16X3) ? 1 : 0;
-  const int split = (prec == PEPS_PREC_TF32X3 || prec == PEPS_PREC_BF16X3) ? 1 : 0;
   long long M = 1, N = 1, K = 1;
   for (char ch : mL) M *= ad[p.a.find(ch)];
   for (char ch : nL) N *= bd[p.b.find(ch)];
@@ -671,7 +741,10 @@ void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, c
   int BN = 16;
   while (BN < N && BN < 128) BN *= 2;
   const long long pad_m = (M + TC_BM - 1) / TC_BM * TC_BM, pad_n = (N + BN - 1) / BN * BN;
-  const size_t wa = pack_words(np * pad_m, K, bf16, split);
+  if (a_pre)
+    PEPS_REQUIRE(a_pre->pad == pad_m && a_pre->ld == (K + (bf16 ? 8 : 4) - 1) / (bf16 ? 8 : 4) * (bf16 ? 8 : 4),
+                 "internal: pre-packed operand layout");
+  const size_t wa = a_pre ? 0 : pack_words(np * pad_m, K, bf16, split);
   const size_t wb_need = pack_words(np * pad_n, K, bf16, split);
   // a cached B operand: packed once into the cache's memory
   PackCache::Entry* cached = nullptr;
@@ -707,7 +780,16 @@ void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, c
   const size_t wp = g.splitk > 1 ? (size_t(g.splitk) * np * M * N + 1) / 2 + 64 : 0;
   double* mem = cx.scratch(wa + wb + wp);   // one reservation: operands, then split partials
   if (g.splitk > 1) g.part = reinterpret_cast<float*>(mem + wa + wb);
-  const Operand oa = pack(cx, A, np, pad_m, a_f64, p.a, ad, mL, kL, bf16, split, mem);
+  Operand oa;
+  if (a_pre) {
+    oa.hi = a_pre->hi;
+    oa.lo = a_pre->lo;
+    oa.rows = M;
+    oa.K = K;
+    oa.ld = a_pre->ld;
+  } else {
+    oa = pack(cx, A, np, pad_m, a_f64, p.a, ad, mL, kL, bf16, split, mem);
+  }
   Operand ob;
   if (!cached || fresh) {
     ob = pack(cx, B, np, pad_n, b_f64, p.b, bd, nL, kL, bf16, split,
@@ -730,22 +812,70 @@ void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, c
   g.K = K;
   g.split = split;
   g.bf16 = bf16;
-  g.out_f64 = c_f64;
-  g.out_lo = (!Clo.null() && !c_f64) ? 1 : 0;
+  if (to_next) {
+    const size_t esz = bf16 ? 2 : 4;
+    char* hi = reinterpret_cast<char*>(chain->next_mem);
+    char* lo = split ? hi + nx.words * sizeof(double) : nullptr;
+    TP ch, cl;
+    ch.n = np;
+    cl.n = split ? np : 0;
+    for (int b = 0; b < np; ++b) {
+      ch.p[b] = hi + size_t(b) * nx.pad * nx.ld * esz;
+      if (split) cl.p[b] = lo + size_t(b) * nx.pad * nx.ld * esz;
+    }
+    g.C = ch;
+    g.Clo = cl;
+    g.out_f64 = 0;
+    g.out_lo = split;
+    g.out_tc = bf16 ? 2 : 1;
+    if (chain->next_out) {
+      TcOperand& o = *chain->next_out;
+      o.hi = hi;
+      o.lo = lo;
+      o.ld = nx.ld;
+      o.pad = nx.pad;
+      o.np = np;
+    }
+  } else {
+    g.out_f64 = c_f64;
+    g.out_lo = (!Clo.null() && !c_f64) ? 1 : 0;
+    g.C = C.all(np);
+    g.Clo = Clo.all(np);
+  }
   {
+    // Epilogue store pattern: one row per lane (a warp stores 32 rows of one
+    // column) or 16 lanes per row through shared memory (2 rows x 16 columns).
+    // Take the one whose warp store touches fewer 32-byte sectors in the
+    // first tile; on a tie, the one along the smaller innermost stride.
     auto inner = [](const Grp& q) {
       long long m = 1LL << 62;
       for (int i = 0; i < q.n; ++i)
         if (q.dim[i] > 1) m = std::min(m, q.s[i]);
       return m;
     };
-    g.cols_fast = inner(g.gn) < inner(g.gm) ? 1 : 0;
+    auto offset = [](const Grp& q, long long idx) {
+      long long o = 0;
+      for (int i = q.n - 1; i >= 0; --i) {
+        o += (idx % q.dim[i]) * q.s[i];
+        idx /= q.dim[i];
+      }
+      return o;
+    };
+    const int esz = g.out_f64 ? 8 : (g.out_tc == 2 ? 2 : 4);
+    auto sectors = [&](bool cols) {
+      std::vector<long long> v;
+      const int ri = cols ? 2 : 32, cj = cols ? 16 : 1;
+      for (int i = 0; i < ri && i < M; ++i)
+        for (int j = 0; j < cj && j < N; ++j) v.push_back((offset(g.gm, i) + offset(g.gn, j)) * esz / 32);
+      std::sort(v.begin(), v.end());
+      return std::unique(v.begin(), v.end()) - v.begin();
+    };
+    const long long sc_cols = sectors(true), sc_rows = sectors(false);
+    g.cols_fast = sc_cols != sc_rows ? (sc_cols < sc_rows ? 1 : 0) : (inner(g.gn) < inner(g.gm) ? 1 : 0);
   }
   g.nprob = np;
   g.pad_m = pad_m;
   g.pad_n = pad_n;
-  g.C = C.all(np);
-  g.Clo = Clo.all(np);
   g.alpha = alpha;
   g.flag = cx.flag;
   const double flops = 2.0 * double(M) * double(N) * double(K) * np;

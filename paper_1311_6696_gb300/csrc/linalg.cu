@@ -26,7 +26,6 @@ namespace {
 
 constexpr int QR_THREADS = 512;
 constexpr int SVD_THREADS = 512;
-constexpr int SVD_MAX_SWEEPS = 60;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -172,6 +171,41 @@ constexpr int QRC_THREADS = 512;
 // products at 64 rows per CTA).
 constexpr int QS = 8;   // threads per column (rows interleaved mod QS)
 
+// Strided dot product and update over rows start, start + QS, ... < end with
+// four rows' loads in flight per step (when the rows live in global memory a
+// thread's loop is otherwise one dependent load after another); fixed
+// summation order.
+__device__ __forceinline__ double dot_qs(const double* __restrict__ x, const double* __restrict__ y, int start,
+                                         int end) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int i = start;
+  for (; i + 3 * QS < end; i += 4 * QS) {
+    const double x0 = x[i], x1 = x[i + QS], x2 = x[i + 2 * QS], x3 = x[i + 3 * QS];
+    const double y0 = y[i], y1 = y[i + QS], y2 = y[i + 2 * QS], y3 = y[i + 3 * QS];
+    a0 = fma(x0, y0, a0);
+    a1 = fma(x1, y1, a1);
+    a2 = fma(x2, y2, a2);
+    a3 = fma(x3, y3, a3);
+  }
+  for (; i < end; i += QS) a0 = fma(x[i], y[i], a0);
+  return (a0 + a1) + (a2 + a3);
+}
+
+// y[i] -= w x[i] over the same rows (x and y are different columns).
+__device__ __forceinline__ void axpy_qs(double w, const double* __restrict__ x, double* __restrict__ y, int start,
+                                        int end) {
+  int i = start;
+  for (; i + 3 * QS < end; i += 4 * QS) {
+    const double x0 = x[i], x1 = x[i + QS], x2 = x[i + 2 * QS], x3 = x[i + 3 * QS];
+    const double y0 = y[i], y1 = y[i + QS], y2 = y[i + 2 * QS], y3 = y[i + 3 * QS];
+    y[i] = fma(-w, x0, y0);
+    y[i + QS] = fma(-w, x1, y1);
+    y[i + 2 * QS] = fma(-w, x2, y2);
+    y[i + 3 * QS] = fma(-w, x3, y3);
+  }
+  for (; i < end; i += QS) y[i] = fma(-w, x[i], y[i]);
+}
+
 // Sum of one double over the cluster's CTAs, all remote loads issued first.
 __device__ __forceinline__ double remote_sum(cg::cluster_group& cl, double* slot, int C) {
   double v[16];
@@ -230,9 +264,7 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_cluster(const QrArgs q, int 
     for (int t = tid; t < (n - j) * QS; t += nt) {
       const int c = j + t / QS, qq = t % QS;
       const double* wc = W + (long long)c * ld - r0;
-      double w = 0.0;
-      for (int i = i0 + ((qq - i0 % QS + QS) % QS); i < r1; i += QS) w = fma(xj[i], wc[i], w);
-      part4[(long long)c * QS + qq] = w;
+      part4[(long long)c * QS + qq] = dot_qs(xj, wc, i0 + ((qq - i0 % QS + QS) % QS), r1);
     }
     __syncthreads();
     const bool has_row = j >= r0 && j < r1;
@@ -286,7 +318,7 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_cluster(const QrArgs q, int 
         double* wc = W + (long long)c * ld - r0;
         const double w = wfin[c];
         if (own && qq == 0) wc[j] -= w;
-        for (int i = i0 + ((qq - i0 % QS + QS) % QS); i < r1; i += QS) wc[i] = fma(-w, vj[i], wc[i]);
+        axpy_qs(w, vj, wc, i0 + ((qq - i0 % QS + QS) % QS), r1);
       }
       if (own && tid == 0) vj[j] = beta;
     }
@@ -310,9 +342,7 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_cluster(const QrArgs q, int 
     for (int t = tid; t < nc * QS; t += nt) {
       const int c = j + t / QS, qq = t % QS;
       const double* qc = Qw + (long long)c * ld - r0;
-      double w = 0.0;
-      for (int i = i0 + ((qq - i0 % QS + QS) % QS); i < r1; i += QS) w = fma(vj[i], qc[i], w);
-      part4[(long long)c * QS + qq] = w;
+      part4[(long long)c * QS + qq] = dot_qs(vj, qc, i0 + ((qq - i0 % QS + QS) % QS), r1);
     }
     __syncthreads();
     for (int c = j + tid; c < k; c += nt) {
@@ -329,7 +359,7 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_cluster(const QrArgs q, int 
       double* qc = Qw + (long long)c * ld - r0;
       const double w = wfin[c];
       if (own && qq == 0) qc[j] -= w;
-      for (int i = i0 + ((qq - i0 % QS + QS) % QS); i < r1; i += QS) qc[i] = fma(-w, vj[i], qc[i]);
+      axpy_qs(w, vj, qc, i0 + ((qq - i0 % QS + QS) % QS), r1);
     }
     __syncthreads();
   }
@@ -357,6 +387,7 @@ struct SvdArgs {
   TP US;             // m x kk row-major
   TP Vt;             // kk x n row-major
   int* flag;
+  int max_sweeps;    // sweep cap (PEPS_ECONVERGE when reached)
 };
 
 // Grid = problems, one CTA each.
@@ -381,7 +412,7 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_jacobi(const SvdArgs s) {
   const int qq = q + (q & 1);   // even number of slots for the round-robin pairing
   const double tol = 1e-15;
   int sweep = 0;
-  for (; sweep < SVD_MAX_SWEEPS; ++sweep) {
+  for (; sweep < s.max_sweeps; ++sweep) {
     if (tid == 0) s_rot = 0;
     __syncthreads();
     for (int round = 0; round < qq - 1; ++round) {
@@ -430,7 +461,7 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_jacobi(const SvdArgs s) {
     __syncthreads();
     if (!rot) break;
   }
-  if (sweep >= SVD_MAX_SWEEPS && tid == 0) atomicOr(s.flag, FLAG_SVD_NOCONV);
+  if (sweep >= s.max_sweeps && tid == 0) atomicOr(s.flag, FLAG_SVD_NOCONV);
   // column norms and a stable descending order
   for (int j = warp; j < q; j += nw) {
     double v = 0.0;
@@ -516,7 +547,7 @@ __global__ void __launch_bounds__(SVC_THREADS) k_svd_cluster(const SvdArgs s, do
   }
   const double tol = 1e-15;
   int sweep = 0, t = 0;
-  for (; sweep < SVD_MAX_SWEEPS; ++sweep) {
+  for (; sweep < s.max_sweeps; ++sweep) {
     int rotated = 0;
     for (int round = 0; round < qq - 1; ++round, ++t) {
       const int b = t & 1;
@@ -616,7 +647,7 @@ __global__ void __launch_bounds__(SVC_THREADS) k_svd_cluster(const SvdArgs s, do
     __syncthreads();
     if (!s_rot) break;        // identical in every CTA (same sums, same decisions)
   }
-  if (sweep >= SVD_MAX_SWEEPS && tid == 0 && rank == 0) atomicOr(s.flag, FLAG_SVD_NOCONV);
+  if (sweep >= s.max_sweeps && tid == 0 && rank == 0) atomicOr(s.flag, FLAG_SVD_NOCONV);
   // column norms of G over all rows, then a stable descending order
   cluster.sync();
   const int b = t & 1;
@@ -829,6 +860,7 @@ void svd_trunc(Ctx& cx, int m, int n, const TP& A, int kk, const TP& US, const T
   s.US = US.all(np);
   s.Vt = Vt.all(np);
   s.flag = cx.flag;
+  s.max_sweeps = std::max(1, cx.svd_cap);
   s.wst = ((long long)s.p * s.q + (long long)s.q * s.q + 2LL * s.q + 31) / 32 * 32;
   s.work = cx.scratch(size_t(np) * s.wst);
   const double flops = 8.0 * 4.0 * double(s.p) * s.q * s.q;

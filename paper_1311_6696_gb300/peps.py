@@ -29,6 +29,7 @@ EXPORTS = [
     "peps_cu0_noalloc", "peps_closure_data", "peps_mlp_param_count", "peps_mlp_init",
     "peps_mlp_loss_grad", "peps_mlp_train", "peps_mlp_predict", "peps_plan_create", "peps_plan_run",
     "peps_plan_env", "peps_plan_launches", "peps_plan_free", "peps_plan_tune",
+    "peps_set_iteration_caps", "peps_wait_selftest",
 ]
 CLOSURE_WIDTH = 256
 
@@ -92,6 +93,8 @@ def _load():
     lib.peps_plan_launches.restype = C.c_longlong
     lib.peps_plan_free.argtypes = [P]
     lib.peps_plan_free.restype = None
+    lib.peps_set_iteration_caps.argtypes = [C.c_int, C.c_int]
+    lib.peps_wait_selftest.argtypes = [C.c_int, P]
     return lib
 
 
@@ -301,6 +304,17 @@ def cu0_noalloc(A_dev, sigma_dev, stream=None):
             raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is "
                              f"cuda:{torch.cuda.current_device()}")
     _check(lib.peps_cu0_noalloc(A_dev.data_ptr(), Ly, Lx, d, D, sigma_dev.data_ptr(), _stream_ptr(stream)))
+
+
+def set_iteration_caps(cu0_half_sweeps: int = 0, jacobi_sweeps: int = 0):
+    """Caps of the CU_0 half-sweeps and the Jacobi sweeps (0: default); see
+    peps_set_iteration_caps."""
+    _check(lib.peps_set_iteration_caps(int(cu0_half_sweeps), int(jacobi_sweeps)))
+
+
+def wait_selftest(budget_us: int = 2000, stream=None):
+    """Runs the bounded-wait self-test (raises PepsError with ETIMEOUT)."""
+    _check(lib.peps_wait_selftest(int(budget_us), _stream_ptr(stream)))
 
 
 # ---------------------------------------------------------------- learned closure

@@ -70,3 +70,23 @@ def test_cu0_noalloc_wrapper_rejects_bad_inputs_before_any_launch():
     for A, s, exc in cases:
         with pytest.raises(exc):
             peps.cu0_noalloc(A, s)
+
+
+def test_iteration_caps_are_validated_on_the_host():
+    from paper_1311_6696_gb300 import peps
+    for bad in ((-1, 0), (0, -5), (2_000_000, 0)):
+        with pytest.raises(peps.PepsError) as e:
+            peps.set_iteration_caps(*bad)
+        assert e.value.code == peps.EINVAL
+    peps.set_iteration_caps(5, 7)
+    peps.set_iteration_caps(0, 0)                   # back to the defaults
+
+
+def test_wait_selftest_without_gpu_is_ecuda():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1311_6696_gb300 import peps
+    with pytest.raises(peps.PepsError) as e:
+        peps.wait_selftest(1000)
+    assert e.value.code == peps.ECUDA
