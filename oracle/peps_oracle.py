@@ -711,6 +711,51 @@ def env_cluster(Ad_or_lat, n: int, chi: int, mode: str = "svd", sweeps: int = 2,
 
 
 # ---------------------------------------------------------------------------
+# Boundary fidelity (Section 5.2, Fig. Fid): distance of the environment of
+# the left-most column, computed with a cluster of delta columns, from the
+# full contraction of the other columns at a large reference bond.
+# ---------------------------------------------------------------------------
+def mps_overlap(P, Q):
+    """<P|Q> of two boundary MPS with the same physical legs (real)."""
+    E = np.ones((1, 1))
+    for a, b in zip(P, Q):
+        E = _ein("ab,auvc->buvc", E, a)
+        E = _ein("buvc,buvd->cd", E, b)
+    return float(E[0, 0])
+
+
+def left_column_boundary(lat: Lat, delta: int, chi: int, mode: str = "var", sweeps: int = 2, seed: int = 0):
+    """The boundary MPS on the right legs of column 0 (the environment of the
+    left-most column).  delta >= Lx-1: the full contraction of columns
+    Lx-1 .. 1 (Section 2).  Otherwise the cluster form (Section 5.2):
+    columns delta .. 1 are absorbed at bond chi into the CU_0 separable
+    boundary (Section 5.1) of the columns right of column delta.  The sweep
+    is the right-to-left one (orientation 3, rows = columns from the right);
+    var noise is keyed by the rows of the part that is absorbed."""
+    o = orientations(lat)[3]
+    L = o.Ly
+    if delta >= L - 1:
+        b, _ = boundary_sweep(o, chi, mode, sweeps, seed, 3, upto=L - 1)
+        return b[L - 1]
+    r0 = L - 1 - delta
+    sep = cu0_sweep(o)[r0]
+    part = Lat(o.A[r0:], list(sep), list(o.bottom), list(o.left[r0:]), list(o.right[r0:]))
+    b, _ = boundary_sweep(part, chi, mode, sweeps, seed, 3, upto=delta)
+    return b[delta]
+
+
+def boundary_fidelity(Ad_or_lat, delta: int, chi: int, chi_ref: int, mode: str = "var", sweeps: int = 2,
+                      seed: int = 0) -> float:
+    """1 - f with f = |tr(rho_ref^T rho)| for unit-norm rho_ref, rho (Fig. Fid):
+    rho = left_column_boundary(delta, chi), rho_ref = the full contraction at chi_ref."""
+    lat = Ad_or_lat if isinstance(Ad_or_lat, Lat) else lattice_from_dense(Ad_or_lat)
+    ref = left_column_boundary(lat, lat.Lx, chi_ref, mode, sweeps, seed)
+    rho = left_column_boundary(lat, delta, chi, mode, sweeps, seed)
+    f = abs(mps_overlap(ref, rho)) / math.sqrt(mps_overlap(ref, ref) * mps_overlap(rho, rho))
+    return 1.0 - f
+
+
+# ---------------------------------------------------------------------------
 # Operators (eq. 1 and eq. 2 conventions: Pauli matrices, S = sigma/2)
 # ---------------------------------------------------------------------------
 SZ = np.array([[1.0, 0.0], [0.0, -1.0]])

@@ -462,3 +462,66 @@ def test_svd_truncation_is_sequential_eckart_young_on_the_dense_boundary():
     want = psi / np.linalg.norm(psi)
     got = got / np.linalg.norm(got)
     assert np.max(np.abs(got - want)) < 1e-10
+
+
+def _dense_row_transfer(row):
+    """The double-layer transfer matrix of one row (ket and bra, physical
+    index traced, left/right legs of dimension 1 at the row's ends), as a
+    dense matrix from the up-leg pairs (u_x, v_x) to the down-leg pairs
+    (n_x, o_x), sites in order, site 0 most significant."""
+    W = None
+    for A in row:
+        w = np.einsum("sulnr,svmoq->uvnolmrq", A, A)      # one site, (u,v) -> (n,o), (l,m) | (r,q)
+        du, dn, dl, dr = A.shape[1], A.shape[3], A.shape[2], A.shape[4]
+        w = w.reshape(du * du, dn * dn, dl * dl, dr * dr)
+        if W is None:
+            assert dl == 1
+            W = w[:, :, 0, :]                                 # [U, N, right]
+        else:
+            W = np.einsum("UNk,unkr->UuNnr", W, w)
+            W = W.reshape(W.shape[0] * W.shape[1], W.shape[2] * W.shape[3], W.shape[4])
+    assert W.shape[2] == 1
+    return W[:, :, 0]
+
+
+def test_boundary_fidelity_matches_dense_transfer_matrices():
+    """Fig. Fid's distance 1 - f, pinned by dense linear algebra on a 4x4 D=2
+    lattice: the exact environment of the left-most column is the product of
+    the dense row transfer matrices of the right-to-left sweep applied to the
+    trivial boundary; the cluster form applies only delta of them to the CU_0
+    product vector.  At exact chi the oracle's MPS form must agree."""
+    from oracle import peps_oracle as O
+    from paper_1311_6696_gb300 import synth
+    Ad = synth.peps_gauss(4, 4, 2, 2, seed=71, mean=0.2, std=1.0)
+    lat = O.lattice_from_dense(Ad)
+    o = O.orientations(lat)[3]
+    L = o.Ly
+    T = [_dense_row_transfer(o.A[r]) for r in range(L)]
+    ones = np.ones(1)
+    ref = ones
+    for r in range(L - 1):
+        ref = ref @ T[r]
+    cu0 = O.cu0_sweep(o)
+    for delta in (1, 2):
+        r0 = L - 1 - delta
+        v = np.ones(1)
+        for m in cu0[r0]:
+            v = np.kron(v, m.ravel())
+        for r in range(r0, L - 1):
+            v = v @ T[r]
+        f = abs(ref @ v) / (np.linalg.norm(ref) * np.linalg.norm(v))
+        got = O.boundary_fidelity(Ad, delta, chi=64, chi_ref=64, mode="svd")
+        assert abs(got - (1.0 - f)) < 1e-12, (delta, got, 1.0 - f)
+        assert got > 1e-6                       # the cluster form is not the full one here
+    assert O.boundary_fidelity(Ad, L - 1, chi=64, chi_ref=64, mode="svd") < 1e-13
+
+
+def test_boundary_fidelity_falls_with_the_cluster_size():
+    """Section 5.2 / Fig. Fid: at a large boundary bond the distance drops
+    with every added column and vanishes when the cluster holds them all."""
+    from oracle import peps_oracle as O
+    from paper_1311_6696_gb300 import synth
+    A = synth.peps_simple_update(6, 6, 2, seed=3, steps=100)
+    d = [O.boundary_fidelity(A, delta, chi=16, chi_ref=32) for delta in (1, 2, 3, 4)]
+    assert all(d[i + 1] < 0.5 * d[i] for i in range(3)), d
+    assert O.boundary_fidelity(A, 5, chi=32, chi_ref=32) < 1e-14
