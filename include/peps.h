@@ -266,6 +266,21 @@ int peps_mlp_predict(const float* w, const float* X, long long n, int d, int D, 
 int peps_set_iteration_caps(int cu0_half_sweeps, int jacobi_sweeps);
 int peps_wait_selftest(int budget_us, void* cuda_stream);
 
+/*
+ * peps_boundary_fidelity -- distance of a cluster environment from the full one.
+ *   Section 5.2, Fig. Fid: the boundary MPS on the right legs of column 0
+ *   (the environment of the left-most column) in the cluster form -- columns
+ *   delta .. 1 absorbed at bond opts->chi into the CU_0 separable boundary
+ *   (Section 5.1) of the columns right of column delta; delta >= Lx-1 is
+ *   the full contraction (Section 2) -- against the full contraction at bond
+ *   chi_ref.  *one_minus_f = 1 - f, f = |tr(rho_ref^T rho)| with both scaled
+ *   to tr(rho^T rho) = 1.  opts->mode, sweeps, precision and seed apply to
+ *   both contractions (var noise keyed by the rows of the absorbed part).
+ *   Needs Lx >= 2; the overlaps are FP64.  Synchronises the stream.
+ */
+int peps_boundary_fidelity(const peps_lattice* lat, const peps_opts* opts, int delta, int chi_ref,
+                           double* one_minus_f, void* cuda_stream);
+
 /* peps_env_ln_norm -- the norm recorded in a full env (PEPS_EINVAL for cluster envs). */
 int peps_env_ln_norm(const peps_env* env, double* ln_norm, int* sign, void* cuda_stream);
 

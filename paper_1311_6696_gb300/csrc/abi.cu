@@ -755,6 +755,36 @@ void cu0_all_sides(Ctx& cx, const peps_lattice* lat, Oriented& ori, Arena& keep,
   cu0_launch(cx, cl, 4);
 }
 
+// ln|<P|Q>| and its sign into out[0], out[1] (device, FP64): transfer
+// matrices from the left, each rescaled to unit norm with the logs summed.
+void mps_ln_overlap(Ctx& cx, const Mps& P, const Mps& Q, double* out) {
+  const int L = int(P.p.size());
+  PEPS_REQUIRE(L == int(Q.p.size()) && L >= 1, "internal: overlap of MPS of different lengths");
+  size_t maxE = 1, maxT = 1;
+  for (int x = 0; x < L; ++x) {
+    maxE = std::max(maxE, size_t(P.dims[x][3]) * Q.dims[x][3]);
+    maxT = std::max(maxT, size_t(Q.dims[x][0]) * P.dims[x][1] * P.dims[x][2] * P.dims[x][3]);
+  }
+  double* lnacc = cx.ws->dalloc(2);
+  fill(cx, lnacc, 2, 0.0);
+  double* E = cx.ws->dalloc(maxE);
+  double* E2 = cx.ws->dalloc(maxE);
+  double* T = cx.ws->dalloc(maxT);
+  fill(cx, E, 1, 1.0);
+  Dims ed = {1, 1};
+  for (int x = 0; x < L; ++x) {
+    PEPS_REQUIRE(P.dims[x][1] == Q.dims[x][1] && P.dims[x][2] == Q.dims[x][2], "internal: overlap legs");
+    const Dims td = ein_dims("ab,auvc->buvc", ed, P.dims[x]);
+    ein(cx, "ab,auvc->buvc", E, ed, P.p[x], P.dims[x], T);
+    const Dims nd = ein_dims("buvc,buvd->cd", td, Q.dims[x]);
+    ein(cx, "buvc,buvd->cd", T, td, Q.p[x], Q.dims[x], E2);
+    if (x + 1 < L) normalize(cx, E2, (long long)numel(nd), lnacc, lnacc + 1);
+    std::swap(E, E2);
+    ed = nd;
+  }
+  finish_norm(cx, lnacc, 1, nullptr, E, out, out + 1);
+}
+
 // Rim positions (orientation o, cut r >= 1, column x), in that order.
 std::vector<RimSite> rim_sites(const Oriented& ori, double* const sig[4], int D) {
   std::vector<RimSite> v;
@@ -1140,6 +1170,63 @@ int peps_wait_selftest(int budget_us, void* cuda_stream) {
     Call c(cuda_stream);
     wait_unset_flag(c.cx, (long long)budget_us * 1000);
     c.finish();
+  });
+}
+
+int peps_boundary_fidelity(const peps_lattice* lat, const peps_opts* opts, int delta, int chi_ref,
+                           double* one_minus_f, void* cuda_stream) {
+  return guard([&] {
+    PEPS_REQUIRE(one_minus_f != nullptr, "NULL argument");
+    PEPS_REQUIRE(delta >= 1, "delta must be >= 1");
+    PEPS_REQUIRE(chi_ref >= 1 && chi_ref <= 4096, "chi_ref must be in [1, 4096]");
+    require_device();
+    check_lattice(lat);
+    const Opts o = check_opts(opts, false);
+    PEPS_REQUIRE(lat->Lx >= 2, "the left-most column's environment needs Lx >= 2");
+    Call c(cuda_stream);
+    Arena keep(c.st);
+    Oriented ori;
+    build_orientations(c.cx, lat, keep, ori);
+    const OLat& o3 = ori.o[3];   // right-left sweep: rows are the columns from the right
+    const int L = o3.Ly, W = o3.Lx, D = lat->D;
+    double* ln = c.ws.dalloc(2);
+    fill(c.cx, ln, 2, 0.0);
+    Opts oref = o;
+    oref.chi = chi_ref;
+    Mps ref, rho;
+    {
+      Engine e(c.cx, oref, lat->d, D, W);
+      ref = e.sweep(o3, 3, L - 1, TP(ln), keep).back();
+    }
+    if (delta >= L - 1) {
+      Engine e(c.cx, o, lat->d, D, W);
+      rho = e.sweep(o3, 3, L - 1, TP(ln + 1), keep).back();
+    } else {
+      double* sig[4];
+      cu0_all_sides(c.cx, lat, ori, keep, sig);
+      const int r0 = L - 1 - delta;
+      OLat part;
+      part.Ly = delta + 1;
+      part.Lx = W;
+      part.d = o3.d;
+      part.sites.assign(o3.sites.begin() + size_t(r0) * W, o3.sites.end());
+      for (int x = 0; x < W; ++x)
+        part.top.push_back(Mat{TP(sig[3] + ((long long)r0 * W + x) * D * D), o3.at(r0, x).du});
+      part.bottom = o3.bottom;
+      part.left.assign(o3.left.begin() + r0, o3.left.end());
+      part.right.assign(o3.right.begin() + r0, o3.right.end());
+      Engine e(c.cx, o, lat->d, D, W);
+      rho = e.sweep(part, 3, delta, TP(ln + 1), keep).back();
+    }
+    double* ov = c.ws.dalloc(6);
+    mps_ln_overlap(c.cx, ref, rho, ov);
+    mps_ln_overlap(c.cx, ref, ref, ov + 2);
+    mps_ln_overlap(c.cx, rho, rho, ov + 4);
+    double h[6];
+    PEPS_CUDA(cudaMemcpyAsync(h, ov, sizeof(h), cudaMemcpyDeviceToHost, c.st));
+    c.finish();
+    PEPS_REQUIRE(h[3] > 0 && h[5] > 0, "zero boundary (degenerate state)");
+    *one_minus_f = 1.0 - std::exp(h[0] - 0.5 * (h[2] + h[4]));
   });
 }
 

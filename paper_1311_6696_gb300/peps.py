@@ -29,7 +29,7 @@ EXPORTS = [
     "peps_cu0_noalloc", "peps_closure_data", "peps_mlp_param_count", "peps_mlp_init",
     "peps_mlp_loss_grad", "peps_mlp_train", "peps_mlp_predict", "peps_plan_create", "peps_plan_run",
     "peps_plan_env", "peps_plan_launches", "peps_plan_free", "peps_plan_tune",
-    "peps_set_iteration_caps", "peps_wait_selftest",
+    "peps_set_iteration_caps", "peps_wait_selftest", "peps_boundary_fidelity",
 ]
 CLOSURE_WIDTH = 256
 
@@ -95,6 +95,8 @@ def _load():
     lib.peps_plan_free.restype = None
     lib.peps_set_iteration_caps.argtypes = [C.c_int, C.c_int]
     lib.peps_wait_selftest.argtypes = [C.c_int, P]
+    lib.peps_boundary_fidelity.argtypes = [C.POINTER(Lattice), C.POINTER(Opts), C.c_int, C.c_int,
+                                           C.POINTER(C.c_double), P]
     return lib
 
 
@@ -276,6 +278,20 @@ def norm(A, chi: int, mode="svd", sweeps: int = 2, precision="fp64", seed: int =
     sg = C.c_int()
     _check(lib.peps_norm(C.byref(inp.lat), C.byref(o), C.byref(ln), C.byref(sg), _stream_ptr(stream)))
     return ln.value, sg.value
+
+
+def boundary_fidelity(A, delta: int, chi: int, chi_ref: int, mode="var", sweeps: int = 2, precision="fp64",
+                      seed: int = 0, stream=None, device=None) -> float:
+    """1 - f of the left-most column's environment with a cluster of delta
+    columns at bond chi against the full contraction at chi_ref; see
+    peps_boundary_fidelity."""
+    _set_device(device)
+    inp = _Input(A)
+    o = _opts(chi, mode, sweeps, precision, 1, seed)
+    out = C.c_double()
+    _check(lib.peps_boundary_fidelity(C.byref(inp.lat), C.byref(o), int(delta), int(chi_ref), C.byref(out),
+                                      _stream_ptr(stream)))
+    return out.value
 
 
 def cu0_noalloc(A_dev, sigma_dev, stream=None):
