@@ -134,6 +134,20 @@ int peps_env_cluster(const peps_lattice* lat, const peps_opts* opts,
                      peps_env** out, void* cuda_stream);
 
 /*
+ * peps_env_cluster_range -- peps_env_cluster for the windows of the anchors
+ *   with row-major index y*Lx + x in [anchor_begin, anchor_end).  The
+ *   windows are independent (Section 5.2: separate processors each contract
+ *   their own clusters and need only the small separable-boundary tensors),
+ *   so a set of calls whose ranges partition [0, Ly*Lx) -- e.g. one per GPU
+ *   -- yields every site's and bond's density matrix exactly once: the
+ *   handle holds those of its own anchors (site (y,x), bonds to (y,x+1) and
+ *   (y+1,x)) and zeros elsewhere.  The CU_0 boundaries are computed in full
+ *   by every call.  0 <= anchor_begin <= anchor_end <= Ly*Lx, else PEPS_EINVAL.
+ */
+int peps_env_cluster_range(const peps_lattice* lat, const peps_opts* opts, long long anchor_begin,
+                           long long anchor_end, peps_env** out, void* cuda_stream);
+
+/*
  * peps_expect_local -- <O> = Tr(rho O) / Tr(rho) at every site or bond.
  *   Section 5.3 (local expectation values from local reduced density matrices).
  *   kind: PEPS_SITE / PEPS_HBOND / PEPS_VBOND.

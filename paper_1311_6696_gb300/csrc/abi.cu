@@ -799,8 +799,9 @@ std::vector<RimSite> rim_sites(const Oriented& ori, double* const sig[4], int D)
   return v;
 }
 
+// Windows of the anchors with row-major index in [a0, a1) (a1 < 0: all).
 void cluster_env(Call& c, const peps_lattice* lat, const Opts& opt, int n, peps_env* env, Oriented& ori,
-                 const float* closure_w) {
+                 const float* closure_w, long long a0 = 0, long long a1 = -1) {
   Ctx& cx = c.cx;
   const int Ly = lat->Ly, Lx = lat->Lx, d = lat->d, D = lat->D, DM2 = D * D;
   double* sig[4];
@@ -834,6 +835,8 @@ void cluster_env(Call& c, const peps_lattice* lat, const Opts& opt, int n, peps_
   std::map<std::array<int, 8>, std::vector<Win>> groups;
   for (int y = 0; y < Ly; ++y)
     for (int x = 0; x < Lx; ++x) {
+      const long long a = (long long)y * Lx + x;
+      if (a < a0 || (a1 >= 0 && a >= a1)) continue;
       const auto rr = window(Ly, y, n), cc = window(Lx, x, n);
       const Win wv{y, x, rr.first, rr.second, cc.first, cc.second};
       const std::array<int, 8> key{wv.r1 - wv.r0, wv.c1 - wv.c0, y - wv.r0, x - wv.c0,
@@ -987,27 +990,33 @@ void cluster_env(Call& c, const peps_lattice* lat, const Opts& opt, int n, peps_
 }
 
 // The whole environment computation of one call, enqueued on c's stream.
-void compute(Call& c, const peps_lattice* lat, const peps_opts* opts, const Opts& o, bool cluster, peps_env* env) {
+void compute(Call& c, const peps_lattice* lat, const peps_opts* opts, const Opts& o, bool cluster, peps_env* env,
+             long long a0 = 0, long long a1 = -1) {
   Oriented ori;
   build_orientations(c.cx, lat, *env->arena, ori);
   if (cluster)
     cluster_env(c, lat, o, opts->n, env, ori,
-                opts->closure == PEPS_CLOSURE_LEARNED ? static_cast<const float*>(opts->closure_weights) : nullptr);
+                opts->closure == PEPS_CLOSURE_LEARNED ? static_cast<const float*>(opts->closure_weights) : nullptr,
+                a0, a1);
   else
     full_env(c, lat, o, env, ori);
 }
 
-int run_env(const peps_lattice* lat, const peps_opts* opts, peps_env** out, void* stream, bool cluster) {
+int run_env(const peps_lattice* lat, const peps_opts* opts, peps_env** out, void* stream, bool cluster,
+            long long a0 = 0, long long a1 = -1) {
   if (out) *out = nullptr;
   return guard([&] {
     PEPS_REQUIRE(out != nullptr, "out is NULL");
     require_device();
     check_lattice(lat);
     const Opts o = check_opts(opts, cluster);
+    if (cluster && a1 >= 0)
+      PEPS_REQUIRE(a0 >= 0 && a0 <= a1 && a1 <= (long long)lat->Ly * lat->Lx,
+                   "anchor range must satisfy 0 <= begin <= end <= Ly*Lx");
     Call c(stream);
     auto env = new_env(lat, cluster ? 1 : 0, c.st);
     const auto t0 = std::chrono::steady_clock::now();
-    compute(c, lat, opts, o, cluster, env.get());
+    compute(c, lat, opts, o, cluster, env.get(), a0, a1);
     const auto t1 = std::chrono::steady_clock::now();
     c.finish();
     if (std::getenv("PEPS_VERBOSE")) {
@@ -1151,6 +1160,15 @@ int peps_env_full(const peps_lattice* lat, const peps_opts* opts, peps_env** out
 
 int peps_env_cluster(const peps_lattice* lat, const peps_opts* opts, peps_env** out, void* cuda_stream) {
   return run_env(lat, opts, out, cuda_stream, true);
+}
+
+int peps_env_cluster_range(const peps_lattice* lat, const peps_opts* opts, long long anchor_begin,
+                           long long anchor_end, peps_env** out, void* cuda_stream) {
+  if (anchor_end < 0) {
+    if (out) *out = nullptr;
+    return fail(PEPS_EINVAL, "anchor range must satisfy 0 <= begin <= end <= Ly*Lx");
+  }
+  return run_env(lat, opts, out, cuda_stream, true, anchor_begin, anchor_end);
 }
 
 int peps_set_iteration_caps(int cu0_half_sweeps, int jacobi_sweeps) {

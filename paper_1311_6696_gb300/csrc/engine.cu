@@ -37,6 +37,7 @@ Engine::Engine(Ctx& c, const Opts& o, int d, int Dmax, int Lmax, int nb)
   X2_ = alloc(*cx.ws, bigN_ * dd * d);   // ket stage with up to one open pair
   x1per_ = (std::max(bigN_ * dd, chi * chi * D2 * dd * dd) + 31) / 32 * 32;
   x2per_ = (bigN_ * dd * d + 31) / 32 * 32;
+  x3per_ = (bigN_ * dd * dd + 31) / 32 * 32;
   X3_ = alloc(*cx.ws, bigN_ * dd * dd);  // bra stage with up to two open pairs
   envN_ = chi * D2 * chi * dd;
   bb_ = alloc(*cx.ws, envN_);
@@ -54,7 +55,7 @@ Engine::Engine(Ctx& c, const Opts& o, int d, int Dmax, int Lmax, int nb)
   tc_ = o.precision != PEPS_PREC_FP64;
   x64_ = !tc_;
   site_packs_ = std::make_unique<PackCache>(cx.ws);
-  main_ = Side{&cx, X1_, X2_, X3_, tmp0_, site_packs_.get(), x1per_ * nb_, x2per_ * nb_};
+  main_ = Side{&cx, X1_, X2_, X3_, tmp0_, site_packs_.get(), x1per_ * nb_, x2per_ * nb_, x3per_ * nb_};
 }
 
 Engine::~Engine() {
@@ -97,7 +98,7 @@ void Engine::enable_dual(cudaStream_t st2) {
               strided(ws2_->dalloc((bigN_ * dd * d_ + 31) / 32 * 32), 1, bigN_ * dd * d_),
               strided(ws2_->dalloc((bigN_ * dd * dd + 31) / 32 * 32), 1, bigN_ * dd * dd),
               strided(ws2_->dalloc(32), 1, 1), cache2_.get(), (x1 + 31) / 32 * 32,
-              (bigN_ * dd * d_ + 31) / 32 * 32};
+              (bigN_ * dd * d_ + 31) / 32 * 32, (bigN_ * dd * dd + 31) / 32 * 32};
   dual_ = true;
 }
 
@@ -114,7 +115,7 @@ void Engine::use(int B) {
   for (TP* t : {&X1_, &X2_, &X3_, &bb_, &tmp0_, &tmp1_}) t->n = B;
   for (auto& t : Lenv_) t.n = B;
   for (auto& t : Renv_) t.n = B;
-  main_ = Side{&cx, X1_, X2_, X3_, tmp0_, site_packs_.get(), x1per_ * B, x2per_ * B};   // the helpers' view
+  main_ = Side{&cx, X1_, X2_, X3_, tmp0_, site_packs_.get(), x1per_ * B, x2per_ * B, x3per_ * B};   // the helpers' view
 }
 
 TP Engine::alloc(Arena& a, size_t per) const {
@@ -152,8 +153,47 @@ Mps Engine::closure_mps(const std::vector<Mat>& mats, Arena&) {
 // (s, then the bra leg pair) so that the second GEMM's rows write contiguous
 // runs, which changes only the FP32 summation order.  Falls back to the plain
 // form where the chain buffers are too small for a padded operand (tiny bonds).
+void Engine::chain_last(const char* s3, const TcOperand& o2, const Dims& x2, const SiteT& A, const TP& X3,
+                        Use* u1, Use* u2) {
+  Ctx& c = *side_->cx;
+  const Dims ad = A.dims();
+  const Dims x3 = ein_dims(s3, x2, ad);
+  TcChain c3;
+  c3.a_pre = &o2;
+  if (u1) u1->op = TcOperand();
+  if (u2) u2->op = TcOperand();
+  const int np = o2.np;
+  const size_t w1 = u1 ? tc_operand_words(u1->spec, x3, u1->bd, np, opt.precision) : 0;
+  const size_t w2 = u2 ? tc_operand_words(u2->spec, x3, u2->bd, np, opt.precision) : 0;
+  if (u1 && X3.p[0] == side_->X3.p[0] && w1 + w2 <= side_->x3n) {
+    c3.next = u1->spec;
+    c3.next_bd = u1->bd;
+    c3.next_mem = side_->X3.d(0);
+    c3.next_cap = w1;
+    c3.next_out = &u1->op;
+    if (u2) {
+      c3.next2 = u2->spec;
+      c3.next2_bd = u2->bd;
+      c3.next2_mem = side_->X3.d(0) + w1;
+      c3.next2_cap = w2;
+      c3.next2_out = &u2->op;
+    }
+  }
+  ein_tc(c, s3, TP(), 0, x2, A.p, 1, ad, X3, 0, opt.precision, 1.0, TP(), side_->cache, &c3);
+}
+
+void Engine::con_use(const Use& u, const TP& X, const Dims& xd, const TP& B, const TP& C) {
+  if (u.op.hi) {
+    TcChain ch;
+    ch.a_pre = &u.op;
+    ein_tc(*side_->cx, u.spec, TP(), 0, xd, B, 1, u.bd, C, 1, opt.precision, 1.0, TP(), nullptr, &ch);
+  } else {
+    con(u.spec, X, x64_, xd, B, true, u.bd, C, true);
+  }
+}
+
 Dims Engine::chain_left_tc(const TP& L, const Dims& ld, const TP& M, const Dims& md, const SiteT& A,
-                           const TP& X3) {
+                           const TP& X3, Use* u1, Use* u2) {
   static const char* s1 = "clma,auvb->clmbvu";
   static const char* s2 = "clmbvu,sulnr->cbsmvnr";
   static const char* s3 = "cbsmvnr,svmoq->cbnroq";
@@ -165,7 +205,7 @@ Dims Engine::chain_left_tc(const TP& L, const Dims& ld, const TP& M, const Dims&
       tc_operand_words(s3, x2, ad, np, opt.precision) > side_->x2n)
     return Dims();
   TcOperand o1, o2;
-  TcChain c1, c2, c3;
+  TcChain c1, c2;
   c1.next = s2;
   c1.next_bd = ad;
   c1.next_mem = side_->X1.d(0);
@@ -179,13 +219,12 @@ Dims Engine::chain_left_tc(const TP& L, const Dims& ld, const TP& M, const Dims&
   c2.next_cap = side_->x2n;
   c2.next_out = &o2;
   ein_tc(c, s2, TP(), 0, x1, A.p, 1, ad, TP(), 0, opt.precision, 1.0, TP(), side_->cache, &c2);
-  c3.a_pre = &o2;
-  ein_tc(c, s3, TP(), 0, x2, A.p, 1, ad, X3, 0, opt.precision, 1.0, TP(), side_->cache, &c3);
+  chain_last(s3, o2, x2, A, X3, u1, u2);
   return x3;
 }
 
 Dims Engine::chain_right_tc(const TP& R, const Dims& rd, const TP& M, const Dims& md, const SiteT& A,
-                            const TP& Y3) {
+                            const TP& Y3, Use* u1, Use* u2) {
   static const char* s1 = "auvb,brqc->auvcqr";
   static const char* s2 = "auvcqr,sulnr->acsvqln";
   static const char* s3 = "acsvqln,svmoq->aclnmo";
@@ -197,7 +236,7 @@ Dims Engine::chain_right_tc(const TP& R, const Dims& rd, const TP& M, const Dims
       tc_operand_words(s3, y2, ad, np, opt.precision) > side_->x2n)
     return Dims();
   TcOperand o1, o2;
-  TcChain c1, c2, c3;
+  TcChain c1, c2;
   c1.next = s2;
   c1.next_bd = ad;
   c1.next_mem = side_->X1.d(0);
@@ -211,15 +250,16 @@ Dims Engine::chain_right_tc(const TP& R, const Dims& rd, const TP& M, const Dims
   c2.next_cap = side_->x2n;
   c2.next_out = &o2;
   ein_tc(c, s2, TP(), 0, y1, A.p, 1, ad, TP(), 0, opt.precision, 1.0, TP(), side_->cache, &c2);
-  c3.a_pre = &o2;
-  ein_tc(c, s3, TP(), 0, y2, A.p, 1, ad, Y3, 0, opt.precision, 1.0, TP(), side_->cache, &c3);
+  chain_last(s3, o2, y2, A, Y3, u1, u2);
   return y3;
 }
 
 Dims Engine::chain_left(const TP& L, const Dims& ld, const TP& M, const Dims& md, const SiteT& A,
-                        const TP& X3) {
+                        const TP& X3, Use* u1, Use* u2) {
+  if (u1) u1->op = TcOperand();
+  if (u2) u2->op = TcOperand();
   if (tc_) {
-    const Dims r = chain_left_tc(L, ld, M, md, A, X3);
+    const Dims r = chain_left_tc(L, ld, M, md, A, X3, u1, u2);
     if (!r.empty()) return r;
   }
   const Dims ad = A.dims();
@@ -233,9 +273,11 @@ Dims Engine::chain_left(const TP& L, const Dims& ld, const TP& M, const Dims& md
 }
 
 Dims Engine::chain_right(const TP& R, const Dims& rd, const TP& M, const Dims& md, const SiteT& A,
-                         const TP& Y3) {
+                         const TP& Y3, Use* u1, Use* u2) {
+  if (u1) u1->op = TcOperand();
+  if (u2) u2->op = TcOperand();
   if (tc_) {
-    const Dims r = chain_right_tc(R, rd, M, md, A, Y3);
+    const Dims r = chain_right_tc(R, rd, M, md, A, Y3, u1, u2);
     if (!r.empty()) return r;
   }
   const Dims ad = A.dims();
@@ -369,24 +411,29 @@ Mps Engine::var_compress(const Mps& T, const OLat& lat, int y, const std::vector
     ld[0] = {1, l.n, l.n, 1};
     copy(cx, Lenv_[0], l.p, (long long)l.n * l.n);
   }
+  // Each chain names the contractions of its result (Use), so that the
+  // tensor-core chain writes their operands directly.
   for (int x = Lx - 1; x >= 1; --x) {
-    const Dims y3 = chain_right(Renv_[x], rd[x], T.p[x], T.dims[x], lat.at(y, x), X3_);
+    Use ur{"aelnmo,cnoe->almc", N.dims[x]};
+    const Dims y3 = chain_right(Renv_[x], rd[x], T.p[x], T.dims[x], lat.at(y, x), X3_, &ur);
     rd[x - 1] = ein_dims("aelnmo,cnoe->almc", y3, N.dims[x]);
-    con("aelnmo,cnoe->almc", X3_, x64_, y3, N.p[x], true, N.dims[x], Renv_[x - 1], true);
+    con_use(ur, X3_, y3, N.p[x], Renv_[x - 1]);
   }
   for (int h = 0; h < opt.sweeps; ++h) {
     if (h % 2 == 0) {
       for (int x = 0; x < Lx; ++x) {
-        const Dims x3 = chain_left(Lenv_[x], ld[x], T.p[x], T.dims[x], lat.at(y, x), X3_);
+        Use ub{"cbnroq,brqe->cnoe", rd[x]}, ul{"cbnroq,cnoe->erqb", N.dims[x]};
+        const Dims x3 =
+            chain_left(Lenv_[x], ld[x], T.p[x], T.dims[x], lat.at(y, x), X3_, &ub, x < Lx - 1 ? &ul : nullptr);
         const Dims bd = ein_dims("cbnroq,brqe->cnoe", x3, rd[x]);
-        con("cbnroq,brqe->cnoe", X3_, x64_, x3, Renv_[x], true, rd[x], bb_, true);
+        con_use(ub, X3_, x3, Renv_[x], bb_);
         PEPS_REQUIRE(bd == N.dims[x], "internal: local tensor shape");
         if (x < Lx - 1) {
           const int m = bd[0] * bd[1] * bd[2], n = bd[3];
           PEPS_REQUIRE(n <= m, "internal: inconsistent bond caps");
           qr_thin(cx, m, n, bb_, n, 1, N.p[x], n, 1, TP());
           ld[x + 1] = ein_dims("cbnroq,cnoe->erqb", x3, N.dims[x]);
-          con("cbnroq,cnoe->erqb", X3_, x64_, x3, N.p[x], true, N.dims[x], Lenv_[x + 1], true);
+          con_use(ul, X3_, x3, N.p[x], Lenv_[x + 1]);
         } else {
           copy(cx, N.p[x], bb_, (long long)numel(bd));
         }
@@ -394,15 +441,22 @@ Mps Engine::var_compress(const Mps& T, const OLat& lat, int y, const std::vector
       centre = Lx - 1;
     } else {
       for (int x = Lx - 1; x >= 0; --x) {
-        const Dims y3 = chain_right(Renv_[x], rd[x], T.p[x], T.dims[x], lat.at(y, x), X3_);
+        // the local vector with the chain result as operand A (tensor cores), or
+        // with the left environment first (FP64, the plain form)
+        Use ub{tc_ ? "aelnmo,clma->cnoe" : nullptr, ld[x]}, ur{"aelnmo,cnoe->almc", N.dims[x]};
+        const Dims y3 = chain_right(Renv_[x], rd[x], T.p[x], T.dims[x], lat.at(y, x), X3_, tc_ ? &ub : nullptr,
+                                    x > 0 ? &ur : nullptr);
         const Dims bd = ein_dims("clma,aelnmo->cnoe", ld[x], y3);
-        con("clma,aelnmo->cnoe", Lenv_[x], true, ld[x], X3_, x64_, y3, bb_, true);
+        if (tc_)
+          con_use(ub, X3_, y3, Lenv_[x], bb_);
+        else
+          con("clma,aelnmo->cnoe", Lenv_[x], true, ld[x], X3_, x64_, y3, bb_, true);
         PEPS_REQUIRE(bd == N.dims[x], "internal: local tensor shape");
         if (x > 0) {
           const int c = bd[0], noe = bd[1] * bd[2] * bd[3];
           qr_thin(cx, noe, c, bb_, 1, noe, N.p[x], 1, noe, TP());
           rd[x - 1] = ein_dims("aelnmo,cnoe->almc", y3, N.dims[x]);
-          con("aelnmo,cnoe->almc", X3_, x64_, y3, N.p[x], true, N.dims[x], Renv_[x - 1], true);
+          con_use(ur, X3_, y3, N.p[x], Renv_[x - 1]);
         } else {
           copy(cx, N.p[x], bb_, (long long)numel(bd));
         }
@@ -482,9 +536,10 @@ void Engine::row_rhos(const OLat& lat, const Mps& T, const Mps& B, int y, const 
     xmin = std::min(xmin, t.first);
   }
   for (int x = 0; x + 1 < Lx && x + 1 < xmax; ++x) {
-    const Dims x3 = chain_left(Lenv_[x], ld[x], T.p[x], T.dims[x], lat.at(y, x), X3_);
+    Use ul{"cbnroq,cnoe->erqb", B.dims[x]};
+    const Dims x3 = chain_left(Lenv_[x], ld[x], T.p[x], T.dims[x], lat.at(y, x), X3_, &ul);
     ld[x + 1] = ein_dims("cbnroq,cnoe->erqb", x3, B.dims[x]);
-    con("cbnroq,cnoe->erqb", X3_, x64_, x3, B.p[x], true, B.dims[x], Lenv_[x + 1], true);
+    con_use(ul, X3_, x3, B.p[x], Lenv_[x + 1]);
     normalize(cx, Lenv_[x + 1], (long long)numel(ld[x + 1]), TP(), tmp0_);
   }
   // Right environments: on the second stream when there is one (they depend
@@ -499,9 +554,10 @@ void Engine::row_rhos(const OLat& lat, const Mps& T, const Mps& B, int y, const 
   }
   copy(*side_->cx, Renv_[Lx - 1], rc.p, (long long)rc.n * rc.n);
   for (int x = Lx - 1; x >= 1 && x - 1 >= xmin; --x) {
-    const Dims y3 = chain_right(Renv_[x], rd[x], T.p[x], T.dims[x], lat.at(y, x), side_->X3);
+    Use ur{"aelnmo,cnoe->almc", B.dims[x]};
+    const Dims y3 = chain_right(Renv_[x], rd[x], T.p[x], T.dims[x], lat.at(y, x), side_->X3, &ur);
     rd[x - 1] = ein_dims("aelnmo,cnoe->almc", y3, B.dims[x]);
-    con("aelnmo,cnoe->almc", side_->X3, x64_, y3, B.p[x], true, B.dims[x], Renv_[x - 1], true);
+    con_use(ur, side_->X3, y3, B.p[x], Renv_[x - 1]);
     normalize(*side_->cx, Renv_[x - 1], (long long)numel(rd[x - 1]), TP(), side_->tmp);
   }
   if (dual_) {
@@ -559,11 +615,12 @@ void Engine::norm_from_top(const OLat& lat, const Mps& T, const TP& lns_acc, con
   copy(cx, Lenv_[0], lc.p, (long long)lc.n * lc.n);
   int cur = 0;
   for (int x = 0; x < Lx; ++x) {
-    const Dims x3 = chain_left(Lenv_[cur], ld, T.p[x], T.dims[x], lat.at(y, x), X3_);
     const Mat& bc = lat.bottom[x];
     const Dims bd = {1, bc.n, bc.n, 1};
+    Use ul{"cbnroq,cnoe->erqb", bd};
+    const Dims x3 = chain_left(Lenv_[cur], ld, T.p[x], T.dims[x], lat.at(y, x), X3_, &ul);
     const Dims nd = ein_dims("cbnroq,cnoe->erqb", x3, bd);
-    con("cbnroq,cnoe->erqb", X3_, x64_, x3, bc.p, true, bd, Lenv_[1 - cur], true);
+    con_use(ul, X3_, x3, bc.p, Lenv_[1 - cur]);
     cur = 1 - cur;
     ld = nd;
     if (x + 1 < Lx) normalize(cx, Lenv_[cur], (long long)numel(ld), extra, tmp0_);

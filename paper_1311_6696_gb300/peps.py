@@ -29,7 +29,7 @@ EXPORTS = [
     "peps_cu0_noalloc", "peps_closure_data", "peps_mlp_param_count", "peps_mlp_init",
     "peps_mlp_loss_grad", "peps_mlp_train", "peps_mlp_predict", "peps_plan_create", "peps_plan_run",
     "peps_plan_env", "peps_plan_launches", "peps_plan_free", "peps_plan_tune",
-    "peps_set_iteration_caps", "peps_wait_selftest", "peps_boundary_fidelity",
+    "peps_set_iteration_caps", "peps_wait_selftest", "peps_boundary_fidelity", "peps_env_cluster_range",
 ]
 CLOSURE_WIDTH = 256
 
@@ -97,6 +97,8 @@ def _load():
     lib.peps_wait_selftest.argtypes = [C.c_int, P]
     lib.peps_boundary_fidelity.argtypes = [C.POINTER(Lattice), C.POINTER(Opts), C.c_int, C.c_int,
                                            C.POINTER(C.c_double), P]
+    lib.peps_env_cluster_range.argtypes = [C.POINTER(Lattice), C.POINTER(Opts), C.c_longlong, C.c_longlong,
+                                           C.POINTER(P), P]
     return lib
 
 
@@ -211,14 +213,20 @@ def env_full(A, chi: int, mode="svd", sweeps: int = 2, precision="fp64", seed: i
 
 
 def env_cluster(A, n: int, chi: int, mode="svd", sweeps: int = 2, precision="fp64", seed: int = 0,
-                stream=None, device=None, closure_weights=None) -> Env:
+                stream=None, device=None, closure_weights=None, anchors=None) -> Env:
     """Cluster environments (window n x n around every site); see peps_env_cluster.
-    closure_weights: a float32 CUDA tensor of learned-closure weights (width 256)."""
+    closure_weights: a float32 CUDA tensor of learned-closure weights (width 256).
+    anchors: (begin, end) -- only the windows of anchors y*Lx+x in [begin, end)
+    (peps_env_cluster_range)."""
     _set_device(device)
     inp = _Input(A)
     o = _opts(chi, mode, sweeps, precision, n, seed, closure_weights)
     h = C.c_void_p()
-    _check(lib.peps_env_cluster(C.byref(inp.lat), C.byref(o), C.byref(h), _stream_ptr(stream)))
+    if anchors is None:
+        _check(lib.peps_env_cluster(C.byref(inp.lat), C.byref(o), C.byref(h), _stream_ptr(stream)))
+    else:
+        a0, a1 = (int(v) for v in anchors)
+        _check(lib.peps_env_cluster_range(C.byref(inp.lat), C.byref(o), a0, a1, C.byref(h), _stream_ptr(stream)))
     return Env(h.value, (inp.lat.Ly, inp.lat.Lx, inp.lat.d), stream)
 
 
