@@ -145,8 +145,6 @@ struct TcOperand {
 //             receives its description.  C and Clo are then ignored.
 // K is ordered as in a plain call, so the result is the same as packing the
 // FP32 output of a plain call.
-//   next2:    with `next`, also write C as operand A of a second contraction
-//             (the same tensor summed over other letters), likewise.
 struct TcChain {
   const TcOperand* a_pre = nullptr;
   const char* next = nullptr;
@@ -154,11 +152,6 @@ struct TcChain {
   double* next_mem = nullptr;
   size_t next_cap = 0;
   TcOperand* next_out = nullptr;
-  const char* next2 = nullptr;
-  Dims next2_bd;
-  double* next2_mem = nullptr;
-  size_t next2_cap = 0;
-  TcOperand* next2_out = nullptr;
 };
 
 // Doubles a TcChain target needs for operand A of `spec` (hi and lo parts).

@@ -5,6 +5,8 @@
 // log-scales, convergence) stays on the device.
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <set>
 
 #include "aux.cuh"
 #include "engine.cuh"
@@ -32,15 +34,17 @@ Engine::Engine(Ctx& c, const Opts& o, int d, int Dmax, int Lmax, int nb)
   PEPS_REQUIRE(nb >= 1 && nb <= MAXB, "internal: problems per engine");
   const size_t chi = size_t(o.chi), D2 = size_t(Dmax) * Dmax, dd = size_t(d) * d;
   bigN_ = chi * chi * D2 * D2;
-  // X1: chain stage 1 (chi^2 D^4), or bond stage 1 (d^2 chi^2 D^4) / bond stage 4 (d^4 chi^2 D^2)
-  X1_ = alloc(*cx.ws, std::max(bigN_ * dd, chi * chi * D2 * dd * dd));
-  X2_ = alloc(*cx.ws, bigN_ * dd * d);   // ket stage with up to one open pair
-  x1per_ = (std::max(bigN_ * dd, chi * chi * D2 * dd * dd) + 31) / 32 * 32;
+  // X1: chain stage 1 (chi^2 D^4; room for a padded tensor-core operand);
+  // X2: ket stage (d chi^2 D^4); X3: bra stage with the physical pair open
+  // (d^2 chi^2 D^4).  The largest intermediates of an environment set.
+  X1_ = alloc(*cx.ws, bigN_ * dd);
+  X2_ = alloc(*cx.ws, bigN_ * dd * d);
+  x1per_ = (bigN_ * dd + 31) / 32 * 32;
   x2per_ = (bigN_ * dd * d + 31) / 32 * 32;
-  x3per_ = (bigN_ * dd * dd + 31) / 32 * 32;
-  X3_ = alloc(*cx.ws, bigN_ * dd * dd);  // bra stage with up to two open pairs
+  X3_ = alloc(*cx.ws, bigN_ * dd);
   envN_ = chi * D2 * chi * dd;
   bb_ = alloc(*cx.ws, envN_);
+  vv_ = alloc(*cx.ws, envN_);
   Lmax = std::max(Lmax, 2);
   Lenv_.resize(Lmax);
   Renv_.resize(Lmax);
@@ -55,7 +59,7 @@ Engine::Engine(Ctx& c, const Opts& o, int d, int Dmax, int Lmax, int nb)
   tc_ = o.precision != PEPS_PREC_FP64;
   x64_ = !tc_;
   site_packs_ = std::make_unique<PackCache>(cx.ws);
-  main_ = Side{&cx, X1_, X2_, X3_, tmp0_, site_packs_.get(), x1per_ * nb_, x2per_ * nb_, x3per_ * nb_};
+  main_ = Side{&cx, X1_, X2_, X3_, tmp0_, site_packs_.get(), x1per_ * nb_, x2per_ * nb_};
 }
 
 Engine::~Engine() {
@@ -74,7 +78,7 @@ Engine::~Engine() {
 
 void Engine::enable_dual(cudaStream_t st2) {
   const size_t chi = size_t(opt.chi), D2 = size_t(Dmax_) * Dmax_, dd = size_t(d_) * d_;
-  const size_t set = (std::max(bigN_ * dd, chi * chi * D2 * dd * dd) + bigN_ * dd * d_ + bigN_ * dd * dd) * 8;
+  const size_t set = (bigN_ * dd + bigN_ * dd * d_ + bigN_ * dd) * 8;
   if (dual_ || nb_ != 1 || set > (size_t(512) << 20)) return;
   ws2_stream_ = st2;
   {
@@ -93,29 +97,28 @@ void Engine::enable_dual(cudaStream_t st2) {
   cx2_->cu0_cap = cx.cu0_cap;
   cx2_->tmp = ws2_->dalloc(8);
   cache2_ = std::make_unique<PackCache>(ws2_.get());
-  const size_t x1 = std::max(bigN_ * dd, chi * chi * D2 * dd * dd);
+  const size_t x1 = bigN_ * dd;
   aux_ = Side{cx2_.get(), strided(ws2_->dalloc((x1 + 31) / 32 * 32), 1, x1),
               strided(ws2_->dalloc((bigN_ * dd * d_ + 31) / 32 * 32), 1, bigN_ * dd * d_),
-              strided(ws2_->dalloc((bigN_ * dd * dd + 31) / 32 * 32), 1, bigN_ * dd * dd),
+              strided(ws2_->dalloc((bigN_ * dd + 31) / 32 * 32), 1, bigN_ * dd),
               strided(ws2_->dalloc(32), 1, 1), cache2_.get(), (x1 + 31) / 32 * 32,
-              (bigN_ * dd * d_ + 31) / 32 * 32, (bigN_ * dd * dd + 31) / 32 * 32};
+              (bigN_ * dd * d_ + 31) / 32 * 32};
   dual_ = true;
 }
 
 size_t Engine::footprint(const Opts& o, int d, int Dmax, int Lmax) {
   const size_t chi = size_t(o.chi), D2 = size_t(Dmax) * Dmax, dd = size_t(d) * d;
   const size_t big = chi * chi * D2 * D2, env = chi * D2 * chi * dd;
-  return std::max(big * dd, chi * chi * D2 * dd * dd) + big * dd * d + big * dd * dd + env +
-         2 * size_t(std::max(Lmax, 2)) * env + 6 * 32;
+  return big * dd + big * dd * d + big * dd + 2 * env + 2 * size_t(std::max(Lmax, 2)) * env + 7 * 32;
 }
 
 void Engine::use(int B) {
   PEPS_REQUIRE(B >= 1 && B <= cap_, "internal: more problems than the engine holds");
   nb_ = B;
-  for (TP* t : {&X1_, &X2_, &X3_, &bb_, &tmp0_, &tmp1_}) t->n = B;
+  for (TP* t : {&X1_, &X2_, &X3_, &bb_, &vv_, &tmp0_, &tmp1_}) t->n = B;
   for (auto& t : Lenv_) t.n = B;
   for (auto& t : Renv_) t.n = B;
-  main_ = Side{&cx, X1_, X2_, X3_, tmp0_, site_packs_.get(), x1per_ * B, x2per_ * B, x3per_ * B};   // the helpers' view
+  main_ = Side{&cx, X1_, X2_, X3_, tmp0_, site_packs_.get(), x1per_ * B, x2per_ * B};   // the helpers' view
 }
 
 TP Engine::alloc(Arena& a, size_t per) const {
@@ -153,47 +156,8 @@ Mps Engine::closure_mps(const std::vector<Mat>& mats, Arena&) {
 // (s, then the bra leg pair) so that the second GEMM's rows write contiguous
 // runs, which changes only the FP32 summation order.  Falls back to the plain
 // form where the chain buffers are too small for a padded operand (tiny bonds).
-void Engine::chain_last(const char* s3, const TcOperand& o2, const Dims& x2, const SiteT& A, const TP& X3,
-                        Use* u1, Use* u2) {
-  Ctx& c = *side_->cx;
-  const Dims ad = A.dims();
-  const Dims x3 = ein_dims(s3, x2, ad);
-  TcChain c3;
-  c3.a_pre = &o2;
-  if (u1) u1->op = TcOperand();
-  if (u2) u2->op = TcOperand();
-  const int np = o2.np;
-  const size_t w1 = u1 ? tc_operand_words(u1->spec, x3, u1->bd, np, opt.precision) : 0;
-  const size_t w2 = u2 ? tc_operand_words(u2->spec, x3, u2->bd, np, opt.precision) : 0;
-  if (u1 && X3.p[0] == side_->X3.p[0] && w1 + w2 <= side_->x3n) {
-    c3.next = u1->spec;
-    c3.next_bd = u1->bd;
-    c3.next_mem = side_->X3.d(0);
-    c3.next_cap = w1;
-    c3.next_out = &u1->op;
-    if (u2) {
-      c3.next2 = u2->spec;
-      c3.next2_bd = u2->bd;
-      c3.next2_mem = side_->X3.d(0) + w1;
-      c3.next2_cap = w2;
-      c3.next2_out = &u2->op;
-    }
-  }
-  ein_tc(c, s3, TP(), 0, x2, A.p, 1, ad, X3, 0, opt.precision, 1.0, TP(), side_->cache, &c3);
-}
-
-void Engine::con_use(const Use& u, const TP& X, const Dims& xd, const TP& B, const TP& C) {
-  if (u.op.hi) {
-    TcChain ch;
-    ch.a_pre = &u.op;
-    ein_tc(*side_->cx, u.spec, TP(), 0, xd, B, 1, u.bd, C, 1, opt.precision, 1.0, TP(), nullptr, &ch);
-  } else {
-    con(u.spec, X, x64_, xd, B, true, u.bd, C, true);
-  }
-}
-
 Dims Engine::chain_left_tc(const TP& L, const Dims& ld, const TP& M, const Dims& md, const SiteT& A,
-                           const TP& X3, Use* u1, Use* u2) {
+                           const TP& X3) {
   static const char* s1 = "clma,auvb->clmbvu";
   static const char* s2 = "clmbvu,sulnr->cbsmvnr";
   static const char* s3 = "cbsmvnr,svmoq->cbnroq";
@@ -205,7 +169,7 @@ Dims Engine::chain_left_tc(const TP& L, const Dims& ld, const TP& M, const Dims&
       tc_operand_words(s3, x2, ad, np, opt.precision) > side_->x2n)
     return Dims();
   TcOperand o1, o2;
-  TcChain c1, c2;
+  TcChain c1, c2, c3;
   c1.next = s2;
   c1.next_bd = ad;
   c1.next_mem = side_->X1.d(0);
@@ -219,12 +183,13 @@ Dims Engine::chain_left_tc(const TP& L, const Dims& ld, const TP& M, const Dims&
   c2.next_cap = side_->x2n;
   c2.next_out = &o2;
   ein_tc(c, s2, TP(), 0, x1, A.p, 1, ad, TP(), 0, opt.precision, 1.0, TP(), side_->cache, &c2);
-  chain_last(s3, o2, x2, A, X3, u1, u2);
+  c3.a_pre = &o2;
+  ein_tc(c, s3, TP(), 0, x2, A.p, 1, ad, X3, 0, opt.precision, 1.0, TP(), side_->cache, &c3);
   return x3;
 }
 
 Dims Engine::chain_right_tc(const TP& R, const Dims& rd, const TP& M, const Dims& md, const SiteT& A,
-                            const TP& Y3, Use* u1, Use* u2) {
+                            const TP& Y3) {
   static const char* s1 = "auvb,brqc->auvcqr";
   static const char* s2 = "auvcqr,sulnr->acsvqln";
   static const char* s3 = "acsvqln,svmoq->aclnmo";
@@ -236,7 +201,7 @@ Dims Engine::chain_right_tc(const TP& R, const Dims& rd, const TP& M, const Dims
       tc_operand_words(s3, y2, ad, np, opt.precision) > side_->x2n)
     return Dims();
   TcOperand o1, o2;
-  TcChain c1, c2;
+  TcChain c1, c2, c3;
   c1.next = s2;
   c1.next_bd = ad;
   c1.next_mem = side_->X1.d(0);
@@ -250,16 +215,15 @@ Dims Engine::chain_right_tc(const TP& R, const Dims& rd, const TP& M, const Dims
   c2.next_cap = side_->x2n;
   c2.next_out = &o2;
   ein_tc(c, s2, TP(), 0, y1, A.p, 1, ad, TP(), 0, opt.precision, 1.0, TP(), side_->cache, &c2);
-  chain_last(s3, o2, y2, A, Y3, u1, u2);
+  c3.a_pre = &o2;
+  ein_tc(c, s3, TP(), 0, y2, A.p, 1, ad, Y3, 0, opt.precision, 1.0, TP(), side_->cache, &c3);
   return y3;
 }
 
 Dims Engine::chain_left(const TP& L, const Dims& ld, const TP& M, const Dims& md, const SiteT& A,
-                        const TP& X3, Use* u1, Use* u2) {
-  if (u1) u1->op = TcOperand();
-  if (u2) u2->op = TcOperand();
+                        const TP& X3) {
   if (tc_) {
-    const Dims r = chain_left_tc(L, ld, M, md, A, X3, u1, u2);
+    const Dims r = chain_left_tc(L, ld, M, md, A, X3);
     if (!r.empty()) return r;
   }
   const Dims ad = A.dims();
@@ -273,11 +237,9 @@ Dims Engine::chain_left(const TP& L, const Dims& ld, const TP& M, const Dims& md
 }
 
 Dims Engine::chain_right(const TP& R, const Dims& rd, const TP& M, const Dims& md, const SiteT& A,
-                         const TP& Y3, Use* u1, Use* u2) {
-  if (u1) u1->op = TcOperand();
-  if (u2) u2->op = TcOperand();
+                         const TP& Y3) {
   if (tc_) {
-    const Dims r = chain_right_tc(R, rd, M, md, A, Y3, u1, u2);
+    const Dims r = chain_right_tc(R, rd, M, md, A, Y3);
     if (!r.empty()) return r;
   }
   const Dims ad = A.dims();
@@ -411,29 +373,24 @@ Mps Engine::var_compress(const Mps& T, const OLat& lat, int y, const std::vector
     ld[0] = {1, l.n, l.n, 1};
     copy(cx, Lenv_[0], l.p, (long long)l.n * l.n);
   }
-  // Each chain names the contractions of its result (Use), so that the
-  // tensor-core chain writes their operands directly.
   for (int x = Lx - 1; x >= 1; --x) {
-    Use ur{"aelnmo,cnoe->almc", N.dims[x]};
-    const Dims y3 = chain_right(Renv_[x], rd[x], T.p[x], T.dims[x], lat.at(y, x), X3_, &ur);
+    const Dims y3 = chain_right(Renv_[x], rd[x], T.p[x], T.dims[x], lat.at(y, x), X3_);
     rd[x - 1] = ein_dims("aelnmo,cnoe->almc", y3, N.dims[x]);
-    con_use(ur, X3_, y3, N.p[x], Renv_[x - 1]);
+    con("aelnmo,cnoe->almc", X3_, x64_, y3, N.p[x], true, N.dims[x], Renv_[x - 1], true);
   }
   for (int h = 0; h < opt.sweeps; ++h) {
     if (h % 2 == 0) {
       for (int x = 0; x < Lx; ++x) {
-        Use ub{"cbnroq,brqe->cnoe", rd[x]}, ul{"cbnroq,cnoe->erqb", N.dims[x]};
-        const Dims x3 =
-            chain_left(Lenv_[x], ld[x], T.p[x], T.dims[x], lat.at(y, x), X3_, &ub, x < Lx - 1 ? &ul : nullptr);
+        const Dims x3 = chain_left(Lenv_[x], ld[x], T.p[x], T.dims[x], lat.at(y, x), X3_);
         const Dims bd = ein_dims("cbnroq,brqe->cnoe", x3, rd[x]);
-        con_use(ub, X3_, x3, Renv_[x], bb_);
+        con("cbnroq,brqe->cnoe", X3_, x64_, x3, Renv_[x], true, rd[x], bb_, true);
         PEPS_REQUIRE(bd == N.dims[x], "internal: local tensor shape");
         if (x < Lx - 1) {
           const int m = bd[0] * bd[1] * bd[2], n = bd[3];
           PEPS_REQUIRE(n <= m, "internal: inconsistent bond caps");
           qr_thin(cx, m, n, bb_, n, 1, N.p[x], n, 1, TP());
           ld[x + 1] = ein_dims("cbnroq,cnoe->erqb", x3, N.dims[x]);
-          con_use(ul, X3_, x3, N.p[x], Lenv_[x + 1]);
+          con("cbnroq,cnoe->erqb", X3_, x64_, x3, N.p[x], true, N.dims[x], Lenv_[x + 1], true);
         } else {
           copy(cx, N.p[x], bb_, (long long)numel(bd));
         }
@@ -441,22 +398,15 @@ Mps Engine::var_compress(const Mps& T, const OLat& lat, int y, const std::vector
       centre = Lx - 1;
     } else {
       for (int x = Lx - 1; x >= 0; --x) {
-        // the local vector with the chain result as operand A (tensor cores), or
-        // with the left environment first (FP64, the plain form)
-        Use ub{tc_ ? "aelnmo,clma->cnoe" : nullptr, ld[x]}, ur{"aelnmo,cnoe->almc", N.dims[x]};
-        const Dims y3 = chain_right(Renv_[x], rd[x], T.p[x], T.dims[x], lat.at(y, x), X3_, tc_ ? &ub : nullptr,
-                                    x > 0 ? &ur : nullptr);
+        const Dims y3 = chain_right(Renv_[x], rd[x], T.p[x], T.dims[x], lat.at(y, x), X3_);
         const Dims bd = ein_dims("clma,aelnmo->cnoe", ld[x], y3);
-        if (tc_)
-          con_use(ub, X3_, y3, Lenv_[x], bb_);
-        else
-          con("clma,aelnmo->cnoe", Lenv_[x], true, ld[x], X3_, x64_, y3, bb_, true);
+        con("clma,aelnmo->cnoe", Lenv_[x], true, ld[x], X3_, x64_, y3, bb_, true);
         PEPS_REQUIRE(bd == N.dims[x], "internal: local tensor shape");
         if (x > 0) {
           const int c = bd[0], noe = bd[1] * bd[2] * bd[3];
           qr_thin(cx, noe, c, bb_, 1, noe, N.p[x], 1, noe, TP());
           rd[x - 1] = ein_dims("aelnmo,cnoe->almc", y3, N.dims[x]);
-          con_use(ur, X3_, y3, N.p[x], Renv_[x - 1]);
+          con("aelnmo,cnoe->almc", X3_, x64_, y3, N.p[x], true, N.dims[x], Renv_[x - 1], true);
         } else {
           copy(cx, N.p[x], bb_, (long long)numel(bd));
         }
@@ -536,10 +486,9 @@ void Engine::row_rhos(const OLat& lat, const Mps& T, const Mps& B, int y, const 
     xmin = std::min(xmin, t.first);
   }
   for (int x = 0; x + 1 < Lx && x + 1 < xmax; ++x) {
-    Use ul{"cbnroq,cnoe->erqb", B.dims[x]};
-    const Dims x3 = chain_left(Lenv_[x], ld[x], T.p[x], T.dims[x], lat.at(y, x), X3_, &ul);
+    const Dims x3 = chain_left(Lenv_[x], ld[x], T.p[x], T.dims[x], lat.at(y, x), X3_);
     ld[x + 1] = ein_dims("cbnroq,cnoe->erqb", x3, B.dims[x]);
-    con_use(ul, X3_, x3, B.p[x], Lenv_[x + 1]);
+    con("cbnroq,cnoe->erqb", X3_, x64_, x3, B.p[x], true, B.dims[x], Lenv_[x + 1], true);
     normalize(cx, Lenv_[x + 1], (long long)numel(ld[x + 1]), TP(), tmp0_);
   }
   // Right environments: on the second stream when there is one (they depend
@@ -554,10 +503,9 @@ void Engine::row_rhos(const OLat& lat, const Mps& T, const Mps& B, int y, const 
   }
   copy(*side_->cx, Renv_[Lx - 1], rc.p, (long long)rc.n * rc.n);
   for (int x = Lx - 1; x >= 1 && x - 1 >= xmin; --x) {
-    Use ur{"aelnmo,cnoe->almc", B.dims[x]};
-    const Dims y3 = chain_right(Renv_[x], rd[x], T.p[x], T.dims[x], lat.at(y, x), side_->X3, &ur);
+    const Dims y3 = chain_right(Renv_[x], rd[x], T.p[x], T.dims[x], lat.at(y, x), side_->X3);
     rd[x - 1] = ein_dims("aelnmo,cnoe->almc", y3, B.dims[x]);
-    con_use(ur, side_->X3, y3, B.p[x], Renv_[x - 1]);
+    con("aelnmo,cnoe->almc", side_->X3, x64_, y3, B.p[x], true, B.dims[x], Renv_[x - 1], true);
     normalize(*side_->cx, Renv_[x - 1], (long long)numel(rd[x - 1]), TP(), side_->tmp);
   }
   if (dual_) {
@@ -581,26 +529,44 @@ void Engine::row_rhos(const OLat& lat, const Mps& T, const Mps& B, int y, const 
     con("cbsnrtoq,cnoe->erqbst", X3_, x64_, x3, B.p[x], true, B.dims[x], bb_, true);
     return w;
   };
-  for (const auto& t : sites) {
-    const int x = t.first;
-    const Dims w = open_site(x);
-    ein(cx, "erqbst,brqe->st", bb_, w, Renv_[x], rd[x], t.second);
-  }
+  // Site x with its physical pair open, pushed in from the right:
+  // V[a,l,m,k,s,t] = sum M R A(s) A(t) B over the bonds and legs right of the site.
+  auto open_site_right = [&](int x) -> Dims {
+    const SiteT& A = lat.at(y, x);
+    const Dims ad = A.dims();
+    const Dims y1 = ein_dims("auvb,brqc->auvrqc", T.dims[x], rd[x]);
+    con("auvb,brqc->auvrqc", T.p[x], true, T.dims[x], Renv_[x], true, rd[x], X1_, x64_);
+    const Dims y2 = ein_dims("auvrqc,sulnr->avqcsln", y1, ad);
+    con("auvrqc,sulnr->avqcsln", X1_, x64_, y1, A.p, true, ad, X2_, x64_, true);
+    const Dims y3 = ein_dims("avqcsln,tvmoq->acslntmo", y2, ad);
+    con("avqcsln,tvmoq->acslntmo", X2_, x64_, y2, A.p, true, ad, X3_, x64_, true);
+    const Dims v = ein_dims("acslntmo,knoc->almkst", y3, B.dims[x]);
+    con("acslntmo,knoc->almkst", X3_, x64_, y3, B.p[x], true, B.dims[x], vv_, true);
+    return v;
+  };
+  // Every target column once, left to right: W(x) (open from the left) gives
+  // rho_site(x) with the right environment; the bond (x, x+1) is W(x) joined
+  // with V(x+1) (open from the right) over the bonds and legs between them --
+  // the same network as pushing W(x) through site x+1 with both pairs open,
+  // contracted in an order whose intermediates stay at d^2 chi^2 D^4.
+  std::map<int, TP> site_dst, bond_dst;
+  for (const auto& t : sites) site_dst[t.first] = t.second;
   for (const auto& t : bonds) {
-    const int x = t.first;
-    PEPS_REQUIRE(x + 1 < Lx, "internal: bond outside the row");
+    PEPS_REQUIRE(t.first + 1 < Lx, "internal: bond outside the row");
+    bond_dst[t.first] = t.second;
+  }
+  std::set<int> cols;
+  for (const auto& kv : site_dst) cols.insert(kv.first);
+  for (const auto& kv : bond_dst) cols.insert(kv.first);
+  for (const int x : cols) {
     const Dims w = open_site(x);
-    const SiteT& A2 = lat.at(y, x + 1);
-    const Dims ad = A2.dims();
-    const Dims x1 = ein_dims("clmaij,auvb->clmuvbij", w, T.dims[x + 1]);
-    con("clmaij,auvb->clmuvbij", bb_, true, w, T.p[x + 1], true, T.dims[x + 1], X1_, x64_);
-    const Dims x2 = ein_dims("clmuvbij,sulnr->cmvbsnrij", x1, ad);
-    con("clmuvbij,sulnr->cmvbsnrij", X1_, x64_, x1, A2.p, true, ad, X2_, x64_, true);
-    const Dims x3 = ein_dims("cmvbsnrij,tvmoq->cbsnrtoqij", x2, ad);
-    con("cmvbsnrij,tvmoq->cbsnrtoqij", X2_, x64_, x2, A2.p, true, ad, X3_, x64_, true);
-    const Dims x4 = ein_dims("cbsnrtoqij,cnoe->erqbstij", x3, B.dims[x + 1]);
-    con("cbsnrtoqij,cnoe->erqbstij", X3_, x64_, x3, B.p[x + 1], true, B.dims[x + 1], X1_, true);
-    ein(cx, "erqbstij,brqe->isjt", X1_, x4, Renv_[x + 1], rd[x + 1], t.second);
+    auto si = site_dst.find(x);
+    if (si != site_dst.end()) ein(cx, "erqbst,brqe->st", bb_, w, Renv_[x], rd[x], si->second);
+    auto bi = bond_dst.find(x);
+    if (bi != bond_dst.end()) {
+      const Dims v = open_site_right(x + 1);
+      ein(cx, "erqbij,brqest->isjt", bb_, w, vv_, v, bi->second);
+    }
   }
 }
 
@@ -615,12 +581,11 @@ void Engine::norm_from_top(const OLat& lat, const Mps& T, const TP& lns_acc, con
   copy(cx, Lenv_[0], lc.p, (long long)lc.n * lc.n);
   int cur = 0;
   for (int x = 0; x < Lx; ++x) {
+    const Dims x3 = chain_left(Lenv_[cur], ld, T.p[x], T.dims[x], lat.at(y, x), X3_);
     const Mat& bc = lat.bottom[x];
     const Dims bd = {1, bc.n, bc.n, 1};
-    Use ul{"cbnroq,cnoe->erqb", bd};
-    const Dims x3 = chain_left(Lenv_[cur], ld, T.p[x], T.dims[x], lat.at(y, x), X3_, &ul);
     const Dims nd = ein_dims("cbnroq,cnoe->erqb", x3, bd);
-    con_use(ul, X3_, x3, bc.p, Lenv_[1 - cur]);
+    con("cbnroq,cnoe->erqb", X3_, x64_, x3, bc.p, true, bd, Lenv_[1 - cur], true);
     cur = 1 - cur;
     ld = nd;
     if (x + 1 < Lx) normalize(cx, Lenv_[cur], (long long)numel(ld), extra, tmp0_);

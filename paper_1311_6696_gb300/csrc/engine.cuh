@@ -110,37 +110,20 @@ class Engine {
   bool tc_ = false;   // tensor-core contractions (chain intermediates stored FP32)
   bool x64_ = true;   // dtype of the chain intermediates X1, X2, X3
 
-  // A contraction that takes the chain's result (X3 / Y3) as operand A: with
-  // the tensor-core chain the result is written straight into its operand
-  // (op), else it is written plain and op stays empty.
-  struct Use {
-    const char* spec = nullptr;
-    Dims bd;
-    TcOperand op;
-  };
-  // absorb chain pieces; u1, u2: up to two contractions of the result
-  Dims chain_left(const TP& L, const Dims& ld, const TP& M, const Dims& md, const SiteT& A, const TP& X3,
-                  Use* u1 = nullptr, Use* u2 = nullptr);
-  Dims chain_right(const TP& R, const Dims& rd, const TP& M, const Dims& md, const SiteT& A, const TP& Y3,
-                   Use* u1 = nullptr, Use* u2 = nullptr);
-  // u->spec with the chain result X (dims xd) as operand A and B as operand B, into C (FP64).
-  void con_use(const Use& u, const TP& X, const Dims& xd, const TP& B, const TP& C);
+  // absorb chain pieces
+  Dims chain_left(const TP& L, const Dims& ld, const TP& M, const Dims& md, const SiteT& A, const TP& X3);
+  Dims chain_right(const TP& R, const Dims& rd, const TP& M, const Dims& md, const SiteT& A, const TP& Y3);
 
   // The stream, scratch, chain buffers and pack cache the contraction helpers use.
   struct Side {
     Ctx* cx;
     TP X1, X2, X3, tmp;
     PackCache* cache;
-    size_t x1n, x2n, x3n;   // doubles from X1.p[0] / X2.p[0] / X3.p[0] (contiguous over the problems)
+    size_t x1n, x2n;   // doubles from X1.p[0] / X2.p[0] (contiguous over the problems)
   };
   // Tensor-core absorb chains: each GEMM writes the next one's operand.
-  Dims chain_left_tc(const TP& L, const Dims& ld, const TP& M, const Dims& md, const SiteT& A, const TP& X3,
-                     Use* u1, Use* u2);
-  Dims chain_right_tc(const TP& R, const Dims& rd, const TP& M, const Dims& md, const SiteT& A, const TP& Y3,
-                      Use* u1, Use* u2);
-  // The third GEMM of a chain: into X3 plain, or into the operands of u1 (and u2).
-  void chain_last(const char* s3, const TcOperand& o2, const Dims& x2, const SiteT& A, const TP& X3, Use* u1,
-                  Use* u2);
+  Dims chain_left_tc(const TP& L, const Dims& ld, const TP& M, const Dims& md, const SiteT& A, const TP& X3);
+  Dims chain_right_tc(const TP& R, const Dims& rd, const TP& M, const Dims& md, const SiteT& A, const TP& Y3);
   Side main_, aux_;
   Side* side_ = &main_;
   bool dual_ = false;
@@ -150,9 +133,9 @@ class Engine {
   cudaStream_t ws2_stream_ = nullptr;
 
   int d_, Dmax_, Lmax_, nb_, cap_;
-  size_t x1per_ = 0, x2per_ = 0, x3per_ = 0;   // doubles per problem of X1_ / X2_ / X3_ (their stride)
+  size_t x1per_ = 0, x2per_ = 0;   // doubles per problem of X1_ / X2_ (their stride)
   size_t bigN_;                 // chi^2 * Dmax^4 (elements of the largest chain intermediate / d)
-  TP X1_, X2_, X3_, bb_;
+  TP X1_, X2_, X3_, bb_, vv_;   // chain buffers; bb_, vv_: local vector / open-site tensors
   std::vector<TP> Lenv_, Renv_;
   size_t envN_;
   TP one_;                      // device scalar 1.0 (shared)

@@ -63,9 +63,6 @@ struct TcArgs {
   long long pad_m, pad_n;   // packed rows per problem (multiples of TC_BM and BN)
   TP C, Clo;         // per problem
   Grp gm, gn;        // output offsets of the M and N groups
-  int dual;          // 1: every element is also written to C2 / C2lo through gm2 / gn2
-  TP C2, Clo2;
-  Grp gm2, gn2;
   double alpha;
   int* flag;
 };
@@ -165,26 +162,20 @@ __device__ __forceinline__ void decomp(const Grp& g, long long idx, long long& o
 // the next contraction (TF32 or BF16, rounded, with the rounded residual in
 // C_lo for the split precisions) -- the values the operand pack would make
 // from the FP32 result.
-__device__ __forceinline__ void put_to(const TcArgs& g, void* C, void* Clo, long long o, float v) {
+__device__ __forceinline__ void put_out(const TcArgs& g, int pb, long long o, float v) {
   if (g.out_f64) {
-    static_cast<double*>(C)[o] = double(v);
+    static_cast<double*>(g.C.p[pb])[o] = double(v);
   } else if (g.out_tc == 2) {
     const __nv_bfloat16 h = __float2bfloat16(v);
-    static_cast<__nv_bfloat16*>(C)[o] = h;
-    if (g.out_lo) static_cast<__nv_bfloat16*>(Clo)[o] = __float2bfloat16(v - __bfloat162float(h));
+    static_cast<__nv_bfloat16*>(g.C.p[pb])[o] = h;
+    if (g.out_lo) static_cast<__nv_bfloat16*>(g.Clo.p[pb])[o] = __float2bfloat16(v - __bfloat162float(h));
   } else if (g.out_tc == 1 || g.out_lo) {
     const float h = round_tf32(v);
-    static_cast<float*>(C)[o] = h;
-    if (g.out_lo) static_cast<float*>(Clo)[o] = round_tf32(v - h);
+    static_cast<float*>(g.C.p[pb])[o] = h;
+    if (g.out_lo) static_cast<float*>(g.Clo.p[pb])[o] = round_tf32(v - h);
   } else {
-    static_cast<float*>(C)[o] = v;
+    static_cast<float*>(g.C.p[pb])[o] = v;
   }
-}
-__device__ __forceinline__ void put_out(const TcArgs& g, int pb, long long o, float v) {
-  put_to(g, g.C.p[pb], g.out_lo ? g.Clo.p[pb] : nullptr, o, v);
-}
-__device__ __forceinline__ void put_out2(const TcArgs& g, int pb, long long o, float v) {
-  put_to(g, g.C2.p[pb], g.out_lo ? g.Clo2.p[pb] : nullptr, o, v);
 }
 
 // One 128 x BN output tile per CTA.
@@ -203,7 +194,6 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ 
   __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], done;
   __shared__ uint32_t tmem_base;
   __shared__ long long offm[TC_BM], offn[BN];
-  __shared__ long long offm2[TC_BM], offn2[BN];   // second output (dual)
   __shared__ float stage_out[4][32][17];   // per warp: 32 rows x 16 columns of the accumulator
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -231,23 +221,15 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ 
   }
   for (int i = tid; i < TC_BM; i += TC_THREADS) {
     const long long m = m0 + i;
-    long long o = -1, o2 = -1;
-    if (m < g.M) {
-      decomp(g.gm, m, o);
-      if (g.dual) decomp(g.gm2, m, o2);
-    }
+    long long o = -1;
+    if (m < g.M) decomp(g.gm, m, o);
     offm[i] = o;
-    offm2[i] = o2;
   }
   for (int i = tid; i < BN; i += TC_THREADS) {
     const long long n = n0 + i;
-    long long o = -1, o2 = -1;
-    if (n < g.N) {
-      decomp(g.gn, n, o);
-      if (g.dual) decomp(g.gn2, n, o2);
-    }
+    long long o = -1;
+    if (n < g.N) decomp(g.gn, n, o);
     offn[i] = o;
-    offn2[i] = o2;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -351,14 +333,6 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ 
           const long long on = offn[c0 + j];
           if (on >= 0) put(om + on, __uint_as_float(r[j]) * alpha);
         }
-        if (g.dual) {
-          const long long om2 = offm2[row];
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const long long on2 = offn2[c0 + j];
-            if (on2 >= 0) put_out2(g, pb, om2 + on2, __uint_as_float(r[j]) * alpha);
-          }
-        }
       } else {
         // through shared memory: 16 lanes per row along the columns
 #pragma unroll
@@ -370,14 +344,6 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ 
         for (int i = lane >> 4; i < 32; i += 2) {
           const long long omi = offm[warp * 32 + i];
           if (omi >= 0 && on >= 0) put(omi + on, stage_out[warp][i][j] * alpha);
-        }
-        if (g.dual) {
-          const long long on2 = offn2[c0 + j];
-#pragma unroll 4
-          for (int i = lane >> 4; i < 32; i += 2) {
-            const long long omi = offm2[warp * 32 + i];
-            if (omi >= 0 && on2 >= 0) put_out2(g, pb, omi + on2, stage_out[warp][i][j] * alpha);
-          }
         }
         __syncwarp();
       }
@@ -407,11 +373,6 @@ __global__ void k_tc_splitk_reduce(const TcArgs g) {
     decomp(g.gm, m, om);
     decomp(g.gn, n, on);
     put_out(g, pb, om + on, v);
-    if (g.dual) {
-      decomp(g.gm2, m, om);
-      decomp(g.gn2, n, on);
-      put_out2(g, pb, om + on, v);
-    }
   }
 }
 
@@ -676,6 +637,7 @@ int tc_available() {
 // taken from A (in the output's order), K over A's summed letters (in A's
 // order), rows padded to the tile height per problem, K padded to 16 bytes.
 struct LayoutA {
+  std::string a;            // the contraction's operand-A letters, in operand order
   std::string rows, ks;
   std::vector<long long> rdim, kdim;
   long long M = 1, K = 1, pad = 0, ld = 0;
@@ -686,6 +648,7 @@ LayoutA layout_a(const char* spec, const Dims& ad, const Dims& bd, int np, int p
   const Parsed p = parse(spec);
   (void)bd;
   LayoutA L;
+  L.a = p.a;
   for (char ch : p.c)
     if (p.a.find(ch) != std::string::npos) {
       L.rows += ch;
@@ -730,12 +693,17 @@ void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, c
   const int bf16 = (prec == PEPS_PREC_BF16 || prec == PEPS_PREC_BF16X3) ? 1 : 0;
   const int split = (prec == PEPS_PREC_TF32X3 || prec == PEPS_PREC_BF16X3) ? 1 : 0;
   // Output strides: C's own (row-major over the output letters), or those of
-  // operand A of the next contraction(s).
-  auto strides_in = [&](const LayoutA& nx) {
-    std::vector<long long> st_out(p.c.size());
-    PEPS_REQUIRE(nx.rows.size() + nx.ks.size() == p.c.size(), "internal: chained operand letters");
+  // operand A of the next contraction.
+  // (output index i is index i of the next contraction's operand A, whose
+  // letters may be named differently there)
+  std::vector<long long> ostr(sc.begin(), sc.end());
+  LayoutA nx;
+  if (to_next) {
+    nx = layout_a(chain->next, cd, chain->next_bd, np, prec);
+    PEPS_REQUIRE(nx.a.size() == p.c.size() && nx.rows.size() + nx.ks.size() == p.c.size(),
+                 "internal: chained operand letters");
     for (size_t i = 0; i < p.c.size(); ++i) {
-      const char ch = p.c[i];
+      const char ch = nx.a[i];
       long long st = 1;
       auto r = nx.rows.find(ch), k = nx.ks.find(ch);
       if (r != std::string::npos) {
@@ -746,22 +714,9 @@ void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, c
         PEPS_REQUIRE(k != std::string::npos && nx.kdim[k] == cd[i], "internal: chained operand letters");
         for (size_t j = k + 1; j < nx.ks.size(); ++j) st *= nx.kdim[j];
       }
-      st_out[i] = st;
+      ostr[i] = st;
     }
-    return st_out;
-  };
-  std::vector<long long> ostr(sc.begin(), sc.end()), ostr2;
-  LayoutA nx, nx2;
-  const bool dual = to_next && chain->next2;
-  if (to_next) {
-    nx = layout_a(chain->next, cd, chain->next_bd, np, prec);
-    ostr = strides_in(nx);
     PEPS_REQUIRE((split ? 2 : 1) * nx.words <= chain->next_cap, "internal: chained operand buffer too small");
-  }
-  if (dual) {
-    nx2 = layout_a(chain->next2, cd, chain->next2_bd, np, prec);
-    ostr2 = strides_in(nx2);
-    PEPS_REQUIRE((split ? 2 : 1) * nx2.words <= chain->next2_cap, "internal: chained operand buffer too small");
   }
   std::string mL, nL, kL;
   TcArgs g;
@@ -773,11 +728,9 @@ void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, c
     if (inA) {
       mL += ch;
       push(g.gm, cd[i], ostr[i]);
-      if (dual) push(g.gm2, cd[i], ostr2[i]);
     } else {
       nL += ch;
       push(g.gn, cd[i], ostr[i]);
-      if (dual) push(g.gn2, cd[i], ostr2[i]);
     }
   }
   for (char ch : p.a)
@@ -866,31 +819,28 @@ void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, c
   g.bf16 = bf16;
   if (to_next) {
     const size_t esz = bf16 ? 2 : 4;
-    auto target = [&](const LayoutA& L, double* mem, TP& ch, TP& cl, TcOperand* out) {
-      char* hi = reinterpret_cast<char*>(mem);
-      char* lo = split ? hi + L.words * sizeof(double) : nullptr;
-      ch.n = np;
-      cl.n = split ? np : 0;
-      for (int b = 0; b < np; ++b) {
-        ch.p[b] = hi + size_t(b) * L.pad * L.ld * esz;
-        if (split) cl.p[b] = lo + size_t(b) * L.pad * L.ld * esz;
-      }
-      if (out) {
-        out->hi = hi;
-        out->lo = lo;
-        out->ld = L.ld;
-        out->pad = L.pad;
-        out->np = np;
-      }
-    };
-    target(nx, chain->next_mem, g.C, g.Clo, chain->next_out);
-    if (dual) {
-      target(nx2, chain->next2_mem, g.C2, g.Clo2, chain->next2_out);
-      g.dual = 1;
+    char* hi = reinterpret_cast<char*>(chain->next_mem);
+    char* lo = split ? hi + nx.words * sizeof(double) : nullptr;
+    TP ch, cl;
+    ch.n = np;
+    cl.n = split ? np : 0;
+    for (int b = 0; b < np; ++b) {
+      ch.p[b] = hi + size_t(b) * nx.pad * nx.ld * esz;
+      if (split) cl.p[b] = lo + size_t(b) * nx.pad * nx.ld * esz;
     }
+    g.C = ch;
+    g.Clo = cl;
     g.out_f64 = 0;
     g.out_lo = split;
     g.out_tc = bf16 ? 2 : 1;
+    if (chain->next_out) {
+      TcOperand& o = *chain->next_out;
+      o.hi = hi;
+      o.lo = lo;
+      o.ld = nx.ld;
+      o.pad = nx.pad;
+      o.np = np;
+    }
   } else {
     g.out_f64 = c_f64;
     g.out_lo = (!Clo.null() && !c_f64) ? 1 : 0;
@@ -917,16 +867,13 @@ void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, c
       return o;
     };
     const int esz = g.out_f64 ? 8 : (g.out_tc == 2 ? 2 : 4);
-    auto sectors_of = [&](const Grp& qm, const Grp& qn, bool cols) {
+    auto sectors = [&](bool cols) {
       std::vector<long long> v;
       const int ri = cols ? 2 : 32, cj = cols ? 16 : 1;
       for (int i = 0; i < ri && i < M; ++i)
-        for (int j = 0; j < cj && j < N; ++j) v.push_back((offset(qm, i) + offset(qn, j)) * esz / 32);
+        for (int j = 0; j < cj && j < N; ++j) v.push_back((offset(g.gm, i) + offset(g.gn, j)) * esz / 32);
       std::sort(v.begin(), v.end());
-      return (long long)(std::unique(v.begin(), v.end()) - v.begin());
-    };
-    auto sectors = [&](bool cols) {
-      return sectors_of(g.gm, g.gn, cols) + (g.dual ? sectors_of(g.gm2, g.gn2, cols) : 0);
+      return std::unique(v.begin(), v.end()) - v.begin();
     };
     const long long sc_cols = sectors(true), sc_rows = sectors(false);
     g.cols_fast = sc_cols != sc_rows ? (sc_cols < sc_rows ? 1 : 0) : (inner(g.gn) < inner(g.gm) ? 1 : 0);
