@@ -157,10 +157,11 @@ Mps Engine::closure_mps(const std::vector<Mat>& mats, Arena&) {
 // runs, which changes only the FP32 summation order.  Falls back to the plain
 // form where the chain buffers are too small for a padded operand (tiny bonds).
 Dims Engine::chain_left_tc(const TP& L, const Dims& ld, const TP& M, const Dims& md, const SiteT& A,
-                           const TP& X3) {
+                           const TP& X3, bool open) {
   static const char* s1 = "clma,auvb->clmbvu";
   static const char* s2 = "clmbvu,sulnr->cbsmvnr";
-  static const char* s3 = "cbsmvnr,svmoq->cbnroq";
+  // bra stage: s traced, or kept open next to the bra's t (a site's density matrix)
+  const char* s3 = open ? "cbsmvnr,tvmoq->cbsnrtoq" : "cbsmvnr,svmoq->cbnroq";
   Ctx& c = *side_->cx;
   const Dims ad = A.dims();
   const Dims x1 = ein_dims(s1, ld, md), x2 = ein_dims(s2, x1, ad), x3 = ein_dims(s3, x2, ad);
@@ -189,10 +190,10 @@ Dims Engine::chain_left_tc(const TP& L, const Dims& ld, const TP& M, const Dims&
 }
 
 Dims Engine::chain_right_tc(const TP& R, const Dims& rd, const TP& M, const Dims& md, const SiteT& A,
-                            const TP& Y3) {
+                            const TP& Y3, bool open) {
   static const char* s1 = "auvb,brqc->auvcqr";
   static const char* s2 = "auvcqr,sulnr->acsvqln";
-  static const char* s3 = "acsvqln,svmoq->aclnmo";
+  const char* s3 = open ? "acsvqln,tvmoq->acslntmo" : "acsvqln,svmoq->aclnmo";
   Ctx& c = *side_->cx;
   const Dims ad = A.dims();
   const Dims y1 = ein_dims(s1, md, rd), y2 = ein_dims(s2, y1, ad), y3 = ein_dims(s3, y2, ad);
@@ -223,7 +224,7 @@ Dims Engine::chain_right_tc(const TP& R, const Dims& rd, const TP& M, const Dims
 Dims Engine::chain_left(const TP& L, const Dims& ld, const TP& M, const Dims& md, const SiteT& A,
                         const TP& X3) {
   if (tc_) {
-    const Dims r = chain_left_tc(L, ld, M, md, A, X3);
+    const Dims r = chain_left_tc(L, ld, M, md, A, X3, false);
     if (!r.empty()) return r;
   }
   const Dims ad = A.dims();
@@ -239,7 +240,7 @@ Dims Engine::chain_left(const TP& L, const Dims& ld, const TP& M, const Dims& md
 Dims Engine::chain_right(const TP& R, const Dims& rd, const TP& M, const Dims& md, const SiteT& A,
                          const TP& Y3) {
   if (tc_) {
-    const Dims r = chain_right_tc(R, rd, M, md, A, Y3);
+    const Dims r = chain_right_tc(R, rd, M, md, A, Y3, false);
     if (!r.empty()) return r;
   }
   const Dims ad = A.dims();
@@ -519,12 +520,15 @@ void Engine::row_rhos(const OLat& lat, const Mps& T, const Mps& B, int y, const 
   auto open_site = [&](int x) -> Dims {
     const SiteT& A = lat.at(y, x);
     const Dims ad = A.dims();
-    const Dims x1 = ein_dims("clma,auvb->clmuvb", ld[x], T.dims[x]);
-    con("clma,auvb->clmuvb", Lenv_[x], true, ld[x], T.p[x], true, T.dims[x], X1_, x64_);
-    const Dims x2 = ein_dims("clmuvb,sulnr->cmvbsnr", x1, ad);
-    con("clmuvb,sulnr->cmvbsnr", X1_, x64_, x1, A.p, true, ad, X2_, x64_, true);
-    const Dims x3 = ein_dims("cmvbsnr,tvmoq->cbsnrtoq", x2, ad);
-    con("cmvbsnr,tvmoq->cbsnrtoq", X2_, x64_, x2, A.p, true, ad, X3_, x64_, true);
+    Dims x3 = tc_ ? chain_left_tc(Lenv_[x], ld[x], T.p[x], T.dims[x], A, X3_, true) : Dims();
+    if (x3.empty()) {
+      const Dims x1 = ein_dims("clma,auvb->clmuvb", ld[x], T.dims[x]);
+      con("clma,auvb->clmuvb", Lenv_[x], true, ld[x], T.p[x], true, T.dims[x], X1_, x64_);
+      const Dims x2 = ein_dims("clmuvb,sulnr->cmvbsnr", x1, ad);
+      con("clmuvb,sulnr->cmvbsnr", X1_, x64_, x1, A.p, true, ad, X2_, x64_, true);
+      x3 = ein_dims("cmvbsnr,tvmoq->cbsnrtoq", x2, ad);
+      con("cmvbsnr,tvmoq->cbsnrtoq", X2_, x64_, x2, A.p, true, ad, X3_, x64_, true);
+    }
     const Dims w = ein_dims("cbsnrtoq,cnoe->erqbst", x3, B.dims[x]);
     con("cbsnrtoq,cnoe->erqbst", X3_, x64_, x3, B.p[x], true, B.dims[x], bb_, true);
     return w;
@@ -534,12 +538,15 @@ void Engine::row_rhos(const OLat& lat, const Mps& T, const Mps& B, int y, const 
   auto open_site_right = [&](int x) -> Dims {
     const SiteT& A = lat.at(y, x);
     const Dims ad = A.dims();
-    const Dims y1 = ein_dims("auvb,brqc->auvrqc", T.dims[x], rd[x]);
-    con("auvb,brqc->auvrqc", T.p[x], true, T.dims[x], Renv_[x], true, rd[x], X1_, x64_);
-    const Dims y2 = ein_dims("auvrqc,sulnr->avqcsln", y1, ad);
-    con("auvrqc,sulnr->avqcsln", X1_, x64_, y1, A.p, true, ad, X2_, x64_, true);
-    const Dims y3 = ein_dims("avqcsln,tvmoq->acslntmo", y2, ad);
-    con("avqcsln,tvmoq->acslntmo", X2_, x64_, y2, A.p, true, ad, X3_, x64_, true);
+    Dims y3 = tc_ ? chain_right_tc(Renv_[x], rd[x], T.p[x], T.dims[x], A, X3_, true) : Dims();
+    if (y3.empty()) {
+      const Dims y1 = ein_dims("auvb,brqc->auvrqc", T.dims[x], rd[x]);
+      con("auvb,brqc->auvrqc", T.p[x], true, T.dims[x], Renv_[x], true, rd[x], X1_, x64_);
+      const Dims y2 = ein_dims("auvrqc,sulnr->avqcsln", y1, ad);
+      con("auvrqc,sulnr->avqcsln", X1_, x64_, y1, A.p, true, ad, X2_, x64_, true);
+      y3 = ein_dims("avqcsln,tvmoq->acslntmo", y2, ad);
+      con("avqcsln,tvmoq->acslntmo", X2_, x64_, y2, A.p, true, ad, X3_, x64_, true);
+    }
     const Dims v = ein_dims("acslntmo,knoc->almkst", y3, B.dims[x]);
     con("acslntmo,knoc->almkst", X3_, x64_, y3, B.p[x], true, B.dims[x], vv_, true);
     return v;

@@ -122,8 +122,11 @@ class Engine {
     size_t x1n, x2n;   // doubles from X1.p[0] / X2.p[0] (contiguous over the problems)
   };
   // Tensor-core absorb chains: each GEMM writes the next one's operand.
-  Dims chain_left_tc(const TP& L, const Dims& ld, const TP& M, const Dims& md, const SiteT& A, const TP& X3);
-  Dims chain_right_tc(const TP& R, const Dims& rd, const TP& M, const Dims& md, const SiteT& A, const TP& Y3);
+  // open: the bra stage keeps the physical index open (X3 / Y3 of a site's density matrix).
+  Dims chain_left_tc(const TP& L, const Dims& ld, const TP& M, const Dims& md, const SiteT& A, const TP& X3,
+                     bool open);
+  Dims chain_right_tc(const TP& R, const Dims& rd, const TP& M, const Dims& md, const SiteT& A, const TP& Y3,
+                      bool open);
   Side main_, aux_;
   Side* side_ = &main_;
   bool dual_ = false;
