@@ -756,6 +756,59 @@ def boundary_fidelity(Ad_or_lat, delta: int, chi: int, chi_ref: int, mode: str =
 
 
 # ---------------------------------------------------------------------------
+# Infinite PEPS (Section 5.4): a CU procedure needs only the dominant D'=1
+# boundary of the infinite lattice (O(dD^5)), followed by a cluster
+# contraction as in the finite case.  Single-site unit cell: every site holds
+# the same tensor A[s,u,l,n,r], every leg has dimension D.
+# ---------------------------------------------------------------------------
+def ipeps_orientations(A):
+    """A as seen by the top-down, bottom-up, left-right and right-left sweeps
+    (the leg permutations of flip_ud and transpose)."""
+    tr = A.transpose(0, 2, 1, 4, 3)
+    return [A, A.transpose(0, 3, 2, 1, 4), tr, tr.transpose(0, 3, 2, 1, 4)]
+
+
+def cu0_infinite(A, tol: float = 1e-13, max_iter: int = 5000):
+    """Dominant separable (D'=1) boundary of the infinite lattice from the top:
+    sigma with sigma ~ b(sigma), b the local CU_0 update (Section 5.1) of a
+    row of copies of A between sigma above and sigma below, its horizontal
+    environments the dominant left / right fixed points of that row.  Each
+    step updates the left environment, the right environment and sigma once,
+    all scaled to unit Frobenius norm, from identities; it stops when none
+    moves by tol."""
+    D = A.shape[1]
+    sig = _fro(np.eye(D))
+    Lm = _fro(np.eye(D))
+    Rm = _fro(np.eye(D))
+    for _ in range(max_iter):
+        Ln = _fro(cu0_lenv(Lm, sig, A, sig))
+        Rn = _fro(cu0_renv(Rm, sig, A, sig))
+        b = _fro(cu0_local(Ln, sig, A, Rn))
+        change = max(float(np.linalg.norm(Ln - Lm)), float(np.linalg.norm(Rn - Rm)),
+                     float(np.linalg.norm(b - sig)))
+        Lm, Rm, sig = Ln, Rn, b
+        if change < tol:
+            return sig
+    raise OracleNotConverged(f"infinite CU0: change {change:.3e} after {max_iter} steps")
+
+
+def ipeps_cluster(A, n: int, chi: int, mode: str = "var", sweeps: int = 2, seed: int = 0, tol: float = 1e-13):
+    """Density matrices of one site, its right bond and its down bond of the
+    infinite PEPS: an n x n window of copies of A (anchor at row and column
+    ceil(n/2)-1, as for interior windows of the finite lattice) closed by the
+    four infinite separable boundaries, contracted by the full routine at chi.
+    Returns dict(rho_site, rho_h, rho_v, sigma) with sigma the four boundary
+    matrices (top, bottom, left, right)."""
+    A = np.asarray(A, dtype=np.float64)
+    sig = [cu0_infinite(Ao, tol) for Ao in ipeps_orientations(A)]
+    rows = [[A for _ in range(n)] for _ in range(n)]
+    W = Lat(rows, [sig[0]] * n, [sig[1]] * n, [sig[2]] * n, [sig[3]] * n)
+    a = -(-n // 2) - 1
+    s, h, v = cluster_anchor(W, a, a, chi, mode, sweeps, seed)
+    return dict(rho_site=s, rho_h=h, rho_v=v, sigma=sig)
+
+
+# ---------------------------------------------------------------------------
 # Operators (eq. 1 and eq. 2 conventions: Pauli matrices, S = sigma/2)
 # ---------------------------------------------------------------------------
 SZ = np.array([[1.0, 0.0], [0.0, -1.0]])

@@ -379,8 +379,8 @@ __global__ void k_tc_splitk_reduce(const TcArgs g) {
 // Gather-copy into a dense [rows][ld] operand: element (r, k) of the output is
 // src[sum(idx_i * stride_i)] with r, k decomposed over the row / K groups.
 // Rounds to TF32 (or converts to BF16); `lo` receives the rounded residual.
-// Tiled transpose: each CTA moves a 32 x 32 (row, k) tile through shared
-// memory, decomposing its 32 row and 32 k offsets once; reads run along
+// Tiled transpose: each CTA moves a 64 x 64 (row, k) tile through shared
+// memory, decomposing its 64 row and 64 k offsets once; reads run along
 // whichever group holds the source's unit stride (rows_fast), writes run along
 // k, so both sides are coalesced whatever the permutation.
 struct PackArgs {
@@ -394,7 +394,11 @@ struct PackArgs {
   int bf16;
 };
 
-constexpr int PK_T = 32;
+// 64 x 64 (row, k) tiles, 256 threads, 16 elements per thread: the offsets
+// of a tile's 64 rows and 64 k are decomposed once (128 threads), then every
+// thread issues all 16 of its loads before it stores, so each warp keeps 16
+// coalesced loads in flight.
+constexpr int PK_T = 64;
 
 // hi = v rounded to the operand type; lo = the rounded residual.  For FP32
 // sources everything stays in FP32 (v - tf32(v) is exact there): the FP64
@@ -430,7 +434,7 @@ __global__ void __launch_bounds__(256) k_pack(const PackArgs p) {
   const int pb = blockIdx.y;
   const long long ktiles = (p.K + PK_T - 1) / PK_T;
   const long long r0 = (blockIdx.x / ktiles) * PK_T, k0 = (blockIdx.x % ktiles) * PK_T;
-  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const int tid = threadIdx.x, tx = tid & (PK_T - 1), ty = tid / PK_T;   // ty in 0..3
   if (tid < PK_T) {
     long long o = -1;
     if (r0 + tid < p.rows) decomp(p.gr, r0 + tid, o);
@@ -442,18 +446,25 @@ __global__ void __launch_bounds__(256) k_pack(const PackArgs p) {
   }
   __syncthreads();
   const T* src = static_cast<const T*>(p.src.p[pb]);
+  constexpr int NQ = PK_T / 4;   // 16 elements per thread
+  T v[NQ];
 #pragma unroll
-  for (int q = 0; q < PK_T / 8; ++q) {
-    const int a = ty + 8 * q;
+  for (int q = 0; q < NQ; ++q) {
+    const int a = ty + 4 * q;
     const int r = p.rows_fast ? tx : a, k = p.rows_fast ? a : tx;
-    T v = T(0);
-    if (ro[r] >= 0 && ko[k] >= 0) v = src[ro[r] + ko[k]];
-    tile[k][r] = v;
+    const long long orr = ro[r], okk = ko[k];
+    v[q] = (orr >= 0 && okk >= 0) ? src[orr + okk] : T(0);
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int a = ty + 4 * q;
+    const int r = p.rows_fast ? tx : a, k = p.rows_fast ? a : tx;
+    tile[k][r] = v[q];
   }
   __syncthreads();
-#pragma unroll
-  for (int q = 0; q < PK_T / 8; ++q) {
-    const int r = ty + 8 * q, k = tx;
+#pragma unroll 4
+  for (int q = 0; q < NQ; ++q) {
+    const int r = ty + 4 * q, k = tx;
     if (ro[r] < 0 || ko[k] < 0) continue;
     split_store(tile[k][r], p, (pb * p.pad + r0 + r) * p.ld + k0 + k);
   }
