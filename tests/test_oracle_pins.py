@@ -525,3 +525,60 @@ def test_boundary_fidelity_falls_with_the_cluster_size():
     d = [O.boundary_fidelity(A, delta, chi=16, chi_ref=32) for delta in (1, 2, 3, 4)]
     assert all(d[i + 1] < 0.5 * d[i] for i in range(3)), d
     assert O.boundary_fidelity(A, 5, chi=32, chi_ref=32) < 1e-14
+
+
+def _finite_copies(A, L):
+    """An L x L OBC lattice with A on every site, its outward legs cut to index 0."""
+    Ad = np.zeros((L, L) + A.shape)
+    for y in range(L):
+        for x in range(L):
+            sl = (slice(None), slice(0, 1) if y == 0 else slice(None), slice(0, 1) if x == 0 else slice(None),
+                  slice(0, 1) if y == L - 1 else slice(None), slice(0, 1) if x == L - 1 else slice(None))
+            Ad[(y, x) + sl] = A[sl]
+    return Ad
+
+
+def test_infinite_cu0_is_the_finite_cu0_deep_inside_a_large_lattice():
+    """Section 5.4: the dominant D'=1 boundary of the infinite lattice is what
+    the finite CU_0 (Section 5.1, pinned above) converges to far from every
+    edge of a lattice of copies; checked in all four directions."""
+    from oracle import peps_oracle as O
+    from paper_1311_6696_gb300 import synth
+    A = synth.peps_gauss(3, 3, 2, 3, seed=5)[1, 1]
+    L = 16
+    lat = O.lattice_from_dense(_finite_copies(A, L))
+    for o, (lo, Ao) in enumerate(zip(O.orientations(lat), O.ipeps_orientations(A))):
+        sig = O.cu0_infinite(Ao)
+        fin = O.cu0_sweep(lo)
+        assert np.max(np.abs(fin[L // 2][L // 2] - sig)) < 1e-12, o
+
+
+def test_ipeps_cluster_of_a_product_state_is_the_closed_form():
+    from oracle import peps_oracle as O
+    rng = np.random.default_rng(3)
+    a = rng.uniform(-1, 1, 2)
+    A = a.reshape(2, 1, 1, 1, 1)
+    r = O.ipeps_cluster(A, 3, 1)
+    z = (a[0] ** 2 - a[1] ** 2) / (a @ a)
+    x = 2 * a[0] * a[1] / (a @ a)
+    assert abs(O.expect(r["rho_site"], O.SZ) - z) < 1e-14
+    assert abs(O.expect(r["rho_site"], O.SX) - x) < 1e-14
+    for k in ("rho_h", "rho_v"):
+        assert abs(O.expect(r[k], O.SDOTS) - (x * x + z * z) / 4) < 1e-14
+
+
+def test_ipeps_cluster_matches_the_finite_cluster_deep_inside():
+    """The iPEPS cluster density matrices equal the finite cluster scheme's at
+    the centre of a large lattice of copies (same window, same closures there)."""
+    from oracle import peps_oracle as O
+    from paper_1311_6696_gb300 import synth
+    A = synth.peps_gauss(3, 3, 2, 2, seed=8)[1, 1]
+    L = 20          # far enough from the edges (the distance decays exponentially: 1e-10 at 14, 1e-13 at 18)
+    fin = O.env_cluster(_finite_copies(A, L), n=3, chi=8, mode="var", anchors=[(L // 2, L // 2)])
+    inf = O.ipeps_cluster(A, 3, 8)
+    c = L // 2
+    for got, want in ((inf["rho_site"], fin["rho_site"][c][c]), (inf["rho_h"], fin["rho_h"][c][c]),
+                      (inf["rho_v"], fin["rho_v"][c][c])):
+        g = got.reshape(got.shape[0] if got.ndim == 2 else 4, -1)
+        w = want.reshape(g.shape)
+        assert np.max(np.abs(g / np.trace(g) - w / np.trace(w))) < 1e-11
