@@ -251,6 +251,29 @@ int peps_mlp_predict(const float* w, const float* X, long long n, int d, int D, 
                      float* sigma, void* cuda_stream);
 
 /*
+ * peps_ipeps_cluster -- local density matrices of an infinite PEPS by the
+ *   cluster update's environment (Section 5.4: a CU procedure for iPEPS needs
+ *   only the dominant D'=1 boundary eigenvector, O(dD^5), followed by a
+ *   cluster contraction as in the finite case).  Single-site unit cell:
+ *   every site holds A[s][u][l][n][r] (d x D^4, every leg D; host or device
+ *   pointer per on_device).  For each side the separable boundary is the
+ *   fixed point of the CU_0 update of an infinite row (Section 5.1) whose
+ *   horizontal environments are the row's own left / right fixed points
+ *   (identities to start, unit-norm matrices, converged when no matrix moves
+ *   by 1e-13; PEPS_ECONVERGE after 25x the CU_0 half-sweep cap).  An
+ *   opts->n x opts->n window of copies of A closed by those four boundaries
+ *   (corners dropped) is then contracted at bond opts->chi as a finite window
+ *   (mode, sweeps, precision, seed as in peps_env_cluster); the anchor sits
+ *   at row and column ceil(n/2)-1.
+ *   rho_site (d x d), rho_h (d^2 x d^2, the bond to the right), rho_v (d^2 x
+ *   d^2, the bond below; zero when n = 1): host arrays, unnormalised, same
+ *   index order as peps_env_rho.  sigma (host, may be NULL): the boundary
+ *   matrices top, bottom, left, right, D x D each.  Synchronises the stream.
+ */
+int peps_ipeps_cluster(const double* A, int d, int D, int on_device, const peps_opts* opts, double* rho_site,
+                       double* rho_h, double* rho_v, double* sigma, void* cuda_stream);
+
+/*
  * Failure detection (the paper has no counterpart).
  *
  * peps_set_iteration_caps -- caps of the library's iterations: the

@@ -1171,6 +1171,78 @@ int peps_env_cluster_range(const peps_lattice* lat, const peps_opts* opts, long 
   return run_env(lat, opts, out, cuda_stream, true, anchor_begin, anchor_end);
 }
 
+int peps_ipeps_cluster(const double* A, int d, int D, int on_device, const peps_opts* opts, double* rho_site,
+                       double* rho_h, double* rho_v, double* sigma, void* cuda_stream) {
+  return guard([&] {
+    PEPS_REQUIRE(A != nullptr && rho_site != nullptr && rho_h != nullptr && rho_v != nullptr, "NULL argument");
+    PEPS_REQUIRE(d >= 1 && d <= 4 && D >= 1 && D <= 16, "d must be in [1, 4] and D in [1, 16]");
+    require_device();
+    const Opts o = check_opts(opts, true);
+    PEPS_REQUIRE(opts->closure == PEPS_CLOSURE_PLAIN, "the infinite lattice uses the plain CU_0 closure");
+    PEPS_REQUIRE(opts->n <= 64, "window size n must be <= 64");
+    const int n = opts->n;
+    Call c(cuda_stream);
+    Arena keep(c.st);
+    // The tensor at the centre of a 3x3 OBC lattice has every leg of dimension
+    // D in all four orientations: its oriented copies are the window's sites.
+    const size_t per = size_t(d) * D * D * D * D;
+    double* dense = keep.dalloc(9 * per);
+    PEPS_CUDA(cudaMemsetAsync(dense, 0, 9 * per * sizeof(double), c.st));
+    PEPS_CUDA(cudaMemcpyAsync(dense + 4 * per, A, per * sizeof(double),
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c.st));
+    const peps_lattice l3{3, 3, d, D, PEPS_F64, dense, 1};
+    Oriented ori;
+    build_orientations(c.cx, &l3, keep, ori);
+    const SiteT* ctr[4];
+    const double* ca[4];
+    for (int k = 0; k < 4; ++k) {
+      ctr[k] = &ori.o[k].at(1, 1);
+      ca[k] = ctr[k]->p.d(0);
+    }
+    double* sig = keep.dalloc(size_t(4) * D * D);
+    cu0_infinite(c.cx, ca, d, D, sig, 25 * c.cx.cu0_cap);
+    // n x n window of copies, closed by the four boundaries (corners dropped);
+    // orientation k sees side s of the window as side map[k][s] of W0
+    auto side = [&](int s) { return Mat{TP(sig + size_t(s) * D * D), D}; };
+    static const int map[4][4] = {{0, 1, 2, 3}, {1, 0, 2, 3}, {2, 3, 0, 1}, {3, 2, 0, 1}};
+    OLat W[4];
+    for (int k = 0; k < 4; ++k) {
+      W[k].Ly = W[k].Lx = n;
+      W[k].d = d;
+      W[k].sites.assign(size_t(n) * n, *ctr[k]);
+      W[k].top.assign(n, side(map[k][0]));
+      W[k].bottom.assign(n, side(map[k][1]));
+      W[k].left.assign(n, side(map[k][2]));
+      W[k].right.assign(n, side(map[k][3]));
+    }
+    const int a = (n + 1) / 2 - 1;
+    const long long d2 = (long long)d * d, d4 = d2 * d2;
+    double* out = keep.dalloc(size_t(d2 + 2 * d4));
+    fill(c.cx, out, d2 + 2 * d4, 0.0);
+    double* lnj = keep.dalloc(4);
+    fill(c.cx, lnj, 4, 0.0);
+    {
+      Engine eng(c.cx, o, d, D, n);
+      auto bt = eng.sweep(W[0], 0, a, TP(lnj), keep);
+      auto bb = eng.sweep(W[1], 1, n - 1 - a, TP(lnj), keep);
+      Engine::Targets tb;
+      if (a + 1 < n) tb.push_back({a, TP(out + d2)});
+      eng.row_rhos(W[0], bt[a], bb[n - 1 - a], a, {{a, TP(out)}}, tb);
+      if (a + 1 < n) {
+        auto bl = eng.sweep(W[2], 2, a, TP(lnj), keep);
+        auto br = eng.sweep(W[3], 3, n - 1 - a, TP(lnj), keep);
+        eng.row_rhos(W[2], bl[a], br[n - 1 - a], a, {}, {{a, TP(out + d2 + d4)}});
+      }
+    }
+    PEPS_CUDA(cudaMemcpyAsync(rho_site, out, sizeof(double) * d2, cudaMemcpyDeviceToHost, c.st));
+    PEPS_CUDA(cudaMemcpyAsync(rho_h, out + d2, sizeof(double) * d4, cudaMemcpyDeviceToHost, c.st));
+    PEPS_CUDA(cudaMemcpyAsync(rho_v, out + d2 + d4, sizeof(double) * d4, cudaMemcpyDeviceToHost, c.st));
+    if (sigma)
+      PEPS_CUDA(cudaMemcpyAsync(sigma, sig, sizeof(double) * 4 * D * D, cudaMemcpyDeviceToHost, c.st));
+    c.finish();
+  });
+}
+
 int peps_set_iteration_caps(int cu0_half_sweeps, int jacobi_sweeps) {
   return guard([&] {
     PEPS_REQUIRE(cu0_half_sweeps >= 0 && cu0_half_sweeps <= 1000000 && jacobi_sweeps >= 0 &&

@@ -414,6 +414,72 @@ __device__ double cta_fro_normalize(double* x, int n, double* red) {
   return s;
 }
 
+// Infinite lattice (Section 5.4): the dominant separable boundary of a row of
+// copies of one tensor, from one side per CTA.  Each step moves the left and
+// the right fixed-point environments of the row once and then the boundary
+// matrix (the local CU_0 update between it and itself), all to unit norm;
+// identities to start; stops when none moves by tol, else at max_iter.
+struct Cu0Inf {
+  const double* A[4];   // the tensor in the four sweep orientations, [s][u][l][n][r], all legs D
+  double* sigma;        // [4][D][D]
+  double* work;         // 4 x cu0_inf_work(d, D) doubles
+  int d, D, max_iter;
+  double tol;
+  int* flag;
+};
+
+__global__ void __launch_bounds__(256) k_cu0_inf(const Cu0Inf a) {
+  __shared__ double red[32];
+  const int o = blockIdx.x, D = a.D, DD = D * D, d = a.d;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const SiteDims sd{D, D, D, D};
+  const long long big = (long long)d * DD * DD;
+  double* Y = a.work + o * (2 * big + 6 * DD + 32);
+  double* Z = Y + big;
+  double* sig = Z + big;
+  double* L = sig + DD;
+  double* R = L + DD;
+  double* Ln = R + DD;
+  double* Rn = Ln + DD;
+  double* b = Rn + DD;
+  const double* A = a.A[o];
+  const double v0 = 1.0 / sqrt(double(D));
+  for (int e = tid; e < DD; e += nt) {
+    const double v = (e / D == e % D) ? v0 : 0.0;
+    sig[e] = v;
+    L[e] = v;
+    R[e] = v;
+  }
+  __syncthreads();
+  bool conv = false;
+  for (int it = 0; it < a.max_iter && !conv; ++it) {
+    cu0_lenv(L, sig, A, sd, d, sig, Y, Z, Ln);
+    cta_fro_normalize(Ln, DD, red);
+    cu0_renv(R, sig, A, sd, d, sig, Y, Z, Rn);
+    cta_fro_normalize(Rn, DD, red);
+    cu0_local(Ln, sig, A, sd, d, Rn, Y, Z, b);
+    cta_fro_normalize(b, DD, red);
+    double c1 = 0.0, c2 = 0.0, c3 = 0.0;
+    for (int e = tid; e < DD; e += nt) {
+      c1 += (Ln[e] - L[e]) * (Ln[e] - L[e]);
+      c2 += (Rn[e] - R[e]) * (Rn[e] - R[e]);
+      c3 += (b[e] - sig[e]) * (b[e] - sig[e]);
+    }
+    c1 = sqrt(block_sum(c1, red));
+    c2 = sqrt(block_sum(c2, red));
+    c3 = sqrt(block_sum(c3, red));
+    for (int e = tid; e < DD; e += nt) {
+      L[e] = Ln[e];
+      R[e] = Rn[e];
+      sig[e] = b[e];
+    }
+    __syncthreads();
+    conv = fmax(c1, fmax(c2, c3)) < a.tol;
+  }
+  if (!conv && tid == 0) atomicOr(a.flag, FLAG_CU0_NOCONV);
+  for (int e = tid; e < DD; e += nt) a.sigma[(long long)o * DD + e] = sig[e];
+}
+
 __global__ void __launch_bounds__(256) k_cu0(const Cu0Lattice* lats, int* flag) {
   __shared__ double red[32];
   const Cu0Lattice L = lats[blockIdx.x];
@@ -521,6 +587,23 @@ void* stage(Ctx& cx, const void* host, size_t bytes) {
   PEPS_CUDA(cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, side[dev_id]));
   PEPS_CUDA(cudaStreamSynchronize(side[dev_id]));
   return dev;
+}
+
+void cu0_infinite(Ctx& cx, const double* const A[4], int d, int D, double* sigma, int max_iter) {
+  const long long DD = (long long)D * D, big = (long long)d * DD * DD;
+  double* work = cx.ws->dalloc(size_t(4) * (2 * big + 6 * DD + 32));
+  Cu0Inf a;
+  for (int o = 0; o < 4; ++o) a.A[o] = A[o];
+  a.sigma = sigma;
+  a.work = work;
+  a.d = d;
+  a.D = D;
+  a.max_iter = max_iter;
+  a.tol = 1e-13;
+  a.flag = cx.flag;
+  Launch L(K_CU0, cx.st, 0, 0);
+  k_cu0_inf<<<4, 256, 0, cx.st>>>(a);
+  PEPS_CHECK_LAUNCH();
 }
 
 std::pair<long long, long long> input_violations_device(Ctx& cx, const void* src, int src_f32, int Ly, int Lx,

@@ -19,6 +19,10 @@ void orient_lattice(Ctx& cx, const void* src, int src_f32, int Ly, int Lx, int d
 // (nonzero entries on outward legs, non-finite entries) of a device lattice.
 std::pair<long long, long long> input_violations_device(Ctx& cx, const void* src, int src_f32, int Ly, int Lx,
                                                         int d, int D);
+// Dominant separable boundaries of the infinite lattice of copies of one tensor
+// (given in the four sweep orientations, all legs D), into sigma[4][D][D];
+// FLAG_CU0_NOCONV if a side needs more than max_iter steps.
+void cu0_infinite(Ctx& cx, const double* const A[4], int d, int D, double* sigma, int max_iter);
 // Writes a NaN into element 0 (PEPS_FAULT=nan).
 void plant_nan_value(Ctx& cx, void* p, int f32);
 // A bounded wait on a flag nothing sets: records FLAG_TIMEOUT in cx.flag after budget_ns.

@@ -30,6 +30,7 @@ EXPORTS = [
     "peps_mlp_loss_grad", "peps_mlp_train", "peps_mlp_predict", "peps_plan_create", "peps_plan_run",
     "peps_plan_env", "peps_plan_launches", "peps_plan_free", "peps_plan_tune",
     "peps_set_iteration_caps", "peps_wait_selftest", "peps_boundary_fidelity", "peps_env_cluster_range",
+    "peps_ipeps_cluster",
 ]
 CLOSURE_WIDTH = 256
 
@@ -99,6 +100,7 @@ def _load():
                                            C.POINTER(C.c_double), P]
     lib.peps_env_cluster_range.argtypes = [C.POINTER(Lattice), C.POINTER(Opts), C.c_longlong, C.c_longlong,
                                            C.POINTER(P), P]
+    lib.peps_ipeps_cluster.argtypes = [P, C.c_int, C.c_int, C.c_int, C.POINTER(Opts), P, P, P, P, P]
     return lib
 
 
@@ -300,6 +302,35 @@ def boundary_fidelity(A, delta: int, chi: int, chi_ref: int, mode="var", sweeps:
     _check(lib.peps_boundary_fidelity(C.byref(inp.lat), C.byref(o), int(delta), int(chi_ref), C.byref(out),
                                       _stream_ptr(stream)))
     return out.value
+
+
+def ipeps_cluster(A, n: int, chi: int, mode="var", sweeps: int = 2, precision="fp64", seed: int = 0,
+                  stream=None, device=None) -> dict:
+    """Density matrices of one site and its right / down bonds of the infinite
+    PEPS with the single tensor A (d, D, D, D, D), from the infinite CU_0
+    boundaries and an n x n cluster at bond chi; see peps_ipeps_cluster."""
+    _set_device(device)
+    try:
+        import torch
+    except ImportError:
+        torch = None
+    if torch is not None and isinstance(A, torch.Tensor):
+        assert A.dim() == 5 and A.dtype == torch.float64 and A.is_contiguous()
+        keep, ptr, on_dev = A, A.data_ptr(), int(A.is_cuda)
+    else:
+        keep = np.ascontiguousarray(A, dtype=np.float64)
+        assert keep.ndim == 5
+        ptr, on_dev = keep.ctypes.data, 0
+    d, D = int(keep.shape[0]), int(keep.shape[1])
+    assert tuple(keep.shape[1:]) == (D,) * 4, "every leg of A must have dimension D"
+    o = _opts(chi, mode, sweeps, precision, n, seed)
+    rs = np.zeros((d, d))
+    rh = np.zeros((d * d, d * d))
+    rv = np.zeros((d * d, d * d))
+    sg = np.zeros((4, D, D))
+    _check(lib.peps_ipeps_cluster(ptr, d, D, on_dev, C.byref(o), rs.ctypes.data, rh.ctypes.data, rv.ctypes.data,
+                                  sg.ctypes.data, _stream_ptr(stream)))
+    return dict(rho_site=rs, rho_h=rh, rho_v=rv, sigma=sg)
 
 
 def cu0_noalloc(A_dev, sigma_dev, stream=None):

@@ -164,6 +164,24 @@ def _heisenberg_gate(tau: float) -> np.ndarray:
     return (v * np.exp(-tau * w)) @ v.T
 
 
+def _qr_pos(M):
+    """Batched thin QR with a non-negative diagonal of R: the factors no longer
+    depend on the sign convention of the LAPACK that computes them."""
+    Q, R = np.linalg.qr(M)
+    s = np.where(np.diagonal(R, axis1=1, axis2=2) < 0, -1.0, 1.0)
+    return Q * s[:, None, :], R * s[:, :, None]
+
+
+def _svd_signed(M):
+    """Batched SVD with the largest-magnitude entry of every left singular
+    vector positive (the right vectors flipped with them)."""
+    U, S, Vt = np.linalg.svd(M)
+    idx = np.argmax(np.abs(U), axis=1)                                  # (n, k)
+    piv = np.take_along_axis(U, idx[:, None, :], axis=1)[:, 0, :]
+    s = np.where(piv < 0, -1.0, 1.0)
+    return U * s[:, None, :], S, Vt * s[:, :, None]
+
+
 def _su_pair(Ga, Gb, lam_a, lam_b, lam_ab, gate, D):
     """Batched simple update of horizontal pairs.
 
@@ -182,15 +200,15 @@ def _su_pair(Ga, Gb, lam_a, lam_b, lam_ab, gate, D):
     # QR-reduce the outer legs: A -> [(u,l,dn), (s,r)], B -> [(u,dn,r), (t,l)]
     Am = A.transpose(0, 2, 3, 4, 1, 5).reshape(n, D ** 3, d * D)
     Bm = B.transpose(0, 2, 4, 5, 1, 3).reshape(n, D ** 3, d * D)
-    Qa, Ra = np.linalg.qr(Am)                         # Ra: (n, k, d*D)
-    Qb, Rb = np.linalg.qr(Bm)
+    Qa, Ra = _qr_pos(Am)                              # Ra: (n, k, d*D)
+    Qb, Rb = _qr_pos(Bm)
     k = Ra.shape[1]
     # shared bond contracted: th[a,s,b,t] = sum_r Ra[a,s,r] Rb[b,t,r]
     th = np.matmul(Ra.reshape(n, k * d, D), Rb.reshape(n, k * d, D).transpose(0, 2, 1))
     # gate on (s, t): th'[a,p,b,q] = sum_st G[p,q,s,t] th[a,s,b,t]
     th = th.reshape(n, k, d, k, d).transpose(0, 1, 3, 2, 4).reshape(n * k * k, d * d)
     th = (th @ gate.T).reshape(n, k, k, d, d).transpose(0, 1, 3, 2, 4).reshape(n, k * d, k * d)
-    U, S, Vt = np.linalg.svd(th)
+    U, S, Vt = _svd_signed(th)
     S = S[:, :D]
     lam = S / S[:, :1]
     Ua = U[:, :, :D]                                  # [(a, s'), r]
