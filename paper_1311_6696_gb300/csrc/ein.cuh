@@ -27,6 +27,10 @@ struct Ctx {
   // Iteration caps of this call (Jacobi SVD sweeps, CU_0 half-sweeps).
   int svd_cap = 60;
   int cu0_cap = 200;
+  // Instrumentation of FP64 contractions that are part of a factorisation:
+  // class to charge (-1: their own) and whether to count their flops.
+  int f64_class = -1;
+  bool f64_flops = true;
 
   Ctx(cudaStream_t s, Arena* w) : st(s), ws(w) {}
   ~Ctx() {

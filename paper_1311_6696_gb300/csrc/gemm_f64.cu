@@ -388,7 +388,8 @@ void ein(Ctx& cx, const char* spec, const TP& A, const Dims& ad, const TP& B,
     const int nblk = int(std::max<long long>(1, std::min<long long>((g.K + kchunk - 1) / kchunk, 4 * num_sms() / np)));
     const long long kc = (g.K + nblk - 1) / nblk;
     double* part = cx.scratch(size_t(nblk) * np * DOT_MAXP);
-    Launch L(K_GEMM_F64, cx.st, 2.0 * double(g.M * g.N * g.NB) * double(g.K) * np, 0);
+    Launch L(cx.f64_class >= 0 ? KClass(cx.f64_class) : K_GEMM_F64, cx.st,
+             cx.f64_flops ? 2.0 * double(g.M * g.N * g.NB) * double(g.K) * np : 0.0, 0);
     k_dot_partial<<<dim3(nblk, np), 256, 0, cx.st>>>(g, kc, part);
     k_dot_finish<<<np, 32, 0, cx.st>>>(g, nblk, part);
     L.more();
@@ -426,7 +427,7 @@ void ein(Ctx& cx, const char* spec, const TP& A, const Dims& ad, const TP& B,
 
   const double flops = 2.0 * double(g.M) * double(g.N) * double(g.K) * double(g.NB) * np;
   {
-    Launch L(K_GEMM_F64, cx.st, flops, 0);
+    Launch L(cx.f64_class >= 0 ? KClass(cx.f64_class) : K_GEMM_F64, cx.st, cx.f64_flops ? flops : 0.0, 0);
     dim3 grid(unsigned(tiles), unsigned(splitk), unsigned(g.NB * np));
     switch (BM) {
       case 16: k_gemm_f64<16, 256><<<grid, 256, 0, cx.st>>>(g); break;

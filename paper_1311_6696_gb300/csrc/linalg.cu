@@ -766,17 +766,131 @@ int cluster_size_for(K kern, int threads, size_t smem) {
 int qr_cluster_size(size_t smem) { return cluster_size_for(k_qr_cluster, QRC_THREADS, smem); }
 }  // namespace
 
+namespace {
+
+constexpr size_t kQrSmemMax = 200 * 1024;
+
+// Shared memory a cluster QR of an m x n matrix needs per CTA with its rows
+// split over c CTAs (rows of the working matrix and of Q, odd column stride).
+size_t qr_smem(int m, int n, int c) {
+  const int k = std::min(m, n);
+  const size_t base = sizeof(double) * (4 * size_t(n) + 2 + k + size_t(n) * QS + n + 2 + QS);
+  const size_t ld = size_t(((m + c - 1) / c) | 1);
+  return base + sizeof(double) * ld * (size_t(n) + k);
+}
+
+// dst[b][i*qrs + j*qcs] = src[b][i*n + j]
+__global__ void k_copy_strided(const TP src, const TP dst, int m, int n, long long qrs, long long qcs) {
+  const double* s = src.d(blockIdx.y);
+  double* d = dst.d(blockIdx.y);
+  const long long total = (long long)m * n;
+  const bool rows_fast = qrs < qcs;   // write along whichever index is contiguous in dst
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = rows_fast ? e % m : e / n, j = rows_fast ? e / m : e % n;
+    d[i * qrs + j * qcs] = s[i * n + j];
+  }
+}
+
+// Leaves of a tall-skinny QR: the smallest power of two L >= 2 that divides m
+// and whose leaves (m / L rows, at least 32 per CTA of a 16-CTA cluster)
+// keep their rows in shared memory; 0 if none.
+int tsqr_leaves(int m, int n) {
+  for (int L = 2; L <= 16; L *= 2) {
+    if (m % L) return 0;
+    const int ml = m / L;
+    if (ml < n || ml < 16 * 32) return 0;
+    if (qr_smem(ml, n, 16) <= kQrSmemMax) return L;
+  }
+  return 0;
+}
+
+}  // namespace
+
+void qr_direct(Ctx& cx, int m, int n, const TP& A, long long rs, long long cs, const TP& Q, long long qrs,
+               long long qcs, const TP& R, double counted_flops);
+
+// Algorithmic flops of one thin QR (the count used for rooflines): 2mn^2 - 2n^3/3.
+double qr_flops(int m, int n) {
+  const double k = std::min(m, n);
+  return 2.0 * m * double(n) * k - 2.0 / 3.0 * k * k * k;
+}
+
+// Tall-skinny QR (Demmel, Grigori, Hoemmen & Langou): the rows are split into
+// L leaves factored together as one batched cluster QR (rows in shared
+// memory), the L stacked R factors are factored once more, and each leaf's Q
+// is its own Q times its block of the second Q (one batched FP64 GEMM).  Q is
+// the Householder Q of A up to the sign of each column; R likewise.
+void qr_tsqr(Ctx& cx, int m, int n, int L, const TP& A, long long rs, long long cs, const TP& Q, long long qrs,
+             long long qcs, const TP& R, int np) {
+  const int ml = m / L;
+  const size_t qn = size_t(ml) * n, rn = size_t(n) * n;
+  double* qleaf = cx.ws->dalloc(size_t(np) * L * qn);
+  double* rstack = cx.ws->dalloc(size_t(np) * L * rn);
+  double* qtree = cx.ws->dalloc(size_t(np) * L * rn);
+  TP Al, Ql, Rl, Bt, Ct, At, Qt;
+  Al.n = Ql.n = Rl.n = Bt.n = Ct.n = np * L;
+  At.n = Qt.n = np;
+  const bool direct_out = (qrs == n && qcs == 1);
+  double* qout = direct_out ? nullptr : cx.ws->dalloc(size_t(np) * m * n);
+  for (int b = 0; b < np; ++b) {
+    At.p[b] = rstack + size_t(b) * L * rn;
+    Qt.p[b] = qtree + size_t(b) * L * rn;
+    for (int i = 0; i < L; ++i) {
+      const int j = b * L + i;
+      Al.p[j] = A.d(b) + (long long)i * ml * rs;
+      Ql.p[j] = qleaf + size_t(j) * qn;
+      Rl.p[j] = rstack + size_t(j) * rn;
+      Bt.p[j] = qtree + size_t(j) * rn;
+      Ct.p[j] = direct_out ? Q.d(b) + size_t(i) * qn : qout + size_t(b) * m * n + size_t(i) * qn;
+    }
+  }
+  // The three steps are charged to the QR class, with the algorithmic flops of
+  // the whole factorisation counted once.
+  qr_direct(cx, ml, n, Al, rs, cs, Ql, n, 1, Rl, qr_flops(m, n) * np);
+  qr_direct(cx, L * n, n, At, n, 1, Qt, n, 1, R, 0.0);
+  cx.f64_class = K_QR;
+  cx.f64_flops = false;
+  ein(cx, "ik,kj->ij", Ql, {ml, n}, Bt, {n, n}, Ct);
+  cx.f64_class = -1;
+  cx.f64_flops = true;
+  if (!direct_out) {
+    TP src;
+    src.n = np;
+    for (int b = 0; b < np; ++b) src.p[b] = qout + size_t(b) * m * n;
+    Launch Lc(K_QR, cx.st);
+    k_copy_strided<<<dim3(unsigned(std::min<long long>(4096, ((long long)m * n + 255) / 256)), np), 256, 0, cx.st>>>(
+        src, Q.all(np), m, n, qrs, qcs);
+    PEPS_CHECK_LAUNCH();
+  }
+}
+
 void qr_thin(Ctx& cx, int m, int n, const TP& A, long long rs, long long cs, const TP& Q, long long qrs,
              long long qcs, const TP& R) {
   PEPS_REQUIRE(m > 0 && n > 0, "qr of an empty matrix");
   const int np = problems({&A, &Q, &R});
   PEPS_REQUIRE(!A.null() && Q.n == np && (R.null() || R.n == np), "internal: qr operands");
+  // Rows that do not fit in the shared memory of a 16-CTA cluster: tall-skinny
+  // QR over leaves that do (more SMs per factorisation, rows on chip).
+  if (m >= n && cx.qr_cmax <= 0 && qr_smem(m, n, 16) > kQrSmemMax) {
+    const int L = tsqr_leaves(m, n);
+    if (L > 1 && np * L <= MAXB) {
+      qr_tsqr(cx, m, n, L, A, rs, cs, Q, qrs, qcs, R, np);
+      return;
+    }
+  }
+  qr_direct(cx, m, n, A, rs, cs, Q, qrs, qcs, R, qr_flops(m, n) * np);
+}
+
+void qr_direct(Ctx& cx, int m, int n, const TP& A, long long rs, long long cs, const TP& Q, long long qrs,
+               long long qcs, const TP& R, double counted_flops) {
+  const int np = problems({&A, &Q, &R});
   const int k = std::min(m, n);
+  // work of the Householder factorisation with Q formed (for the cluster-size model)
   const double flops = 4.0 * m * double(n) * k - 4.0 / 3.0 * double(k) * k * k;
-  const size_t kQrSmemMax = 200 * 1024;
   const size_t base = sizeof(double) * (4 * size_t(n) + 2 + k + size_t(n) * QS + n + 2 + QS);
   auto ld_of = [&](int c) { return (((m + c - 1) / c) | 1); };   // odd column stride
-  auto full_of = [&](int c) { return base + sizeof(double) * size_t(ld_of(c)) * (size_t(n) + k); };
+  auto full_of = [&](int c) { return qr_smem(m, n, c); };
   // Cluster size: rows per CTA >= 32; among the sizes whose rows fit in shared
   // memory, the one with the least estimated time for all problems: waves of
   // clusters over the SMs x (FP64 work per CTA + three cluster barriers per column).
@@ -823,7 +937,7 @@ void qr_thin(Ctx& cx, int m, int n, const TP& A, long long rs, long long cs, con
   a.W = w;
   a.Qw = w + size_t(np) * a.wst;
   a.tau = a.Qw + size_t(np) * a.qst;
-  Launch L(K_QR, cx.st, flops * np, 0);
+  Launch L(K_QR, cx.st, counted_flops, 0);
   if (C <= 1) {
     k_qr_house<<<np, QR_THREADS, 0, cx.st>>>(a);
   } else {
