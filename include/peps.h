@@ -206,6 +206,11 @@ int peps_norm(const peps_lattice* lat, const peps_opts* opts,
  *   (different streams, or different host threads) race.  The call clears
  *   its status words itself.  Allocates nothing; synchronises the stream.
  *   Fails with PEPS_ECONVERGE if a cut needs more than 200 half-sweeps.
+ *   Cost: the whole lattice runs on one 256-thread CTA (one SM), about
+ *   Ly * Lx * h * 8 d D^5 FP64 flops for h half-sweeps per cut; at the
+ *   largest sizes with slowly converging cuts a call can take many minutes.
+ *   The Python binding checks rank, shapes, dtype (float64), contiguity and
+ *   device of both tensors before calling, since the C side cannot.
  */
 int peps_cu0_noalloc(const double* A, int Ly, int Lx, int d, int D, double* sigma,
                      void* cuda_stream);

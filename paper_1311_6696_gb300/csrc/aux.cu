@@ -480,6 +480,59 @@ __global__ void __launch_bounds__(256) k_cu0_inf(const Cu0Inf a) {
   for (int e = tid; e < DD; e += nt) a.sigma[(long long)o * DD + e] = sig[e];
 }
 
+// A site of a CU_0 row: its tensor and effective leg dimensions.
+struct Cu0Site {
+  const double* A;
+  SiteDims sd;
+};
+
+// One cut of the separable boundary (Section 5.1): ALS half-sweeps over the
+// row's sites that fit the matrices nxt(x) (on the down legs of site x)
+// between the row and the matrices above it, prv(x).  On entry nxt holds the
+// start and Lm[0], Rm[(Lx-1)*DM2] the row's left / right closures; the right
+// environments are built here.  Each local update is b_x itself, scaled to
+// unit Frobenius norm.  Returns whether a half-sweep moved no matrix by tol.
+// site(x) may stage the tensor in scratch (it is called again for every use).
+template <class SiteF, class PrvF, class NxtF>
+__device__ bool cu0_cut(int Lx, int d, int DM2, SiteF site, PrvF prv, NxtF nxt, double* Lm, double* Rm, double* Y,
+                        double* Z, double* b, int max_half, double tol, double* red) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int x = Lx - 1; x >= 1; --x) {
+    const Cu0Site st = site(x);
+    cu0_renv(Rm + (long long)x * DM2, prv(x), st.A, st.sd, d, nxt(x), Y, Z, Rm + (long long)(x - 1) * DM2);
+    cta_fro_normalize(Rm + (long long)(x - 1) * DM2, st.sd.dl * st.sd.dl, red);
+  }
+  bool conv = false;
+  for (int h = 0; h < max_half && !conv; ++h) {
+    double change = 0.0;
+    for (int step = 0; step < Lx; ++step) {
+      const int x = (h % 2 == 0) ? step : Lx - 1 - step;
+      const Cu0Site st = site(x);
+      const SiteDims sd = st.sd;
+      cu0_local(Lm + (long long)x * DM2, prv(x), st.A, sd, d, Rm + (long long)x * DM2, Y, Z, b);
+      cta_fro_normalize(b, sd.dn * sd.dn, red);
+      double* cur = nxt(x);
+      double part = 0.0;
+      for (int e = tid; e < sd.dn * sd.dn; e += nt) {
+        const double df = b[e] - cur[e];
+        part += df * df;
+      }
+      change = fmax(change, sqrt(block_sum(part, red)));
+      for (int e = tid; e < sd.dn * sd.dn; e += nt) cur[e] = b[e];
+      __syncthreads();
+      if (h % 2 == 0 && x < Lx - 1) {
+        cu0_lenv(Lm + (long long)x * DM2, prv(x), st.A, sd, d, cur, Y, Z, Lm + (long long)(x + 1) * DM2);
+        cta_fro_normalize(Lm + (long long)(x + 1) * DM2, sd.dr * sd.dr, red);
+      } else if (h % 2 == 1 && x > 0) {
+        cu0_renv(Rm + (long long)x * DM2, prv(x), st.A, sd, d, cur, Y, Z, Rm + (long long)(x - 1) * DM2);
+        cta_fro_normalize(Rm + (long long)(x - 1) * DM2, sd.dl * sd.dl, red);
+      }
+    }
+    conv = change < tol;
+  }
+  return conv;
+}
+
 __global__ void __launch_bounds__(256) k_cu0(const Cu0Lattice* lats, int* flag) {
   __shared__ double red[32];
   const Cu0Lattice L = lats[blockIdx.x];
@@ -518,41 +571,9 @@ __global__ void __launch_bounds__(256) k_cu0(const Cu0Lattice* lats, int* flag) 
       for (int e = tid; e < dl * dl; e += nt) Lm[e] = L.left[(long long)r * DM2 + e];
     }
     __syncthreads();
-    for (int x = Lx - 1; x >= 1; --x) {
-      const SiteDims sd = dims(r, x);
-      cu0_renv(Rm + (long long)x * DM2, outm(r, x), site(r, x), sd, d, outm(r + 1, x), Y, Z,
-               Rm + (long long)(x - 1) * DM2);
-      cta_fro_normalize(Rm + (long long)(x - 1) * DM2, sd.dl * sd.dl, red);
-    }
-    bool conv = false;
-    for (int h = 0; h < L.max_half && !conv; ++h) {
-      double change = 0.0;
-      for (int step = 0; step < Lx; ++step) {
-        const int x = (h % 2 == 0) ? step : Lx - 1 - step;
-        const SiteDims sd = dims(r, x);
-        cu0_local(Lm + (long long)x * DM2, outm(r, x), site(r, x), sd, d, Rm + (long long)x * DM2, Y, Z, b);
-        cta_fro_normalize(b, sd.dn * sd.dn, red);
-        double* cur = outm(r + 1, x);
-        double part = 0.0;
-        for (int e = tid; e < sd.dn * sd.dn; e += nt) {
-          const double df = b[e] - cur[e];
-          part += df * df;
-        }
-        change = fmax(change, sqrt(block_sum(part, red)));
-        for (int e = tid; e < sd.dn * sd.dn; e += nt) cur[e] = b[e];
-        __syncthreads();
-        if (h % 2 == 0 && x < Lx - 1) {
-          cu0_lenv(Lm + (long long)x * DM2, outm(r, x), site(r, x), sd, d, cur, Y, Z,
-                   Lm + (long long)(x + 1) * DM2);
-          cta_fro_normalize(Lm + (long long)(x + 1) * DM2, sd.dr * sd.dr, red);
-        } else if (h % 2 == 1 && x > 0) {
-          cu0_renv(Rm + (long long)x * DM2, outm(r, x), site(r, x), sd, d, cur, Y, Z,
-                   Rm + (long long)(x - 1) * DM2);
-          cta_fro_normalize(Rm + (long long)(x - 1) * DM2, sd.dl * sd.dl, red);
-        }
-      }
-      conv = change < L.tol;
-    }
+    const bool conv = cu0_cut(
+        Lx, d, DM2, [&](int x) { return Cu0Site{site(r, x), dims(r, x)}; }, [&](int x) { return outm(r, x); },
+        [&](int x) { return outm(r + 1, x); }, Lm, Rm, Y, Z, b, L.max_half, L.tol, red);
     if (!conv && tid == 0) atomicOr(flag, FLAG_CU0_NOCONV);
     __syncthreads();
   }
@@ -823,37 +844,10 @@ __global__ void __launch_bounds__(256) k_cu0_dense(const DenseCu0 a) {
       Lm[0] = 1.0;
     }
     __syncthreads();
-    for (int x = Lx - 1; x >= 1; --x) {
-      const SiteDims sd = load_dense_site(a, r, x, As);
-      cu0_renv(Rm + (long long)x * DM2, P(x), As, sd, d, N(x), Y, Z, Rm + (long long)(x - 1) * DM2);
-      cta_fro_normalize(Rm + (long long)(x - 1) * DM2, sd.dl * sd.dl, red);
-    }
-    bool conv = false;
-    for (int h = 0; h < a.max_half && !conv; ++h) {
-      double change = 0.0;
-      for (int step = 0; step < Lx; ++step) {
-        const int x = (h % 2 == 0) ? step : Lx - 1 - step;
-        const SiteDims sd = load_dense_site(a, r, x, As);
-        cu0_local(Lm + (long long)x * DM2, P(x), As, sd, d, Rm + (long long)x * DM2, Y, Z, b);
-        cta_fro_normalize(b, sd.dn * sd.dn, red);
-        double part = 0.0;
-        for (int e = tid; e < sd.dn * sd.dn; e += nt) {
-          const double df = b[e] - N(x)[e];
-          part += df * df;
-        }
-        change = fmax(change, sqrt(block_sum(part, red)));
-        for (int e = tid; e < sd.dn * sd.dn; e += nt) N(x)[e] = b[e];
-        __syncthreads();
-        if (h % 2 == 0 && x < Lx - 1) {
-          cu0_lenv(Lm + (long long)x * DM2, P(x), As, sd, d, N(x), Y, Z, Lm + (long long)(x + 1) * DM2);
-          cta_fro_normalize(Lm + (long long)(x + 1) * DM2, sd.dr * sd.dr, red);
-        } else if (h % 2 == 1 && x > 0) {
-          cu0_renv(Rm + (long long)x * DM2, P(x), As, sd, d, N(x), Y, Z, Rm + (long long)(x - 1) * DM2);
-          cta_fro_normalize(Rm + (long long)(x - 1) * DM2, sd.dl * sd.dl, red);
-        }
-      }
-      conv = change < a.tol;
-    }
+    // the same cut routine as the library's CU_0, each site staged from the dense layout
+    const bool conv = cu0_cut(
+        Lx, d, DM2, [&](int x) { return Cu0Site{As, load_dense_site(a, r, x, As)}; }, P, N, Lm, Rm, Y, Z, b,
+        a.max_half, a.tol, red);
     if (!conv && tid == 0) atomicOr(flag, FLAG_CU0_NOCONV);
     for (int x = 0; x < Lx; ++x) {
       const int dn = dense_dims(a, r, x).dn;

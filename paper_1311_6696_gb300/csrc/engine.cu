@@ -77,7 +77,7 @@ Engine::~Engine() {
 }
 
 void Engine::enable_dual(cudaStream_t st2) {
-  const size_t chi = size_t(opt.chi), D2 = size_t(Dmax_) * Dmax_, dd = size_t(d_) * d_;
+  const size_t dd = size_t(d_) * d_;
   const size_t set = (bigN_ * dd + bigN_ * dd * d_ + bigN_ * dd) * 8;
   if (dual_ || nb_ != 1 || set > (size_t(512) << 20)) return;
   ws2_stream_ = st2;
