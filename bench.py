@@ -304,6 +304,7 @@ def run_ours(args, rank, world, dist):
             del e64, p64
 
     cluster = cluster_section(args, peps, torch, st, flush) if args.cluster else None
+    fidelity = fidelity_section(peps, torch, st) if args.fidelity and rank == 0 else None
 
     ms_step, e_ms, value, e2e = aggregate(sum(times) / len(times), sum(etimes) / len(etimes), envs, world,
                                           dist, dev)
@@ -380,6 +381,8 @@ def run_ours(args, rank, world, dist):
             res["speedup_vs_fp64_path"] = round(fp64["ms_per_step"] / ms_step, 3)
     if cluster is not None:
         res["cluster"] = cluster
+    if fidelity is not None:
+        res["fidelity"] = fidelity
     if clk:
         res["clocks"] = clk
     if not args.no_cpu_baseline:
@@ -428,6 +431,23 @@ def cluster_section(args, peps, torch, st, flush):
                                 "plan_create_s": round(t_create, 1)}
         del env
         plan.free()
+    return out
+
+
+def fidelity_section(peps, torch, st):
+    """Section 5.2 / Fig. Fid on the paper's setting: 1 - f of the left-most
+    column's environment of a 20x20 simple-update Heisenberg PEPS (D=4),
+    clusters of delta = 1..4 columns and the full contraction at D' in
+    {4, 8, 16, 32, 64}, against the full contraction at D' = 100 (FP64)."""
+    A = torch.from_numpy(load_input("20x20_D4_su")).cuda()
+    out = {"workload": "20x20 OBC PEPS d=2 D=4, seeded simple-update Heisenberg generator (tau=0.01, 400 steps); "
+                       "var, FP64; reference: full contraction at D'=100", "one_minus_f": {}}
+    t0 = time.perf_counter()
+    for delta in (1, 2, 3, 4, 19):
+        key = "full" if delta == 19 else f"delta={delta}"
+        out["one_minus_f"][key] = {str(chi): peps.boundary_fidelity(A, delta, chi=chi, chi_ref=100, stream=st)
+                                   for chi in (4, 8, 16, 32, 64)}
+    out["seconds"] = round(time.perf_counter() - t0, 1)
     return out
 
 
@@ -591,6 +611,7 @@ def main():
     ap.add_argument("--dominant", default=None, help="kernel class timed for the roofline (skips the probe replay)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cluster", action="store_true", help="add the 14x14 D=6 cluster section")
+    ap.add_argument("--fidelity", action="store_true", help="add the boundary-fidelity section (Fig. Fid)")
     ap.add_argument("--tune", action="store_true", help="choose the plan's launch configuration by measurement")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-budget", type=float, default=20.0)

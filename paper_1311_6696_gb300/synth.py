@@ -133,6 +133,7 @@ WORKLOADS = {
     "16x16_D4": dict(Ly=16, Lx=16, d=2, D=4, gen="gauss", seed=5),
     "20x20_D8_su": dict(Ly=20, Lx=20, d=2, D=8, gen="su", seed=4),
     "16x16_D4_su": dict(Ly=16, Lx=16, d=2, D=4, gen="su", seed=5),
+    "20x20_D4_su": dict(Ly=20, Lx=20, d=2, D=4, gen="su", seed=6),
 }
 
 
