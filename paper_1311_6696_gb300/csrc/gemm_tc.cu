@@ -357,6 +357,211 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ 
   }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Persistent form (no split-K): one CTA per SM walks the output tiles t =
+// blockIdx.x, blockIdx.x + gridDim.x, ...  Warp 4 (one thread) streams the
+// operand tiles through the smem ring with TMA, warp 5 (one thread) issues the
+// MMAs into one of two TMEM accumulators, and warps 0-3 drain the other one
+// (tcgen05.ld, then the same stores as k_gemm_tc), so a tile's epilogue runs
+// while the next tile is loaded and multiplied.  Every wait is bounded.
+constexpr int TCP_THREADS = 192;
+
+template <int BN>
+__global__ void __launch_bounds__(TCP_THREADS) k_gemm_tc_persist(const __grid_constant__ CUtensorMap ta,
+                                                                 const __grid_constant__ CUtensorMap tb,
+                                                                 const __grid_constant__ CUtensorMap tal,
+                                                                 const __grid_constant__ CUtensorMap tbl,
+                                                                 const TcArgs g) {
+  constexpr int A_BYTES = TC_BM * TC_ROWB;
+  constexpr int B_BYTES = BN * TC_ROWB;
+  constexpr int NCOL = BN < 32 ? 32 : BN;   // TMEM columns of one accumulator
+  extern __shared__ __align__(1024) uint8_t dsm[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
+  const int stage_bytes = g.split ? 2 * (A_BYTES + B_BYTES) : (A_BYTES + B_BYTES);
+  __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], tfull[2], tempty[2], drain;
+  __shared__ uint32_t tmem_base;
+  __shared__ long long offm[TC_BM], offn[BN];
+  __shared__ float stage_out[4][32][17];
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long tiles_n = (g.N + BN - 1) / BN;
+  const long long tiles = ((g.M + TC_BM - 1) / TC_BM) * tiles_n;
+  const long long total = tiles * g.nprob;
+  if (tid == 0) {
+    for (int s = 0; s < g.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    mbar_init(&drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(2 * NCOL));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 4 && lane == 0) {
+    // TMA producer, running ahead across tiles
+    bool ok = true;
+    int it = 0;
+    for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
+      const int pb = int(t / tiles);
+      const long long tt = t % tiles;
+      const int ra = int(pb * g.pad_m + (tt / tiles_n) * TC_BM), rb = int(pb * g.pad_n + (tt % tiles_n) * BN);
+      for (int kt = 0; kt < g.ktiles; ++kt, ++it) {
+        const int s = it % g.stages;
+        const uint32_t round = uint32_t(it / g.stages);
+        ok = mbar_wait(&empty[s], (round & 1u) ^ 1u, g.flag);
+        if (!ok) break;
+        uint8_t* st = base + s * stage_bytes;
+        mbar_expect_tx(&full[s], uint32_t(stage_bytes));
+        const int kx = kt * (TC_ROWB / (g.bf16 ? 2 : 4));
+        tma_load_2d(st, &ta, &full[s], kx, ra);
+        tma_load_2d(st + A_BYTES, &tb, &full[s], kx, rb);
+        if (g.split) {
+          tma_load_2d(st + A_BYTES + B_BYTES, &tal, &full[s], kx, ra);
+          tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tbl, &full[s], kx, rb);
+        }
+      }
+    }
+    // no copy of ours may still be landing in shared memory when the CTA leaves:
+    // wait (bounded) for the last round issued into every slot
+    for (int j = it - 1; j >= 0 && j >= it - g.stages; --j)
+      mbar_wait(&full[j % g.stages], uint32_t(j / g.stages) & 1u, g.flag);
+  } else if (warp == 5 && lane == 0) {
+    // MMA issuer: tile i accumulates in TMEM buffer i % 2
+    const uint32_t afmt = g.bf16 ? 1u : 2u;
+    const uint32_t idesc = (1u << 4) | (afmt << 7) | (afmt << 10) | (uint32_t(BN >> 3) << 17) |
+                           (uint32_t(TC_BM >> 4) << 24);
+    bool ok = true;
+    int it = 0, i = 0;
+    for (long long t = blockIdx.x; t < total && ok; t += gridDim.x, ++i) {
+      const int buf = i & 1;
+      const uint32_t use = uint32_t(i >> 1);
+      ok = mbar_wait(&tempty[buf], (use & 1u) ^ 1u, g.flag);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t acc_t = tmem + uint32_t(buf * NCOL);
+      for (int kt = 0; kt < g.ktiles; ++kt, ++it) {
+        const int s = it % g.stages;
+        const uint32_t round = uint32_t(it / g.stages);
+        ok = mbar_wait(&full[s], round & 1u, g.flag);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        uint8_t* st = base + s * stage_bytes;
+        const uint64_t da = sdesc(st), db = sdesc(st + A_BYTES);
+        const uint64_t dal = sdesc(st + A_BYTES + B_BYTES), dbl = sdesc(st + 2 * A_BYTES + B_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint64_t o = uint64_t(kk * 2);
+          const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+          if (g.bf16) {
+            mma_f16(acc_t, da + o, db + o, idesc, acc);
+            if (g.split) {
+              mma_f16(acc_t, da + o, dbl + o, idesc, 1u);
+              mma_f16(acc_t, dal + o, db + o, idesc, 1u);
+            }
+          } else {
+            mma_tf32(acc_t, da + o, db + o, idesc, acc);
+            if (g.split) {
+              mma_tf32(acc_t, da + o, dbl + o, idesc, 1u);
+              mma_tf32(acc_t, dal + o, db + o, idesc, 1u);
+            }
+          }
+        }
+        mma_commit(&empty[s]);
+      }
+      if (ok) mma_commit(&tfull[buf]);
+    }
+    // every MMA issued here has finished before TMEM is released (bounded wait)
+    mma_commit(&drain);
+    mbar_wait(&drain, 0u, g.flag);
+  } else if (warp < 4) {
+    // epilogue: drain the accumulator of tile i while tile i+1 is computed.
+    // The four warps run the same number of iterations and reach both named
+    // barriers in every one of them; a warp whose wait ran out (the status word
+    // is set) only stops doing work, so no warp is left waiting at a barrier.
+    const float alpha = float(g.alpha);
+    bool dead = false;
+    int i = 0;
+    for (long long t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+      const int buf = i & 1;
+      const uint32_t use = uint32_t(i >> 1);
+      const int pb = int(t / tiles);
+      const long long tt = t % tiles;
+      const long long m0 = (tt / tiles_n) * TC_BM, n0 = (tt % tiles_n) * BN;
+      asm volatile("bar.sync 1, 128;" ::: "memory");   // the previous tile's offsets are no longer read
+      {
+        const long long m = m0 + tid;
+        long long o = -1;
+        if (m < g.M) decomp(g.gm, m, o);
+        offm[tid] = o;
+      }
+      for (int c = tid; c < BN; c += 128) {
+        const long long n = n0 + c;
+        long long o = -1;
+        if (n < g.N) decomp(g.gn, n, o);
+        offn[c] = o;
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (dead) continue;
+      const bool waited = mbar_wait(&tfull[buf], use & 1u, g.flag);
+      if (!__all_sync(0xffffffffu, waited)) {
+        dead = true;
+        continue;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int row = warp * 32 + lane;
+      const long long om = offm[row];
+      const uint32_t acc_t = tmem + uint32_t(buf * NCOL) + (uint32_t(warp * 32) << 16);
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(acc_t + uint32_t(c0), r);
+        if (!g.cols_fast) {
+          if (om < 0) continue;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const long long on = offn[c0 + j];
+            if (on >= 0) put_out(g, pb, om + on, __uint_as_float(r[j]) * alpha);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) stage_out[warp][lane][j] = __uint_as_float(r[j]);
+          __syncwarp();
+          const int j = lane & 15;
+          const long long on = offn[c0 + j];
+#pragma unroll 4
+          for (int q = lane >> 4; q < 32; q += 2) {
+            const long long omi = offm[warp * 32 + q];
+            if (omi >= 0 && on >= 0) put_out(g, pb, omi + on, stage_out[warp][q][j] * alpha);
+          }
+          __syncwarp();
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * NCOL));
+  }
+}
+
 // Split-K: out[p][m, n] = alpha * sum_s part[s][p][m][n] (fixed order), through
 // the output offset groups.
 __global__ void k_tc_splitk_reduce(const TcArgs g) {
@@ -623,10 +828,24 @@ void launch_tc(Ctx& cx, const CUtensorMap& ta, const CUtensorMap& tb, const CUte
   g.stages = std::max(1, std::min({TC_STAGES, (budget - 1024) / stage, g.splitk > 1 ? g.kt_per : g.ktiles}));
   const size_t smem = size_t(stage) * g.stages + 1024;
   static std::once_flag once;
+  static int nsm = 0;
   std::call_once(once, [] {
     PEPS_CUDA(cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    PEPS_CUDA(cudaFuncSetAttribute(k_gemm_tc_persist<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    int dev = 0;
+    PEPS_CUDA(cudaGetDevice(&dev));
+    PEPS_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   });
-  k_gemm_tc<BN><<<dim3(unsigned(tiles), unsigned(std::max(1, g.splitk))), TC_THREADS, smem, cx.st>>>(ta, tb, tal, tbl, g);
+  if (g.splitk > 1 || tiles <= nsm) {
+    // split-K partials, or no more tiles than SMs: one tile per CTA
+    k_gemm_tc<BN><<<dim3(unsigned(tiles), unsigned(std::max(1, g.splitk))), TC_THREADS, smem, cx.st>>>(ta, tb, tal,
+                                                                                                        tbl, g);
+  } else {
+    // the ring holds at least two stages so the next tile's operands stream in
+    g.stages = std::max(1, std::min(TC_STAGES, (budget - 1024) / stage));
+    const size_t psmem = size_t(stage) * g.stages + 1024;
+    k_gemm_tc_persist<BN><<<unsigned(nsm), TCP_THREADS, psmem, cx.st>>>(ta, tb, tal, tbl, g);
+  }
   PEPS_CHECK_LAUNCH();
 }
 
