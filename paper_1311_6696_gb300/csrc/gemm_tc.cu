@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -362,12 +363,14 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 // Persistent form (no split-K): one CTA per SM walks the output tiles t =
-// blockIdx.x, blockIdx.x + gridDim.x, ...  Warp 4 (one thread) streams the
-// operand tiles through the smem ring with TMA, warp 5 (one thread) issues the
-// MMAs into one of two TMEM accumulators, and warps 0-3 drain the other one
-// (tcgen05.ld, then the same stores as k_gemm_tc), so a tile's epilogue runs
-// while the next tile is loaded and multiplied.  Every wait is bounded.
-constexpr int TCP_THREADS = 192;
+// blockIdx.x, blockIdx.x + gridDim.x, ...  Warp 8 (one thread) streams the
+// operand tiles through the smem ring with TMA, warp 9 (one thread) issues the
+// MMAs into one of two TMEM accumulators, and warps 0-7 drain the other one
+// (tcgen05.ld, then the same stores as k_gemm_tc) -- warp w reads TMEM lanes
+// 32*(w%4).. and the columns of half w/4 -- so a tile's epilogue runs while
+// the next tile is loaded and multiplied.  Every wait is bounded.
+constexpr int TCP_THREADS = 320;
+constexpr int TCP_EPI = 8;   // epilogue warps
 
 template <int BN>
 __global__ void __launch_bounds__(TCP_THREADS) k_gemm_tc_persist(const __grid_constant__ CUtensorMap ta,
@@ -384,7 +387,7 @@ __global__ void __launch_bounds__(TCP_THREADS) k_gemm_tc_persist(const __grid_co
   __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], tfull[2], tempty[2], drain;
   __shared__ uint32_t tmem_base;
   __shared__ long long offm[TC_BM], offn[BN];
-  __shared__ float stage_out[4][32][17];
+  __shared__ float stage_out[TCP_EPI][32][17];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long tiles_n = (g.N + BN - 1) / BN;
@@ -397,7 +400,7 @@ __global__ void __launch_bounds__(TCP_THREADS) k_gemm_tc_persist(const __grid_co
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 4);
+      mbar_init(&tempty[b], TCP_EPI);
     }
     mbar_init(&drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -412,7 +415,7 @@ __global__ void __launch_bounds__(TCP_THREADS) k_gemm_tc_persist(const __grid_co
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
 
-  if (warp == 4 && lane == 0) {
+  if (warp == TCP_EPI && lane == 0) {
     // TMA producer, running ahead across tiles
     bool ok = true;
     int it = 0;
@@ -440,7 +443,7 @@ __global__ void __launch_bounds__(TCP_THREADS) k_gemm_tc_persist(const __grid_co
     // wait (bounded) for the last round issued into every slot
     for (int j = it - 1; j >= 0 && j >= it - g.stages; --j)
       mbar_wait(&full[j % g.stages], uint32_t(j / g.stages) & 1u, g.flag);
-  } else if (warp == 5 && lane == 0) {
+  } else if (warp == TCP_EPI + 1 && lane == 0) {
     // MMA issuer: tile i accumulates in TMEM buffer i % 2
     const uint32_t afmt = g.bf16 ? 1u : 2u;
     const uint32_t idesc = (1u << 4) | (afmt << 7) | (afmt << 10) | (uint32_t(BN >> 3) << 17) |
@@ -488,12 +491,14 @@ __global__ void __launch_bounds__(TCP_THREADS) k_gemm_tc_persist(const __grid_co
     // every MMA issued here has finished before TMEM is released (bounded wait)
     mma_commit(&drain);
     mbar_wait(&drain, 0u, g.flag);
-  } else if (warp < 4) {
+  } else if (warp < TCP_EPI) {
     // epilogue: drain the accumulator of tile i while tile i+1 is computed.
-    // The four warps run the same number of iterations and reach both named
+    // The eight warps run the same number of iterations and reach both named
     // barriers in every one of them; a warp whose wait ran out (the status word
     // is set) only stops doing work, so no warp is left waiting at a barrier.
     const float alpha = float(g.alpha);
+    const int quarter = warp & 3, half = warp >> 2;
+    const int cbeg = BN >= 32 ? half * (BN / 2) : (half ? BN : 0), cend = BN >= 32 ? cbeg + BN / 2 : (half ? BN : BN);
     bool dead = false;
     int i = 0;
     for (long long t = blockIdx.x; t < total; t += gridDim.x, ++i) {
@@ -502,20 +507,20 @@ __global__ void __launch_bounds__(TCP_THREADS) k_gemm_tc_persist(const __grid_co
       const int pb = int(t / tiles);
       const long long tt = t % tiles;
       const long long m0 = (tt / tiles_n) * TC_BM, n0 = (tt % tiles_n) * BN;
-      asm volatile("bar.sync 1, 128;" ::: "memory");   // the previous tile's offsets are no longer read
-      {
+      asm volatile("bar.sync 1, 256;" ::: "memory");   // the previous tile's offsets are no longer read
+      if (tid < TC_BM) {
         const long long m = m0 + tid;
         long long o = -1;
         if (m < g.M) decomp(g.gm, m, o);
         offm[tid] = o;
       }
-      for (int c = tid; c < BN; c += 128) {
+      for (int c = tid - TC_BM; c >= 0 && c < BN; c += 128) {
         const long long n = n0 + c;
         long long o = -1;
         if (n < g.N) decomp(g.gn, n, o);
         offn[c] = o;
       }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      asm volatile("bar.sync 1, 256;" ::: "memory");
       if (dead) continue;
       const bool waited = mbar_wait(&tfull[buf], use & 1u, g.flag);
       if (!__all_sync(0xffffffffu, waited)) {
@@ -523,10 +528,10 @@ __global__ void __launch_bounds__(TCP_THREADS) k_gemm_tc_persist(const __grid_co
         continue;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int row = warp * 32 + lane;
+      const int row = quarter * 32 + lane;
       const long long om = offm[row];
-      const uint32_t acc_t = tmem + uint32_t(buf * NCOL) + (uint32_t(warp * 32) << 16);
-      for (int c0 = 0; c0 < BN; c0 += 16) {
+      const uint32_t acc_t = tmem + uint32_t(buf * NCOL) + (uint32_t(quarter * 32) << 16);
+      for (int c0 = cbeg; c0 < cend; c0 += 16) {
         uint32_t r[16];
         tmem_ld16(acc_t + uint32_t(c0), r);
         if (!g.cols_fast) {
@@ -544,7 +549,7 @@ __global__ void __launch_bounds__(TCP_THREADS) k_gemm_tc_persist(const __grid_co
           const long long on = offn[c0 + j];
 #pragma unroll 4
           for (int q = lane >> 4; q < 32; q += 2) {
-            const long long omi = offm[warp * 32 + q];
+            const long long omi = offm[quarter * 32 + q];
             if (omi >= 0 && on >= 0) put_out(g, pb, omi + on, stage_out[warp][q][j] * alpha);
           }
           __syncwarp();
@@ -829,14 +834,16 @@ void launch_tc(Ctx& cx, const CUtensorMap& ta, const CUtensorMap& tb, const CUte
   const size_t smem = size_t(stage) * g.stages + 1024;
   static std::once_flag once;
   static int nsm = 0;
+  static bool persist = true;   // PEPS_TC_PERSIST=0 keeps every GEMM on the one-tile kernel
   std::call_once(once, [] {
     PEPS_CUDA(cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     PEPS_CUDA(cudaFuncSetAttribute(k_gemm_tc_persist<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     int dev = 0;
     PEPS_CUDA(cudaGetDevice(&dev));
     PEPS_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (const char* e = std::getenv("PEPS_TC_PERSIST")) persist = std::atoi(e) != 0;
   });
-  if (g.splitk > 1 || tiles <= nsm) {
+  if (!persist || g.splitk > 1 || tiles <= nsm) {
     // split-K partials, or no more tiles than SMs: one tile per CTA
     k_gemm_tc<BN><<<dim3(unsigned(tiles), unsigned(std::max(1, g.splitk))), TC_THREADS, smem, cx.st>>>(ta, tb, tal,
                                                                                                         tbl, g);
