@@ -8,4 +8,6 @@ routes through it.
 * :mod:`oracle.peps_oracle` -- the method of the paper, step by step.
 * :mod:`oracle.bruteforce` -- state vectors of small PEPS (the plain
   definition), used to pin the oracle.
+* :mod:`oracle.update_oracle` -- the tensor update of the full / cluster
+  update (reduced-tensor ALS, Section 2) and its imaginary-time driver.
 """
