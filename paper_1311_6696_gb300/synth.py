@@ -326,3 +326,25 @@ def peps_simple_update(Ly: int, Lx: int, D: int, seed: int, tau: float = 0.01, s
                 * np.sqrt(lam_dn(y, x))[None, None, None, :, None] * np.sqrt(lam_rt(y, x))[None, None, None, None, :]
             A[y, x] = t / np.linalg.norm(t)
     return A
+
+
+def gram4(A: np.ndarray) -> float:
+    """Fingerprint of a dense lattice that survives a change of bond gauge: a
+    weighted sum over sites and legs k of Tr(G_k^2), G_k = M_k M_k^T with M_k
+    the site tensor matricised as (leg k) x (the other legs).  Inserting an
+    orthogonal matrix and its transpose on a bond leaves it unchanged.  The
+    simple-update generator fixes a bond's gauge only up to such a rotation
+    inside a block of equal singular values (the Heisenberg model's spin
+    symmetry makes them), and which rotation LAPACK returns there differs
+    between platforms: the bytes are not portable, this sum is."""
+    Ly, Lx = A.shape[:2]
+    w = uniform01(98, Ly * Lx * 5).reshape(Ly, Lx, 5)
+    tot = 0.0
+    for y in range(Ly):
+        for x in range(Lx):
+            T = A[y, x]
+            for k in range(5):
+                M = np.moveaxis(T, k, 0).reshape(T.shape[k], -1)
+                G = M @ M.T
+                tot += float(w[y, x, k] * np.sum(G * G))
+    return tot

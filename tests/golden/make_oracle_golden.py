@@ -10,7 +10,7 @@ quantities -- <sigma_z> on its 20 sites and <S.S> on its 19 bonds -- which in
 the full method use the top boundary above the last row and the bottom
 closure, exactly as here.
 
-Usage:  python tests/golden/make_oracle_golden.py c4 [--chi 128]
+Usage:  python tests/golden/make_oracle_golden.py c4 [--chi 128] [--refresh-input]
 """
 from __future__ import annotations
 
@@ -33,11 +33,12 @@ from paper_1311_6696_gb300 import synth  # noqa: E402
 
 
 def fingerprint(A: np.ndarray) -> dict:
-    """sha256 of the bytes (identical generator and platform) and a few
-    weighted sums (same input up to rounding on another platform)."""
+    """sha256 of the bytes and a weighted sum (identical generator and
+    platform), and the gauge-invariant gram4 (same state on any platform)."""
     w = synth.uniform01(99, A.size).reshape(A.shape) - 0.5
     return {"sha256": hashlib.sha256(np.ascontiguousarray(A).tobytes()).hexdigest(),
-            "wsum": float(np.sum(A * w)), "sum": float(np.sum(A)), "sumsq": float(np.sum(A * A))}
+            "wsum": float(np.sum(A * w)), "sum": float(np.sum(A)), "sumsq": float(np.sum(A * A)),
+            "gram4": synth.gram4(A)}
 
 
 def last_row_and_norm(A: np.ndarray, chi: int, mode: str = "var", sweeps: int = 2, seed: int = 0,
@@ -71,14 +72,27 @@ def main():
     ap.add_argument("workload", choices=sorted(WORKLOADS))
     ap.add_argument("--chi", type=int, default=128)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--refresh-input", action="store_true",
+                    help="rewrite only the input fingerprint of an existing file, after checking that the "
+                         "generator still gives the same bytes it was computed from")
     a = ap.parse_args()
     w = WORKLOADS[a.workload]
     A = synth.workload(w["name"])
+    out = a.out or os.path.join(HERE, f"oracle_{w['name']}_chi{a.chi}.json")
+    if a.refresh_input:
+        res = json.load(open(out))
+        fp = fingerprint(A)
+        if fp["sha256"] != res["input"]["sha256"]:
+            sys.exit("the generator's output changed: recompute the oracle result instead")
+        res["input"] = fp
+        with open(out, "w") as f:
+            json.dump(res, f, indent=1)
+        print("refreshed", out)
+        return
     res = {"workload": w["desc"], "chi": a.chi, "mode": "var", "sweeps": 2, "seed": 0,
            "input": fingerprint(A), "what": "oracle (FP64 CPU): ln|<psi|psi>| by the top-down sweep and the "
                                             "last row's <sigma_z> (sites) and <S.S> (horizontal bonds)"}
     res.update(last_row_and_norm(A, a.chi, log=lambda m: print(m, flush=True)))
-    out = a.out or os.path.join(HERE, f"oracle_{w['name']}_chi{a.chi}.json")
     with open(out, "w") as f:
         json.dump(res, f, indent=1)
     print("wrote", out)

@@ -277,8 +277,10 @@ def test_20x20_D8_su_chi128_against_stored_oracle(peps):
     from paper_1311_6696_gb300 import synth
     gold = json.load(open(path))
     A = synth.workload("20x20_D8_su")
-    w = synth.uniform01(99, A.size).reshape(A.shape) - 0.5
-    assert abs(float(np.sum(A * w)) - gold["input"]["wsum"]) < 1e-9 * max(1.0, abs(gold["input"]["wsum"]))
+    # the same state: a gauge-invariant sum (the generator's bytes differ
+    # between platforms by rotations inside degenerate singular blocks)
+    g4 = synth.gram4(A)
+    assert abs(g4 - gold["input"]["gram4"]) < 1e-9 * abs(gold["input"]["gram4"]), (g4, gold["input"]["gram4"])
     g = peps.env_full(torch.from_numpy(A).cuda(), chi=128, mode="var", precision="bf16x3")
     y = gold["row"]
     sz = g.expect("site", O.SZ).reshape(20, 20)[y]
