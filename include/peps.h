@@ -309,6 +309,43 @@ int peps_set_iteration_caps(int cu0_half_sweeps, int jacobi_sweeps);
 int peps_wait_selftest(int budget_us, void* cuda_stream);
 
 /*
+ * peps_bond_update -- the tensor update of the full update (FU) for a set of
+ *   bonds.  Section 2: after a Trotter gate acts on a bond, the two tensors
+ *   of the bond are refit by alternating least squares, one tensor at a
+ *   time, each solving N_l A_l = b_l; the unknowns are the reduced tensors
+ *   (Section 2, footnote: O(D^6) linear systems).  Each site is split by a
+ *   thin QR, left site as (u l n) x (s r), right site as (u n r) x (t l); N
+ *   is the norm network with the two reduced tensors removed, contracted
+ *   from the full (sandwich) environment at bond opts->chi.  Every bond of
+ *   the call uses the environment of the input state -- the bonds of one
+ *   Trotter set updated independently, the parallel scheme of Sections 4.4
+ *   and 5.2.
+ *   Rules where the paper is silent: N is symmetrised and replaced by its
+ *   positive part; the ALS starts from the truncated SVD of the gated pair;
+ *   each system is shifted by 1e-12 * trace / size and solved by Cholesky;
+ *   the result is split by an SVD into U sqrt(S) | sqrt(S) V^T (largest entry
+ *   of every U column positive), the new bond keeps min(D, k_l d, k_r d)
+ *   values (zero beyond), and both new tensors are scaled to unit norm.
+ *   lat:       device lattice (on_device = 1), F64 or F32, read only.
+ *   opts:      chi, mode, sweeps, precision, seed of the environment
+ *              (n, closure ignored).
+ *   gate:      host, (d*d) x (d*d) row-major, G[(s t), (s' t')] with s the
+ *              first site (left / upper) of every bond.
+ *   bonds:     host, 3 * nbonds ints (kind, y, x): kind 0 the bond
+ *              (y,x)-(y,x+1), kind 1 the bond (y,x)-(y+1,x); no site in two
+ *              bonds (PEPS_EINVAL otherwise).
+ *   als_iters: ALS rounds (each a left and a right solve), 1..1000.
+ *   A_out:     device, the lattice's dtype and layout; may be lat->A (the
+ *              update in place); sites outside the bonds are copied.
+ *   cost:      host, nbonds doubles or NULL: |psi - G phi|^2_N / |G phi|^2_N
+ *              of every bond after the fit.
+ *   Needs d*D*D <= 160 (Cholesky systems in shared memory).  Synchronises
+ *   the stream.
+ */
+int peps_bond_update(const peps_lattice* lat, const peps_opts* opts, const double* gate, const int* bonds,
+                     int nbonds, int als_iters, void* A_out, double* cost, void* cuda_stream);
+
+/*
  * peps_boundary_fidelity -- distance of a cluster environment from the full one.
  *   Section 5.2, Fig. Fid: the boundary MPS on the right legs of column 0
  *   (the environment of the left-most column) in the cluster form -- columns

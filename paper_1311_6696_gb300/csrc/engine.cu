@@ -11,6 +11,7 @@
 #include "aux.cuh"
 #include "engine.cuh"
 #include "linalg.cuh"
+#include "update.cuh"
 
 namespace peps {
 
@@ -468,24 +469,16 @@ std::vector<Mps> Engine::sweep(const OLat& lat, int tag, int upto, const TP& lna
   return out;
 }
 
-void Engine::row_rhos(const OLat& lat, const Mps& T, const Mps& B, int y, const Targets& sites,
-                      const Targets& bonds) {
+void Engine::row_envs(const OLat& lat, const Mps& T, const Mps& B, int y, int xmin, int xmax,
+                      std::vector<Dims>& ld, std::vector<Dims>& rd) {
   const int Lx = lat.Lx;
-  std::vector<Dims> ld(Lx), rd(Lx);
+  ld.assign(Lx, Dims());
+  rd.assign(Lx, Dims());
   const Mat& lc = lat.left[y];
   const Mat& rc = lat.right[y];
   ld[0] = {1, lc.n, lc.n, 1};
   copy(cx, Lenv_[0], lc.p, (long long)lc.n * lc.n);
   rd[Lx - 1] = {1, rc.n, rc.n, 1};
-  int xmax = 0, xmin = lat.Lx;
-  for (const auto& t : sites) {
-    xmax = std::max(xmax, t.first + 1);
-    xmin = std::min(xmin, t.first);
-  }
-  for (const auto& t : bonds) {
-    xmax = std::max(xmax, t.first + 2);
-    xmin = std::min(xmin, t.first);
-  }
   for (int x = 0; x + 1 < Lx && x + 1 < xmax; ++x) {
     const Dims x3 = chain_left(Lenv_[x], ld[x], T.p[x], T.dims[x], lat.at(y, x), X3_);
     ld[x + 1] = ein_dims("cbnroq,cnoe->erqb", x3, B.dims[x]);
@@ -517,40 +510,55 @@ void Engine::row_rhos(const OLat& lat, const Mps& T, const Mps& B, int y, const 
     PEPS_CUDA(cudaStreamWaitEvent(cx.st, e, 0));
     PEPS_CUDA(cudaEventDestroy(e));
   }
-  auto open_site = [&](int x) -> Dims {
-    const SiteT& A = lat.at(y, x);
-    const Dims ad = A.dims();
-    Dims x3 = tc_ ? chain_left_tc(Lenv_[x], ld[x], T.p[x], T.dims[x], A, X3_, true) : Dims();
-    if (x3.empty()) {
-      const Dims x1 = ein_dims("clma,auvb->clmuvb", ld[x], T.dims[x]);
-      con("clma,auvb->clmuvb", Lenv_[x], true, ld[x], T.p[x], true, T.dims[x], X1_, x64_);
-      const Dims x2 = ein_dims("clmuvb,sulnr->cmvbsnr", x1, ad);
-      con("clmuvb,sulnr->cmvbsnr", X1_, x64_, x1, A.p, true, ad, X2_, x64_, true);
-      x3 = ein_dims("cmvbsnr,tvmoq->cbsnrtoq", x2, ad);
-      con("cmvbsnr,tvmoq->cbsnrtoq", X2_, x64_, x2, A.p, true, ad, X3_, x64_, true);
-    }
-    const Dims w = ein_dims("cbsnrtoq,cnoe->erqbst", x3, B.dims[x]);
-    con("cbsnrtoq,cnoe->erqbst", X3_, x64_, x3, B.p[x], true, B.dims[x], bb_, true);
-    return w;
-  };
-  // Site x with its physical pair open, pushed in from the right:
-  // V[a,l,m,k,s,t] = sum M R A(s) A(t) B over the bonds and legs right of the site.
-  auto open_site_right = [&](int x) -> Dims {
-    const SiteT& A = lat.at(y, x);
-    const Dims ad = A.dims();
-    Dims y3 = tc_ ? chain_right_tc(Renv_[x], rd[x], T.p[x], T.dims[x], A, X3_, true) : Dims();
-    if (y3.empty()) {
-      const Dims y1 = ein_dims("auvb,brqc->auvrqc", T.dims[x], rd[x]);
-      con("auvb,brqc->auvrqc", T.p[x], true, T.dims[x], Renv_[x], true, rd[x], X1_, x64_);
-      const Dims y2 = ein_dims("auvrqc,sulnr->avqcsln", y1, ad);
-      con("auvrqc,sulnr->avqcsln", X1_, x64_, y1, A.p, true, ad, X2_, x64_, true);
-      y3 = ein_dims("avqcsln,tvmoq->acslntmo", y2, ad);
-      con("avqcsln,tvmoq->acslntmo", X2_, x64_, y2, A.p, true, ad, X3_, x64_, true);
-    }
-    const Dims v = ein_dims("acslntmo,knoc->almkst", y3, B.dims[x]);
-    con("acslntmo,knoc->almkst", X3_, x64_, y3, B.p[x], true, B.dims[x], vv_, true);
-    return v;
-  };
+}
+
+Dims Engine::open_left(const Mps& T, const Mps& B, int x, const SiteT& A, const Dims& ldx) {
+  const Dims ad = A.dims();
+  Dims x3 = tc_ ? chain_left_tc(Lenv_[x], ldx, T.p[x], T.dims[x], A, X3_, true) : Dims();
+  if (x3.empty()) {
+    const Dims x1 = ein_dims("clma,auvb->clmuvb", ldx, T.dims[x]);
+    con("clma,auvb->clmuvb", Lenv_[x], true, ldx, T.p[x], true, T.dims[x], X1_, x64_);
+    const Dims x2 = ein_dims("clmuvb,sulnr->cmvbsnr", x1, ad);
+    con("clmuvb,sulnr->cmvbsnr", X1_, x64_, x1, A.p, true, ad, X2_, x64_, true);
+    x3 = ein_dims("cmvbsnr,tvmoq->cbsnrtoq", x2, ad);
+    con("cmvbsnr,tvmoq->cbsnrtoq", X2_, x64_, x2, A.p, true, ad, X3_, x64_, true);
+  }
+  const Dims w = ein_dims("cbsnrtoq,cnoe->erqbst", x3, B.dims[x]);
+  con("cbsnrtoq,cnoe->erqbst", X3_, x64_, x3, B.p[x], true, B.dims[x], bb_, true);
+  return w;
+}
+
+// V[a,l,m,k,s,t] = sum M R A(s) A(t) B over the bonds and legs right of the site.
+Dims Engine::open_right(const Mps& T, const Mps& B, int x, const SiteT& A, const Dims& rdx) {
+  const Dims ad = A.dims();
+  Dims y3 = tc_ ? chain_right_tc(Renv_[x], rdx, T.p[x], T.dims[x], A, X3_, true) : Dims();
+  if (y3.empty()) {
+    const Dims y1 = ein_dims("auvb,brqc->auvrqc", T.dims[x], rdx);
+    con("auvb,brqc->auvrqc", T.p[x], true, T.dims[x], Renv_[x], true, rdx, X1_, x64_);
+    const Dims y2 = ein_dims("auvrqc,sulnr->avqcsln", y1, ad);
+    con("auvrqc,sulnr->avqcsln", X1_, x64_, y1, A.p, true, ad, X2_, x64_, true);
+    y3 = ein_dims("avqcsln,tvmoq->acslntmo", y2, ad);
+    con("avqcsln,tvmoq->acslntmo", X2_, x64_, y2, A.p, true, ad, X3_, x64_, true);
+  }
+  const Dims v = ein_dims("acslntmo,knoc->almkst", y3, B.dims[x]);
+  con("acslntmo,knoc->almkst", X3_, x64_, y3, B.p[x], true, B.dims[x], vv_, true);
+  return v;
+}
+
+void Engine::row_rhos(const OLat& lat, const Mps& T, const Mps& B, int y, const Targets& sites,
+                      const Targets& bonds) {
+  const int Lx = lat.Lx;
+  int xmax = 0, xmin = lat.Lx;
+  for (const auto& t : sites) {
+    xmax = std::max(xmax, t.first + 1);
+    xmin = std::min(xmin, t.first);
+  }
+  for (const auto& t : bonds) {
+    xmax = std::max(xmax, t.first + 2);
+    xmin = std::min(xmin, t.first);
+  }
+  std::vector<Dims> ld, rd;
+  row_envs(lat, T, B, y, xmin, xmax, ld, rd);
   // Every target column once, left to right: W(x) (open from the left) gives
   // rho_site(x) with the right environment; the bond (x, x+1) is W(x) joined
   // with V(x+1) (open from the right) over the bonds and legs between them --
@@ -566,14 +574,57 @@ void Engine::row_rhos(const OLat& lat, const Mps& T, const Mps& B, int y, const 
   for (const auto& kv : site_dst) cols.insert(kv.first);
   for (const auto& kv : bond_dst) cols.insert(kv.first);
   for (const int x : cols) {
-    const Dims w = open_site(x);
+    const Dims w = open_left(T, B, x, lat.at(y, x), ld[x]);
     auto si = site_dst.find(x);
     if (si != site_dst.end()) ein(cx, "erqbst,brqe->st", bb_, w, Renv_[x], rd[x], si->second);
     auto bi = bond_dst.find(x);
     if (bi != bond_dst.end()) {
-      const Dims v = open_site_right(x + 1);
+      const Dims v = open_right(T, B, x + 1, lat.at(y, x + 1), rd[x + 1]);
       ein(cx, "erqbij,brqest->isjt", bb_, w, vv_, v, bi->second);
     }
+  }
+}
+
+void Engine::row_bond_norms(const OLat& lat, const Mps& T, const Mps& B, int y, const std::vector<BondNorm>& bonds) {
+  PEPS_REQUIRE(nb_ == 1, "internal: bond norms are computed for one lattice");
+  const int Lx = lat.Lx;
+  int xmax = 0, xmin = Lx;
+  for (const auto& b : bonds) {
+    PEPS_REQUIRE(b.x >= 0 && b.x + 1 < Lx, "internal: bond outside the row");
+    xmax = std::max(xmax, b.x + 2);
+    xmin = std::min(xmin, b.x);
+  }
+  std::vector<Dims> ld, rd;
+  row_envs(lat, T, B, y, xmin, xmax, ld, rd);
+  for (const auto& b : bonds) {
+    const SiteT& L = lat.at(y, b.x);
+    const SiteT& R = lat.at(y, b.x + 1);
+    const int d = L.d;
+    // the two sites as matrices, then their thin QR (Householder, FP64)
+    const int dl5[5] = {d, L.du, L.dl, L.dn, L.dr}, pl[5] = {1, 2, 3, 0, 4};
+    const int dr5[5] = {d, R.du, R.dl, R.dn, R.dr}, pr[5] = {1, 3, 4, 0, 2};
+    permute5(cx, L.p.d(0), dl5, pl, b.ml);
+    permute5(cx, R.p.d(0), dr5, pr, b.mr);
+    const int ml = L.du * L.dl * L.dn, nl = d * L.dr, mr = R.du * R.dn * R.dr, nr = d * R.dl;
+    const int kl = std::min(ml, nl), kr = std::min(mr, nr);
+    qr_thin(cx, ml, nl, TP(b.ml), nl, 1, TP(b.xl), 1, ml, TP(b.al));
+    qr_thin(cx, mr, nr, TP(b.mr), nr, 1, TP(b.xr), 1, mr, TP(b.ar));
+    SiteT XL, XR;
+    XL.p = TP(b.xl);
+    XL.d = kl;
+    XL.du = L.du;
+    XL.dl = L.dl;
+    XL.dn = L.dn;
+    XL.dr = 1;
+    XR.p = TP(b.xr);
+    XR.d = kr;
+    XR.du = R.du;
+    XR.dl = 1;
+    XR.dn = R.dn;
+    XR.dr = R.dr;
+    const Dims w = open_left(T, B, b.x, XL, ld[b.x]);
+    const Dims v = open_right(T, B, b.x + 1, XR, rd[b.x + 1]);
+    ein(cx, "erqbij,brqest->isjt", bb_, w, vv_, v, TP(b.N));
   }
 }
 

@@ -78,6 +78,24 @@ class Engine {
   void row_rhos(const OLat& lat, const Mps& T, const Mps& B, int y, const Targets& sites,
                 const Targets& bonds);
 
+  // The tensor update of the full update (Section 2, reduced tensors): for the
+  // pair (x, x+1) of row y, each site is split by a QR into an isometry and a
+  // reduced tensor, A(x) = X_l a_l over the legs (u l n) | (s r) and
+  // A(x+1) = X_r a_r over (u n r) | (t l), and the norm network with a_l, a_r
+  // and their conjugates removed is contracted into N[kl][kr][kl][kr]: the
+  // bond density-matrix network with the isometries in place of the sites.
+  struct BondNorm {
+    int x = 0;                          // left column of the pair
+    double* ml = nullptr;               // scratch: the left site as (u l n) x (s r)
+    double* mr = nullptr;               // scratch: the right site as (u n r) x (t l)
+    double* xl = nullptr;               // [kl][u l n]
+    double* xr = nullptr;               // [kr][u n r]
+    double* al = nullptr;               // [kl][s][r]
+    double* ar = nullptr;               // [kr][t][l]
+    double* N = nullptr;                // [kl][kr][kl][kr]
+  };
+  void row_bond_norms(const OLat& lat, const Mps& T, const Mps& B, int y, const std::vector<BondNorm>& bonds);
+
   // ln|<psi|psi>| from the top boundary above the last row (writes out[0], out[1] = sign).
   void norm_from_top(const OLat& lat, const Mps& T, const TP& lns_acc, const TP& out);
 
@@ -92,6 +110,13 @@ class Engine {
 
  private:
   Mps closure_mps(const std::vector<Mat>& mats, Arena& keep);
+  // Row environments of row y: Lenv_[x] for x < xmax, Renv_[x] for x >= xmin.
+  void row_envs(const OLat& lat, const Mps& T, const Mps& B, int y, int xmin, int xmax, std::vector<Dims>& ld,
+                std::vector<Dims>& rd);
+  // Site tensor A at column x with its physical pair open: W[e,r,q,b,s,t]
+  // (pushed in from the left, into bb_) and V[a,l,m,k,s,t] (from the right, into vv_).
+  Dims open_left(const Mps& T, const Mps& B, int x, const SiteT& A, const Dims& ldx);
+  Dims open_right(const Mps& T, const Mps& B, int x, const SiteT& A, const Dims& rdx);
   Mps absorb_compress(const Mps& T, const OLat& lat, int y, int tag, const TP& lnacc, Arena& keep);
   Mps product_mps(const Mps& T, const OLat& lat, int y, Arena& keep);
   void left_canonicalize(Mps& P, Arena& keep);
