@@ -1121,7 +1121,12 @@ void ein_tc(Ctx& cx, const char* spec, const TP& A, int a_f64, const Dims& ad, c
   g.alpha = alpha;
   g.flag = cx.flag;
   const double flops = 2.0 * double(M) * double(N) * double(K) * np;
-  Launch L(K_GEMM_TC, cx.st, flops, 0);
+  // algorithmic bytes: both packed operands read once, the output written once
+  // (as the next contraction's packed operand, FP64, or FP32 with its residual)
+  const double in_b = (bf16 ? 2.0 : 4.0) * (split ? 2.0 : 1.0);
+  const double out_b = to_next ? in_b : (g.out_f64 ? 8.0 : (g.out_lo ? 8.0 : 4.0));
+  const double bytes = double(np) * (double(M) * K * in_b + double(N) * K * in_b + double(M) * N * out_b);
+  Launch L(K_GEMM_TC, cx.st, flops, bytes);
   switch (BN) {
     case 16: launch_tc<16>(cx, ta, tb, tal, tbl, g, tiles); break;
     case 32: launch_tc<32>(cx, ta, tb, tal, tbl, g, tiles); break;
