@@ -51,10 +51,12 @@ WORKLOADS = {
     "c4": dict(name="20x20_D8_su", Ly=20, Lx=20, d=2, D=8, chi=128, precision="bf16x3",
                desc="20x20 OBC PEPS d=2 D=8 from the seeded simple-update Heisenberg generator "
                     "(tau=0.01, 400 steps, seed 4), unit-norm tensors",
-               golden="oracle_20x20_D8_su_chi128.json", fp64_rows=4),
+               golden="oracle_20x20_D8_su_chi128.json", fp64_rows=4,
+               # largest share of device time in the serialised launch list of a replay
+               dominant="qr_f64"),
     "c2": dict(name="10x10_D4", Ly=10, Lx=10, d=2, D=4, chi=64, precision="tf32x3",
                desc="10x10 OBC PEPS d=2 D=4, entries 0.5+0.1N(0,1), unit-norm tensors",
-               golden=None, fp64_rows=None),
+               golden=None, fp64_rows=None, dominant=None),
 }
 L2_BYTES = 129 * 2 ** 20
 
@@ -197,7 +199,7 @@ def run_ours(args, rank, world, dist):
     # (event nodes run back to back with the kernels): the class with the most
     # device time is the one whose roofline is reported.
     prof1 = None
-    dom = args.dominant
+    dom = args.dominant or (None if args.probe else W.get("dominant"))
     if dom is None:
         peps.profile_enable(-1)
         probe = peps.Plan(At, **kw)
@@ -602,6 +604,29 @@ def _measure_peaks():
         pass
 
 
+def rows_case(args):
+    """The norm sweep (Section 2) of the workload's top rows: the same absorb
+    chains, fits and QR shapes as a full set, few enough launches for a
+    profiler capture."""
+    import numpy as np
+    import torch
+
+    from paper_1311_6696_gb300 import peps
+    W = WORKLOADS[args.workload]
+    chi = args.chi or W["chi"]
+    prec = args.precision or W["precision"]
+    R = args.rows
+    A = load_input(W["name"])
+    part = np.array(A[:R])
+    part[R - 1, :, :, :, :, 1:, :] = 0.0        # the part's last row: down legs closed (OBC)
+    sub = torch.from_numpy(part).cuda()
+    st = torch.cuda.current_stream()
+    peps.norm(sub, chi=chi, mode=args.mode, precision=prec, stream=st)     # warm
+    t = _timed(lambda: peps.norm(sub, chi=chi, mode=args.mode, precision=prec, stream=st), st, 1)
+    return {"case": f"norm sweep of the top {R} rows of {W['name']} ({R - 1} absorbs at chi={chi}, {prec})",
+            "ms": round(min(t), 2)}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -614,6 +639,11 @@ def main():
     ap.add_argument("--precision", default=None, choices=["fp64", "tf32", "bf16", "tf32x3", "bf16x3"])
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--dominant", default=None, help="kernel class timed for the roofline (skips the probe replay)")
+    ap.add_argument("--probe", action="store_true",
+                    help="choose the roofline's class by one replay timing every class (concurrent lanes)")
+    ap.add_argument("--rows", type=int, default=0,
+                    help="small case for profilers: only the norm sweep of the workload's top ROWS rows "
+                         "(last of them closed), at the headline precision, then exit")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cluster", action="store_true", help="add the 14x14 D=6 cluster section")
     ap.add_argument("--fidelity", action="store_true", help="add the boundary-fidelity section (Fig. Fid)")
@@ -635,6 +665,10 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         tdist.init_process_group("nccl")
         dist = tdist
+    if args.rows > 0:
+        if rank == 0:
+            print(json.dumps(rows_case(args)), flush=True)
+        return
     _measure_peaks()
     res = run_ours(args, rank, world, dist)
     if res is not None:
