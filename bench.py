@@ -217,7 +217,9 @@ def run_ours(args, rank, world, dist):
     # The dominant class is timed inside every replay (event nodes around its
     # launches).
     t0 = time.perf_counter()
-    peps.profile_enable(1 << peps.class_index(dom))
+    # the roofline's class and the absorb contractions' class, timed by event
+    # nodes around their launches inside every replay
+    peps.profile_enable((1 << peps.class_index(dom)) | (1 << peps.class_index(absorb)))
     plan = peps.Plan(At, **kw, tune=args.tune)
     peps.profile_enable(0)
     t_plan = time.perf_counter() - t0
@@ -381,7 +383,7 @@ def run_ours(args, rank, world, dist):
                 "steps": len(etimes)},
         "gpu_launches": int(launches),
         "roofline": roof(dom),
-        "roofline_absorb": roof(absorb, prof1) if (prof1 and absorb != dom and prof1[absorb]["launches"]) else None,
+        "roofline_absorb": roof(absorb) if (absorb != dom and prof[absorb]["launches"]) else None,
         "replay_kernel_ms": {k: round(v["ms"], 3) for k, v in prof1.items() if v["launches"]} if prof1 else None,
         "wall_s_timed": round(t_wall, 3),
     }
