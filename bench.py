@@ -337,8 +337,10 @@ def run_ours(args, rank, world, dist):
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
         if cls == "gemm_tc":
             if prec.startswith("bf16"):
-                peak, note = pk.get("bf16_tflops_sustained", 1716.1), \
-                    "of measured bf16 dense, sustained (cuBLAS, MEASURED_PEAKS.json)"
+                peak = pk.get("bf16_tflops_sustained", 1716.1)
+                note = ("of measured bf16 dense, sustained (cuBLAS, MEASURED_PEAKS.json)" if pk else
+                        "of measured bf16 dense, sustained (cuBLAS; this pool's earlier MEASURED_PEAKS.json "
+                        "value, the file being absent)")
             else:
                 peak, note = TF32_PEAK_TFLOPS, "of measured tf32 dense (torch matmul 8192^3, best of 5)"
             bound = "tensor"
@@ -359,7 +361,9 @@ def run_ours(args, rank, world, dist):
             r["hbm_view"] = {"achieved": round(gbs, 2), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 5),
                              "algorithmic_bytes_per_launch": round(d["bytes"] / max(1, d["launches"]), 1),
                              "flops_per_byte": round(d["flops"] / d["bytes"], 2),
-                             "peak_source": "of measured HBM copy bandwidth (MEASURED_PEAKS.json)"}
+                             "peak_source": "of measured HBM copy bandwidth (MEASURED_PEAKS.json)" if pk else
+                             "of measured HBM copy bandwidth (this pool's earlier MEASURED_PEAKS.json value, "
+                             "the file being absent)"}
         return r
 
     h2d = int(A.nbytes)
