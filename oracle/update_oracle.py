@@ -23,6 +23,9 @@ What it computes (Lubasch, Cirac, Banuls, "Unifying PEPS contractions"):
   site tensors and the reduced leg k in place of the physical leg.
 * Sections 4.4 and 5.2 (parallel CU): the bonds of one Trotter set are
   updated independently, every one from the environment of the same state.
+* Section 5 (cluster update CU_delta): the environment of a row's (column's)
+  bonds is the exact contraction of the rows (columns) within distance delta,
+  closed beyond them by the separable CU_0 boundaries of Section 5.1.
 
 Readings where the paper is silent (the CUDA path follows the same rules,
 written out here and in its own code, never shared):
@@ -49,6 +52,11 @@ written out here and in its own code, never shared):
 * Reported cost: d / <Theta|N|Theta> with the (positive) N.
 * Vertical bonds use the transposed lattice (rows of the transpose are the
   columns), as the density matrices of vertical bonds do.
+* CU_delta: the cluster of a row is rows r - delta .. r + delta clipped at
+  the lattice edge, all columns, closed by the CU_0 matrices of the cuts
+  above and below it (at the lattice edge these are the lattice's own
+  closures) and on the sides by the lattice's closures; var noise keyed by
+  the strip's own rows.
 
 Index conventions as in ``peps_oracle``: A[s, u, l, n, r].
 """
@@ -237,6 +245,27 @@ def update_pair(Lv, Rv, M1, A1, B1, M2, A2, B2, G, D, iters):
     return B1n / np.linalg.norm(B1n), B2n / np.linalg.norm(B2n), c
 
 
+def _check_disjoint(bonds):
+    seen = set()
+    for kind, y, x in bonds:
+        a, b = (y, x), ((y, x + 1) if kind == 0 else (y + 1, x))
+        if a in seen or b in seen:
+            raise ValueError("a site is in two bonds")
+        seen.update([a, b])
+
+
+def _store(out, D, kind, y, x, n1, n2):
+    """New tensors of the pair (computed in the frame of ``kind``) into the
+    dense lattice."""
+    if kind == 1:
+        n1, n2 = n1.transpose(0, 2, 1, 4, 3), n2.transpose(0, 2, 1, 4, 3)
+        p1, p2 = (y, x), (y + 1, x)
+    else:
+        p1, p2 = (y, x), (y, x + 1)
+    out[p1] = _pad_site(n1, D)
+    out[p2] = _pad_site(n2, D)
+
+
 def update_bonds(Ad, G, bonds, chi, mode="var", sweeps=2, seed=0, iters=8):
     """Apply the two-site gate G (d^2 x d^2) to every bond of ``bonds`` and
     refit, all from the full environment of the input state (the parallel
@@ -245,12 +274,7 @@ def update_bonds(Ad, G, bonds, chi, mode="var", sweeps=2, seed=0, iters=8):
     lattice and the relative cost of every bond."""
     Ad = np.asarray(Ad, dtype=np.float64)
     Ly, Lx, d, D = Ad.shape[0], Ad.shape[1], Ad.shape[2], Ad.shape[3]
-    seen = set()
-    for kind, y, x in bonds:
-        a, b = (y, x), ((y, x + 1) if kind == 0 else (y + 1, x))
-        if a in seen or b in seen:
-            raise ValueError("a site is in two bonds")
-        seen.update([a, b])
+    _check_disjoint(bonds)
     lat = O.lattice_from_dense(Ad)
     o = O.orientations(lat)
     out = Ad.copy()
@@ -271,13 +295,66 @@ def update_bonds(Ad, G, bonds, chi, mode="var", sweeps=2, seed=0, iters=8):
             L, R = O.row_envs(T, B, src, r)
             A1, A2 = src.A[r][c], src.A[r][c + 1]
             n1, n2, costs[i] = update_pair(L[c], R[c + 1], T[c], A1, B[c], T[c + 1], A2, B[c + 1], G, D, iters)
-            if kind == 1:
-                n1, n2 = n1.transpose(0, 2, 1, 4, 3), n2.transpose(0, 2, 1, 4, 3)
-                p1, p2 = (y, x), (y + 1, x)
-            else:
-                p1, p2 = (y, x), (y, x + 1)
-            out[p1] = _pad_site(n1, D)
-            out[p2] = _pad_site(n2, D)
+            _store(out, D, kind, y, x, n1, n2)
+    return out, costs
+
+
+# ---------------------------------------------------------------------------
+# Cluster update CU_delta (Section 5: a cluster of size delta around a row is
+# every row within distance delta of it, and likewise for columns; outside it
+# the environment is the separable CU_0 boundary of Section 5.1)
+# ---------------------------------------------------------------------------
+def strip_lattice(lat, cu0, r, delta, frame):
+    """Rows r - delta .. r + delta (clipped) of ``lat`` with every column,
+    closed above and below by the CU_0 matrices of those cuts and on the
+    sides by the lattice's own closures.  frame 0: lat's rows; frame 1: the
+    rows of the transposed lattice (columns of lat), with cu0 the CU_0
+    matrices of lat's four orientations (top, bottom, left, right)."""
+    sT, sB, sL, sR = cu0 if frame == 0 else (cu0[2], cu0[3], cu0[0], cu0[1])
+    src = lat if frame == 0 else O.transpose(lat)
+    H, W = src.Ly, src.Lx
+    r0, r1 = max(0, r - delta), min(H - 1, r + delta)
+    A = [[src.A[i][c] for c in range(W)] for i in range(r0, r1 + 1)]
+    top = [sT[r0][c] for c in range(W)]
+    bottom = [sB[H - 1 - r1][c] for c in range(W)]
+    left = [sL[0][i] for i in range(r0, r1 + 1)]
+    right = [sR[0][i] for i in range(r0, r1 + 1)]
+    return O.Lat(A, top, bottom, left, right), r0
+
+
+def update_bonds_cluster(Ad, G, bonds, delta, chi, mode="var", sweeps=2, seed=0, iters=8,
+                         tol=1e-13, max_half=200):
+    """As update_bonds, but every bond's environment is the cluster of size
+    delta around its row (horizontal bonds) or column (vertical bonds):
+    delta = 0 is CU_0 (a generalised simple update), delta >= L - 1 the full
+    update.  All bonds use the CU_0 boundaries and clusters of the input state
+    (the parallel CU of Section 5.4)."""
+    Ad = np.asarray(Ad, dtype=np.float64)
+    D = Ad.shape[3]
+    _check_disjoint(bonds)
+    if delta < 0:
+        raise ValueError("delta must be >= 0")
+    lat = O.lattice_from_dense(Ad)
+    cu0 = O.cu0_all(lat, tol, max_half)
+    out = Ad.copy()
+    costs = [None] * len(bonds)
+    rows = {}
+    for i, (kind, y, x) in enumerate(bonds):
+        r, c = (y, x) if kind == 0 else (x, y)
+        rows.setdefault((kind, r), []).append((i, y, x, c))
+    for (kind, r), sel in rows.items():
+        S, r0 = strip_lattice(lat, cu0, r, delta, kind)
+        rr = r - r0
+        so = O.orientations(S)
+        tag = 0 if kind == 0 else 2
+        tb, _ = O.boundary_sweep(so[0], chi, mode, sweeps, seed, tag, upto=rr)
+        bb, _ = O.boundary_sweep(so[1], chi, mode, sweeps, seed, tag + 1, upto=S.Ly - 1 - rr)
+        T, B = tb[rr], bb[S.Ly - 1 - rr]
+        L, R = O.row_envs(T, B, S, rr)
+        for i, y, x, c in sel:
+            A1, A2 = S.A[rr][c], S.A[rr][c + 1]
+            n1, n2, costs[i] = update_pair(L[c], R[c + 1], T[c], A1, B[c], T[c + 1], A2, B[c + 1], G, D, iters)
+            _store(out, D, kind, y, x, n1, n2)
     return out, costs
 
 
@@ -311,12 +388,16 @@ def energy(Ad, chi, mode="svd"):
     return float(np.sum(e))
 
 
-def evolve(Ad, tau, steps, chi, mode="var", iters=8, sweeps=2, seed=0):
+def evolve(Ad, tau, steps, chi, mode="var", iters=8, sweeps=2, seed=0, delta=None):
     """``steps`` first-order Trotter steps of exp(-tau H), every set updated
-    in parallel from its own environment."""
+    in parallel from its own environment: the full one (delta None) or the
+    clusters of size delta."""
     G = heisenberg_gate(tau)
     A = np.asarray(Ad, dtype=np.float64)
     for _ in range(steps):
         for s in trotter_sets(A.shape[0], A.shape[1]):
-            A, _ = update_bonds(A, G, s, chi, mode, sweeps, seed, iters)
+            if delta is None:
+                A, _ = update_bonds(A, G, s, chi, mode, sweeps, seed, iters)
+            else:
+                A, _ = update_bonds_cluster(A, G, s, delta, chi, mode, sweeps, seed, iters)
     return A

@@ -11,7 +11,10 @@ from one environment), against things the oracle's own formulas do not fix:
 * stationarity of the ALS result for a general N;
 * the imaginary-time evolution against the paper's FU energy of the 4x4
   Heisenberg model at D=2 (Table EFU) and the variational bound (exact
-  energy, Appendix A).
+  energy, Appendix A);
+* the cluster update CU_delta (Section 5): delta >= L-1 is the full update
+  bit for bit, an exact gate stays exact with a cluster environment, and the
+  CU_1 and CU_0 evolutions reach the paper's energies (Tables ECU1, ECU0).
 """
 from __future__ import annotations
 
@@ -191,10 +194,10 @@ def _e_exact():
             return float(line.split()[1])
 
 
-def _e_fu_table():
+def _e_fu_table(kind="D"):
     for line in open(os.path.join(GOLDEN, "fu_heisenberg_4x4_table.txt")):
         p = line.split()
-        if p and p[0] == "D" and p[1] == "2":
+        if p and p[0] == kind and p[1] == "2":
             return float(p[5]), float(p[7])
 
 
@@ -210,3 +213,47 @@ def test_full_update_reaches_the_paper_fu_energy_at_4x4_D2():
     e_tab, tol = _e_fu_table()
     assert _e_exact() < e_fu < e_su
     assert abs(e_fu - e_tab) < tol, (e_fu, e_tab, e_su)
+
+
+@pytest.mark.parametrize("set_index", [0, 2])
+def test_cluster_covering_the_lattice_is_the_full_update(set_index):
+    A = synth.peps_simple_update(4, 4, 2, seed=0, steps=30)
+    G = U.heisenberg_gate(0.05)
+    s = U.trotter_sets(4, 4)[set_index]
+    a, ca = U.update_bonds(A, G, s, chi=16, mode="var")
+    b, cb = U.update_bonds_cluster(A, G, s, 3, chi=16, mode="var")
+    assert np.array_equal(a, b) and ca == cb
+
+
+@pytest.mark.parametrize("delta", [0, 1])
+def test_exact_gate_is_exact_with_a_cluster_environment(delta):
+    """Any positive N holds the gated pair exactly when the bond can."""
+    Ad = _rand_lattice(3, 3, 2, 4, seed=23)
+    y, x = 1, 1
+    Ad[y, x, :, :, :, :, 1:] = 0.0
+    Ad[y, x + 1, :, :, 1:, :, :] = 0.0
+    G = U.heisenberg_gate(0.7) @ np.diag([1.0, 2.0, 0.5, 1.5])
+    new, cost = U.update_bonds_cluster(Ad, G, [(0, y, x)], delta, chi=64, mode="svd", iters=6)
+    want = _apply_two_site(BF.state_vector(BF.dense_lattice(Ad)), [2] * 9, 4, 5, G)
+    got = BF.state_vector(BF.dense_lattice(new))
+    assert cost[0] < 1e-12 and _overlap_distance(got, want) < 1e-12
+
+
+def test_cu1_reaches_the_paper_energy_at_4x4_D2():
+    """CU_1 with D' = 4 from the simple-update state (Table ECU1); 150 steps
+    are within 3e-5 of the evolution's limit."""
+    A = synth.peps_simple_update(4, 4, 2, seed=0)
+    A = U.evolve(A, tau=0.01, steps=150, chi=4, mode="svd", iters=6, delta=1)
+    e = U.energy(A, chi=64) / 16
+    e_tab, tol = _e_fu_table("CU1")
+    assert abs(e - e_tab) < tol, (e, e_tab)
+
+
+def test_cu0_keeps_the_paper_energy_at_4x4_D2():
+    """CU_0 (a generalised simple update) from the simple-update state stays at
+    Table ECU0's energy."""
+    A = synth.peps_simple_update(4, 4, 2, seed=0)
+    A = U.evolve(A, tau=0.01, steps=30, chi=4, mode="svd", iters=6, delta=0)
+    e = U.energy(A, chi=64) / 16
+    e_tab, tol = _e_fu_table("CU0")
+    assert abs(e - e_tab) < tol, (e, e_tab)
