@@ -315,6 +315,7 @@ def run_ours(args, rank, world, dist):
 
     cluster = cluster_section(args, peps, torch, st, flush) if args.cluster else None
     fidelity = fidelity_section(peps, torch, st) if args.fidelity and rank == 0 else None
+    update = update_section(args, peps, torch, st) if args.update and rank == 0 else None
 
     ms_step, e_ms, value, e2e = aggregate(sum(times) / len(times), sum(etimes) / len(etimes), envs, world,
                                           dist, dev)
@@ -406,6 +407,8 @@ def run_ours(args, rank, world, dist):
         res["cluster"] = cluster
     if fidelity is not None:
         res["fidelity"] = fidelity
+    if update is not None:
+        res["update"] = update
     if clk:
         res["clocks"] = clk
     if not args.no_cpu_baseline:
@@ -466,6 +469,39 @@ def fidelity_section(peps, torch, st):
         out["one_minus_f"][key] = {str(chi): peps.boundary_fidelity(A, delta, chi=chi, chi_ref=100, stream=st)
                                    for chi in (4, 8, 16, 32, 64)}
     out["seconds"] = round(time.perf_counter() - t0, 1)
+    return out
+
+
+def update_section(args, peps, torch, st):
+    """The tensor update (Section 2) under the parallel schedule, timed per
+    Trotter set: the full update and the cluster updates CU_delta, beside the
+    time t_B of one boundary step (the quantities of the paper's timing model,
+    Section 5.4: sequential FU 2(L-2) t_B + L t_U per set, parallel CU_delta
+    2(delta-1) t_B + t_U per row)."""
+    import numpy as np
+    from paper_1311_6696_gb300 import synth
+    name, chi, prec = "20x20_D4_su", 16, "bf16x3"
+    A0 = torch.from_numpy(synth.workload(name)).to("cuda")
+    Ly = int(A0.shape[0])
+    h = np.array([[0.25, 0, 0, 0], [0, -0.25, 0.5, 0], [0, 0.5, -0.25, 0], [0, 0, 0, 0.25]])
+    w, v = np.linalg.eigh(h)
+    G = (v * np.exp(-0.01 * w)) @ v.T
+    sets = peps.trotter_sets(Ly, int(A0.shape[1]))
+    kw = dict(chi=chi, mode="var", precision=prec, iters=8, stream=st)
+    peps.norm(A0, chi=chi, mode="var", precision=prec, stream=st)
+    t_sweep = min(_timed(lambda: peps.norm(A0, chi=chi, mode="var", precision=prec, stream=st), st, 2))
+    out = {"workload": f"{name} (20x20 D=4 simple-update Heisenberg, seed 6), chi={chi}, var, {prec}, "
+                       "gate exp(-0.01 h), 8 ALS rounds; every schedule starts from the same state",
+           "t_B_ms": round(t_sweep / (Ly - 1), 3), "sweep_ms": round(t_sweep, 2), "per_schedule": {}}
+    for name_s, delta in [("FU", None), ("CU_0", 0), ("CU_1", 1), ("CU_2", 2), ("CU_3", 3)]:
+        A = A0.clone()
+        peps.bond_update(A.clone(), G, sets[0], delta=delta, **kw)       # warm
+        times = [min(_timed(lambda: peps.bond_update(A, G, s_, delta=delta, **kw), st, 1)) for s_ in sets]
+        out["per_schedule"][name_s] = {"set_ms": [round(t, 2) for t in times],
+                                       "step_ms": round(sum(times), 2)}
+    fu = out["per_schedule"]["FU"]["step_ms"]
+    for k, v_ in out["per_schedule"].items():
+        v_["fu_over_this"] = round(fu / v_["step_ms"], 3)
     return out
 
 
@@ -658,6 +694,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cluster", action="store_true", help="add the 14x14 D=6 cluster section")
     ap.add_argument("--fidelity", action="store_true", help="add the boundary-fidelity section (Fig. Fid)")
+    ap.add_argument("--update", action="store_true",
+                    help="add the tensor-update section: FU and CU_delta Trotter sets on the 20x20 D=4 lattice")
     ap.add_argument("--tune", action="store_true", help="choose the plan's launch configuration by measurement")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-budget", type=float, default=20.0)

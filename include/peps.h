@@ -346,6 +346,27 @@ int peps_bond_update(const peps_lattice* lat, const peps_opts* opts, const doubl
                      int nbonds, int als_iters, void* A_out, double* cost, void* cuda_stream);
 
 /*
+ * peps_bond_update_cluster -- the same tensor update with the cluster
+ *   update's environment, CU_delta.  Section 5: the cluster of size delta
+ *   around a row is every row within distance delta of it (and likewise for
+ *   columns); the environment of a horizontal bond in row y is the exact
+ *   contraction (at bond opts->chi) of rows y-delta .. y+delta, clipped at the
+ *   lattice edge, over all columns, closed above and below by the CU_0
+ *   separable boundaries of those cuts (Section 5.1; at the lattice edge the
+ *   lattice's own closures).  Vertical bonds use the column strip.  delta = 0
+ *   is CU_0 (Section 5.1, a generalised simple update); delta >= L-1 is the
+ *   full update.  Every bond of the call uses the CU_0 boundaries and clusters
+ *   of the input state (the parallel CU of Section 5.4): one strip per row or
+ *   column holding bonds, each with its own two sweeps of at most delta rows.
+ *   Arguments, rules and errors as peps_bond_update; delta < 0 fails with
+ *   PEPS_EINVAL; a CU_0 boundary that needs more than its half-sweep cap
+ *   fails with PEPS_ECONVERGE.
+ */
+int peps_bond_update_cluster(const peps_lattice* lat, const peps_opts* opts, int delta, const double* gate,
+                             const int* bonds, int nbonds, int als_iters, void* A_out, double* cost,
+                             void* cuda_stream);
+
+/*
  * peps_boundary_fidelity -- distance of a cluster environment from the full one.
  *   Section 5.2, Fig. Fid: the boundary MPS on the right legs of column 0
  *   (the environment of the left-most column) in the cluster form -- columns

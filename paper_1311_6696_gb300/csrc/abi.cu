@@ -696,162 +696,6 @@ void full_env(Call& c, const peps_lattice* lat, const Opts& opt, peps_env* env, 
   e.has_norm = true;
 }
 
-// Tensor update of a set of bonds (Section 2: the gate's action refit by ALS
-// on the reduced tensors), every bond from the full environment of the input
-// state -- the bonds of one Trotter set updated independently, the parallel
-// schedule of Sections 4.4 and 5.2.  Horizontal bonds use the row sweeps,
-// vertical bonds the column sweeps (rows of the transposed lattice); only the
-// boundaries the bonds' rows need are computed.
-void bond_update(Call& c, const peps_lattice* lat, const Opts& opt, const double* gate_host, const int* bonds,
-                 int nb, int iters, void* out, double* cost_host, Oriented& ori) {
-  Ctx& cx = c.cx;
-  const int Ly = lat->Ly, Lx = lat->Lx, d = lat->d, D = lat->D;
-  struct Job {
-    int o = 0, r = 0, c = 0, y1 = 0, x1 = 0, y2 = 0, x2 = 0;
-    int kl = 0, kr = 0, Do = 0, Dn = 0, ml = 0, mr = 0;
-    SiteT L, R;
-    Engine::BondNorm bn;
-    double *al_new = nullptr, *ar_new = nullptr, *q = nullptr, *nl = nullptr, *nr = nullptr;
-  };
-  std::vector<Job> jobs(nb);
-  int up[4] = {-1, -1, -1, -1};
-  std::map<std::pair<int, int>, std::vector<int>> rows;
-  for (int i = 0; i < nb; ++i) {
-    Job& j = jobs[i];
-    const int kind = bonds[3 * i], y = bonds[3 * i + 1], x = bonds[3 * i + 2];
-    j.o = kind == 0 ? 0 : 2;
-    j.r = kind == 0 ? y : x;
-    j.c = kind == 0 ? x : y;
-    j.y1 = y;
-    j.x1 = x;
-    j.y2 = kind == 0 ? y : y + 1;
-    j.x2 = kind == 0 ? x + 1 : x;
-    const OLat& ol = ori.o[j.o];
-    j.L = ol.at(j.r, j.c);
-    j.R = ol.at(j.r, j.c + 1);
-    j.ml = j.L.du * j.L.dl * j.L.dn;
-    j.mr = j.R.du * j.R.dn * j.R.dr;
-    j.kl = std::min(j.ml, d * j.L.dr);
-    j.kr = std::min(j.mr, d * j.R.dl);
-    j.Do = j.L.dr;
-    j.Dn = std::min({D, j.kl * d, j.kr * d});
-    PEPS_REQUIRE(j.kl * j.Dn <= kCholMax && j.kr * j.Dn <= kCholMax,
-                 "bond update: a reduced system has more than " + std::to_string(kCholMax) +
-                     " unknowns per physical value (d*D*D too large)");
-    Engine::BondNorm& b = j.bn;
-    b.x = j.c;
-    b.ml = cx.ws->dalloc(size_t(j.ml) * d * j.L.dr);
-    b.mr = cx.ws->dalloc(size_t(j.mr) * d * j.R.dl);
-    b.xl = cx.ws->dalloc(size_t(j.kl) * j.ml);
-    b.xr = cx.ws->dalloc(size_t(j.kr) * j.mr);
-    b.al = cx.ws->dalloc(size_t(j.kl) * d * j.L.dr);
-    b.ar = cx.ws->dalloc(size_t(j.kr) * d * j.R.dl);
-    b.N = cx.ws->dalloc(size_t(j.kl) * j.kr * j.kl * j.kr);
-    j.al_new = cx.ws->dalloc(size_t(j.kl) * d * j.Dn);
-    j.ar_new = cx.ws->dalloc(size_t(j.Dn) * d * j.kr);
-    j.q = cx.ws->dalloc(2);
-    j.nl = cx.ws->dalloc(size_t(d) * j.ml * j.Dn);
-    j.nr = cx.ws->dalloc(size_t(d) * j.R.du * j.Dn * j.R.dn * j.R.dr);
-    const int H = j.o == 0 ? Ly : Lx;
-    up[j.o] = std::max(up[j.o], j.r);
-    up[j.o + 1] = std::max(up[j.o + 1], H - 1 - j.r);
-    rows[{j.o, j.r}].push_back(i);
-  }
-  double* gate = static_cast<double*>(stage(cx, gate_host, sizeof(double) * d * d * d * d));
-  double* lnacc = cx.ws->dalloc(4);
-  fill(cx, lnacc, 4, 0.0);
-  Arena keep(c.st, size_t(64) << 20, /*async=*/false);
-  {
-    Lanes lanes(c, opt, d, D, std::max(Ly, Lx));
-    const int nl = int(lanes.l.size());
-    Published pub;
-    for (int o = 0; o < 4; ++o) {
-      const int n = (o < 2 ? Ly : Lx);
-      pub.b[o].resize(n);
-      pub.ev[o].assign(n, nullptr);
-      pub.ready[o].assign(n, 0);
-    }
-    // jobs: the needed sweeps first on every lane, then one job per row
-    std::vector<int> sweeps;
-    for (int o = 0; o < 4; ++o)
-      if (up[o] >= 0) sweeps.push_back(o);
-    std::vector<std::pair<int, int>> row_keys;
-    for (auto& kv : rows) row_keys.push_back(kv.first);
-    const int njobs = int(sweeps.size() + row_keys.size());
-    std::vector<std::vector<int>> plan(nl);
-    for (int i = 0; i < njobs; ++i) plan[i % nl].push_back(i);
-    run_lanes(lanes, njobs, [&](Lane& L, int job) {
-      if (job < int(sweeps.size())) {
-        const int o = sweeps[job];
-        try {
-          L.eng->sweep(ori.o[o], o, up[o], lnacc + o, keep, [&](int y, const Mps& m) { pub.put(o, y, m, L.st); });
-        } catch (...) {
-          pub.fail(std::current_exception());
-          throw;
-        }
-        return;
-      }
-      const auto key = row_keys[job - sweeps.size()];
-      const int o = key.first, r = key.second, H = o == 0 ? Ly : Lx;
-      const Mps& T = pub.get(o, r, L.st);
-      const Mps& B = pub.get(o + 1, H - 1 - r, L.st);
-      std::vector<Engine::BondNorm> bn;
-      for (int i : rows[key]) bn.push_back(jobs[i].bn);
-      L.eng->row_bond_norms(ori.o[o], T, B, r, bn);
-    }, &plan);
-    lanes.join();
-  }
-  // ALS per shape group (one batched sequence per group)
-  std::map<std::array<int, 4>, std::vector<BondAls>> groups;
-  for (auto& j : jobs) {
-    BondAls a;
-    a.N = j.bn.N;
-    a.al = j.bn.al;
-    a.ar = j.bn.ar;
-    a.al_new = j.al_new;
-    a.ar_new = j.ar_new;
-    a.q = j.q;
-    groups[{j.kl, j.kr, j.Do, j.Dn}].push_back(a);
-  }
-  for (auto& kv : groups)
-    bond_als(cx, d, kv.first[0], kv.first[1], kv.first[2], kv.first[3], gate, kv.second, iters);
-  // new site tensors A = X a, unit Frobenius norm, into the output lattice
-  static const int perms[4][4] = {{0, 1, 2, 3}, {2, 1, 0, 3}, {1, 0, 3, 2}, {3, 0, 1, 2}};
-  std::vector<SiteStore> st;
-  for (auto& j : jobs) {
-    ein(cx, "km,ksr->smr", TP(j.bn.xl), {j.kl, j.ml}, TP(j.al_new), {j.kl, d, j.Dn}, TP(j.nl));
-    ein(cx, "kunr,ltk->tulnr", TP(j.bn.xr), {j.kr, j.R.du, j.R.dn, j.R.dr}, TP(j.ar_new), {j.Dn, d, j.kr},
-        TP(j.nr));
-    normalize(cx, TP(j.nl), (long long)d * j.ml * j.Dn, TP());
-    normalize(cx, TP(j.nr), (long long)d * j.R.du * j.Dn * j.R.dn * j.R.dr, TP());
-    SiteStore a, b;
-    a.src = j.nl;
-    a.y = j.y1;
-    a.x = j.x1;
-    const int da[5] = {d, j.L.du, j.L.dl, j.L.dn, j.Dn};
-    const int db[5] = {d, j.R.du, j.Dn, j.R.dn, j.R.dr};
-    std::memcpy(a.dims, da, sizeof(da));
-    std::memcpy(a.perm, perms[j.o], sizeof(a.perm));
-    b.src = j.nr;
-    b.y = j.y2;
-    b.x = j.x2;
-    std::memcpy(b.dims, db, sizeof(db));
-    std::memcpy(b.perm, perms[j.o], sizeof(b.perm));
-    st.push_back(a);
-    st.push_back(b);
-  }
-  const size_t bytes = size_t(Ly) * Lx * d * D * D * D * D * (lat->dtype == PEPS_F32 ? 4 : 8);
-  if (out != lat->A) PEPS_CUDA(cudaMemcpyAsync(out, lat->A, bytes, cudaMemcpyDeviceToDevice, c.st));
-  store_sites(cx, out, lat->dtype == PEPS_F32, Lx, d, D, st);
-  if (cost_host) {
-    std::vector<double> qh(size_t(2) * nb);
-    for (int i = 0; i < nb; ++i)
-      PEPS_CUDA(cudaMemcpyAsync(&qh[2 * i], jobs[i].q, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
-    PEPS_CUDA(cudaStreamSynchronize(c.st));
-    for (int i = 0; i < nb; ++i) cost_host[i] = qh[2 * i + 1] > 0 ? qh[2 * i] / qh[2 * i + 1] : 0.0;
-  }
-}
-
 // Window of the cluster scheme (Section 5.3): n x n around (i) clipped at [0, L).
 std::pair<int, int> window(int L, int i, int n) {
   const int h = (n + 1) / 2;
@@ -957,6 +801,211 @@ std::vector<RimSite> rim_sites(const Oriented& ori, double* const sig[4], int D)
 }
 
 // Windows of the anchors with row-major index in [a0, a1) (a1 < 0: all).
+// Tensor update of a set of bonds (Section 2: the gate's action refit by ALS
+// on the reduced tensors), every bond from the full environment of the input
+// state -- the bonds of one Trotter set updated independently, the parallel
+// schedule of Sections 4.4 and 5.2.  Horizontal bonds use the row sweeps,
+// vertical bonds the column sweeps (rows of the transposed lattice); only the
+// boundaries the bonds' rows need are computed.
+// delta < 0: the full environment (FU).  delta >= 0: the cluster update
+// CU_delta (Section 5): a row's bonds see the exact contraction of the rows
+// within distance delta of it (all columns), closed above and below by the
+// CU_0 separable boundaries of Section 5.1; a column's bonds likewise.
+void bond_update(Call& c, const peps_lattice* lat, const Opts& opt, const double* gate_host, const int* bonds,
+                 int nb, int iters, void* out, double* cost_host, Oriented& ori, int delta = -1) {
+  Ctx& cx = c.cx;
+  const int Ly = lat->Ly, Lx = lat->Lx, d = lat->d, D = lat->D;
+  struct Job {
+    int o = 0, r = 0, c = 0, y1 = 0, x1 = 0, y2 = 0, x2 = 0;
+    int kl = 0, kr = 0, Do = 0, Dn = 0, ml = 0, mr = 0;
+    SiteT L, R;
+    Engine::BondNorm bn;
+    double *al_new = nullptr, *ar_new = nullptr, *q = nullptr, *nl = nullptr, *nr = nullptr;
+  };
+  std::vector<Job> jobs(nb);
+  int up[4] = {-1, -1, -1, -1};
+  std::map<std::pair<int, int>, std::vector<int>> rows;
+  for (int i = 0; i < nb; ++i) {
+    Job& j = jobs[i];
+    const int kind = bonds[3 * i], y = bonds[3 * i + 1], x = bonds[3 * i + 2];
+    j.o = kind == 0 ? 0 : 2;
+    j.r = kind == 0 ? y : x;
+    j.c = kind == 0 ? x : y;
+    j.y1 = y;
+    j.x1 = x;
+    j.y2 = kind == 0 ? y : y + 1;
+    j.x2 = kind == 0 ? x + 1 : x;
+    const OLat& ol = ori.o[j.o];
+    j.L = ol.at(j.r, j.c);
+    j.R = ol.at(j.r, j.c + 1);
+    j.ml = j.L.du * j.L.dl * j.L.dn;
+    j.mr = j.R.du * j.R.dn * j.R.dr;
+    j.kl = std::min(j.ml, d * j.L.dr);
+    j.kr = std::min(j.mr, d * j.R.dl);
+    j.Do = j.L.dr;
+    j.Dn = std::min({D, j.kl * d, j.kr * d});
+    PEPS_REQUIRE(j.kl * j.Dn <= kCholMax && j.kr * j.Dn <= kCholMax,
+                 "bond update: a reduced system has more than " + std::to_string(kCholMax) +
+                     " unknowns per physical value (d*D*D too large)");
+    Engine::BondNorm& b = j.bn;
+    b.x = j.c;
+    b.ml = cx.ws->dalloc(size_t(j.ml) * d * j.L.dr);
+    b.mr = cx.ws->dalloc(size_t(j.mr) * d * j.R.dl);
+    b.xl = cx.ws->dalloc(size_t(j.kl) * j.ml);
+    b.xr = cx.ws->dalloc(size_t(j.kr) * j.mr);
+    b.al = cx.ws->dalloc(size_t(j.kl) * d * j.L.dr);
+    b.ar = cx.ws->dalloc(size_t(j.kr) * d * j.R.dl);
+    b.N = cx.ws->dalloc(size_t(j.kl) * j.kr * j.kl * j.kr);
+    j.al_new = cx.ws->dalloc(size_t(j.kl) * d * j.Dn);
+    j.ar_new = cx.ws->dalloc(size_t(j.Dn) * d * j.kr);
+    j.q = cx.ws->dalloc(2);
+    j.nl = cx.ws->dalloc(size_t(d) * j.ml * j.Dn);
+    j.nr = cx.ws->dalloc(size_t(d) * j.R.du * j.Dn * j.R.dn * j.R.dr);
+    const int H = j.o == 0 ? Ly : Lx;
+    up[j.o] = std::max(up[j.o], j.r);
+    up[j.o + 1] = std::max(up[j.o + 1], H - 1 - j.r);
+    rows[{j.o, j.r}].push_back(i);
+  }
+  double* gate = static_cast<double*>(stage(cx, gate_host, sizeof(double) * d * d * d * d));
+  double* lnacc = cx.ws->dalloc(4);
+  fill(cx, lnacc, 4, 0.0);
+  Arena keep(c.st, size_t(64) << 20, /*async=*/false);
+  if (delta >= 0) {
+    // CU_delta: one strip per row (orientation 0) or column (orientation 2)
+    // holding bonds, each with its own two short sweeps, on the lanes
+    double* sig[4];
+    cu0_all_sides(cx, lat, ori, keep, sig);
+    const int DM2 = D * D;
+    auto S = [&](int o, int r, int x, int dim) {
+      const OLat& L = ori.o[o];
+      return Mat{TP(sig[o] + ((long long)r * L.Lx + x) * DM2), dim};
+    };
+    std::vector<std::pair<int, int>> row_keys;
+    for (auto& kv : rows) row_keys.push_back(kv.first);
+    Lanes lanes(c, opt, d, D, std::max(Ly, Lx));
+    const int nl = int(lanes.l.size());
+    double* lnj = cx.ws->dalloc(size_t(nl) * 64);
+    run_lanes(lanes, int(row_keys.size()), [&](Lane& L, int job) {
+      const int o = row_keys[job].first, r = row_keys[job].second;
+      const int H = o == 0 ? Ly : Lx, W = o == 0 ? Lx : Ly;
+      const int r0 = std::max(0, r - delta), r1 = std::min(H - 1, r + delta), h = r1 - r0 + 1, rr = r - r0;
+      OLat S0 = sub(ori.o[o], r0, r1, 0, W - 1);
+      OLat S1 = sub(ori.o[o + 1], H - 1 - r1, H - 1 - r0, 0, W - 1);
+      for (int j = 0; j < W; ++j) {
+        S0.top.push_back(S(o, r0, j, S0.at(0, j).du));
+        S0.bottom.push_back(S(o + 1, H - 1 - r1, j, S0.at(h - 1, j).dn));
+      }
+      for (int i = 0; i < h; ++i) {
+        S0.left.push_back(ori.o[o].left[r0 + i]);
+        S0.right.push_back(ori.o[o].right[r0 + i]);
+      }
+      S1.top = S0.bottom;
+      S1.bottom = S0.top;
+      for (int i = 0; i < h; ++i) {
+        S1.left.push_back(S0.left[h - 1 - i]);
+        S1.right.push_back(S0.right[h - 1 - i]);
+      }
+      const int li = int(&L - lanes.l.data());
+      double* lj = lnj + size_t(li) * 64;
+      fill(*L.cx, lj, 2, 0.0);
+      auto bt = L.eng->sweep(S0, o, rr, TP(lj), keep);
+      auto bb = L.eng->sweep(S1, o + 1, h - 1 - rr, TP(lj + 1), keep);
+      std::vector<Engine::BondNorm> bn;
+      for (int i : rows[row_keys[job]]) bn.push_back(jobs[i].bn);
+      L.eng->row_bond_norms(S0, bt[rr], bb[h - 1 - rr], rr, bn);
+    });
+    lanes.join();
+  } else {
+    Lanes lanes(c, opt, d, D, std::max(Ly, Lx));
+    const int nl = int(lanes.l.size());
+    Published pub;
+    for (int o = 0; o < 4; ++o) {
+      const int n = (o < 2 ? Ly : Lx);
+      pub.b[o].resize(n);
+      pub.ev[o].assign(n, nullptr);
+      pub.ready[o].assign(n, 0);
+    }
+    // jobs: the needed sweeps first on every lane, then one job per row
+    std::vector<int> sweeps;
+    for (int o = 0; o < 4; ++o)
+      if (up[o] >= 0) sweeps.push_back(o);
+    std::vector<std::pair<int, int>> row_keys;
+    for (auto& kv : rows) row_keys.push_back(kv.first);
+    const int njobs = int(sweeps.size() + row_keys.size());
+    std::vector<std::vector<int>> plan(nl);
+    for (int i = 0; i < njobs; ++i) plan[i % nl].push_back(i);
+    run_lanes(lanes, njobs, [&](Lane& L, int job) {
+      if (job < int(sweeps.size())) {
+        const int o = sweeps[job];
+        try {
+          L.eng->sweep(ori.o[o], o, up[o], lnacc + o, keep, [&](int y, const Mps& m) { pub.put(o, y, m, L.st); });
+        } catch (...) {
+          pub.fail(std::current_exception());
+          throw;
+        }
+        return;
+      }
+      const auto key = row_keys[job - sweeps.size()];
+      const int o = key.first, r = key.second, H = o == 0 ? Ly : Lx;
+      const Mps& T = pub.get(o, r, L.st);
+      const Mps& B = pub.get(o + 1, H - 1 - r, L.st);
+      std::vector<Engine::BondNorm> bn;
+      for (int i : rows[key]) bn.push_back(jobs[i].bn);
+      L.eng->row_bond_norms(ori.o[o], T, B, r, bn);
+    }, &plan);
+    lanes.join();
+  }
+  // ALS per shape group (one batched sequence per group)
+  std::map<std::array<int, 4>, std::vector<BondAls>> groups;
+  for (auto& j : jobs) {
+    BondAls a;
+    a.N = j.bn.N;
+    a.al = j.bn.al;
+    a.ar = j.bn.ar;
+    a.al_new = j.al_new;
+    a.ar_new = j.ar_new;
+    a.q = j.q;
+    groups[{j.kl, j.kr, j.Do, j.Dn}].push_back(a);
+  }
+  for (auto& kv : groups)
+    bond_als(cx, d, kv.first[0], kv.first[1], kv.first[2], kv.first[3], gate, kv.second, iters);
+  // new site tensors A = X a, unit Frobenius norm, into the output lattice
+  static const int perms[4][4] = {{0, 1, 2, 3}, {2, 1, 0, 3}, {1, 0, 3, 2}, {3, 0, 1, 2}};
+  std::vector<SiteStore> st;
+  for (auto& j : jobs) {
+    ein(cx, "km,ksr->smr", TP(j.bn.xl), {j.kl, j.ml}, TP(j.al_new), {j.kl, d, j.Dn}, TP(j.nl));
+    ein(cx, "kunr,ltk->tulnr", TP(j.bn.xr), {j.kr, j.R.du, j.R.dn, j.R.dr}, TP(j.ar_new), {j.Dn, d, j.kr},
+        TP(j.nr));
+    normalize(cx, TP(j.nl), (long long)d * j.ml * j.Dn, TP());
+    normalize(cx, TP(j.nr), (long long)d * j.R.du * j.Dn * j.R.dn * j.R.dr, TP());
+    SiteStore a, b;
+    a.src = j.nl;
+    a.y = j.y1;
+    a.x = j.x1;
+    const int da[5] = {d, j.L.du, j.L.dl, j.L.dn, j.Dn};
+    const int db[5] = {d, j.R.du, j.Dn, j.R.dn, j.R.dr};
+    std::memcpy(a.dims, da, sizeof(da));
+    std::memcpy(a.perm, perms[j.o], sizeof(a.perm));
+    b.src = j.nr;
+    b.y = j.y2;
+    b.x = j.x2;
+    std::memcpy(b.dims, db, sizeof(db));
+    std::memcpy(b.perm, perms[j.o], sizeof(b.perm));
+    st.push_back(a);
+    st.push_back(b);
+  }
+  const size_t bytes = size_t(Ly) * Lx * d * D * D * D * D * (lat->dtype == PEPS_F32 ? 4 : 8);
+  if (out != lat->A) PEPS_CUDA(cudaMemcpyAsync(out, lat->A, bytes, cudaMemcpyDeviceToDevice, c.st));
+  store_sites(cx, out, lat->dtype == PEPS_F32, Lx, d, D, st);
+  if (cost_host) {
+    std::vector<double> qh(size_t(2) * nb);
+    for (int i = 0; i < nb; ++i)
+      PEPS_CUDA(cudaMemcpyAsync(&qh[2 * i], jobs[i].q, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    PEPS_CUDA(cudaStreamSynchronize(c.st));
+    for (int i = 0; i < nb; ++i) cost_host[i] = qh[2 * i + 1] > 0 ? qh[2 * i] / qh[2 * i + 1] : 0.0;
+  }
+}
+
 void cluster_env(Call& c, const peps_lattice* lat, const Opts& opt, int n, peps_env* env, Oriented& ori,
                  const float* closure_w, long long a0 = 0, long long a1 = -1) {
   Ctx& cx = c.cx;
@@ -1309,6 +1358,44 @@ double time_plan(peps_plan* p, cudaStream_t st, int reps) {
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
+namespace {
+
+int bond_update_call(const peps_lattice* lat, const peps_opts* opts, int delta, const double* gate, const int* bonds,
+                     int nbonds, int als_iters, void* A_out, double* cost, void* cuda_stream) {
+  return guard([&] {
+    require_device();
+    check_lattice(lat);
+    const Opts o = check_opts(opts, false);
+    PEPS_REQUIRE(lat->on_device, "the bond update reads and writes device lattices (on_device = 1)");
+    PEPS_REQUIRE(gate != nullptr && bonds != nullptr && A_out != nullptr, "gate, bonds and A_out must be non-NULL");
+    PEPS_REQUIRE(nbonds >= 1, "nbonds must be >= 1");
+    PEPS_REQUIRE(als_iters >= 1 && als_iters <= 1000, "als_iters must be in [1, 1000]");
+    const int d = lat->d, d4 = d * d * d * d;
+    for (int i = 0; i < d4; ++i) PEPS_REQUIRE(std::isfinite(gate[i]), "the gate has a non-finite entry");
+    std::vector<char> used(size_t(lat->Ly) * lat->Lx, 0);
+    for (int i = 0; i < nbonds; ++i) {
+      const int kind = bonds[3 * i], y = bonds[3 * i + 1], x = bonds[3 * i + 2];
+      PEPS_REQUIRE(kind == 0 || kind == 1, "bond kind must be 0 (horizontal) or 1 (vertical)");
+      const int y2 = kind == 0 ? y : y + 1, x2 = kind == 0 ? x + 1 : x;
+      PEPS_REQUIRE(y >= 0 && x >= 0 && y2 < lat->Ly && x2 < lat->Lx, "bond outside the lattice");
+      char& a = used[size_t(y) * lat->Lx + x];
+      char& b = used[size_t(y2) * lat->Lx + x2];
+      PEPS_REQUIRE(!a && !b, "two bonds of one call share a site");
+      a = b = 1;
+    }
+    cudaPointerAttributes at;
+    PEPS_CUDA(cudaPointerGetAttributes(&at, A_out));
+    PEPS_REQUIRE(at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged, "A_out is not a device pointer");
+    Call c(cuda_stream);
+    Arena keep(c.st, size_t(64) << 20, /*async=*/false);
+    Oriented ori;
+    build_orientations(c.cx, lat, keep, ori);
+    bond_update(c, lat, o, gate, bonds, nbonds, als_iters, A_out, cost, ori, delta);
+    c.finish();
+  });
+}
+}  // namespace
+
 extern "C" {
 
 int peps_env_full(const peps_lattice* lat, const peps_opts* opts, peps_env** out, void* cuda_stream) {
@@ -1420,39 +1507,17 @@ int peps_wait_selftest(int budget_us, void* cuda_stream) {
   });
 }
 
+
 int peps_bond_update(const peps_lattice* lat, const peps_opts* opts, const double* gate, const int* bonds,
                      int nbonds, int als_iters, void* A_out, double* cost, void* cuda_stream) {
-  return guard([&] {
-    require_device();
-    check_lattice(lat);
-    const Opts o = check_opts(opts, false);
-    PEPS_REQUIRE(lat->on_device, "the bond update reads and writes device lattices (on_device = 1)");
-    PEPS_REQUIRE(gate != nullptr && bonds != nullptr && A_out != nullptr, "gate, bonds and A_out must be non-NULL");
-    PEPS_REQUIRE(nbonds >= 1, "nbonds must be >= 1");
-    PEPS_REQUIRE(als_iters >= 1 && als_iters <= 1000, "als_iters must be in [1, 1000]");
-    const int d = lat->d, d4 = d * d * d * d;
-    for (int i = 0; i < d4; ++i) PEPS_REQUIRE(std::isfinite(gate[i]), "the gate has a non-finite entry");
-    std::vector<char> used(size_t(lat->Ly) * lat->Lx, 0);
-    for (int i = 0; i < nbonds; ++i) {
-      const int kind = bonds[3 * i], y = bonds[3 * i + 1], x = bonds[3 * i + 2];
-      PEPS_REQUIRE(kind == 0 || kind == 1, "bond kind must be 0 (horizontal) or 1 (vertical)");
-      const int y2 = kind == 0 ? y : y + 1, x2 = kind == 0 ? x + 1 : x;
-      PEPS_REQUIRE(y >= 0 && x >= 0 && y2 < lat->Ly && x2 < lat->Lx, "bond outside the lattice");
-      char& a = used[size_t(y) * lat->Lx + x];
-      char& b = used[size_t(y2) * lat->Lx + x2];
-      PEPS_REQUIRE(!a && !b, "two bonds of one call share a site");
-      a = b = 1;
-    }
-    cudaPointerAttributes at;
-    PEPS_CUDA(cudaPointerGetAttributes(&at, A_out));
-    PEPS_REQUIRE(at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged, "A_out is not a device pointer");
-    Call c(cuda_stream);
-    Arena keep(c.st, size_t(64) << 20, /*async=*/false);
-    Oriented ori;
-    build_orientations(c.cx, lat, keep, ori);
-    bond_update(c, lat, o, gate, bonds, nbonds, als_iters, A_out, cost, ori);
-    c.finish();
-  });
+  return bond_update_call(lat, opts, -1, gate, bonds, nbonds, als_iters, A_out, cost, cuda_stream);
+}
+
+int peps_bond_update_cluster(const peps_lattice* lat, const peps_opts* opts, int delta, const double* gate,
+                             const int* bonds, int nbonds, int als_iters, void* A_out, double* cost,
+                             void* cuda_stream) {
+  if (delta < 0) return peps_set_error(PEPS_EINVAL, "delta must be >= 0");
+  return bond_update_call(lat, opts, delta, gate, bonds, nbonds, als_iters, A_out, cost, cuda_stream);
 }
 
 int peps_boundary_fidelity(const peps_lattice* lat, const peps_opts* opts, int delta, int chi_ref,

@@ -30,7 +30,7 @@ EXPORTS = [
     "peps_mlp_loss_grad", "peps_mlp_train", "peps_mlp_predict", "peps_plan_create", "peps_plan_run",
     "peps_plan_env", "peps_plan_launches", "peps_plan_free", "peps_plan_tune",
     "peps_set_iteration_caps", "peps_wait_selftest", "peps_boundary_fidelity", "peps_env_cluster_range",
-    "peps_ipeps_cluster", "peps_bond_update",
+    "peps_ipeps_cluster", "peps_bond_update", "peps_bond_update_cluster",
 ]
 CLOSURE_WIDTH = 256
 
@@ -102,6 +102,8 @@ def _load():
                                            C.POINTER(P), P]
     lib.peps_ipeps_cluster.argtypes = [P, C.c_int, C.c_int, C.c_int, C.POINTER(Opts), P, P, P, P, P]
     lib.peps_bond_update.argtypes = [C.POINTER(Lattice), C.POINTER(Opts), P, P, C.c_int, C.c_int, P, P, P]
+    lib.peps_bond_update_cluster.argtypes = [C.POINTER(Lattice), C.POINTER(Opts), C.c_int, P, P, C.c_int,
+                                             C.c_int, P, P, P]
     return lib
 
 
@@ -456,13 +458,14 @@ def class_index(name: str) -> int:
 
 
 def bond_update(A, gate, bonds, chi: int, mode="var", sweeps: int = 2, precision="fp64", seed: int = 0,
-                iters: int = 8, out=None, stream=None, device=None):
-    """The full update's tensor update (Section 2) of every bond in ``bonds``
-    ((kind, y, x): kind 0 = (y,x)-(y,x+1), 1 = (y,x)-(y+1,x); no shared
-    sites), all from the environment of the input state; see
-    peps_bond_update.  A: contiguous CUDA tensor (Ly,Lx,d,D,D,D,D); out: a
-    tensor like A (default: A itself, updated in place).  Returns (out, cost)
-    with cost[i] = |psi - G phi|^2_N / |G phi|^2_N of bond i."""
+                iters: int = 8, out=None, stream=None, device=None, delta=None):
+    """The tensor update (Section 2) of every bond in ``bonds`` ((kind, y, x):
+    kind 0 = (y,x)-(y,x+1), 1 = (y,x)-(y+1,x); no shared sites), all from the
+    environment of the input state: the full one (delta None, see
+    peps_bond_update) or the cluster of size delta (see
+    peps_bond_update_cluster).  A: contiguous CUDA tensor (Ly,Lx,d,D,D,D,D);
+    out: a tensor like A (default: A itself, updated in place).  Returns
+    (out, cost) with cost[i] = |psi - G phi|^2_N / |G phi|^2_N of bond i."""
     import torch
     _set_device(device)
     assert isinstance(A, torch.Tensor) and A.is_cuda, "A must be a CUDA tensor"
@@ -477,8 +480,13 @@ def bond_update(A, gate, bonds, chi: int, mode="var", sweeps: int = 2, precision
     b = np.ascontiguousarray(np.asarray(bonds, dtype=np.int32).reshape(-1, 3))
     cost = np.zeros(len(b))
     o = _opts(chi, mode, sweeps, precision, 1, seed)
-    _check(lib.peps_bond_update(C.byref(inp.lat), C.byref(o), g.ctypes.data, b.ctypes.data, int(len(b)),
-                                int(iters), out.data_ptr(), cost.ctypes.data, _stream_ptr(stream)))
+    if delta is None:
+        _check(lib.peps_bond_update(C.byref(inp.lat), C.byref(o), g.ctypes.data, b.ctypes.data, int(len(b)),
+                                    int(iters), out.data_ptr(), cost.ctypes.data, _stream_ptr(stream)))
+    else:
+        _check(lib.peps_bond_update_cluster(C.byref(inp.lat), C.byref(o), int(delta), g.ctypes.data,
+                                            b.ctypes.data, int(len(b)), int(iters), out.data_ptr(),
+                                            cost.ctypes.data, _stream_ptr(stream)))
     return out, cost
 
 
@@ -494,12 +502,13 @@ def trotter_sets(Ly: int, Lx: int):
 
 
 def evolve(A, gate, steps: int, chi: int, mode="var", sweeps: int = 2, precision="fp64", seed: int = 0,
-           iters: int = 8, stream=None, device=None):
-    """``steps`` Trotter steps of the full update in place on the CUDA tensor
-    A: every set of trotter_sets updated from its own environment (the
-    parallel schedule).  Returns A."""
+           iters: int = 8, stream=None, device=None, delta=None):
+    """``steps`` Trotter steps in place on the CUDA tensor A, every set of
+    trotter_sets updated from its own environment (the parallel schedule):
+    the full update (delta None) or the cluster update CU_delta.  Returns A."""
     Ly, Lx = int(A.shape[0]), int(A.shape[1])
     for _ in range(steps):
         for s in trotter_sets(Ly, Lx):
-            bond_update(A, gate, s, chi, mode, sweeps, precision, seed, iters, stream=stream, device=device)
+            bond_update(A, gate, s, chi, mode, sweeps, precision, seed, iters, stream=stream, device=device,
+                        delta=delta)
     return A

@@ -140,10 +140,10 @@ def test_bond_update_input_errors(env):
     peps.bond_update(A, G, [(0, 0, 0)], chi=8)
 
 
-def _e_fu_table():
+def _e_fu_table(kind="D"):
     for line in open(os.path.join(GOLDEN, "fu_heisenberg_4x4_table.txt")):
         p = line.split()
-        if p and p[0] == "D" and p[1] == "2":
+        if p and p[0] == kind and p[1] == "2":
             return float(p[5]), float(p[7])
 
 
@@ -160,3 +160,55 @@ def test_gpu_full_update_reaches_the_paper_fu_energy_at_4x4_D2(env):
     e_site = float(np.sum(h)) / 16
     e_tab, tol = _e_fu_table()
     assert abs(e_site - e_tab) < tol, (e_site, e_tab)
+
+
+# ------------------------------------------------------------------ cluster update CU_delta (Section 5)
+@pytest.mark.parametrize("delta", [0, 1, 2])
+@pytest.mark.parametrize("set_index", [0, 3])
+def test_fp64_cluster_update_matches_the_oracle(env, delta, set_index):
+    torch, peps = env
+    from paper_1311_6696_gb300 import synth
+    A = synth.peps_simple_update(5, 4, 3, seed=11, steps=60)
+    G = U.heisenberg_gate(0.05)
+    bonds = U.trotter_sets(5, 4)[set_index]
+    want, wcost = U.update_bonds_cluster(A, G, bonds, delta, chi=12, mode="var", iters=6)
+    At = torch.from_numpy(A).cuda()
+    out, cost = peps.bond_update(At, G, bonds, chi=12, mode="var", iters=6, out=torch.empty_like(At), delta=delta)
+    got = out.cpu().numpy()
+    _compare(got, want, bonds, 1e-9)
+    assert np.max(np.abs(np.array(cost) - np.array(wcost))) < 1e-9
+    for y, x in _untouched(bonds, 5, 4):
+        assert np.array_equal(got[y, x], A[y, x])
+
+
+def test_cluster_covering_the_lattice_is_the_full_update_on_the_gpu(env):
+    torch, peps = env
+    from paper_1311_6696_gb300 import synth
+    A = torch.from_numpy(synth.peps_simple_update(5, 4, 3, seed=11, steps=60)).cuda()
+    G = U.heisenberg_gate(0.05)
+    for bonds in U.trotter_sets(5, 4):
+        a, ca = peps.bond_update(A, G, bonds, chi=12, mode="var", iters=6, out=torch.empty_like(A))
+        b, cb = peps.bond_update(A, G, bonds, chi=12, mode="var", iters=6, out=torch.empty_like(A), delta=4)
+        assert torch.max(torch.abs(a - b)).item() < 1e-12
+        assert np.max(np.abs(ca - cb)) < 1e-12
+
+
+def test_cluster_update_rejects_a_negative_delta(env):
+    torch, peps = env
+    from paper_1311_6696_gb300 import synth
+    A = torch.from_numpy(synth.peps_gauss(3, 3, 2, 2, 1)).cuda()
+    with pytest.raises(peps.PepsError):
+        peps.bond_update(A, np.eye(4), [(0, 0, 0)], chi=8, delta=-1)
+
+
+def test_gpu_cu1_reaches_the_paper_energy_at_4x4_D2(env):
+    """The parallel CU_1 on the GPU (D' = 4, Table ECU1)."""
+    torch, peps = env
+    from paper_1311_6696_gb300 import synth
+    A = torch.from_numpy(synth.peps_simple_update(4, 4, 2, seed=0)).cuda()
+    G = U.heisenberg_gate(0.01)
+    peps.evolve(A, G, steps=160, chi=4, mode="svd", iters=6, delta=1)
+    e = peps.env_full(A, chi=64, mode="svd")
+    h = np.concatenate([e.expect("hbond", O.SDOTS), e.expect("vbond", O.SDOTS)])
+    e_tab, tol = _e_fu_table("CU1")
+    assert abs(float(np.sum(h)) / 16 - e_tab) < tol
