@@ -238,14 +238,11 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_cluster(const QrArgs q, int 
   double* part4 = tau_s + k;        // [n][QS] quarter sums
   double* wfin = part4 + (long long)n * QS;   // [n]
   double* coef = wfin + n;          // [2] scale, beta of the current reflector
-  double* W;                        // [n][ld] my rows, column-major (row i at i - r0)
-  double* Qw;                       // [k][ld]
+  double* W;                        // [n][ld] my rows, column-major (row i at i - r0); Q is formed in place
   if (in_smem) {
     W = coef + 2 + QS;
-    Qw = W + (long long)n * ld;
   } else {
     W = q.W + pb * q.wst + (long long)rank * ld * n;
-    Qw = q.Qw + pb * q.qst + (long long)rank * ld * k;
   }
   for (long long e = tid; e < (long long)rows * n; e += nt) {
     const int li = int(e % rows), j = int(e / rows);
@@ -325,53 +322,63 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_cluster(const QrArgs q, int 
     __syncthreads();
     if (j + 1 < k) partials(j + 1, 1 - b);
   }
-  // Q = H_0 ... H_{k-1} [I_k; 0], accumulated backwards on the same row split.
-  for (long long e = tid; e < (long long)rows * k; e += nt) {
-    const int li = int(e % rows), c = int(e / rows);
-    Qw[(long long)c * ld + li] = (r0 + li == c) ? 1.0 : 0.0;
-  }
-  cluster.sync();
-  for (int j = k - 1, t0 = 0; j >= 0; --j, ++t0) {
-    const double tau = tau_s[j];
-    if (tau == 0.0) continue;
-    const int b = t0 & 1;
-    const bool own = (j >= r0 && j < r1);
-    const int i0 = max(r0, j + 1);
-    const double* vj = W + (long long)j * ld - r0;
-    const int nc = k - j;
-    for (int t = tid; t < nc * QS; t += nt) {
-      const int c = j + t / QS, qq = t % QS;
-      const double* qc = Qw + (long long)c * ld - r0;
-      part4[(long long)c * QS + qq] = dot_qs(vj, qc, i0 + ((qq - i0 % QS + QS) % QS), r1);
-    }
-    __syncthreads();
-    for (int c = j + tid; c < k; c += nt) {
-      const double* qc = Qw + (long long)c * ld - r0;
-      double w = own ? qc[j] : 0.0;
-      for (int qq = 0; qq < QS; ++qq) w += part4[(long long)c * QS + qq];
-      wpart[b * n + c] = w;
-    }
-    cluster.sync();
-    for (int c = j + tid; c < k; c += nt) wfin[c] = tau * remote_sum(cluster, wpart + b * n + c, C);
-    __syncthreads();
-    for (int t = tid; t < nc * QS; t += nt) {
-      const int c = j + t / QS, qq = t % QS;
-      double* qc = Qw + (long long)c * ld - r0;
-      const double w = wfin[c];
-      if (own && qq == 0) qc[j] -= w;
-      axpy_qs(w, vj, qc, i0 + ((qq - i0 % QS + QS) % QS), r1);
-    }
-    __syncthreads();
-  }
-  for (long long e = tid; e < (long long)rows * k; e += nt) {
-    const int li = int(e % rows), c = int(e / rows);
-    Qo[(r0 + li) * q.qrs + c * q.qcs] = Qw[(long long)c * ld + li];
-  }
+  // R first: Q is formed over W below.
   if (Ro) {
     for (long long e = tid; e < (long long)rows * n; e += nt) {
       const int li = int(e % rows), j = int(e / rows), i = r0 + li;
       if (i < k) Ro[(long long)i * n + j] = (j >= i) ? W[(long long)j * ld + li] : 0.0;
     }
+  }
+  __syncthreads();
+  // Q = H_0 ... H_{k-1} [I_k; 0], formed backwards in place on the same row
+  // split: column j keeps its reflector below the diagonal until step j,
+  // columns c > j already hold Q's columns and are zero in rows <= j.  Rows
+  // above the diagonal (R) are cleared first.
+  for (long long e = tid; e < (long long)rows * k; e += nt) {
+    const int li = int(e % rows), c = int(e / rows);
+    if (r0 + li < c) W[(long long)c * ld + li] = 0.0;
+  }
+  cluster.sync();
+  int nsync = 0;   // double-buffer index: advances only with a cluster barrier
+  for (int j = k - 1; j >= 0; --j) {
+    const double tau = tau_s[j];
+    const bool own = (j >= r0 && j < r1);
+    const int i0 = max(r0, j + 1);
+    double* vj = W + (long long)j * ld - r0;          // vj[i] for global row i
+    const int nc = k - j - 1;                         // columns j+1 .. k-1
+    if (tau != 0.0 && nc > 0) {                       // uniform across the cluster
+      const int b = nsync & 1;
+      ++nsync;
+      for (int t = tid; t < nc * QS; t += nt) {
+        const int c = j + 1 + t / QS, qq = t % QS;
+        const double* qc = W + (long long)c * ld - r0;
+        part4[(long long)c * QS + qq] = dot_qs(vj, qc, i0 + ((qq - i0 % QS + QS) % QS), r1);
+      }
+      __syncthreads();
+      for (int c = j + 1 + tid; c < k; c += nt) {
+        double w = 0.0;
+        for (int qq = 0; qq < QS; ++qq) w += part4[(long long)c * QS + qq];
+        wpart[b * n + c] = w;
+      }
+      cluster.sync();
+      for (int c = j + 1 + tid; c < k; c += nt) wfin[c] = tau * remote_sum(cluster, wpart + b * n + c, C);
+      __syncthreads();
+      for (int t = tid; t < nc * QS; t += nt) {
+        const int c = j + 1 + t / QS, qq = t % QS;
+        double* qc = W + (long long)c * ld - r0;
+        const double w = wfin[c];
+        if (own && qq == 0) qc[j] = -w;
+        axpy_qs(w, vj, qc, i0 + ((qq - i0 % QS + QS) % QS), r1);
+      }
+    }
+    __syncthreads();                                  // every read of the reflector is done
+    for (int i = i0 + tid; i < r1; i += nt) vj[i] *= -tau;
+    if (own && tid == 0) vj[j] = 1.0 - tau;
+    __syncthreads();
+  }
+  for (long long e = tid; e < (long long)rows * k; e += nt) {
+    const int li = int(e % rows), c = int(e / rows);
+    Qo[(r0 + li) * q.qrs + c * q.qcs] = W[(long long)c * ld + li];
   }
   cluster.sync();   // no CTA leaves while others may still read its shared memory
 }
@@ -776,7 +783,7 @@ size_t qr_smem(int m, int n, int c) {
   const int k = std::min(m, n);
   const size_t base = sizeof(double) * (4 * size_t(n) + 2 + k + size_t(n) * QS + n + 2 + QS);
   const size_t ld = size_t(((m + c - 1) / c) | 1);
-  return base + sizeof(double) * ld * (size_t(n) + k);
+  return base + sizeof(double) * ld * size_t(n);
 }
 
 // dst[b][i*qrs + j*qcs] = src[b][i*n + j]
@@ -928,9 +935,9 @@ void qr_direct(Ctx& cx, int m, int n, const TP& A, long long rs, long long cs, c
   if (C <= 1) {
     a.wst = (long long)m * n;
     a.qst = (long long)m * k;
-  } else {   // the global-memory fallback uses [C][n][ld] / [C][k][ld] blocks per problem
+  } else {   // the global-memory fallback uses [C][n][ld] blocks per problem (Q formed in place)
     a.wst = (long long)C * ld * n;
-    a.qst = (long long)C * ld * k;
+    a.qst = 0;
   }
   a.tst = k;
   double* w = cx.scratch(size_t(np) * (a.wst + a.qst + a.tst) + 64);
