@@ -71,7 +71,12 @@ def _peaks():
 
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
 # stands, keyed by (workload, class); an entry is dropped whenever its kernel changes.
-TRAFFIC = {}
+TRAFFIC = {
+    # (workload, class): (dram read + write bytes per launch, source)
+    ("c4", "qr_f64"): (4.54e6, "ncu --set full, mean of the 2 captured k_qr_cluster launches (stacked R "
+                               "0.61 MB, tall-skinny leaves 8.47 MB) of the chi=128 fit; "
+                               "profiles/k_qr_cluster_rows3_20x20_D8_chi128.md"),
+}
 
 # Dense FP64 and TF32 peaks: measured at start-up by _measure_peaks (torch
 # matmul 8192^3 on this GPU); these values (one earlier measurement on a GB300,
