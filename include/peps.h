@@ -256,6 +256,41 @@ int peps_mlp_predict(const float* w, const float* X, long long n, int d, int D, 
                      float* sigma, void* cuda_stream);
 
 /*
+ * Checkpoint and resume (the paper keeps boundaries on disk or in memory,
+ * Section 5.4; these calls make results and training state durable).
+ * peps_mlp_train_state -- peps_mlp_train with the AdamW state held by the
+ *   caller: adam_m, adam_v are device float* of peps_mlp_param_count each
+ *   (zero them before the first call), *step (host) the steps already taken
+ *   with them; on success *step += steps.  Bias correction and the seeded
+ *   minibatch stream continue from *step, so a run split into calls with the
+ *   same seed, n and batch gives the same weights as one call.
+ * peps_mlp_save / peps_mlp_load -- weights (and, when adam_m / adam_v are
+ *   non-NULL, the AdamW moments and *step) to / from a file: one JSON header
+ *   line padded to 512 bytes ({"format":"peps-mlp", d, D, width, params,
+ *   state, step}), then the float32 arrays.  Loading checks the shape; a file
+ *   without optimizer state loads zero moments and step 0.  w, adam_m, adam_v
+ *   are device pointers.
+ * peps_env_save / peps_env_load -- an environment handle's results (the
+ *   density matrices of every site and bond, ln|<psi|psi>| and its sign,
+ *   the lattice shape) to / from a file: a 512-byte JSON header line
+ *   ({"format":"peps-env", kind, Ly, Lx, d, D, has_norm, array sizes}), then
+ *   the float64 arrays.  peps_env_load creates a new handle (free it with
+ *   peps_env_free) that peps_expect_local, peps_env_rho and peps_env_ln_norm
+ *   read like the original.  A file of another format, shape or size fails
+ *   with PEPS_EINVAL; file errors with PEPS_EINVAL naming the path.
+ *   All synchronise the stream.
+ */
+int peps_mlp_train_state(float* w, float* adam_m, float* adam_v, long long* step, const float* X, const float* Y,
+                         long long n, int d, int D, int width, int steps, int batch, float lr, float weight_decay,
+                         unsigned long long seed, double* final_loss, void* cuda_stream);
+int peps_mlp_save(const char* path, const float* w, const float* adam_m, const float* adam_v, long long step, int d,
+                  int D, int width, void* cuda_stream);
+int peps_mlp_load(const char* path, float* w, float* adam_m, float* adam_v, long long* step, int d, int D, int width,
+                  void* cuda_stream);
+int peps_env_save(const peps_env* env, const char* path, void* cuda_stream);
+int peps_env_load(const char* path, peps_env** out, void* cuda_stream);
+
+/*
  * peps_ipeps_cluster -- local density matrices of an infinite PEPS by the
  *   cluster update's environment (Section 5.4: a CU procedure for iPEPS needs
  *   only the dominant D'=1 boundary eigenvector, O(dD^5), followed by a

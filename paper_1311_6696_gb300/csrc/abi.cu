@@ -1396,6 +1396,62 @@ int bond_update_call(const peps_lattice* lat, const peps_opts* opts, int delta, 
 }
 }  // namespace
 
+namespace {
+
+// Checkpoint files: one JSON header line padded with spaces to kCkptHeader
+// bytes, then the arrays as raw little-endian values.
+constexpr size_t kCkptHeader = 512;
+
+void ckpt_write(const char* path, const std::string& json, const std::vector<std::pair<const void*, size_t>>& parts) {
+  PEPS_REQUIRE(path != nullptr, "path is NULL");
+  PEPS_REQUIRE(json.size() + 1 <= kCkptHeader, "internal: checkpoint header too long");
+  std::string hdr = json;
+  hdr.resize(kCkptHeader - 1, ' ');
+  hdr.push_back('\n');
+  FILE* f = std::fopen(path, "wb");
+  PEPS_REQUIRE(f != nullptr, std::string("cannot open ") + path + " for writing");
+  bool ok = std::fwrite(hdr.data(), 1, hdr.size(), f) == hdr.size();
+  for (auto& p : parts) ok = ok && (p.second == 0 || std::fwrite(p.first, 1, p.second, f) == p.second);
+  ok = (std::fclose(f) == 0) && ok;
+  PEPS_REQUIRE(ok, std::string("writing ") + path + " failed");
+}
+
+struct CkptIn {
+  std::string hdr;
+  std::vector<char> body;
+};
+
+CkptIn ckpt_read(const char* path, const char* format) {
+  PEPS_REQUIRE(path != nullptr, "path is NULL");
+  FILE* f = std::fopen(path, "rb");
+  PEPS_REQUIRE(f != nullptr, std::string("cannot open ") + path);
+  CkptIn c;
+  c.hdr.resize(kCkptHeader);
+  const bool ok = std::fread(&c.hdr[0], 1, kCkptHeader, f) == kCkptHeader;
+  if (ok) {
+    char buf[1 << 16];
+    size_t r;
+    while ((r = std::fread(buf, 1, sizeof(buf), f)) > 0) c.body.insert(c.body.end(), buf, buf + r);
+  }
+  std::fclose(f);
+  PEPS_REQUIRE(ok, std::string(path) + " is shorter than a checkpoint header");
+  PEPS_REQUIRE(c.hdr.find(std::string("\"format\":\"") + format + "\"") != std::string::npos,
+               std::string(path) + " is not a " + format + " checkpoint");
+  return c;
+}
+
+long long ckpt_int(const std::string& hdr, const char* key) {
+  const std::string k = std::string("\"") + key + "\":";
+  const size_t at = hdr.find(k);
+  PEPS_REQUIRE(at != std::string::npos, std::string("checkpoint header lacks ") + key);
+  char* end = nullptr;
+  const long long v = std::strtoll(hdr.c_str() + at + k.size(), &end, 10);
+  PEPS_REQUIRE(end != hdr.c_str() + at + k.size(), std::string("checkpoint header: bad value for ") + key);
+  return v;
+}
+
+}  // namespace
+
 extern "C" {
 
 int peps_env_full(const peps_lattice* lat, const peps_opts* opts, peps_env** out, void* cuda_stream) {
@@ -1773,6 +1829,144 @@ int peps_mlp_train(float* w, const float* X, const float* Y, long long n, int d,
     Call c(cuda_stream);
     mlp_train(c.cx, m, w, X, Y, n, steps, batch, lr, weight_decay, seed, final_loss);
     c.finish();
+  });
+}
+
+int peps_mlp_train_state(float* w, float* adam_m, float* adam_v, long long* step, const float* X, const float* Y,
+                         long long n, int d, int D, int width, int steps, int batch, float lr, float weight_decay,
+                         unsigned long long seed, double* final_loss, void* cuda_stream) {
+  return guard([&] {
+    PEPS_REQUIRE(w && adam_m && adam_v && step && X && Y && n > 0, "NULL argument or empty training set");
+    PEPS_REQUIRE(*step >= 0, "step must be >= 0");
+    require_device();
+    PEPS_REQUIRE(tc_available(), "the learned closure runs on sm_103 tensor cores");
+    const MlpDims m = mlp_dims(d, D, width);
+    Call c(cuda_stream);
+    mlp_train(c.cx, m, w, X, Y, n, steps, batch, lr, weight_decay, seed, final_loss, adam_m, adam_v, *step);
+    c.finish();
+    *step += steps;
+  });
+}
+
+int peps_mlp_save(const char* path, const float* w, const float* adam_m, const float* adam_v, long long step, int d,
+                  int D, int width, void* cuda_stream) {
+  return guard([&] {
+    PEPS_REQUIRE(w != nullptr, "w is NULL");
+    PEPS_REQUIRE((adam_m == nullptr) == (adam_v == nullptr), "pass both AdamW moments or neither");
+    require_device();
+    const MlpDims m = mlp_dims(d, D, width);
+    const size_t P = size_t(m.params());
+    const bool state = adam_m != nullptr;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<float> hw(P), hm(state ? P : 0), hv(state ? P : 0);
+    PEPS_CUDA(cudaMemcpyAsync(hw.data(), w, P * sizeof(float), cudaMemcpyDeviceToHost, st));
+    if (state) {
+      PEPS_CUDA(cudaMemcpyAsync(hm.data(), adam_m, P * sizeof(float), cudaMemcpyDeviceToHost, st));
+      PEPS_CUDA(cudaMemcpyAsync(hv.data(), adam_v, P * sizeof(float), cudaMemcpyDeviceToHost, st));
+    }
+    PEPS_CUDA(cudaStreamSynchronize(st));
+    const std::string json = "{\"format\":\"peps-mlp\",\"version\":1,\"d\":" + std::to_string(d) +
+                             ",\"D\":" + std::to_string(D) + ",\"width\":" + std::to_string(width) +
+                             ",\"params\":" + std::to_string(P) + ",\"state\":" + std::to_string(state ? 1 : 0) +
+                             ",\"step\":" + std::to_string(step) + ",\"dtype\":\"f32\"}";
+    ckpt_write(path, json, {{hw.data(), P * sizeof(float)}, {hm.data(), hm.size() * sizeof(float)},
+                            {hv.data(), hv.size() * sizeof(float)}});
+  });
+}
+
+int peps_mlp_load(const char* path, float* w, float* adam_m, float* adam_v, long long* step, int d, int D, int width,
+                  void* cuda_stream) {
+  return guard([&] {
+    PEPS_REQUIRE(w != nullptr, "w is NULL");
+    PEPS_REQUIRE((adam_m == nullptr) == (adam_v == nullptr), "pass both AdamW moments or neither");
+    require_device();
+    const MlpDims m = mlp_dims(d, D, width);
+    const size_t P = size_t(m.params());
+    const CkptIn c = ckpt_read(path, "peps-mlp");
+    PEPS_REQUIRE(ckpt_int(c.hdr, "d") == d && ckpt_int(c.hdr, "D") == D && ckpt_int(c.hdr, "width") == width &&
+                     ckpt_int(c.hdr, "params") == (long long)P,
+                 "the checkpoint holds a network of another shape");
+    const bool state = ckpt_int(c.hdr, "state") != 0;
+    PEPS_REQUIRE(c.body.size() == (state ? 3 : 1) * P * sizeof(float), "checkpoint body has the wrong size");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    PEPS_CUDA(cudaMemcpyAsync(w, c.body.data(), P * sizeof(float), cudaMemcpyHostToDevice, st));
+    if (adam_m) {
+      if (state) {
+        PEPS_CUDA(cudaMemcpyAsync(adam_m, c.body.data() + P * sizeof(float), P * sizeof(float),
+                                  cudaMemcpyHostToDevice, st));
+        PEPS_CUDA(cudaMemcpyAsync(adam_v, c.body.data() + 2 * P * sizeof(float), P * sizeof(float),
+                                  cudaMemcpyHostToDevice, st));
+      } else {
+        PEPS_CUDA(cudaMemsetAsync(adam_m, 0, P * sizeof(float), st));
+        PEPS_CUDA(cudaMemsetAsync(adam_v, 0, P * sizeof(float), st));
+      }
+    }
+    if (step) *step = state ? ckpt_int(c.hdr, "step") : 0;
+    PEPS_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+int peps_env_save(const peps_env* env, const char* path, void* cuda_stream) {
+  return guard([&] {
+    PEPS_REQUIRE(env != nullptr, "env is NULL");
+    require_device();
+    const EnvData& e = env->data;
+    const size_t d2 = size_t(e.d) * e.d, d4 = d2 * d2;
+    const size_t ns = size_t(e.Ly) * e.Lx * d2, nh = std::max<size_t>(1, size_t(e.Ly) * (e.Lx - 1) * d4),
+                 nv = std::max<size_t>(1, size_t(e.Ly - 1) * e.Lx * d4);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<double> hs(ns), hh(nh), hv(nv), hl(2);
+    PEPS_CUDA(cudaMemcpyAsync(hs.data(), e.rho_site, ns * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PEPS_CUDA(cudaMemcpyAsync(hh.data(), e.rho_h, nh * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PEPS_CUDA(cudaMemcpyAsync(hv.data(), e.rho_v, nv * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PEPS_CUDA(cudaMemcpyAsync(hl.data(), e.lnnorm, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PEPS_CUDA(cudaStreamSynchronize(st));
+    const std::string json = "{\"format\":\"peps-env\",\"version\":1,\"kind\":" + std::to_string(env->kind) +
+                             ",\"Ly\":" + std::to_string(e.Ly) + ",\"Lx\":" + std::to_string(e.Lx) +
+                             ",\"d\":" + std::to_string(e.d) + ",\"D\":" + std::to_string(e.D) +
+                             ",\"has_norm\":" + std::to_string(e.has_norm ? 1 : 0) + ",\"n_site\":" +
+                             std::to_string(ns) + ",\"n_h\":" + std::to_string(nh) + ",\"n_v\":" +
+                             std::to_string(nv) + ",\"dtype\":\"f64\"}";
+    ckpt_write(path, json, {{hs.data(), ns * sizeof(double)}, {hh.data(), nh * sizeof(double)},
+                            {hv.data(), nv * sizeof(double)}, {hl.data(), 2 * sizeof(double)}});
+  });
+}
+
+int peps_env_load(const char* path, peps_env** out, void* cuda_stream) {
+  if (out) *out = nullptr;
+  return guard([&] {
+    PEPS_REQUIRE(out != nullptr, "out is NULL");
+    require_device();
+    const CkptIn c = ckpt_read(path, "peps-env");
+    peps_lattice shape{};
+    shape.Ly = int(ckpt_int(c.hdr, "Ly"));
+    shape.Lx = int(ckpt_int(c.hdr, "Lx"));
+    shape.d = int(ckpt_int(c.hdr, "d"));
+    shape.D = int(ckpt_int(c.hdr, "D"));
+    PEPS_REQUIRE(shape.Ly >= 1 && shape.Lx >= 1 && shape.Ly <= 4096 && shape.Lx <= 4096 && shape.d >= 1 &&
+                     shape.d <= 4 && shape.D >= 1 && shape.D <= 16,
+                 "checkpoint header: lattice shape out of range");
+    const int kind = int(ckpt_int(c.hdr, "kind"));
+    const size_t d2 = size_t(shape.d) * shape.d, d4 = d2 * d2;
+    const size_t ns = size_t(shape.Ly) * shape.Lx * d2, nh = std::max<size_t>(1, size_t(shape.Ly) * (shape.Lx - 1) * d4),
+                 nv = std::max<size_t>(1, size_t(shape.Ly - 1) * shape.Lx * d4);
+    PEPS_REQUIRE(ckpt_int(c.hdr, "n_site") == (long long)ns && ckpt_int(c.hdr, "n_h") == (long long)nh &&
+                     ckpt_int(c.hdr, "n_v") == (long long)nv,
+                 "checkpoint header: array sizes do not match the lattice shape");
+    PEPS_REQUIRE(c.body.size() == (ns + nh + nv + 2) * sizeof(double), "checkpoint body has the wrong size");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    auto env = new_env(&shape, kind, st);
+    EnvData& e = env->data;
+    e.has_norm = ckpt_int(c.hdr, "has_norm") != 0;
+    const char* b = c.body.data();
+    PEPS_CUDA(cudaMemcpyAsync(e.rho_site, b, ns * sizeof(double), cudaMemcpyHostToDevice, st));
+    PEPS_CUDA(cudaMemcpyAsync(e.rho_h, b + ns * sizeof(double), nh * sizeof(double), cudaMemcpyHostToDevice, st));
+    PEPS_CUDA(cudaMemcpyAsync(e.rho_v, b + (ns + nh) * sizeof(double), nv * sizeof(double), cudaMemcpyHostToDevice,
+                              st));
+    PEPS_CUDA(cudaMemcpyAsync(e.lnnorm, b + (ns + nh + nv) * sizeof(double), 2 * sizeof(double),
+                              cudaMemcpyHostToDevice, st));
+    PEPS_CUDA(cudaStreamSynchronize(st));
+    *out = env.release();
   });
 }
 

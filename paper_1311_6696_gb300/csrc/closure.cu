@@ -437,15 +437,21 @@ void mlp_loss_grad(Ctx& cx, const MlpDims& m, const float* w, const float* X, co
 }
 
 void mlp_train(Ctx& cx, const MlpDims& m, float* w, const float* X, const float* Y, long long n, int steps,
-               int batch, float lr, float wd, unsigned long long seed, double* final_loss_host) {
+               int batch, float lr, float wd, unsigned long long seed, double* final_loss_host, float* m1_ext,
+               float* m2_ext, long long t0) {
   PEPS_REQUIRE(n > 0 && steps > 0 && batch > 0, "empty training set, steps or batch");
+  PEPS_REQUIRE(t0 >= 0, "negative step count");
   const long long B = std::min<long long>(batch, n);
   const size_t P = size_t(m.params()), W = m.W, o = m.out(), F = m.F();
   float* grad = cx.ws->falloc(P);
-  float* m1 = cx.ws->falloc(P);
-  float* m2 = cx.ws->falloc(P);
-  PEPS_CUDA(cudaMemsetAsync(m1, 0, P * sizeof(float), cx.st));
-  PEPS_CUDA(cudaMemsetAsync(m2, 0, P * sizeof(float), cx.st));
+  float* m1 = m1_ext;
+  float* m2 = m2_ext;
+  if (!m1 || !m2) {   // state of this call only
+    m1 = cx.ws->falloc(P);
+    m2 = cx.ws->falloc(P);
+    PEPS_CUDA(cudaMemsetAsync(m1, 0, P * sizeof(float), cx.st));
+    PEPS_CUDA(cudaMemsetAsync(m2, 0, P * sizeof(float), cx.st));
+  }
   float* Xb = cx.ws->falloc(B * F);
   float* Yb = cx.ws->falloc(B * o);
   float* H1 = cx.ws->falloc(B * W);
@@ -458,7 +464,8 @@ void mlp_train(Ctx& cx, const MlpDims& m, float* w, const float* X, const float*
   double* loss_acc = cx.ws->dalloc(1);
   PEPS_CUDA(cudaMemsetAsync(loss_acc, 0, sizeof(double), cx.st));
   long long* didx = static_cast<long long*>(cx.ws->alloc(sizeof(long long) * size_t(steps) * B));
-  // minibatch indices: a seeded shuffle per epoch (host side, uploaded once)
+  // minibatch indices: a seeded shuffle per epoch (host side, uploaded once);
+  // a run resumed at step t0 continues the same stream
   std::vector<long long> idx(size_t(steps) * B), perm(n);
   std::iota(perm.begin(), perm.end(), 0LL);
   unsigned long long st = seed * 0x9E3779B97F4A7C15ULL + 1;
@@ -470,12 +477,14 @@ void mlp_train(Ctx& cx, const MlpDims& m, float* w, const float* X, const float*
     return z ^ (z >> 31);
   };
   long long pos = n;
-  for (size_t i = 0; i < idx.size(); ++i) {
+  const long long skip = t0 * B;
+  for (long long i = 0; i < skip + (long long)idx.size(); ++i) {
     if (pos >= n) {
       for (long long k = n - 1; k > 0; --k) std::swap(perm[k], perm[next() % (unsigned long long)(k + 1)]);
       pos = 0;
     }
-    idx[i] = perm[pos++];
+    const long long v = perm[pos++];
+    if (i >= skip) idx[size_t(i - skip)] = v;
   }
   PEPS_CUDA(cudaMemcpyAsync(didx, idx.data(), sizeof(long long) * idx.size(), cudaMemcpyHostToDevice, cx.st));
   const int tail = std::min(steps, 20);
@@ -491,7 +500,7 @@ void mlp_train(Ctx& cx, const MlpDims& m, float* w, const float* X, const float*
     const bool rec = t >= steps - tail;
     loss_grad_buf(cx, m, w, Xb, Yb, B, rec ? loss_acc : part + grid_for(B), rec ? 1 : 0, grad, H1, H2, Yo, dYo,
                   dH1, dH2, part);
-    const float c1 = 1.f - std::pow(b1, float(t + 1)), c2 = 1.f - std::pow(b2, float(t + 1));
+    const float c1 = 1.f - std::pow(b1, float(t0 + t + 1)), c2 = 1.f - std::pow(b2, float(t0 + t + 1));
     Launch l(K_AUX, cx.st);
     k_adamw<<<grid_for(P), 256, 0, cx.st>>>(w, grad, m1, m2, (long long)P, lr, wd, b1, b2, eps, c1, c2);
     PEPS_CHECK_LAUNCH();

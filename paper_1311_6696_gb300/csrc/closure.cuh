@@ -39,8 +39,12 @@ void mlp_init(Ctx& cx, const MlpDims& m, float* w, unsigned long long seed);
 void mlp_predict(Ctx& cx, const MlpDims& m, const float* w, const float* X, long long n, float* sigma);
 void mlp_loss_grad(Ctx& cx, const MlpDims& m, const float* w, const float* X, const float* Y, long long n,
                    double* loss_dev, float* grad);
+// m1_ext / m2_ext: caller-owned AdamW moments (else zeroed state of this call
+// only); t0: steps already taken with them (bias correction and the position
+// in the seeded minibatch stream continue from there).
 void mlp_train(Ctx& cx, const MlpDims& m, float* w, const float* X, const float* Y, long long n, int steps,
-               int batch, float lr, float wd, unsigned long long seed, double* final_loss_host);
+               int batch, float lr, float wd, unsigned long long seed, double* final_loss_host,
+               float* m1_ext = nullptr, float* m2_ext = nullptr, long long t0 = 0);
 
 // Replace sigma[e] by pred[e] where pred is finite with positive trace (else keep).
 void closure_apply(Ctx& cx, int D, const float* pred, double* const* host_targets, long long n);

@@ -8,6 +8,7 @@ Python fallback.
 from __future__ import annotations
 
 import ctypes as C
+import json
 import os
 
 import numpy as np
@@ -30,7 +31,8 @@ EXPORTS = [
     "peps_mlp_loss_grad", "peps_mlp_train", "peps_mlp_predict", "peps_plan_create", "peps_plan_run",
     "peps_plan_env", "peps_plan_launches", "peps_plan_free", "peps_plan_tune",
     "peps_set_iteration_caps", "peps_wait_selftest", "peps_boundary_fidelity", "peps_env_cluster_range",
-    "peps_ipeps_cluster", "peps_bond_update", "peps_bond_update_cluster",
+    "peps_ipeps_cluster", "peps_bond_update", "peps_bond_update_cluster", "peps_mlp_train_state",
+    "peps_mlp_save", "peps_mlp_load", "peps_env_save", "peps_env_load",
 ]
 CLOSURE_WIDTH = 256
 
@@ -104,6 +106,13 @@ def _load():
     lib.peps_bond_update.argtypes = [C.POINTER(Lattice), C.POINTER(Opts), P, P, C.c_int, C.c_int, P, P, P]
     lib.peps_bond_update_cluster.argtypes = [C.POINTER(Lattice), C.POINTER(Opts), C.c_int, P, P, C.c_int,
                                              C.c_int, P, P, P]
+    lib.peps_mlp_train_state.argtypes = [P, P, P, C.POINTER(C.c_longlong), P, P, C.c_longlong, C.c_int, C.c_int,
+                                         C.c_int, C.c_int, C.c_int, C.c_float, C.c_float, C.c_ulonglong,
+                                         C.POINTER(C.c_double), P]
+    lib.peps_mlp_save.argtypes = [C.c_char_p, P, P, P, C.c_longlong, C.c_int, C.c_int, C.c_int, P]
+    lib.peps_mlp_load.argtypes = [C.c_char_p, P, P, P, C.POINTER(C.c_longlong), C.c_int, C.c_int, C.c_int, P]
+    lib.peps_env_save.argtypes = [P, C.c_char_p, P]
+    lib.peps_env_load.argtypes = [C.c_char_p, C.POINTER(P), P]
     return lib
 
 
@@ -418,6 +427,63 @@ def mlp_train(w, X, Y, d: int, D: int, width: int = CLOSURE_WIDTH, steps: int = 
     _check(lib.peps_mlp_train(w.data_ptr(), X.data_ptr(), Y.data_ptr(), X.shape[0], d, D, width, steps, batch,
                               lr, weight_decay, int(seed), C.byref(loss), _stream_ptr(stream)))
     return loss.value
+
+
+class AdamState:
+    """AdamW moments and step count of a closure network, held by the caller
+    so that training can be split over calls and checkpointed."""
+
+    def __init__(self, w):
+        import torch
+        self.m = torch.zeros_like(w)
+        self.v = torch.zeros_like(w)
+        self.step = 0
+
+
+def mlp_train_state(w, state: AdamState, X, Y, d: int, D: int, width: int = CLOSURE_WIDTH, steps: int = 200,
+                    batch: int = 256, lr: float = 1e-3, weight_decay: float = 1e-4, seed: int = 0,
+                    stream=None) -> float:
+    """mlp_train continuing from ``state`` (updated in place); see peps_mlp_train_state."""
+    loss = C.c_double()
+    step = C.c_longlong(state.step)
+    _check(lib.peps_mlp_train_state(w.data_ptr(), state.m.data_ptr(), state.v.data_ptr(), C.byref(step),
+                                    X.data_ptr(), Y.data_ptr(), X.shape[0], d, D, width, steps, batch, lr,
+                                    weight_decay, int(seed), C.byref(loss), _stream_ptr(stream)))
+    state.step = step.value
+    return loss.value
+
+
+def mlp_save(path: str, w, d: int, D: int, width: int = CLOSURE_WIDTH, state: AdamState | None = None,
+             stream=None):
+    """Weights (and optimizer state) to a checkpoint file; see peps_mlp_save."""
+    _check(lib.peps_mlp_save(os.fsencode(path), w.data_ptr(), state.m.data_ptr() if state else None,
+                             state.v.data_ptr() if state else None, state.step if state else 0, d, D, width,
+                             _stream_ptr(stream)))
+
+
+def mlp_load(path: str, w, d: int, D: int, width: int = CLOSURE_WIDTH, state: AdamState | None = None,
+             stream=None):
+    """Weights (and optimizer state) from a checkpoint file into ``w`` / ``state``; see peps_mlp_load."""
+    step = C.c_longlong(0)
+    _check(lib.peps_mlp_load(os.fsencode(path), w.data_ptr(), state.m.data_ptr() if state else None,
+                             state.v.data_ptr() if state else None, C.byref(step), d, D, width,
+                             _stream_ptr(stream)))
+    if state is not None:
+        state.step = step.value
+
+
+def env_save(env, path: str, stream=None):
+    """An environment's results to a checkpoint file; see peps_env_save."""
+    _check(lib.peps_env_save(env._h, os.fsencode(path), _stream_ptr(stream)))
+
+
+def env_load(path: str, stream=None) -> "Env":
+    """A new environment handle from a checkpoint file; see peps_env_load."""
+    h = C.c_void_p()
+    _check(lib.peps_env_load(os.fsencode(path), C.byref(h), _stream_ptr(stream)))
+    with open(path, "rb") as f:
+        hdr = json.loads(f.read(512).decode().strip())
+    return Env(h.value, (hdr["Ly"], hdr["Lx"], hdr["d"]), stream)
 
 
 def mlp_predict(w, X, d: int, D: int, width: int = CLOSURE_WIDTH, stream=None):
