@@ -13,7 +13,15 @@ separable-boundary tensors (Section 5.2).  Here each rank
    all-reduce (sum) of arrays in which each rank filled only its own anchors
    (``gather_rhos``): every entry has exactly one owner, so the sum is exact.
 
-Only the partition and the assembly live here; every contraction runs in the
+The tensor update shards the same way (Section 5.4: with the cluster update
+different rows or columns are updated simultaneously on different processors,
+and only small tensors are exchanged after each set of Trotter gates).  Each
+rank updates the bonds of whole row (column) strips of one set
+(``row_partition``) from the input state -- recomputing the CU_0 boundaries
+itself -- and the updated site tensors are assembled on every rank by one
+all-reduce in which each site has one owner (``merge_updates``).
+
+Only the partitions and the assembly live here; every contraction runs in the
 library.
 """
 from __future__ import annotations
@@ -83,3 +91,64 @@ def env_cluster_sharded(A, n: int, chi: int, rank: int, world: int, dist=None, d
     env = peps.env_cluster(A, n=n, chi=chi, anchors=(a0, a1), **kw)
     parts = {k: env.rho(k) for k in ("site", "hbond", "vbond")}
     return gather_rhos(parts, dist, device)
+
+
+def row_partition(bonds, world: int):
+    """The bonds of one Trotter set grouped by the strip they are updated in
+    (horizontal bonds by row, vertical bonds by column), the strips dealt to
+    the ranks in contiguous blocks of about equal bond count."""
+    assert world >= 1
+    rows = {}
+    for b in bonds:
+        kind, y, x = (int(v) for v in b)
+        rows.setdefault((kind, y if kind == 0 else x), []).append((kind, y, x))
+    keys = sorted(rows)
+    total = sum(len(rows[k]) for k in keys)
+    parts = [[] for _ in range(world)]
+    acc, r = 0, 0
+    for k in keys:
+        while r < world - 1 and acc >= total * (r + 1) / world:
+            r += 1
+        parts[r].extend(rows[k])
+        acc += len(rows[k])
+    return parts
+
+
+def bond_sites(bonds):
+    """The sites the bonds touch."""
+    out = []
+    for kind, y, x in bonds:
+        out.append((y, x))
+        out.append((y, x + 1) if kind == 0 else (y + 1, x))
+    return out
+
+
+def merge_updates(A_old, A_new, mine, dist):
+    """The lattice with every rank's updated sites: A_new's sites listed in
+    ``mine`` (this rank's), A_old's where no rank updated.  One all-reduce of
+    the owned values and one of the ownership mask; each site has at most one
+    owner, so the assembly is exact.  Torch tensors, any device."""
+    import torch
+    contrib = torch.zeros_like(A_new)
+    mask = torch.zeros(A_new.shape[:2], dtype=A_new.dtype, device=A_new.device)
+    for y, x in mine:
+        contrib[y, x] = A_new[y, x]
+        mask[y, x] = 1.0
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(contrib, op=dist.ReduceOp.SUM)
+        dist.all_reduce(mask, op=dist.ReduceOp.SUM)
+    return torch.where(mask[:, :, None, None, None, None, None] > 0, contrib, A_old)
+
+
+def bond_update_sharded(A, gate, bonds, chi: int, rank: int, world: int, dist=None, delta=None, **kw):
+    """One Trotter set updated over ``world`` ranks (this one updating
+    row_partition(...)[rank]) and assembled on every rank; the same result as
+    one call of peps.bond_update over all the bonds.  A: CUDA tensor
+    (Ly,Lx,d,D,D,D,D), not modified; returns the new lattice.  kw: the
+    options of peps.bond_update."""
+    from . import peps
+    mine = row_partition(bonds, world)[rank]
+    new = A.clone()
+    if mine:
+        peps.bond_update(A, gate, mine, chi, out=new, delta=delta, **kw)
+    return merge_updates(A, new, bond_sites(mine), dist)

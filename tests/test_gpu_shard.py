@@ -53,3 +53,22 @@ def test_bad_anchor_ranges_are_einval(peps):
         assert e.value.code == peps.EINVAL
     e = peps.env_cluster(A, n=2, chi=4, anchors=(0, 0))          # empty: nothing computed
     assert np.all(e.rho("site") == 0.0)
+
+
+@pytest.mark.parametrize("delta", [None, 1])
+def test_update_shares_merged_equal_one_update(peps, delta):
+    """The tensor update of a Trotter set split into row strips for 3 ranks
+    (Section 5.4), each share computed from the same input and merged, equals
+    one call over the whole set."""
+    import torch
+    from oracle import update_oracle as U
+    from paper_1311_6696_gb300 import shard, synth
+    A = torch.from_numpy(synth.peps_simple_update(6, 5, 3, seed=5, steps=40)).cuda()
+    G = U.heisenberg_gate(0.05)
+    for s in U.trotter_sets(6, 5):
+        whole, _ = peps.bond_update(A, G, s, chi=12, mode="var", out=torch.empty_like(A), delta=delta)
+        merged = A.clone()
+        for r in range(3):
+            new = shard.bond_update_sharded(A, G, s, 12, r, 3, None, delta=delta, mode="var")
+            merged = shard.merge_updates(merged, new, shard.bond_sites(shard.row_partition(s, 3)[r]), None)
+        assert torch.max(torch.abs(merged - whole)).item() < 1e-12

@@ -106,3 +106,67 @@ def test_two_gloo_ranks_assemble_the_whole_cluster_environment():
     for k in ("site", "hbond", "vbond"):
         assert np.array_equal(f0[k], f1[k])
         assert np.array_equal(f0[k], whole[k])
+
+
+# ------------------------------------------------------------------ the tensor update over ranks (Section 5.4)
+def test_row_partition_keeps_strips_whole_and_balances():
+    from oracle import update_oracle as U
+    from paper_1311_6696_gb300 import shard
+    for (Ly, Lx, world) in ((6, 5, 2), (6, 5, 3), (20, 20, 8), (4, 4, 16)):
+        for s in U.trotter_sets(Ly, Lx):
+            parts = shard.row_partition(s, world)
+            assert len(parts) == world
+            assert sorted(b for p in parts for b in p) == sorted(s)
+            strips = {}
+            for r, p in enumerate(parts):
+                for kind, y, x in p:
+                    strips.setdefault((kind, y if kind == 0 else x), set()).add(r)
+            assert all(len(v) == 1 for v in strips.values())
+            biggest = max(sum(1 for b in s if (b[1] if b[0] == 0 else b[2]) == k[1]) for k in strips)
+            for p in parts:
+                assert len(p) <= len(s) / world + biggest
+
+
+def _update_worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    from oracle import update_oracle as U
+    from paper_1311_6696_gb300 import shard, synth
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    A = synth.peps_simple_update(5, 4, 2, seed=7, steps=40)
+    G = U.heisenberg_gate(0.05)
+    out = []
+    for s in U.trotter_sets(5, 4):
+        mine = shard.row_partition(s, world)[rank]
+        new, _ = U.update_bonds_cluster(A, G, mine, 1, chi=8, mode="var") if mine else (A, [])
+        merged = shard.merge_updates(torch.from_numpy(A), torch.from_numpy(np.asarray(new)),
+                                     shard.bond_sites(mine), dist)
+        out.append(merged.numpy())
+    dist.destroy_process_group()
+    q.put((rank, out))
+
+
+def test_two_gloo_ranks_reproduce_one_cluster_update_of_each_set():
+    """Each rank refits its strips' bonds (the oracle stands in for the GPU);
+    the merged lattice equals one update of the whole set, bit for bit."""
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    from oracle import update_oracle as U
+    from paper_1311_6696_gb300 import synth
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _port()
+    ps = [ctx.Process(target=_update_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = dict(q.get(timeout=300) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    A = synth.peps_simple_update(5, 4, 2, seed=7, steps=40)
+    G = U.heisenberg_gate(0.05)
+    for i, s in enumerate(U.trotter_sets(5, 4)):
+        whole, _ = U.update_bonds_cluster(A, G, s, 1, chi=8, mode="var")
+        assert np.array_equal(res[0][i], whole) and np.array_equal(res[1][i], whole)
