@@ -417,7 +417,10 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_jacobi(const SvdArgs s) {
   for (long long e = tid; e < (long long)q * q; e += nt) V[e] = ((e % q) == (e / q)) ? 1.0 : 0.0;
   __syncthreads();
   const int qq = q + (q & 1);   // even number of slots for the round-robin pairing
-  const double tol = 1e-15;
+  // a pair is orthogonal once |gamma| <= tol sqrt(alpha beta); rounding alone
+  // leaves |gamma| / sqrt(alpha beta) of order p * eps after a rotation, so the
+  // threshold scales with the row count (as in LAPACK's one-sided Jacobi)
+  const double tol = fmax(1e-15, 4.0 * double(p) * 2.220446049250313e-16);
   int sweep = 0;
   for (; sweep < s.max_sweeps; ++sweep) {
     if (tid == 0) s_rot = 0;
@@ -552,7 +555,10 @@ __global__ void __launch_bounds__(SVC_THREADS) k_svd_cluster(const SvdArgs s, do
     const int li = int(e % vr), j = int(e / vr);
     V[(long long)j * cv + li] = (v0 + li == j) ? 1.0 : 0.0;
   }
-  const double tol = 1e-15;
+  // a pair is orthogonal once |gamma| <= tol sqrt(alpha beta); rounding alone
+  // leaves |gamma| / sqrt(alpha beta) of order p * eps after a rotation, so the
+  // threshold scales with the row count (as in LAPACK's one-sided Jacobi)
+  const double tol = fmax(1e-15, 4.0 * double(p) * 2.220446049250313e-16);
   int sweep = 0, t = 0;
   for (; sweep < s.max_sweeps; ++sweep) {
     int rotated = 0;
