@@ -10,6 +10,17 @@
  *   - the environment of every site, in factored form        (Section 2: N_l, b_l)
  *   - local expectation values <O> = Tr(rho O)/Tr(rho)       (Section 5.3)
  *   - the same environments in the cluster scheme CU         (Section 5, 5.2, 5.3)
+ *   - the distance of a cluster boundary from the full one   (Section 5.2, Fig. Fid)
+ *   - the environments of an infinite PEPS by the CU         (Section 5.4)
+ *   - the tensor update that consumes the environments: the gate's action
+ *     refit by ALS on the reduced tensors, with the full environment (full
+ *     update) or the cluster environment CU_delta         (Section 2; Section 5)
+ *
+ * Around these: recorded plans (CUDA graphs) with an autotuner, the learned
+ * cluster closure (a small MLP trained on the GPU), profiling counters,
+ * failure detection (iteration caps, bounded waits, host-side fault
+ * injection), checkpoint / resume of env handles and closure training, and
+ * one entry point that allocates no device memory (peps_cu0_noalloc).
  *
  * Every step runs in the library's CUDA kernels; there is no CPU fallback.
  * A call made without a usable CUDA device fails with PEPS_ECUDA.
