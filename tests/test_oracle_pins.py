@@ -582,3 +582,51 @@ def test_ipeps_cluster_matches_the_finite_cluster_deep_inside():
         g = got.reshape(got.shape[0] if got.ndim == 2 else 4, -1)
         w = want.reshape(g.shape)
         assert np.max(np.abs(g / np.trace(g) - w / np.trace(w))) < 1e-11
+
+
+# ------------------------------------------------------------------ var mode at truncated chi
+def _var_fit_trace(seed, Ly, Lx, D, chi, halves):
+    """Distance |P - F|^2 / |P|^2 of the var fit F (after h half-sweeps) from
+    the exact product MPS P of the second absorb, and the projection defect
+    (<P|F> - <F|F>) / |P|^2, for h = 1 .. halves."""
+    A = synth.peps_gauss(Ly, Lx, 2, D, seed, mean=0.0, std=1.0)
+    lat = O.lattice_from_dense(A)
+    T, _ = O.absorb_compress(O.closure_mps(lat.top), lat, 0, 64, "svd", 2, 0, 0)
+    y = 1
+    P = O.product_mps(T, lat, y)
+    Ax = lat.A[y]
+    phys = [Ax[x].shape[3] ** 2 for x in range(Lx)]
+    prod = [T[k].shape[3] * Ax[k].shape[4] ** 2 for k in range(Lx - 1)]
+    caps = O.bond_caps(phys, prod, chi)
+    assert any(prod[k] > caps[k] for k in range(Lx - 1))          # it truncates
+    pp = O.mps_overlap(P, P)
+    out = []
+    for h in range(1, halves + 1):
+        F, _ = O.var_compress(T, lat, y, caps, h, 0, 0)
+        pf, ff = O.mps_overlap(P, F), O.mps_overlap(F, F)
+        out.append(((pp + ff - 2 * pf) / pp, (pf - ff) / pp))
+    return out
+
+
+@pytest.mark.parametrize("seed,Ly,Lx,D,chi", [(5, 4, 5, 2, 3), (7, 4, 6, 2, 4), (9, 3, 5, 3, 5)])
+def test_var_fit_at_truncated_chi_is_monotone_and_a_projection(seed, Ly, Lx, D, chi):
+    """Section 2's one-site ALS with N_l = 1: every local step replaces the
+    centre tensor by the projection b_l, so |P - F| never grows from one
+    half-sweep to the next, and after each half-sweep <P|F> = <F|F>."""
+    tr = _var_fit_trace(seed, Ly, Lx, D, chi, 6)
+    for (d0, _), (d1, _) in zip(tr, tr[1:]):
+        assert d1 <= d0 + 1e-12
+    assert tr[-1][0] < tr[0][0]                                     # it does improve
+    for _, defect in tr:
+        assert abs(defect) < 1e-12
+
+
+def test_var_fit_pins_catch_a_swapped_environment(monkeypatch):
+    """The same pins fail when the local vector uses the right environment
+    with its ket and bra legs swapped (a plausible index slip)."""
+    real = O.close_left
+    monkeypatch.setattr(O, "close_left", lambda X3, R: real(X3, R.transpose(0, 2, 1, 3)))
+    tr = _var_fit_trace(5, 4, 5, 2, 3, 4)
+    broken = any(d1 > d0 + 1e-12 for (d0, _), (d1, _) in zip(tr, tr[1:])) or \
+        any(abs(g) > 1e-12 for _, g in tr)
+    assert broken
