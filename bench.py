@@ -21,10 +21,19 @@ whole environment set) and evaluates <S.S>.  The line also reports
 * the FP64 oracle on the host cores (a bounded sample, costed up to the whole
   environment set by operation count).
 
+The roofline is that of the kernel class with the largest share of
+exclusive device time in a launch list of one replay (the FP64 QR at this
+workload); the absorb contractions are reported beside it, against the BF16
+peak and against HBM.
+
 ``--workload c2`` runs the 10x10 D=4 chi=64 lattice instead (entries
 0.5 + 0.1 N(0,1)), with the FP64 path timed on the whole set.  ``--cluster``
 adds the cluster scheme on the 14x14 D=6 lattice (all 196 windows at chi=36,
-n = 2, 4, 6).
+n = 2, 4, 6); ``--fidelity`` the boundary distance 1 - f of Fig. Fid on the
+20x20 D=4 simple-update lattice; ``--update`` the tensor update's Trotter
+steps (full update and CU_0 .. CU_3) on that lattice beside the boundary
+step time t_B.  ``--rows R`` runs only the norm sweep of the top R rows (a
+small case for profiler captures) and exits.
 
 Launch: ``python bench.py [--gpus N --steps K --warmup W]``; for N > 1 run
 under ``torch.distributed.run`` with one process per GPU.  The full
